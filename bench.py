@@ -1,0 +1,355 @@
+"""Benchmark: plateau-reduced gradient steps on one GB300 (or N replicas under torchrun).
+
+A step is one pass of the whole hot path on a resident job: draw the antithetic
+perturbations (Sec. 3.2), bind theta +- tau into the scene, path-trace the R
+perturbed renders with the per-pixel loss reduced inside the render kernel, form
+the gradient of Eq. 10 and apply Adam -- all on the device.
+
+Workload: the occlusion scene (256x256, three diffuse spheres and a 0.4^3 box on a
+plane under a 1x1 area light, depth 4, 16 spp, theta = box centre, sigma = 0.05,
+N = 16 renders = 8 antithetic pairs), synthetic and seeded.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import platform
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "smoothed-gradient steps/s"
+UNIT = "steps/s"
+# Algorithmic FP32 operations (add/sub/mul = 1, fma = 2, div/sqrt/rsqrt = 1; compares
+# and min/max not counted) per unit of work of the path tracer.
+FLOPS = {"sphere_test": 22, "quad_test": 32, "box_test": 12, "path": 27, "vertex": 120}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2211_17263_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload_name):
+    """DRAM bytes per render launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_trace_occlusion-256x256_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != _kernel_source_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(wl, target, nthreads=0, budget_s=10.0, max_steps=20):
+    """The FP64 oracle on whole steps of the same workload, repeated until about
+    `budget_s` seconds of wall time have passed (bounded by `max_steps`)."""
+    import oracle
+    cores = nthreads or os.cpu_count() or 1
+    n, t0 = 0, time.perf_counter()
+    while n < max_steps and (n == 0 or time.perf_counter() - t0 < budget_s):
+        oracle.smoothed_grad(wl, target=target, nthreads=cores, step=n)
+        n += 1
+    dt = (time.perf_counter() - t0) / n
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} whole steps ({wl.renders} renders at {wl.width}x{wl.height}, {wl.spp} spp), "
+                      f"{dt:.2f} s each", "cpu_model": _cpu_model()}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    wl = workloads.config_occlusion()
+    target = oracle.render_target(wl)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.smoothed_grad(wl, target=target, nthreads=cores, step=0)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.smoothed_grad(wl, target=target, nthreads=cores, step=k)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "renders": wl.renders, "pairs": wl.pairs, "width": wl.width,
+                   "height": wl.height, "spp": wl.spp, "depth": wl.depth, "D": wl.D, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} whole steps ({wl.renders} renders at {wl.width}x{wl.height}, "
+                                   f"{wl.spp} spp)", "cpu_model": _cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import workloads
+    from paper_2211_17263_gb300 import api
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = workloads.config_occlusion(seed=rank)  # one independent replica per rank
+    ctx = api.Context(local)
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=f"cuda:{local}")  # noqa: E731
+    target = scene.render_batch(dev(wl.theta_ref[None]), wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
+                                seed=wl.seed, step=0, tag=3, crn=1)[0]
+    target_host = target.cpu().numpy()
+    job = api.Job(scene, wl, target_host)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        job.step(stream)
+    torch.cuda.synchronize()
+
+    # algorithmic work of one step (counting kernel variant, untimed)
+    ctx.counters_enable(True)
+    job.step(stream)
+    counts = ctx.counters_read()
+    ctx.counters_enable(False)
+    flops_step = (counts[0] * FLOPS["sphere_test"] + counts[1] * FLOPS["quad_test"] + counts[2] * FLOPS["box_test"]
+                  + counts[3] * FLOPS["path"] + counts[4] * FLOPS["vertex"])
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ctx.kernel_timing(True)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the timed events)
+        starts[k].record(stream)
+        job.step(stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    trace_ms, launches = ctx.kernel_timing_read()
+    ctx.kernel_timing(False)
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    state = job.read()
+
+    # end to end through the C ABI with host buffers: H2D inputs, gradient, Adam, D2H results
+    e2e = None
+    theta_h = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32)).pin_memory()
+    sigma_h = torch.from_numpy(np.ascontiguousarray(wl.sigma, np.float32)).pin_memory()
+    target_h = torch.from_numpy(target_host).pin_memory()
+    theta_d, sigma_d = torch.empty_like(theta_h, device=f"cuda:{local}"), torch.empty_like(sigma_h, device=f"cuda:{local}")
+    target_d = torch.empty_like(target_h, device=f"cuda:{local}")
+    m_d = torch.zeros_like(theta_d)
+    v_d = torch.zeros_like(theta_d)
+    g_d = torch.empty_like(theta_d)
+    L_d = torch.empty(wl.renders, dtype=torch.float32, device=f"cuda:{local}")
+    out_h = torch.empty(2 * wl.D + wl.renders, dtype=torch.float32).pin_memory()
+    h2d = 4 * (2 * wl.D + 4 * wl.width * wl.height)
+    d2h = 4 * (2 * wl.D + wl.renders)
+
+    def e2e_step(k):
+        theta_d.copy_(theta_h, non_blocking=True)
+        sigma_d.copy_(sigma_h, non_blocking=True)
+        target_d.copy_(target_h, non_blocking=True)
+        opts = scene.grad_opts(wl, step=k)
+        scene.smoothed_grad(theta_d, sigma_d, target_d, opts, grad=g_d, losses=L_d)
+        ctx.adam_step(theta_d, m_d, v_d, g_d, k + 1, wl.lr)
+        out_h[: wl.D].copy_(theta_d, non_blocking=True)
+        out_h[wl.D: 2 * wl.D].copy_(g_d, non_blocking=True)
+        out_h[2 * wl.D:].copy_(L_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        theta_h.copy_(out_h[: wl.D])
+
+    for k in range(args.warmup):
+        e2e_step(k)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank == 0:
+        peaks = _measured_peaks()
+        props = torch.cuda.get_device_properties(local)
+        sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+        fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+        trace_avg_ms = trace_ms / max(launches, 1)
+        achieved = flops_step / (trace_avg_ms * 1e-3) / 1e12
+        value = world * 1000.0 / step_ms
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "renders": wl.renders, "pairs": wl.pairs, "width": wl.width,
+                       "height": wl.height, "spp": wl.spp, "depth": wl.depth, "D": wl.D,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "mpaths_per_s": world * wl.paths_per_step / (step_ms * 1e-3) / 1e6,
+            "wall_s": wall,
+            "render_kernel_ms": trace_avg_ms,
+            "work_per_step": {"sphere_tests": counts[0], "quad_tests": counts[1], "box_tests": counts[2],
+                              "paths": counts[3], "vertices": counts[4], "shadow_rays": counts[5],
+                              "closest_hit_rays": counts[6]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": _profiled_traffic(wl.name),
+                         "kernel": "k_trace", "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
+                                                            f" x 2 flop x {sm_max:.0f} MHz"},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "final_loss_mean": float(np.mean(state["losses"])),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, target_host)
+        print(json.dumps(line), flush=True)
+    job.release()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

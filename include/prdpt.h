@@ -1,0 +1,232 @@
+/*
+ * prdpt.h -- C ABI of the GB300 (sm_103a) plateau-reduced gradient library.
+ *
+ * The library computes the plateau-reduced gradient of Fischer & Ritschel,
+ * "Plateau-reduced Differentiable Path Tracing": the image loss L of a path-traced
+ * scene is convolved with a Gaussian kernel over the scene parameters theta
+ * (Eq. 6), and the gradient of the smoothed loss is estimated by perturbing
+ * theta, path-tracing the perturbed scenes and weighting each render's loss by the
+ * kernel gradient over the sampling density (Eq. 10, Eq. 11, Algorithm 1). The
+ * renderer is treated as a black box; only its forward image is needed.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a prdpt_status; 0 is success. No exception crosses the ABI.
+ *    On failure prdpt_last_error() returns a message owned by the library, valid
+ *    until the next call on the same context from the same thread.
+ *  - Pointers named *_dev are device pointers owned by the caller (for instance
+ *    torch tensor storage); *_host pointers are host memory owned by the caller.
+ *    The library never frees caller memory and never keeps caller pointers after
+ *    a call returns, except where a call says so.
+ *  - Calls taking `stream` (a cudaStream_t, NULL = legacy default stream) only
+ *    enqueue work and return; their device-side results are ready when the stream
+ *    reaches that point. Calls without a stream are synchronous.
+ *  - Images are row-major [H][W] of float4 (R, G, B, pad); pixel (0,0) is the top
+ *    left; the pad channel is written as 0 and ignored on input.
+ *  - Random numbers: Philox4x32-10 with key = 64-bit seed; counter words
+ *    (c0, c1, c2, c3). Perturbation draws use (pair or draw index, block, step,
+ *    1 << 28); path samples use (pixel y*W+x, sample | vertex << 16 | slot << 24,
+ *    step, tag << 28 | render field), slot 0 = BSDF / Russian roulette, slot 1 =
+ *    light sample, slot 2 = pixel jitter. Uniforms are ((word >> 9) * 2 + 1) / 2^24.
+ *  - Limits: at most PRDPT_MAX_PRIMS primitives, PRDPT_MAX_MATS materials,
+ *    PRDPT_MAX_LIGHTS emitters, PRDPT_MAX_D parameters and PRDPT_MAX_PAIRS
+ *    antithetic pairs per call. Width and height at most 8192, spp at most 65535,
+ *    depth at most 64.
+ */
+#ifndef PRDPT_H
+#define PRDPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prdpt_ctx prdpt_ctx;
+typedef int32_t prdpt_status;
+
+#define PRDPT_OK 0
+#define PRDPT_E_INVALID_ARG 1   /* an argument is out of range or inconsistent */
+#define PRDPT_E_OUT_OF_BUDGET 2 /* the allocation would exceed the context's HBM budget */
+#define PRDPT_E_CUDA 3          /* a CUDA runtime call failed */
+#define PRDPT_E_TIMEOUT 4       /* a bounded device-side wait expired */
+#define PRDPT_E_NOT_READY 5     /* the result is not available yet */
+#define PRDPT_E_NOT_FOUND 6     /* unknown scene or job handle */
+#define PRDPT_E_DEVICE 7        /* a kernel reported an error through the status word */
+
+#define PRDPT_MAX_PRIMS 32
+#define PRDPT_MAX_MATS 32
+#define PRDPT_MAX_LIGHTS 8
+#define PRDPT_MAX_D 64
+#define PRDPT_MAX_PAIRS 256
+
+/* primitive, material, binding and sampler kinds */
+#define PRDPT_PRIM_SPHERE 0
+#define PRDPT_PRIM_QUAD 1
+#define PRDPT_PRIM_BOX 2
+#define PRDPT_MAT_DIFFUSE 0
+#define PRDPT_MAT_MIRROR 1
+#define PRDPT_MAT_DIELECTRIC 2
+#define PRDPT_BIND_PRIM_POS 0     /* theta_d sets primitive `index`'s centre component */
+#define PRDPT_BIND_SPHERE_RADIUS 1 /* theta_d sets sphere `index`'s radius (absolute value) */
+#define PRDPT_BIND_MAT_ALBEDO 2   /* theta_d sets material `index`'s albedo channel, clamped to [0,1] */
+#define PRDPT_BIND_MAT_EMISSION 3 /* theta_d sets material `index`'s emission channel, clamped to >= 0 */
+#define PRDPT_SAMPLER_RADIAL 0    /* q ~ |grad kappa| as a vector norm; exact 1-D sampler of the paper */
+#define PRDPT_SAMPLER_PERDIM 1    /* literal per-dimension two-sided inverse CDF */
+#define PRDPT_SAMPLER_GAUSS 2     /* tau ~ N(0, sigma^2): no importance sampling ("noIS") */
+
+/* Scene in host memory; copied by prdpt_scene_upload.
+ *  prim_geom: [n_prims][9] floats; sphere: centre(3), radius; quad: centre(3),
+ *    edge u(3), edge v(3) (orthogonal; one-sided emitters radiate along
+ *    normalize(u x v)); box: centre(3), half size(3).
+ *  mat_param: [n_mats][8] floats: albedo(3), emission(3), ior, unused.
+ *  camera: eye(3), look-at(3), up(3), vertical field of view in degrees.
+ *  background: constant radiance of rays that leave the scene. */
+typedef struct {
+    int32_t n_prims, n_mats;
+    const int32_t* prim_type;
+    const int32_t* prim_mat;
+    const float* prim_geom;
+    const int32_t* mat_type;
+    const float* mat_param;
+    const float* camera;
+    const float* background;
+} prdpt_scene_desc;
+
+/* theta_d -> scene field. `component` is 0..2 (x/y/z or R/G/B); unused for radius. */
+typedef struct {
+    int32_t kind, index, component;
+} prdpt_param_binding;
+
+/* Forward rendering options (Eq. 3: `spp` Monte-Carlo paths per pixel). */
+typedef struct {
+    int32_t width, height, spp, depth;
+    int32_t rr_start;          /* 0-based vertex index from which Russian roulette applies; -1 = never */
+    uint64_t seed;
+    uint32_t step, tag;        /* Philox counter word 2 and stream tag (2 = path, 3 = target) */
+    int32_t crn;               /* 1: every render uses path field 0; 0: render i uses field i */
+    int32_t threads_per_pixel; /* launch shape (1, 2, 4 or 8); 0 = automatic */
+} prdpt_render_opts;
+
+/* Gradient-estimator options (Eq. 10, Algorithm 1). R = 2 * pairs renders. */
+typedef struct {
+    int32_t pairs;             /* P antithetic pairs (Algorithm 1's N = 2P) */
+    int32_t width, height, spp, depth, rr_start;
+    int32_t sampler;           /* PRDPT_SAMPLER_* */
+    int32_t antithetic;        /* 1: renders 2p, 2p+1 use +tau_p, -tau_p; 0: 2P independent draws */
+    int32_t crn;               /* 1: all renders share path samples (field 0); 0: render r uses field r+1 */
+    uint64_t seed;
+    uint32_t step;             /* optimiser step: Philox counter word 2 of every draw */
+    int32_t threads_per_pixel; /* launch shape (1, 2, 4 or 8); 0 = automatic */
+} prdpt_grad_opts;
+
+/* A resident optimisation job: scene parameters, Adam state and target stay on
+ * the device between steps (Adam, Sec. 3.4; bandwidth schedule, Sec. 3.3). */
+typedef struct {
+    prdpt_grad_opts grad;      /* grad.step is the first step index */
+    const float* theta0_host;  /* [D] initial parameters */
+    const float* sigma0_host;  /* [D] kernel bandwidth */
+    const float* target_host;  /* [H][W][4] target image */
+    float lr, beta1, beta2, eps;
+    float sigma_min;           /* lower end of the linear bandwidth decay */
+    int32_t anneal;            /* 1: sigma constant for total_steps/2 steps, then linear to sigma_min */
+    int32_t total_steps;       /* schedule length (used only when anneal = 1) */
+} prdpt_job_desc;
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes bounds the device
+ * memory the context may allocate (0 = no bound). */
+prdpt_status prdpt_create(prdpt_ctx** out, int32_t device, uint64_t hbm_budget_bytes);
+
+/* Destroy a context and free all library-owned device memory. Synchronises the device. */
+prdpt_status prdpt_destroy(prdpt_ctx* ctx);
+
+/* Message describing the last failure on this context (never NULL). */
+const char* prdpt_last_error(prdpt_ctx* ctx);
+
+/* Copy a scene and its parameter bindings (the map theta -> scene, Eq. 1's
+ * f(x, theta)) into device memory. D = number of bindings (1..PRDPT_MAX_D).
+ * Synchronous. Emissive boxes are rejected. */
+prdpt_status prdpt_scene_upload(prdpt_ctx* ctx, const prdpt_scene_desc* scene, const prdpt_param_binding* binds,
+                                int32_t D, int32_t* scene_id_out);
+
+/* Free a scene. Jobs using it must have been released. Synchronous. */
+prdpt_status prdpt_scene_release(prdpt_ctx* ctx, int32_t scene_id);
+
+/* Render n scenes at parameter vectors thetas_dev [n][D] (Eq. 3 per pixel):
+ * images_dev [n][H][W][4]. Render i uses path field (crn ? 0 : i). */
+prdpt_status prdpt_render_batch(prdpt_ctx* ctx, int32_t scene_id, const float* thetas_dev, int32_t n,
+                                const prdpt_render_opts* opts, float* images_dev, void* stream);
+
+/* The perturbations and weights a gradient call with the same options draws
+ * (Sec. 3.2, Eq. 11): tau_dev [2P][D] (tau of render r; antithetic renders are
+ * negated) and w_dev [2P][D] (d kappa / q of render r). sigma_dev [D]. */
+prdpt_status prdpt_sample_perturbations(prdpt_ctx* ctx, int32_t D, const float* sigma_dev,
+                                        const prdpt_grad_opts* opts, float* tau_dev, float* w_dev, void* stream);
+
+/* One plateau-reduced gradient (Eq. 10): grad_dev[d] = (1/2P) sum_p w_pd (L_2p - L_2p+1)
+ * with L_r the image MSE (1/3HW) sum (I_r - T)^2 of render r at theta + tau_r.
+ * theta_dev, sigma_dev: [D]; target_dev: [H][W][4]; grad_dev: [D];
+ * losses_dev: [2P] or NULL. The perturbed images never reach device memory:
+ * each render's loss is reduced inside the render kernel. */
+prdpt_status prdpt_smoothed_grad(prdpt_ctx* ctx, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
+                                 const prdpt_grad_opts* opts, const float* target_dev, float* grad_dev,
+                                 float* losses_dev, void* stream);
+
+/* One Adam update (PyTorch defaults' formula; t is the 1-based step) of D
+ * parameters in place: theta_dev, m_dev, v_dev [D], grad_dev [D]. */
+prdpt_status prdpt_adam_step(prdpt_ctx* ctx, int32_t D, float* theta_dev, float* m_dev, float* v_dev,
+                             const float* grad_dev, int32_t t, float lr, float beta1, float beta2, float eps,
+                             void* stream);
+
+/* Create a resident job on a scene: copies theta0, sigma0 and the target into
+ * library-owned device memory (charged to the HBM budget). Synchronous. */
+prdpt_status prdpt_job_create(prdpt_ctx* ctx, int32_t scene_id, const prdpt_job_desc* desc, int32_t* job_out);
+
+/* One optimisation step of a resident job, all on the device: draw perturbations,
+ * render and reduce losses, form the gradient, apply Adam, advance the step and
+ * the bandwidth schedule. No host synchronisation; capturable in a CUDA graph
+ * once the context has run one step with the same shape. */
+prdpt_status prdpt_step(prdpt_ctx* ctx, int32_t job_id, void* stream);
+
+/* One step of each of n resident jobs, packed into one sampler launch and one
+ * persistent render launch (the jobs' renders share the GPU). Each job's result
+ * is identical to what prdpt_step would give it alone. */
+prdpt_status prdpt_step_batch(prdpt_ctx* ctx, const int32_t* job_ids, int32_t n, void* stream);
+
+/* Copy a job's current parameters [D], last gradient [D], last per-render losses
+ * [2P] and completed-step count to the host (any pointer may be NULL).
+ * Synchronises the job's last stream and checks the device status word. */
+prdpt_status prdpt_job_read(prdpt_ctx* ctx, int32_t job_id, float* theta_host, float* grad_host,
+                            float* losses_host, int32_t* steps_host);
+
+/* Free a job's device memory. Synchronous. */
+prdpt_status prdpt_job_release(prdpt_ctx* ctx, int32_t job_id);
+
+/* Philox4x32-10 words for counters (c0_base + i, c1, c2, c3), key = seed:
+ * words_dev [n][4]. Exposed so that the random streams can be checked bit for bit. */
+prdpt_status prdpt_philox_words(prdpt_ctx* ctx, uint64_t seed, uint32_t c0_base, uint32_t c1, uint32_t c2,
+                                uint32_t c3, int32_t n, uint32_t* words_dev, void* stream);
+
+/* Work counters of the render kernel (the algorithmic work of Eq. 3's path
+ * samples), accumulated while enabled: [0] ray-sphere tests, [1] ray-quad tests,
+ * [2] ray-box tests, [3] camera paths, [4] surface vertices, [5] shadow rays,
+ * [6] closest-hit rays, [7] unused. enable=1 zeroes them and makes later render
+ * launches use the counting kernel variant; enable=0 returns to the uncounted
+ * variant. prdpt_counters_read copies them to counts_host[8] (synchronous). */
+prdpt_status prdpt_counters_enable(prdpt_ctx* ctx, int32_t enable);
+prdpt_status prdpt_counters_read(prdpt_ctx* ctx, uint64_t* counts_host);
+
+/* CUDA-event timing of the render kernel: while enabled, every render launch is
+ * bracketed by two events recorded on its own stream. prdpt_kernel_timing_read
+ * waits for the recorded launches and returns their summed duration (ms) and
+ * count, then forgets them. Not for use inside CUDA-graph capture. */
+prdpt_status prdpt_kernel_timing_enable(prdpt_ctx* ctx, int32_t enable);
+prdpt_status prdpt_kernel_timing_read(prdpt_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Synchronise `stream` and check the context's device status word. */
+prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRDPT_H */

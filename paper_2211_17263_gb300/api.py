@@ -1,0 +1,174 @@
+"""Torch-facing convenience layer over the C ABI (marshalling only).
+
+PyTorch supplies device memory and streams; every computation runs in
+libprdpt.so. Tensors passed in must be contiguous CUDA float32 tensors on the
+context's device; outputs are allocated here with torch and filled by the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor):
+    if not t.is_cuda or t.dtype not in (torch.float32, torch.int32, torch.uint32) or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32/int32 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Context:
+    """A library context on one CUDA device (owns scenes and resident jobs)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        capi.load()
+        self.device = device
+        self.handle = capi.prdpt_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.handle is not None:
+            capi.prdpt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- scenes ---------------------------------------------------------------------------
+    def upload_scene(self, scene, bindings) -> "Scene":
+        return Scene(self, scene, bindings)
+
+    # -- counters ---------------------------------------------------------------------------
+    def counters_enable(self, on: bool = True):
+        capi.prdpt_counters_enable(self.handle, 1 if on else 0)
+
+    def counters_read(self):
+        return capi.prdpt_counters_read(self.handle)
+
+    def kernel_timing(self, on: bool = True):
+        capi.prdpt_kernel_timing_enable(self.handle, 1 if on else 0)
+
+    def kernel_timing_read(self):
+        return capi.prdpt_kernel_timing_read(self.handle)
+
+    def sync(self, stream=None):
+        capi.prdpt_sync(self.handle, _stream_ptr(stream))
+
+    def philox_words(self, seed, c0_base, c1, c2, c3, n, stream=None) -> torch.Tensor:
+        out = torch.empty((n, 4), dtype=torch.int32, device=f"cuda:{self.device}")
+        capi.prdpt_philox_words(self.handle, seed, c0_base, c1, c2, c3, n, _dev_ptr(out), _stream_ptr(stream))
+        return out
+
+    def sample_perturbations(self, sigma: torch.Tensor, pairs, sampler=0, antithetic=1, seed=0, step=0,
+                             stream=None):
+        D = sigma.numel()
+        R = 2 * pairs
+        tau = torch.empty((R, D), dtype=torch.float32, device=sigma.device)
+        w = torch.empty((R, D), dtype=torch.float32, device=sigma.device)
+        o = capi.prdpt_grad_opts(pairs=pairs, width=1, height=1, spp=1, depth=1, rr_start=-1, sampler=sampler,
+                                 antithetic=antithetic, crn=1, seed=seed, step=step, threads_per_pixel=0)
+        capi.prdpt_sample_perturbations(self.handle, D, _dev_ptr(sigma), o, _dev_ptr(tau), _dev_ptr(w),
+                                        _stream_ptr(stream))
+        return tau, w
+
+    def adam_step(self, theta, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        capi.prdpt_adam_step(self.handle, theta.numel(), _dev_ptr(theta), _dev_ptr(m), _dev_ptr(v), _dev_ptr(grad),
+                             t, lr, beta1, beta2, eps, _stream_ptr(stream))
+
+
+class Scene:
+    """An uploaded scene plus its parameter bindings (theta -> scene fields)."""
+
+    def __init__(self, ctx: Context, scene, bindings):
+        self.ctx = ctx
+        arrays = [np.ascontiguousarray(scene.prim_type, np.int32), np.ascontiguousarray(scene.prim_mat, np.int32),
+                  np.ascontiguousarray(scene.prim_geom, np.float32), np.ascontiguousarray(scene.mat_type, np.int32),
+                  np.ascontiguousarray(scene.mat_param, np.float32), np.ascontiguousarray(scene.camera, np.float32),
+                  np.ascontiguousarray(scene.background, np.float32)]
+        desc = capi.prdpt_scene_desc(int(arrays[0].shape[0]), int(arrays[3].shape[0]), *[_np_ptr(a) for a in arrays])
+        b = np.ascontiguousarray(bindings, np.int32).reshape(-1, 3)
+        self.D = int(b.shape[0])
+        binds = (capi.prdpt_param_binding * self.D)(*[capi.prdpt_param_binding(*map(int, row)) for row in b])
+        self.id = capi.prdpt_scene_upload(ctx.handle, desc, binds, self.D)
+
+    def render_batch(self, thetas: torch.Tensor, width, height, spp, depth, rr_start=-1, seed=0, step=0, tag=2,
+                     crn=1, threads_per_pixel=0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        thetas = thetas.reshape(-1, self.D)
+        n = thetas.shape[0]
+        if out is None:
+            out = torch.empty((n, height, width, 4), dtype=torch.float32, device=thetas.device)
+        o = capi.prdpt_render_opts(width=width, height=height, spp=spp, depth=depth, rr_start=rr_start, seed=seed,
+                                   step=step, tag=tag, crn=crn, threads_per_pixel=threads_per_pixel)
+        capi.prdpt_render_batch(self.ctx.handle, self.id, _dev_ptr(thetas), n, o, _dev_ptr(out), _stream_ptr(stream))
+        return out
+
+    def grad_opts(self, wl, step=0, pairs=None, sampler=None, antithetic=None, crn=None, threads_per_pixel=0):
+        return capi.prdpt_grad_opts(
+            pairs=wl.pairs if pairs is None else pairs, width=wl.width, height=wl.height, spp=wl.spp,
+            depth=wl.depth, rr_start=wl.rr_start, sampler=wl.sampler if sampler is None else sampler,
+            antithetic=wl.antithetic if antithetic is None else antithetic, crn=wl.crn if crn is None else crn,
+            seed=wl.seed, step=step, threads_per_pixel=threads_per_pixel)
+
+    def smoothed_grad(self, theta: torch.Tensor, sigma: torch.Tensor, target: torch.Tensor, opts,
+                      grad: torch.Tensor | None = None, losses: torch.Tensor | None = None, stream=None):
+        if grad is None:
+            grad = torch.empty(self.D, dtype=torch.float32, device=theta.device)
+        if losses is None:
+            losses = torch.empty(2 * opts.pairs, dtype=torch.float32, device=theta.device)
+        capi.prdpt_smoothed_grad(self.ctx.handle, self.id, _dev_ptr(theta), _dev_ptr(sigma), opts, _dev_ptr(target),
+                                 _dev_ptr(grad), _dev_ptr(losses), _stream_ptr(stream))
+        return grad, losses
+
+
+class Job:
+    """A resident optimisation job: parameters, Adam state and target live on the device."""
+
+    def __init__(self, scene: Scene, wl, target_host: np.ndarray, step0=0, threads_per_pixel=0, anneal=None,
+                 lr=None, sampler=None):
+        self.scene = scene
+        self.D = scene.D
+        self.R = 2 * wl.pairs
+        self._theta0 = np.ascontiguousarray(wl.theta0, np.float32)
+        self._sigma0 = np.ascontiguousarray(wl.sigma, np.float32)
+        self._target = np.ascontiguousarray(target_host, np.float32)
+        if self._target.shape != (wl.height, wl.width, 4):
+            raise ValueError("target must be [H, W, 4] float32")
+        desc = capi.prdpt_job_desc(
+            grad=scene.grad_opts(wl, step=step0, sampler=sampler, threads_per_pixel=threads_per_pixel),
+            theta0_host=_np_ptr(self._theta0), sigma0_host=_np_ptr(self._sigma0), target_host=_np_ptr(self._target),
+            lr=wl.lr if lr is None else lr, beta1=0.9, beta2=0.999, eps=1e-8, sigma_min=wl.sigma_min,
+            anneal=wl.anneal if anneal is None else anneal, total_steps=wl.steps)
+        self.id = capi.prdpt_job_create(scene.ctx.handle, scene.id, desc)
+
+    def step(self, stream=None):
+        capi.prdpt_step(self.scene.ctx.handle, self.id, _stream_ptr(stream))
+
+    def read(self):
+        theta = np.zeros(self.D, np.float32)
+        grad = np.zeros(self.D, np.float32)
+        losses = np.zeros(self.R, np.float32)
+        steps = capi.prdpt_job_read(self.scene.ctx.handle, self.id, _np_ptr(theta), _np_ptr(grad), _np_ptr(losses))
+        return {"theta": theta, "grad": grad, "losses": losses, "steps": steps}
+
+    def release(self):
+        if self.id is not None:
+            capi.prdpt_job_release(self.scene.ctx.handle, self.id)
+            self.id = None
+
+
+def step_batch(ctx: Context, jobs, stream=None):
+    capi.prdpt_step_batch(ctx.handle, [j.id for j in jobs], _stream_ptr(stream))

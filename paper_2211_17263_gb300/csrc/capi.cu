@@ -1,0 +1,824 @@
+// capi.cu -- host implementation of the C ABI declared in include/prdpt.h.
+//
+// Owns the context (device, HBM budget, scenes, resident jobs, scratch buffers for
+// the stateless calls, descriptor arrays for packed launches) and turns each call
+// into at most two kernel launches: k_instantiate (sampler + scene binding) and
+// k_trace (persistent render with the fused loss / gradient / Adam epilogue).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/prdpt.h"
+#include "internal.h"
+
+using namespace prdpt;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+prdpt_status fail(prdpt_status code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define PRDPT_CUDA(call)                                                                          \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(PRDPT_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Scene {
+    BaseScene host;
+    BaseScene* dev = nullptr;
+    int D = 0;
+    int jobs = 0;
+};
+
+struct Job {
+    int scene = -1;
+    int D = 0, R = 0, tiles = 0;
+    size_t bytes = 0;
+    // device buffers
+    float *theta = nullptr, *m = nullptr, *v = nullptr, *sigma0 = nullptr, *grad = nullptr, *losses = nullptr;
+    float *w = nullptr, *partials = nullptr;
+    int* step = nullptr;
+    unsigned *done = nullptr, *queue = nullptr;
+    InstScene* scenes = nullptr;
+    float4* target = nullptr;
+    InstJob inst{};
+    TraceJob trace{};
+};
+
+}  // namespace
+
+struct prdpt_ctx {
+    int device = 0;
+    int sms = 0;
+    int occ_grad = 1, occ_render = 1;
+    uint64_t budget = 0, used = 0;
+    std::map<void*, size_t> allocs;
+    std::vector<Scene*> scenes;
+    std::vector<Job*> jobs;
+    // control block: [0] status, [1..4] unused, then counters, queues
+    int* status = nullptr;
+    unsigned long long* counters = nullptr;
+    bool counting = false;
+    // scratch of the stateless calls (grown on demand)
+    InstScene* s_scenes = nullptr;
+    size_t s_scenes_n = 0;
+    float* s_w = nullptr;
+    size_t s_w_n = 0;
+    float* s_partials = nullptr;
+    size_t s_partials_n = 0;
+    unsigned* s_ctl = nullptr;  // [0] queue, [1] done counter, [2] batch queue
+    // packed launches
+    std::vector<int> batch_ids;
+    InstJob* d_inst = nullptr;
+    TraceJob* d_trace = nullptr;
+    size_t batch_cap = 0;
+    int batch_items = 0, batch_blocks = 0;
+    // optional CUDA-event timing of the render kernel, recorded on its launch stream
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+    std::mutex mu;
+};
+
+namespace {
+
+prdpt_status dev_alloc(prdpt_ctx* c, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(PRDPT_E_OUT_OF_BUDGET, "allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget (" +
+                                               std::to_string(c->used) + " of " + std::to_string(c->budget) + " used)");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(PRDPT_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->allocs[*p] = bytes;
+    c->used += bytes;
+    return PRDPT_OK;
+}
+
+void dev_free(prdpt_ctx* c, void* p) {
+    if (!p) return;
+    auto it = c->allocs.find(p);
+    if (it != c->allocs.end()) {
+        c->used -= it->second;
+        c->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
+template <typename T>
+prdpt_status grow(prdpt_ctx* c, T** p, size_t* cap, size_t n) {
+    if (*cap >= n) return PRDPT_OK;
+    dev_free(c, *p);
+    *p = nullptr;
+    *cap = 0;
+    prdpt_status st = dev_alloc(c, reinterpret_cast<void**>(p), n * sizeof(T));
+    if (st) return st;
+    *cap = n;
+    return PRDPT_OK;
+}
+
+bool is_emissive(const float* mp) { return mp[3] > 0.f || mp[4] > 0.f || mp[5] > 0.f; }
+
+double radial_constant(int D) { return std::sqrt(2.0) * std::exp(std::lgamma(0.5 * (D + 1)) - std::lgamma(0.5 * D)); }
+
+prdpt_status check_common(int W, int H, int spp, int depth, int rr_start) {
+    if (W < 1 || H < 1 || W > 8192 || H > 8192) return fail(PRDPT_E_INVALID_ARG, "width/height must be in 1..8192");
+    if (spp < 1 || spp > 65535) return fail(PRDPT_E_INVALID_ARG, "spp must be in 1..65535");
+    if (depth < 1 || depth > 64) return fail(PRDPT_E_INVALID_ARG, "depth must be in 1..64");
+    if (rr_start < -1 || rr_start > 64) return fail(PRDPT_E_INVALID_ARG, "rr_start must be -1 or 0..64");
+    return PRDPT_OK;
+}
+
+Scene* get_scene(prdpt_ctx* c, int id) {
+    if (id < 0 || id >= (int)c->scenes.size()) return nullptr;
+    return c->scenes[id];
+}
+
+Job* get_job(prdpt_ctx* c, int id) {
+    if (id < 0 || id >= (int)c->jobs.size()) return nullptr;
+    return c->jobs[id];
+}
+
+int choose_k(prdpt_ctx* c, int requested, int R, int W, int H, int spp, bool render) {
+    if (requested == 1 || requested == 2 || requested == 4 || requested == 8) return requested;
+    const long long capacity = (long long)c->sms * (render ? c->occ_render : c->occ_grad) * kBlock;
+    const long long work = (long long)R * W * H;
+    int k = 1;
+    while (k < 8 && 2 * k <= spp && work * k < 2 * capacity) k *= 2;
+    return k;
+}
+
+void tiles_for(int k, int W, int H, int* tiles_x, int* tiles) {
+    int tw, th;
+    tile_shape(k, &tw, &th);
+    *tiles_x = (W + tw - 1) / tw;
+    *tiles = *tiles_x * ((H + th - 1) / th);
+}
+
+int grid_for(prdpt_ctx* c, int items, bool render) {
+    const int cap = c->sms * (render ? c->occ_render : c->occ_grad);
+    return items < cap ? items : cap;
+}
+
+// Launch the render kernel, bracketed by events on its stream when timing is on.
+cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStream_t stream) {
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (c->timing) {
+        if (!c->ev_free.empty()) {
+            ev = c->ev_free.back();
+            c->ev_free.pop_back();
+        } else {
+            cudaError_t e = cudaEventCreate(&ev.first);
+            if (e == cudaSuccess) e = cudaEventCreate(&ev.second);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventRecord(ev.first, stream);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_trace(L, render, grid_for(c, L.total_items, render), stream);
+    if (e != cudaSuccess) return e;
+    if (c->timing) {
+        e = cudaEventRecord(ev.second, stream);
+        if (e != cudaSuccess) return e;
+        c->ev_used.push_back(ev);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* prdpt_last_error(prdpt_ctx*) { return g_err.c_str(); }
+
+prdpt_status prdpt_create(prdpt_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
+    if (!out) return fail(PRDPT_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    PRDPT_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(PRDPT_E_INVALID_ARG, "no such CUDA device");
+    PRDPT_CUDA(cudaSetDevice(device));
+    prdpt_ctx* c = new prdpt_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(PRDPT_E_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+    }
+    c->sms = prop.multiProcessorCount;
+    c->occ_grad = trace_blocks_per_sm(false);
+    c->occ_render = trace_blocks_per_sm(true);
+    void* p = nullptr;
+    prdpt_status st = dev_alloc(c, &p, 128);  // status word, then 8 counters
+    if (st) {
+        delete c;
+        return st;
+    }
+    c->status = static_cast<int*>(p);
+    c->counters = reinterpret_cast<unsigned long long*>(static_cast<char*>(p) + 16);
+    st = dev_alloc(c, &p, 64);
+    if (st) {
+        prdpt_destroy(c);
+        return st;
+    }
+    c->s_ctl = static_cast<unsigned*>(p);
+    if (cudaMemset(c->status, 0, 128) != cudaSuccess || cudaMemset(c->s_ctl, 0, 64) != cudaSuccess) {
+        prdpt_destroy(c);
+        return fail(PRDPT_E_CUDA, "cudaMemset of the control block failed");
+    }
+    *out = c;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_destroy(prdpt_ctx* c) {
+    if (!c) return PRDPT_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : c->allocs) cudaFree(kv.first);
+    for (auto& ev : c->ev_used) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    for (auto& ev : c->ev_free) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    for (Scene* s : c->scenes) delete s;
+    for (Job* j : c->jobs) delete j;
+    delete c;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_scene_upload(prdpt_ctx* c, const prdpt_scene_desc* sd, const prdpt_param_binding* binds,
+                                int32_t D, int32_t* scene_id_out) {
+    if (!c || !sd || !binds || !scene_id_out) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (sd->n_prims < 1 || sd->n_prims > kMaxPrims) return fail(PRDPT_E_INVALID_ARG, "n_prims must be in 1..32");
+    if (sd->n_mats < 1 || sd->n_mats > kMaxMats) return fail(PRDPT_E_INVALID_ARG, "n_mats must be in 1..32");
+    if (D < 1 || D > kMaxD) return fail(PRDPT_E_INVALID_ARG, "D must be in 1..64");
+    if (!sd->prim_type || !sd->prim_mat || !sd->prim_geom || !sd->mat_type || !sd->mat_param || !sd->camera ||
+        !sd->background)
+        return fail(PRDPT_E_INVALID_ARG, "scene array is NULL");
+    BaseScene B;
+    std::memset(&B, 0, sizeof(B));
+    B.n_prims = sd->n_prims;
+    B.n_mats = sd->n_mats;
+    B.D = D;
+    for (int i = 0; i < sd->n_mats; ++i) {
+        if (sd->mat_type[i] < 0 || sd->mat_type[i] > 2) return fail(PRDPT_E_INVALID_ARG, "bad material type");
+        B.mat_type[i] = sd->mat_type[i];
+        for (int q = 0; q < 8; ++q) B.mat_param[i][q] = sd->mat_param[8 * i + q];
+    }
+    std::vector<bool> emission_bound(sd->n_mats, false);
+    for (int d = 0; d < D; ++d) {
+        const int k = binds[d].kind, idx = binds[d].index, comp = binds[d].component;
+        if (k == kBindPos || k == kBindRadius) {
+            if (idx < 0 || idx >= sd->n_prims) return fail(PRDPT_E_INVALID_ARG, "binding: primitive index out of range");
+            if (k == kBindRadius && sd->prim_type[idx] != kSphere)
+                return fail(PRDPT_E_INVALID_ARG, "binding: radius of a non-sphere");
+        } else if (k == kBindAlbedo || k == kBindEmission) {
+            if (idx < 0 || idx >= sd->n_mats) return fail(PRDPT_E_INVALID_ARG, "binding: material index out of range");
+            if (k == kBindEmission) emission_bound[idx] = true;
+        } else {
+            return fail(PRDPT_E_INVALID_ARG, "binding: unknown kind");
+        }
+        if (k != kBindRadius && (comp < 0 || comp > 2)) return fail(PRDPT_E_INVALID_ARG, "binding: component must be 0..2");
+        B.bind_kind[d] = k;
+        B.bind_index[d] = idx;
+        B.bind_comp[d] = (k == kBindRadius) ? 0 : comp;
+    }
+    int n_light_candidates = 0;
+    for (int i = 0; i < sd->n_prims; ++i) {
+        const int t = sd->prim_type[i], m = sd->prim_mat[i];
+        if (t < 0 || t > 2) return fail(PRDPT_E_INVALID_ARG, "bad primitive type");
+        if (m < 0 || m >= sd->n_mats) return fail(PRDPT_E_INVALID_ARG, "primitive material out of range");
+        const bool can_emit = is_emissive(&sd->mat_param[8 * m]) || emission_bound[m];
+        if (t == kBox && can_emit) return fail(PRDPT_E_INVALID_ARG, "emissive boxes are not supported");
+        if (can_emit) ++n_light_candidates;
+        B.prim_type[i] = t;
+        B.prim_mat[i] = m;
+        for (int q = 0; q < 9; ++q) B.prim_geom[i][q] = sd->prim_geom[9 * i + q];
+        if (t == kSphere) ++B.n_sph;
+        if (t == kQuad) ++B.n_quad;
+        if (t == kBox) ++B.n_box;
+    }
+    if (n_light_candidates > kMaxLights) return fail(PRDPT_E_INVALID_ARG, "more than 8 emitters");
+    int next[3] = {0, B.n_sph, B.n_sph + B.n_quad};  // record slots grouped by type, stable
+    for (int i = 0; i < sd->n_prims; ++i) B.prim_slot[i] = next[B.prim_type[i]]++;
+    // camera basis (double, then rounded)
+    double eye[3], look[3], up[3];
+    for (int q = 0; q < 3; ++q) {
+        eye[q] = sd->camera[q];
+        look[q] = sd->camera[3 + q];
+        up[q] = sd->camera[6 + q];
+    }
+    double f[3] = {look[0] - eye[0], look[1] - eye[1], look[2] - eye[2]};
+    double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fn > 0)) return fail(PRDPT_E_INVALID_ARG, "camera eye equals look-at");
+    for (double& x : f) x /= fn;
+    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rn > 0)) return fail(PRDPT_E_INVALID_ARG, "camera up is parallel to the view direction");
+    for (double& x : r) x /= rn;
+    double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    for (int q = 0; q < 3; ++q) {
+        B.eye[q] = float(eye[q]);
+        B.fwd[q] = float(f[q]);
+        B.right[q] = float(r[q]);
+        B.up[q] = float(u[q]);
+        B.bg[q] = sd->background[q];
+    }
+    const double vfov = sd->camera[9];
+    if (!(vfov > 0 && vfov < 180)) return fail(PRDPT_E_INVALID_ARG, "field of view must be in (0, 180) degrees");
+    B.tan_half = float(std::tan(0.5 * vfov * M_PI / 180.0));
+
+    Scene* s = new Scene();
+    s->host = B;
+    s->D = D;
+    void* p = nullptr;
+    prdpt_status st = dev_alloc(c, &p, sizeof(BaseScene));
+    if (st) {
+        delete s;
+        return st;
+    }
+    s->dev = static_cast<BaseScene*>(p);
+    cudaError_t e = cudaMemcpy(s->dev, &s->host, sizeof(BaseScene), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(c, s->dev);
+        delete s;
+        return fail(PRDPT_E_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    c->scenes.push_back(s);
+    *scene_id_out = (int)c->scenes.size() - 1;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_scene_release(prdpt_ctx* c, int32_t scene_id) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Scene* s = get_scene(c, scene_id);
+    if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
+    if (s->jobs) return fail(PRDPT_E_INVALID_ARG, "scene still has jobs");
+    cudaDeviceSynchronize();
+    dev_free(c, s->dev);
+    delete s;
+    c->scenes[scene_id] = nullptr;
+    return PRDPT_OK;
+}
+
+static void fill_inst_common(InstJob& J, const Scene* s, int R, int D, int W, int H) {
+    std::memset(&J, 0, sizeof(J));
+    J.base = s->dev;
+    J.R = R;
+    J.D = D;
+    J.W = W;
+    J.H = H;
+    J.c_radial = float(radial_constant(D));
+}
+
+prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* thetas_dev, int32_t n,
+                                const prdpt_render_opts* o, float* images_dev, void* stream) {
+    if (!c || !o || !thetas_dev || !images_dev) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Scene* s = get_scene(c, scene_id);
+    if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
+    if (n < 1 || n > kMaxRenders) return fail(PRDPT_E_INVALID_ARG, "n must be in 1..512");
+    if (prdpt_status st = check_common(o->width, o->height, o->spp, o->depth, o->rr_start)) return st;
+    if (o->tag > 15) return fail(PRDPT_E_INVALID_ARG, "tag must be in 0..15");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)n)) return st;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    InstLaunch IL{};
+    fill_inst_common(IL.job0, s, n, s->D, o->width, o->height);
+    IL.job0.scenes = c->s_scenes;
+    IL.job0.theta = thetas_dev;
+    IL.job0.seed = o->seed;
+    IL.job0.step = o->step;
+    IL.job0.tag = o->tag;
+    IL.job0.crn = o->crn;
+    IL.job0.render_mode = 1;
+    IL.total_blocks = n;
+    IL.queue_reset = c->s_ctl + 0;
+    PRDPT_CUDA(launch_instantiate(IL, st_));
+    const int k = choose_k(c, o->threads_per_pixel, n, o->width, o->height, o->spp, true);
+    TraceLaunch TL{};
+    TraceJob& J = TL.job0;
+    J.scenes = c->s_scenes;
+    J.images = reinterpret_cast<float4*>(images_dev);
+    J.W = o->width;
+    J.H = o->height;
+    J.spp = o->spp;
+    J.depth = o->depth;
+    J.rr_start = o->rr_start;
+    J.R = n;
+    J.D = s->D;
+    J.k = k;
+    tiles_for(k, o->width, o->height, &J.tiles_x, &J.tiles);
+    TL.total_items = n * J.tiles;
+    TL.queue = c->s_ctl + 0;
+    TL.counters = c->counting ? c->counters : nullptr;
+    TL.status = c->status;
+    PRDPT_CUDA(timed_trace(c, TL, true, st_));
+    return PRDPT_OK;
+}
+
+static prdpt_status check_grad_opts(const prdpt_grad_opts* o) {
+    if (o->pairs < 1 || o->pairs > kMaxPairs) return fail(PRDPT_E_INVALID_ARG, "pairs must be in 1..256");
+    if (o->sampler < 0 || o->sampler > 2) return fail(PRDPT_E_INVALID_ARG, "unknown sampler");
+    return check_common(o->width, o->height, o->spp, o->depth, o->rr_start);
+}
+
+static void fill_inst_grad(InstJob& J, const Scene* s, const prdpt_grad_opts* o) {
+    fill_inst_common(J, s, 2 * o->pairs, s->D, o->width, o->height);
+    J.seed = o->seed;
+    J.step = o->step;
+    J.tag = kTagPath;
+    J.sampler = o->sampler;
+    J.antithetic = o->antithetic ? 1 : 0;
+    J.crn = o->crn ? 1 : 0;
+    J.render_mode = 0;
+}
+
+prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* sigma_dev, const prdpt_grad_opts* o,
+                                        float* tau_dev, float* w_dev, void* stream) {
+    if (!c || !o || !sigma_dev || !tau_dev || !w_dev) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    if (D < 1 || D > kMaxD) return fail(PRDPT_E_INVALID_ARG, "D must be in 1..64");
+    if (o->pairs < 1 || o->pairs > kMaxPairs) return fail(PRDPT_E_INVALID_ARG, "pairs must be in 1..256");
+    if (o->sampler < 0 || o->sampler > 2) return fail(PRDPT_E_INVALID_ARG, "unknown sampler");
+    std::lock_guard<std::mutex> lk(c->mu);
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    // reuse the theta slot for a zero vector: the draws do not depend on theta
+    if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)kMaxD)) return st;
+    PRDPT_CUDA(cudaMemsetAsync(c->s_w, 0, sizeof(float) * D, static_cast<cudaStream_t>(stream)));
+    InstLaunch IL{};
+    std::memset(&IL.job0, 0, sizeof(InstJob));
+    IL.job0.R = 2 * o->pairs;
+    IL.job0.D = D;
+    IL.job0.W = 1;
+    IL.job0.H = 1;
+    IL.job0.c_radial = float(radial_constant(D));
+    IL.job0.theta = c->s_w;
+    IL.job0.sigma = sigma_dev;
+    IL.job0.tau_out = tau_dev;
+    IL.job0.w_out = w_dev;
+    IL.job0.seed = o->seed;
+    IL.job0.step = o->step;
+    IL.job0.sampler = o->sampler;
+    IL.job0.antithetic = o->antithetic ? 1 : 0;
+    IL.total_blocks = 2 * o->pairs;  // scenes == null: draws only, no scene binding
+    PRDPT_CUDA(launch_instantiate(IL, static_cast<cudaStream_t>(stream)));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
+                                 const prdpt_grad_opts* o, const float* target_dev, float* grad_dev,
+                                 float* losses_dev, void* stream) {
+    if (!c || !o || !theta_dev || !sigma_dev || !target_dev || !grad_dev)
+        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Scene* s = get_scene(c, scene_id);
+    if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
+    if (prdpt_status st = check_grad_opts(o)) return st;
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    const int R = 2 * o->pairs, D = s->D;
+    const int k = choose_k(c, o->threads_per_pixel, R, o->width, o->height, o->spp, false);
+    int tiles_x, tiles;
+    tiles_for(k, o->width, o->height, &tiles_x, &tiles);
+    if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)R)) return st;
+    if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)R * D > (size_t)kMaxD ? (size_t)R * D : (size_t)kMaxD))
+        return st;
+    if (prdpt_status st = grow(c, &c->s_partials, &c->s_partials_n, (size_t)R * tiles)) return st;
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    InstLaunch IL{};
+    fill_inst_grad(IL.job0, s, o);
+    IL.job0.scenes = c->s_scenes;
+    IL.job0.theta = theta_dev;
+    IL.job0.sigma = sigma_dev;
+    IL.job0.w_out = c->s_w;
+    IL.total_blocks = R;
+    IL.queue_reset = c->s_ctl + 0;
+    PRDPT_CUDA(launch_instantiate(IL, st_));
+    TraceLaunch TL{};
+    TraceJob& J = TL.job0;
+    J.scenes = c->s_scenes;
+    J.target = reinterpret_cast<const float4*>(target_dev);
+    J.partials = c->s_partials;
+    J.done = c->s_ctl + 1;
+    J.w = c->s_w;
+    J.grad_out = grad_dev;
+    J.loss_out = losses_dev;
+    J.W = o->width;
+    J.H = o->height;
+    J.spp = o->spp;
+    J.depth = o->depth;
+    J.rr_start = o->rr_start;
+    J.R = R;
+    J.D = D;
+    J.antithetic = o->antithetic ? 1 : 0;
+    J.k = k;
+    J.tiles_x = tiles_x;
+    J.tiles = tiles;
+    TL.total_items = R * tiles;
+    TL.queue = c->s_ctl + 0;
+    TL.counters = c->counting ? c->counters : nullptr;
+    TL.status = c->status;
+    PRDPT_CUDA(timed_trace(c, TL, false, st_));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_adam_step(prdpt_ctx* c, int32_t D, float* theta_dev, float* m_dev, float* v_dev,
+                             const float* grad_dev, int32_t t, float lr, float beta1, float beta2, float eps,
+                             void* stream) {
+    if (!c || !theta_dev || !m_dev || !v_dev || !grad_dev) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    if (D < 1 || t < 1) return fail(PRDPT_E_INVALID_ARG, "D and t must be >= 1");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    PRDPT_CUDA(launch_adam(D, theta_dev, m_dev, v_dev, grad_dev, t, lr, beta1, beta2, eps,
+                           static_cast<cudaStream_t>(stream)));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_desc* d, int32_t* job_out) {
+    if (!c || !d || !job_out || !d->theta0_host || !d->sigma0_host || !d->target_host)
+        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Scene* s = get_scene(c, scene_id);
+    if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
+    const prdpt_grad_opts* o = &d->grad;
+    if (prdpt_status st = check_grad_opts(o)) return st;
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    Job* j = new Job();
+    j->scene = scene_id;
+    j->D = s->D;
+    j->R = 2 * o->pairs;
+    const int D = j->D, R = j->R, W = o->width, H = o->height;
+    const int k = choose_k(c, o->threads_per_pixel, R, W, H, o->spp, false);
+    int tiles_x, tiles;
+    tiles_for(k, W, H, &tiles_x, &tiles);
+    j->tiles = tiles;
+    // one device block per job: small state first, then w, partials, scenes, target
+    const size_t small = 6 * sizeof(float) * kMaxD + sizeof(float) * kMaxRenders + 64;
+    const size_t off_w = (small + 255) & ~size_t(255);
+    const size_t off_p = (off_w + sizeof(float) * R * D + 255) & ~size_t(255);
+    const size_t off_s = (off_p + sizeof(float) * R * tiles + 255) & ~size_t(255);
+    const size_t off_t = (off_s + sizeof(InstScene) * R + 255) & ~size_t(255);
+    const size_t total = off_t + sizeof(float4) * (size_t)W * H;
+    void* base = nullptr;
+    if (prdpt_status st = dev_alloc(c, &base, total)) {
+        delete j;
+        return st;
+    }
+    j->bytes = total;
+    char* b = static_cast<char*>(base);
+    j->theta = reinterpret_cast<float*>(b);
+    j->m = j->theta + kMaxD;
+    j->v = j->m + kMaxD;
+    j->sigma0 = j->v + kMaxD;
+    j->grad = j->sigma0 + kMaxD;
+    j->losses = j->grad + kMaxD;
+    j->step = reinterpret_cast<int*>(j->losses + kMaxRenders);
+    j->done = reinterpret_cast<unsigned*>(j->step + 1);
+    j->queue = j->done + 1;
+    j->w = reinterpret_cast<float*>(b + off_w);
+    j->partials = reinterpret_cast<float*>(b + off_p);
+    j->scenes = reinterpret_cast<InstScene*>(b + off_s);
+    j->target = reinterpret_cast<float4*>(b + off_t);
+    cudaError_t e = cudaMemset(base, 0, off_w);
+    if (e == cudaSuccess) e = cudaMemcpy(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(j->target, d->target_host, sizeof(float4) * (size_t)W * H, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(c, base);
+        delete j;
+        return fail(PRDPT_E_CUDA, std::string("job upload: ") + cudaGetErrorString(e));
+    }
+    InstJob& I = j->inst;
+    fill_inst_grad(I, s, o);
+    I.scenes = j->scenes;
+    I.theta = j->theta;
+    I.sigma = j->sigma0;
+    I.w_out = j->w;
+    I.step_dev = j->step;
+    I.anneal = d->anneal ? 1 : 0;
+    I.total_steps = d->total_steps;
+    I.sigma_min = d->sigma_min;
+    TraceJob& T = j->trace;
+    std::memset(&T, 0, sizeof(T));
+    T.scenes = j->scenes;
+    T.target = j->target;
+    T.partials = j->partials;
+    T.done = j->done;
+    T.w = j->w;
+    T.grad_out = j->grad;
+    T.loss_out = j->losses;
+    T.theta = j->theta;
+    T.m = j->m;
+    T.v = j->v;
+    T.step_dev = j->step;
+    T.lr = d->lr;
+    T.b1 = d->beta1;
+    T.b2 = d->beta2;
+    T.eps = d->eps;
+    T.W = W;
+    T.H = H;
+    T.spp = o->spp;
+    T.depth = o->depth;
+    T.rr_start = o->rr_start;
+    T.R = R;
+    T.D = D;
+    T.antithetic = o->antithetic ? 1 : 0;
+    T.k = k;
+    T.tiles_x = tiles_x;
+    T.tiles = tiles;
+    s->jobs++;
+    c->jobs.push_back(j);
+    *job_out = (int)c->jobs.size() - 1;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    Job* j = get_job(c, job_id);
+    if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    InstLaunch IL{};
+    IL.job0 = j->inst;
+    IL.total_blocks = j->R;
+    IL.queue_reset = j->queue;
+    PRDPT_CUDA(launch_instantiate(IL, st_));
+    TraceLaunch TL{};
+    TL.job0 = j->trace;
+    TL.total_items = j->R * j->tiles;
+    TL.queue = j->queue;
+    TL.counters = c->counting ? c->counters : nullptr;
+    TL.status = c->status;
+    PRDPT_CUDA(timed_trace(c, TL, false, st_));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, void* stream) {
+    if (!c || !job_ids || n < 1) return fail(PRDPT_E_INVALID_ARG, "bad job list");
+    std::lock_guard<std::mutex> lk(c->mu);
+    std::vector<int> ids(job_ids, job_ids + n);
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    if (ids != c->batch_ids) {
+        std::vector<InstJob> inst(n);
+        std::vector<TraceJob> trace(n);
+        int blocks = 0, items = 0;
+        for (int i = 0; i < n; ++i) {
+            Job* j = get_job(c, ids[i]);
+            if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job in batch");
+            for (int q = 0; q < i; ++q)
+                if (ids[q] == ids[i]) return fail(PRDPT_E_INVALID_ARG, "a job appears twice in a batch");
+            inst[i] = j->inst;
+            inst[i].block_begin = blocks;
+            blocks += j->R;
+            trace[i] = j->trace;
+            trace[i].item_begin = items;
+            items += j->R * j->tiles;
+        }
+        PRDPT_CUDA(cudaStreamSynchronize(st_));  // the old descriptors may still be in use
+        if ((size_t)n > c->batch_cap) {
+            dev_free(c, c->d_inst);
+            dev_free(c, c->d_trace);
+            c->d_inst = nullptr;
+            c->d_trace = nullptr;
+            c->batch_cap = 0;
+            void* p = nullptr;
+            if (prdpt_status st = dev_alloc(c, &p, sizeof(InstJob) * n)) return st;
+            c->d_inst = static_cast<InstJob*>(p);
+            if (prdpt_status st = dev_alloc(c, &p, sizeof(TraceJob) * n)) return st;
+            c->d_trace = static_cast<TraceJob*>(p);
+            c->batch_cap = n;
+        }
+        PRDPT_CUDA(cudaMemcpy(c->d_inst, inst.data(), sizeof(InstJob) * n, cudaMemcpyHostToDevice));
+        PRDPT_CUDA(cudaMemcpy(c->d_trace, trace.data(), sizeof(TraceJob) * n, cudaMemcpyHostToDevice));
+        c->batch_ids = ids;
+        c->batch_blocks = blocks;
+        c->batch_items = items;
+    }
+    InstLaunch IL{};
+    IL.jobs = c->d_inst;
+    IL.njobs = n;
+    IL.total_blocks = c->batch_blocks;
+    IL.queue_reset = c->s_ctl + 2;
+    PRDPT_CUDA(launch_instantiate(IL, st_));
+    TraceLaunch TL{};
+    TL.jobs = c->d_trace;
+    TL.njobs = n;
+    TL.total_items = c->batch_items;
+    TL.queue = c->s_ctl + 2;
+    TL.counters = c->counting ? c->counters : nullptr;
+    TL.status = c->status;
+    PRDPT_CUDA(timed_trace(c, TL, false, st_));
+    return PRDPT_OK;
+}
+
+static prdpt_status check_status(prdpt_ctx* c) {
+    int st = 0;
+    PRDPT_CUDA(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) return fail(PRDPT_E_DEVICE, "device status word " + std::to_string(st));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_job_read(prdpt_ctx* c, int32_t job_id, float* theta_host, float* grad_host, float* losses_host,
+                            int32_t* steps_host) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    Job* j = get_job(c, job_id);
+    if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    PRDPT_CUDA(cudaDeviceSynchronize());
+    if (prdpt_status st = check_status(c)) return st;
+    if (theta_host) PRDPT_CUDA(cudaMemcpy(theta_host, j->theta, sizeof(float) * j->D, cudaMemcpyDeviceToHost));
+    if (grad_host) PRDPT_CUDA(cudaMemcpy(grad_host, j->grad, sizeof(float) * j->D, cudaMemcpyDeviceToHost));
+    if (losses_host) PRDPT_CUDA(cudaMemcpy(losses_host, j->losses, sizeof(float) * j->R, cudaMemcpyDeviceToHost));
+    if (steps_host) PRDPT_CUDA(cudaMemcpy(steps_host, j->step, sizeof(int), cudaMemcpyDeviceToHost));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_job_release(prdpt_ctx* c, int32_t job_id) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Job* j = get_job(c, job_id);
+    if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
+    PRDPT_CUDA(cudaDeviceSynchronize());
+    dev_free(c, j->theta);
+    Scene* s = get_scene(c, j->scene);
+    if (s) s->jobs--;
+    for (int q : c->batch_ids)
+        if (q == job_id) {
+            c->batch_ids.clear();
+            break;
+        }
+    delete j;
+    c->jobs[job_id] = nullptr;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_philox_words(prdpt_ctx* c, uint64_t seed, uint32_t c0_base, uint32_t c1, uint32_t c2, uint32_t c3,
+                                int32_t n, uint32_t* words_dev, void* stream) {
+    if (!c || !words_dev || n < 0) return fail(PRDPT_E_INVALID_ARG, "bad argument");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    PRDPT_CUDA(launch_philox(seed, c0_base, c1, c2, c3, n, words_dev, static_cast<cudaStream_t>(stream)));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_counters_enable(prdpt_ctx* c, int32_t enable) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    if (enable) PRDPT_CUDA(cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long)));
+    c->counting = enable != 0;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_counters_read(prdpt_ctx* c, uint64_t* counts_host) {
+    if (!c || !counts_host) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    PRDPT_CUDA(cudaDeviceSynchronize());
+    PRDPT_CUDA(cudaMemcpy(counts_host, c->counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_kernel_timing_enable(prdpt_ctx* c, int32_t enable) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->timing = enable != 0;
+    for (auto& ev : c->ev_used) c->ev_free.push_back(ev);
+    c->ev_used.clear();
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_kernel_timing_read(prdpt_ctx* c, double* total_ms, int64_t* launches) {
+    if (!c || !total_ms || !launches) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    double tot = 0.0;
+    for (auto& ev : c->ev_used) {
+        PRDPT_CUDA(cudaEventSynchronize(ev.second));
+        float ms = 0.f;
+        PRDPT_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (int64_t)c->ev_used.size();
+    for (auto& ev : c->ev_used) c->ev_free.push_back(ev);
+    c->ev_used.clear();
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_sync(prdpt_ctx* c, void* stream) {
+    if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    PRDPT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return check_status(c);
+}
+
+}  // extern "C"

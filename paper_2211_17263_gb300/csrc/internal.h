@@ -1,0 +1,145 @@
+// internal.h -- device-side data layout shared by the kernels and the C ABI host code.
+//
+// Memory layout in HBM (all library-owned except where noted):
+//   BaseScene   one per uploaded scene: primitives in natural order, materials,
+//               parameter bindings and the host-computed camera basis (~3.6 KB).
+//   InstScene   one per render of a launch: the scene instantiated at theta +- tau
+//               (Eq. 10's P(theta - tau_i)), primitives grouped by type, derived
+//               constants precomputed (quad normals, reciprocal edge lengths, box
+//               corners, light areas) and the render's random-stream words. Each
+//               render CTA copies it into shared memory (~3.4 KB).
+//   partials    [R][tiles] FP32 tile sums of squared pixel errors.
+//   weights     [R][D] FP32 estimator weights d kappa / q of each render.
+//   per job     theta, Adam m and v, sigma0, gradient, losses, step counter, target.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace prdpt {
+
+constexpr int kMaxPrims = 32;
+constexpr int kMaxMats = 32;
+constexpr int kMaxLights = 8;
+constexpr int kMaxD = 64;
+constexpr int kMaxPairs = 256;
+constexpr int kMaxRenders = 2 * kMaxPairs;
+constexpr int kBlock = 256;      // render CTA size
+constexpr int kInstBlock = 64;   // instantiation CTA size (one thread per parameter)
+constexpr float kEps = 1e-4f;    // ray t_min and surface offset (scene units)
+
+constexpr unsigned kTagPerturb = 1u;
+constexpr unsigned kTagPath = 2u;
+constexpr unsigned kTagTarget = 3u;
+
+enum : int { kSphere = 0, kQuad = 1, kBox = 2 };
+enum : int { kDiffuse = 0, kMirror = 1, kDielectric = 2 };
+enum : int { kBindPos = 0, kBindRadius = 1, kBindAlbedo = 2, kBindEmission = 3 };
+enum : int { kRadial = 0, kPerDim = 1, kGauss = 2 };
+
+// Device status word bits.
+enum : int { kStatusBadItem = 1, kStatusBadScene = 2 };
+
+struct BaseScene {
+    int n_prims, n_mats, n_sph, n_quad, n_box, D;
+    int prim_type[kMaxPrims], prim_mat[kMaxPrims], prim_slot[kMaxPrims];
+    float prim_geom[kMaxPrims][9];
+    int mat_type[kMaxMats];
+    float mat_param[kMaxMats][8];
+    int bind_kind[kMaxD], bind_index[kMaxD], bind_comp[kMaxD];
+    float eye[3], fwd[3], right[3], up[3], tan_half;
+    float bg[3];
+};
+
+// Primitive records (4 x float4, grouped: spheres, quads, boxes):
+//   sphere: [0] centre, radius   [1] r^2, 1/r, mat (int bits), prim (int bits)
+//   quad:   [0] centre, mat      [1] unit normal, prim   [2] u, 1/(u.u)   [3] v, 1/(v.v)
+//   box:    [0] min corner, mat  [1] max corner, prim
+// Materials (2 x float4): [0] albedo, type (int bits)  [1] emission, ior.
+// Lights: int4 (kind, record slot, prim, mat) and the emitter's area.
+struct __align__(16) InstScene {
+    int n_sph, n_quad, n_box, n_lights;
+    unsigned seed_lo, seed_hi, step, c3;  // path stream: key and counter words 2, 3
+    float4 eye;    // xyz, tan(vfov/2)
+    float4 fwd;    // xyz, aspect W/H
+    float4 right;  // xyz, 0
+    float4 up;     // xyz, 0
+    float4 bg;     // background radiance, 0
+    int4 light[kMaxLights];
+    float light_area[kMaxLights];
+    float4 mat[kMaxMats][2];
+    float4 prim[kMaxPrims][4];
+};
+static_assert(sizeof(InstScene) % 16 == 0, "InstScene must be float4-copyable");
+
+// Per-job description of one instantiation launch (sampler + scene binding).
+struct InstJob {
+    const BaseScene* base;
+    InstScene* scenes;        // [R] out
+    const float* theta;       // grad mode: [D] centre; render mode: [R][D] parameter vectors
+    const float* sigma;       // grad mode: [D] bandwidth (sigma0 when annealing)
+    float* tau_out;           // [R][D] or null
+    float* w_out;             // [R][D] or null
+    const int* step_dev;      // resident job: device step counter (added to `step`), else null
+    unsigned long long seed;
+    unsigned step, tag;
+    int R, D, W, H, sampler, antithetic, crn, render_mode;
+    int anneal, total_steps;
+    float sigma_min, c_radial;  // c_radial = sqrt(2) Gamma((D+1)/2) / Gamma(D/2)
+    int block_begin;          // first CTA index of this job in a packed launch
+};
+
+// Per-job description of one render launch.
+struct TraceJob {
+    const InstScene* scenes;  // [R]
+    const float4* target;     // [H][W] (gradient mode) or null
+    float4* images;           // [R][H][W] (render mode) or null
+    float* partials;          // [R][tiles]
+    unsigned* done;           // tiles finished (reset to 0 by the CTA that finalises)
+    const float* w;           // [R][D]
+    float* grad_out;          // [D] or null
+    float* loss_out;          // [R] or null
+    float* theta;             // Adam state (null: no optimiser step)
+    float* m;
+    float* v;
+    int* step_dev;
+    float lr, b1, b2, eps;
+    int W, H, spp, depth, rr_start, R, D, antithetic, k, tiles_x, tiles;
+    int item_begin;           // first work item of this job in a packed launch
+};
+
+struct TraceLaunch {
+    TraceJob job0;            // used when jobs == null (single job, passed by value)
+    const TraceJob* jobs;     // packed launch: [njobs] in device memory
+    int njobs, total_items;
+    unsigned* queue;          // work-queue head, zeroed by the instantiation launch
+    unsigned long long* counters;  // [8] or null (null: the uncounted kernel variant runs)
+    int* status;
+};
+
+struct InstLaunch {
+    InstJob job0;
+    const InstJob* jobs;
+    int njobs, total_blocks;
+    unsigned* queue_reset;    // zeroed by CTA 0
+};
+
+// Launchers (kernels.cu). All enqueue on `stream` and return the launch error.
+cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream);
+cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream);
+cudaError_t launch_adam(int D, float* theta, float* m, float* v, const float* g, int t, float lr, float b1,
+                        float b2, float eps, cudaStream_t stream);
+cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, unsigned c2, unsigned c3, int n,
+                          uint32_t* out, cudaStream_t stream);
+// Resident CTAs per SM of the render kernel.
+int trace_blocks_per_sm(bool render_mode);
+
+// Tile shape of the render kernel for k threads per pixel: TW x TH pixels, TW*TH*k = kBlock.
+__host__ __device__ inline void tile_shape(int k, int* tw, int* th) {
+    int npix = kBlock / k;
+    *tw = (k <= 2) ? 16 : 8;
+    *th = npix / *tw;
+}
+
+}  // namespace prdpt

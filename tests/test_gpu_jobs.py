@@ -1,0 +1,81 @@
+"""GPU tests of resident jobs: prdpt_step (sampler + render + Eq. 10 gradient + Adam
+on the device) against the oracle's own FP64 trajectory, and packed multi-job
+steps (prdpt_step_batch) against each job run alone."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_helpers import GRAD_REL, grad_rel_error
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    from paper_2211_17263_gb300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _job(ctx, wl, target):
+    from paper_2211_17263_gb300 import api
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    return api.Job(scene, wl, target)
+
+
+def test_job_steps_follow_oracle_trajectory(ctx):
+    wl = workloads.config_small()
+    target = oracle.render_target(wl)
+    job = _job(ctx, wl, target)
+    th = wl.theta0.astype(np.float64)
+    m = np.zeros(wl.D)
+    v = np.zeros(wl.D)
+    for t in range(4):
+        job.step()
+        st = job.read()
+        ref = oracle.smoothed_grad(wl, theta=th.astype(np.float32), target=target, step=t)
+        assert st["steps"] == t + 1
+        assert grad_rel_error(st["grad"], ref["grad"], ref["weights"], ref["losses"]) <= GRAD_REL
+        assert np.allclose(st["losses"], ref["losses"], rtol=1e-4)
+        th, m, v = oracle.adam(th, m, v, ref["grad"], t + 1, wl.lr)
+        assert np.allclose(st["theta"], th, rtol=0, atol=2e-5 * (t + 1)), (st["theta"], th)
+    job.release()
+
+
+def test_packed_steps_equal_alone(ctx):
+    wls = [workloads.scaled(workloads.config_small(seed=1), width=48, height=40, spp=4, pairs=3),
+           workloads.scaled(workloads.config_occlusion(seed=2), width=64, height=64, spp=4, pairs=4),
+           workloads.scaled(workloads.config_gi_box(seed=3), width=40, height=32, spp=4, pairs=2)]
+    targets = [oracle.render_target(w) for w in wls]
+    alone = []
+    for w, t in zip(wls, targets):
+        j = _job(ctx, w, t)
+        for _ in range(3):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    from paper_2211_17263_gb300 import api
+    jobs = [_job(ctx, w, t) for w, t in zip(wls, targets)]
+    for _ in range(3):
+        api.step_batch(ctx, jobs)
+    for j, a in zip(jobs, alone):
+        b = j.read()
+        assert b["steps"] == 3
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(a[key], b[key]), key
+        j.release()
+
+
+def test_job_release_and_reuse_of_batch(ctx):
+    from paper_2211_17263_gb300 import api
+    wl = workloads.scaled(workloads.config_small(), width=16, height=16, spp=1, pairs=1)
+    target = oracle.render_target(wl)
+    a, b = _job(ctx, wl, target), _job(ctx, wl, target)
+    api.step_batch(ctx, [a, b])
+    a.release()
+    api.step_batch(ctx, [b])
+    assert b.read()["steps"] == 2
+    b.release()

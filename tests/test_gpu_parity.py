@@ -1,0 +1,162 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the
+same seeded inputs and the same Philox streams.
+
+* Philox words: bit-exact.
+* Perturbations tau and weights w (Sec. 3.2, Eq. 11): the oracle's FP64 values
+  rounded to FP32, within a few FP32 ulps (CUDA's logf / sqrtf / sincospif error
+  bounds are 1-2 ulp).
+* Images (Eq. 3): mean abs error <= 1e-4 and <= 0.1 % outlier pixels (> 1e-3).
+* Gradient (Eq. 10): relative error <= 1e-3; per-render losses to 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_helpers import GRAD_REL, assert_image_parity, grad_rel_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    from paper_2211_17263_gb300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+
+
+# ---------------------------------------------------------------- random streams
+@pytest.mark.parametrize("c1,c2,c3", [(0, 0, 0), (5 | (3 << 16) | (1 << 24), 17, (2 << 28) | 9),
+                                      (0xFFFF, 0xFFFFFFFF, 0xFFFFFFFF)])
+def test_philox_bit_exact(ctx, c1, c2, c3):
+    n = 1 << 18
+    for seed in (0, 0x0123456789ABCDEF):
+        gpu = ctx.philox_words(seed, 7, c1, c2, c3, n).cpu().numpy().view(np.uint32)
+        ref = oracle.philox_words(seed, c1, c2, c3, 7, n)
+        assert np.array_equal(gpu, ref)
+
+
+@pytest.mark.parametrize("sampler", [0, 1, 2])
+@pytest.mark.parametrize("D", [1, 2, 3, 9, 64])
+@pytest.mark.parametrize("antithetic", [1, 0])
+def test_perturbations_match_oracle(ctx, sampler, D, antithetic):
+    rng = np.random.default_rng(D)
+    sigma = rng.uniform(0.05, 0.5, size=D).astype(np.float32)
+    P, seed, step = 16, 1234, 7
+    tau, w = ctx.sample_perturbations(_t(sigma), P, sampler=sampler, antithetic=antithetic, seed=seed, step=step)
+    tau, w = tau.cpu().numpy(), w.cpu().numpy()
+    for r in range(2 * P):
+        idx = r // 2 if antithetic else r
+        _, tf, wd = oracle.sample(sampler, sigma, seed, step, idx)
+        sgn = -1.0 if (antithetic and r % 2) else 1.0
+        ref_tau, ref_w = sgn * tf.astype(np.float64), sgn * wd
+        scale = np.abs(ref_tau).max()
+        assert np.allclose(tau[r], ref_tau, rtol=4e-6, atol=4e-6 * scale), (r, tau[r], ref_tau)
+        assert np.allclose(w[r], ref_w, rtol=4e-6, atol=4e-6 * np.abs(ref_w).max()), (r, w[r], ref_w)
+        if sampler != 2:
+            assert np.array_equal(np.sign(tau[r]), np.sign(ref_tau))
+
+
+# ---------------------------------------------------------------- images
+CASES = {
+    "small": lambda: workloads.scaled(workloads.config_small(), width=64, height=64, spp=4),
+    "occlusion": lambda: workloads.scaled(workloads.config_occlusion(), width=72, height=52, spp=8),
+    "gi-box": lambda: workloads.scaled(workloads.config_gi_box(), width=56, height=40, spp=8),
+    "caustic": lambda: workloads.scaled(workloads.config_caustic(), width=48, height=40, spp=16),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("k", [1, 4])
+def test_render_matches_oracle(ctx, name, k):
+    wl = CASES[name]()
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    thetas = np.stack([wl.theta_ref, wl.theta0, wl.theta0 + 0.03]).astype(np.float32)
+    img = scene.render_batch(_t(thetas), wl.width, wl.height, wl.spp, wl.depth, wl.rr_start, seed=wl.seed, step=3,
+                             tag=2, crn=0, threads_per_pixel=k)
+    torch.cuda.synchronize()
+    img = img.cpu().numpy()
+    ref = oracle.render(wl.scene, wl.bindings, thetas, wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
+                        wl.seed, 3, 2, 0)
+    assert np.all(img[..., 3] == 0.0)
+    assert_image_parity(img[..., :3], ref, what=f"{name} k={k}")
+
+
+def test_render_edge_sizes(ctx):
+    wl = workloads.config_occlusion()
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    for (W, H, spp) in [(1, 1, 1), (7, 3, 2), (17, 33, 1), (33, 17, 3)]:
+        for k in (1, 2, 8):
+            img = scene.render_batch(_t(wl.theta_ref[None]), W, H, spp, wl.depth, wl.rr_start, seed=1, step=0,
+                                     tag=3, crn=1, threads_per_pixel=k).cpu().numpy()
+            ref = oracle.render(wl.scene, wl.bindings, wl.theta_ref[None], W, H, spp, wl.depth, wl.rr_start, 1, 0, 3,
+                                1)
+            diff = np.abs(img[..., :3] - ref)
+            assert diff.mean() <= 1e-4 and (diff.max(-1) > 1e-3).sum() <= max(1, int(1e-3 * W * H)), (W, H, k)
+
+
+# ---------------------------------------------------------------- gradient
+def _grad_case(ctx, wl, step=0, k=0):
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = oracle.render_target(wl)
+    opts = scene.grad_opts(wl, step=step, threads_per_pixel=k)
+    g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
+    torch.cuda.synchronize()
+    ref = oracle.smoothed_grad(wl, target=target, step=step)
+    return g.cpu().numpy(), L.cpu().numpy(), ref
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gradient_matches_oracle(ctx, name):
+    wl = CASES[name]()
+    wl.pairs = min(wl.pairs, 8)
+    g, L, ref = _grad_case(ctx, wl, step=2)
+    assert np.allclose(L, ref["losses"], rtol=1e-4, atol=1e-9), (L, ref["losses"])
+    err = grad_rel_error(g, ref["grad"], ref["weights"], ref["losses"])
+    assert err <= GRAD_REL, (name, err, g, ref["grad"])
+
+
+@pytest.mark.parametrize("sampler,antithetic,crn", [(1, 1, 1), (2, 1, 1), (0, 0, 1), (0, 1, 0)])
+def test_gradient_estimator_variants(ctx, sampler, antithetic, crn):
+    wl = CASES["small"]()
+    wl.sampler, wl.antithetic, wl.crn = sampler, antithetic, crn
+    g, L, ref = _grad_case(ctx, wl, step=1)
+    assert np.allclose(L, ref["losses"], rtol=1e-4, atol=1e-9)
+    assert grad_rel_error(g, ref["grad"], ref["weights"], ref["losses"]) <= GRAD_REL
+
+
+def test_gradient_full_size_small_config(ctx):
+    wl = workloads.config_small()
+    for k in (1, 2, 8):
+        g, L, ref = _grad_case(ctx, wl, step=0, k=k)
+        assert grad_rel_error(g, ref["grad"], ref["weights"], ref["losses"]) <= GRAD_REL, k
+
+
+def test_invisible_parameter_exact_zero_on_gpu(ctx):
+    wl = workloads.scaled(workloads.config_small(), width=32, height=32, spp=2, pairs=4)
+    sc = wl.scene
+    sc.prim_geom = np.vstack([sc.prim_geom, [[50.0, 50.0, 50.0, 0.05, 0, 0, 0, 0, 0]]]).astype(np.float32)
+    sc.prim_type = np.append(sc.prim_type, 0).astype(np.int32)
+    sc.prim_mat = np.append(sc.prim_mat, 0).astype(np.int32)
+    wl.bindings = np.array([[workloads.BIND_PRIM_POS, sc.n_prims - 1, 0]], np.int32)
+    wl.theta0 = wl.theta_ref = np.array([50.0], np.float32)
+    wl.sigma = np.array([0.1], np.float32)
+    g, L, _ = _grad_case(ctx, wl)
+    assert g[0] == 0.0 and np.array_equal(L[0::2], L[1::2])
+
+
+def test_deterministic_across_launch_shapes(ctx):
+    wl = CASES["occlusion"]()
+    wl.pairs = 4
+    g1, L1, _ = _grad_case(ctx, wl, k=1)
+    g1b, L1b, _ = _grad_case(ctx, wl, k=1)
+    assert np.array_equal(g1, g1b) and np.array_equal(L1, L1b)  # bitwise reproducible
+    g4, L4, ref = _grad_case(ctx, wl, k=4)
+    assert np.allclose(L4, L1, rtol=1e-6)
