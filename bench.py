@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-pixels", type=int, default=0, help="pixels per warp work item (8, 16, 32; 0 = auto)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -226,7 +227,7 @@ def main():
     target = scene.render_batch(dev(wl.theta_ref[None]), wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
                                 seed=wl.seed, step=0, tag=3, crn=1)[0]
     target_host = target.cpu().numpy()
-    job = api.Job(scene, wl, target_host)
+    job = api.Job(scene, wl, target_host, block_pixels=args.block_pixels)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         job.step(stream)

@@ -104,7 +104,8 @@ typedef struct {
     uint64_t seed;
     uint32_t step, tag;        /* Philox counter word 2 and stream tag (2 = path, 3 = target) */
     int32_t crn;               /* 1: every render uses path field 0; 0: render i uses field i */
-    int32_t threads_per_pixel; /* launch shape (1, 2, 4 or 8); 0 = automatic */
+    int32_t block_pixels;      /* pixels per warp work item (8, 16 or 32); 0 = automatic */
+    int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
 } prdpt_render_opts;
 
 /* Gradient-estimator options (Eq. 10, Algorithm 1). R = 2 * pairs renders. */
@@ -116,7 +117,8 @@ typedef struct {
     int32_t crn;               /* 1: all renders share path samples (field 0); 0: render r uses field r+1 */
     uint64_t seed;
     uint32_t step;             /* optimiser step: Philox counter word 2 of every draw */
-    int32_t threads_per_pixel; /* launch shape (1, 2, 4 or 8); 0 = automatic */
+    int32_t block_pixels;      /* pixels per warp work item (8, 16 or 32); 0 = automatic */
+    int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
 } prdpt_grad_opts;
 
 /* A resident optimisation job: scene parameters, Adam state and target stay on

@@ -464,8 +464,8 @@ static void onb(v3 n, v3* t1, v3* t2) {
 }
 
 /* Uniforms for (pixel, sample, vertex, slot) of one render's path stream.
- * slot 0: BSDF u1, u2, dielectric choice, Russian roulette
- * slot 1: light-point u1, u2, light choice, unused
+ * slot 0: light-point u1, u2, BSDF u1, u2
+ * slot 1: light choice, Russian roulette, dielectric choice, unused
  * slot 2: pixel jitter x, y (vertex 0 only) */
 static void path_uniforms(const orc_trace_opts* o, uint32_t pixel, int s, int b, int slot, double u[4]) {
     uint32_t c1 = (uint32_t)s | ((uint32_t)b << 16) | ((uint32_t)slot << 24);
@@ -492,6 +492,7 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
 
     v3 L = V(0, 0, 0), beta = V(1, 1, 1);
     int specular = 1; /* emission is counted on camera rays and after specular bounces */
+    double u1[4];     /* slot 1 of the current vertex */
     for (int b = 0; b < o->depth; ++b) {
         double t;
         v3 ng;
@@ -505,13 +506,14 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
         v3 p = add(org, mul(dir, t));
         if (specular && is_emissive(m) && dot(dir, ng) < 0.0) L = add(L, hmul(beta, m->emission));
         int last = (b + 1 >= o->depth);
+        path_uniforms(o, pixel, s, b, 0, u);
+        path_uniforms(o, pixel, s, b, 1, u1);
 
         if (m->type == M_DIFFUSE) {
             v3 ns = dot(ng, dir) < 0.0 ? ng : mul(ng, -1.0);
             v3 po = add(p, mul(ns, ORC_EPS));
             if (sc->n_lights > 0) { /* next-event estimation: one light, uniform area sample */
-                path_uniforms(o, pixel, s, b, 1, u);
-                int li = (int)floor(u[2] * sc->n_lights);
+                int li = (int)floor(u1[0] * sc->n_lights);
                 if (li > sc->n_lights - 1) li = sc->n_lights - 1;
                 const orc_prim* lp = &sc->prim[sc->light[li]];
                 v3 y, ny;
@@ -541,18 +543,16 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
                 }
             }
             if (last) break;
-            path_uniforms(o, pixel, s, b, 0, u);
-            double rad = sqrt(u[0]), phi = 2.0 * M_PI * u[1];
+            double rad = sqrt(u[2]), phi = 2.0 * M_PI * u[3];
             v3 t1, t2;
             onb(ns, &t1, &t2);
-            v3 wo = add(add(mul(t1, rad * cos(phi)), mul(t2, rad * sin(phi))), mul(ns, sqrt(fmax(0.0, 1.0 - u[0]))));
+            v3 wo = add(add(mul(t1, rad * cos(phi)), mul(t2, rad * sin(phi))), mul(ns, sqrt(fmax(0.0, 1.0 - u[2]))));
             beta = hmul(beta, m->albedo);
             org = po;
             dir = normalize(wo);
             specular = 0;
         } else if (m->type == M_MIRROR) {
             if (last) break;
-            path_uniforms(o, pixel, s, b, 0, u);
             v3 ns = dot(ng, dir) < 0.0 ? ng : mul(ng, -1.0);
             dir = normalize(sub(dir, mul(ns, 2.0 * dot(dir, ns))));
             org = add(p, mul(ns, ORC_EPS));
@@ -560,7 +560,6 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
             specular = 1;
         } else { /* smooth dielectric: exact unpolarised Fresnel, reflect or refract */
             if (last) break;
-            path_uniforms(o, pixel, s, b, 0, u);
             double ci = -dot(dir, ng);
             double eta;
             v3 n;
@@ -576,7 +575,7 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
                 double rp = (ci - eta * ct) / (ci + eta * ct);
                 F = 0.5 * (rs * rs + rp * rp);
             }
-            if (u[2] < F) {
+            if (u1[2] < F) {
                 dir = normalize(add(dir, mul(n, 2.0 * ci)));
                 org = add(p, mul(n, ORC_EPS));
             } else {
@@ -587,9 +586,9 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
             specular = 1;
         }
         if (maxc(beta) <= 0.0) break; /* nothing more can be added */
-        if (o->rr_start >= 0 && b >= o->rr_start) { /* Russian roulette (slot 0, fourth uniform) */
+        if (o->rr_start >= 0 && b >= o->rr_start) { /* Russian roulette (slot 1, second uniform) */
             double q = fmin(0.95, maxc(beta));
-            if (u[3] >= q) break;
+            if (u1[1] >= q) break;
             beta = mul(beta, 1.0 / q);
         }
     }

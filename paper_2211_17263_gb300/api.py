@@ -80,7 +80,7 @@ class Context:
         tau = torch.empty((R, D), dtype=torch.float32, device=sigma.device)
         w = torch.empty((R, D), dtype=torch.float32, device=sigma.device)
         o = capi.prdpt_grad_opts(pairs=pairs, width=1, height=1, spp=1, depth=1, rr_start=-1, sampler=sampler,
-                                 antithetic=antithetic, crn=1, seed=seed, step=step, threads_per_pixel=0)
+                                 antithetic=antithetic, crn=1, seed=seed, step=step, block_pixels=0)
         capi.prdpt_sample_perturbations(self.handle, D, _dev_ptr(sigma), o, _dev_ptr(tau), _dev_ptr(w),
                                         _stream_ptr(stream))
         return tau, w
@@ -106,22 +106,24 @@ class Scene:
         self.id = capi.prdpt_scene_upload(ctx.handle, desc, binds, self.D)
 
     def render_batch(self, thetas: torch.Tensor, width, height, spp, depth, rr_start=-1, seed=0, step=0, tag=2,
-                     crn=1, threads_per_pixel=0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                     crn=1, block_pixels=0, ctas_per_sm=0, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
         thetas = thetas.reshape(-1, self.D)
         n = thetas.shape[0]
         if out is None:
             out = torch.empty((n, height, width, 4), dtype=torch.float32, device=thetas.device)
         o = capi.prdpt_render_opts(width=width, height=height, spp=spp, depth=depth, rr_start=rr_start, seed=seed,
-                                   step=step, tag=tag, crn=crn, threads_per_pixel=threads_per_pixel)
+                                   step=step, tag=tag, crn=crn, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm)
         capi.prdpt_render_batch(self.ctx.handle, self.id, _dev_ptr(thetas), n, o, _dev_ptr(out), _stream_ptr(stream))
         return out
 
-    def grad_opts(self, wl, step=0, pairs=None, sampler=None, antithetic=None, crn=None, threads_per_pixel=0):
+    def grad_opts(self, wl, step=0, pairs=None, sampler=None, antithetic=None, crn=None, block_pixels=0,
+                  ctas_per_sm=0):
         return capi.prdpt_grad_opts(
             pairs=wl.pairs if pairs is None else pairs, width=wl.width, height=wl.height, spp=wl.spp,
             depth=wl.depth, rr_start=wl.rr_start, sampler=wl.sampler if sampler is None else sampler,
             antithetic=wl.antithetic if antithetic is None else antithetic, crn=wl.crn if crn is None else crn,
-            seed=wl.seed, step=step, threads_per_pixel=threads_per_pixel)
+            seed=wl.seed, step=step, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm)
 
     def smoothed_grad(self, theta: torch.Tensor, sigma: torch.Tensor, target: torch.Tensor, opts,
                       grad: torch.Tensor | None = None, losses: torch.Tensor | None = None, stream=None):
@@ -137,8 +139,8 @@ class Scene:
 class Job:
     """A resident optimisation job: parameters, Adam state and target live on the device."""
 
-    def __init__(self, scene: Scene, wl, target_host: np.ndarray, step0=0, threads_per_pixel=0, anneal=None,
-                 lr=None, sampler=None):
+    def __init__(self, scene: Scene, wl, target_host: np.ndarray, step0=0, block_pixels=0, ctas_per_sm=0,
+                 anneal=None, lr=None, sampler=None):
         self.scene = scene
         self.D = scene.D
         self.R = 2 * wl.pairs
@@ -148,7 +150,8 @@ class Job:
         if self._target.shape != (wl.height, wl.width, 4):
             raise ValueError("target must be [H, W, 4] float32")
         desc = capi.prdpt_job_desc(
-            grad=scene.grad_opts(wl, step=step0, sampler=sampler, threads_per_pixel=threads_per_pixel),
+            grad=scene.grad_opts(wl, step=step0, sampler=sampler, block_pixels=block_pixels,
+                                 ctas_per_sm=ctas_per_sm),
             theta0_host=_np_ptr(self._theta0), sigma0_host=_np_ptr(self._sigma0), target_host=_np_ptr(self._target),
             lr=wl.lr if lr is None else lr, beta1=0.9, beta2=0.999, eps=1e-8, sigma_min=wl.sigma_min,
             anneal=wl.anneal if anneal is None else anneal, total_steps=wl.steps)

@@ -52,7 +52,7 @@ class prdpt_render_opts(C.Structure):
     _fields_ = [
         ("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32), ("depth", C.c_int32),
         ("rr_start", C.c_int32), ("seed", C.c_uint64), ("step", C.c_uint32), ("tag", C.c_uint32),
-        ("crn", C.c_int32), ("threads_per_pixel", C.c_int32),
+        ("crn", C.c_int32), ("block_pixels", C.c_int32), ("ctas_per_sm", C.c_int32),
     ]
 
 
@@ -60,7 +60,8 @@ class prdpt_grad_opts(C.Structure):
     _fields_ = [
         ("pairs", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
         ("depth", C.c_int32), ("rr_start", C.c_int32), ("sampler", C.c_int32), ("antithetic", C.c_int32),
-        ("crn", C.c_int32), ("seed", C.c_uint64), ("step", C.c_uint32), ("threads_per_pixel", C.c_int32),
+        ("crn", C.c_int32), ("seed", C.c_uint64), ("step", C.c_uint32), ("block_pixels", C.c_int32),
+        ("ctas_per_sm", C.c_int32),
     ]
 
 

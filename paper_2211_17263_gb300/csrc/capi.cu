@@ -41,11 +41,13 @@ struct Scene {
 
 struct Job {
     int scene = -1;
-    int D = 0, R = 0, tiles = 0;
+    int D = 0, R = 0, tiles = 0, ctas_per_sm = 0;
     size_t bytes = 0;
     // device buffers
     float *theta = nullptr, *m = nullptr, *v = nullptr, *sigma0 = nullptr, *grad = nullptr, *losses = nullptr;
-    float *w = nullptr, *partials = nullptr;
+    float* w = nullptr;
+    double *partials = nullptr, *losses_d = nullptr;
+    unsigned* rdone = nullptr;
     int* step = nullptr;
     unsigned *done = nullptr, *queue = nullptr;
     InstScene* scenes = nullptr;
@@ -73,9 +75,13 @@ struct prdpt_ctx {
     size_t s_scenes_n = 0;
     float* s_w = nullptr;
     size_t s_w_n = 0;
-    float* s_partials = nullptr;
+    double* s_partials = nullptr;
     size_t s_partials_n = 0;
-    unsigned* s_ctl = nullptr;  // [0] queue, [1] done counter, [2] batch queue
+    double* s_losses = nullptr;
+    size_t s_losses_n = 0;
+    unsigned* s_rdone = nullptr;  // per-render block counters (all zero between launches)
+    size_t s_rdone_n = 0;
+    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2] batch queue
     // packed launches
     std::vector<int> batch_ids;
     InstJob* d_inst = nullptr;
@@ -146,29 +152,45 @@ Job* get_job(prdpt_ctx* c, int id) {
     return c->jobs[id];
 }
 
-int choose_k(prdpt_ctx* c, int requested, int R, int W, int H, int spp, bool render) {
-    if (requested == 1 || requested == 2 || requested == 4 || requested == 8) return requested;
-    const long long capacity = (long long)c->sms * (render ? c->occ_render : c->occ_grad) * kBlock;
-    const long long work = (long long)R * W * H;
-    int k = 1;
-    while (k < 8 && 2 * k <= spp && work * k < 2 * capacity) k *= 2;
-    return k;
+// Pixels per warp work item: the largest of 32, 16, 8 that still gives every
+// resident warp at least two items (small jobs use small blocks to fill the GPU).
+int choose_block(prdpt_ctx* c, int requested, int R, int W, int H, bool render) {
+    if (requested == 8 || requested == 16 || requested == 32) return requested;
+    const long long warps = (long long)c->sms * (render ? c->occ_render : c->occ_grad) * (kBlock / 32);
+    for (int px : {32, 16}) {
+        int bw, bh;
+        block_shape(px, &bw, &bh);
+        const long long items = (long long)R * ((W + bw - 1) / bw) * ((H + bh - 1) / bh);
+        if (items >= 2 * warps) return px;
+    }
+    return 8;
 }
 
-void tiles_for(int k, int W, int H, int* tiles_x, int* tiles) {
-    int tw, th;
-    tile_shape(k, &tw, &th);
-    *tiles_x = (W + tw - 1) / tw;
-    *tiles = *tiles_x * ((H + th - 1) / th);
+void tiles_for(int pixels, int W, int H, int* bw, int* bh, int* tiles_x, int* tiles) {
+    block_shape(pixels, bw, bh);
+    *tiles_x = (W + *bw - 1) / *bw;
+    *tiles = *tiles_x * ((H + *bh - 1) / *bh);
 }
 
-int grid_for(prdpt_ctx* c, int items, bool render) {
-    const int cap = c->sms * (render ? c->occ_render : c->occ_grad);
-    return items < cap ? items : cap;
+// Zero-initialised device array that grows on demand (kernels leave it zeroed).
+template <typename T>
+prdpt_status grow_zeroed(prdpt_ctx* c, T** p, size_t* cap, size_t n) {
+    if (*cap >= n) return PRDPT_OK;
+    if (prdpt_status st = grow(c, p, cap, n)) return st;
+    if (cudaMemset(*p, 0, n * sizeof(T)) != cudaSuccess) return fail(PRDPT_E_CUDA, "cudaMemset failed");
+    return PRDPT_OK;
+}
+
+int grid_for(prdpt_ctx* c, int items, bool render, int ctas_per_sm) {
+    const int occ = render ? c->occ_render : c->occ_grad;
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+    const int cap = c->sms * per_sm;
+    const int need = (items + kBlock / 32 - 1) / (kBlock / 32);
+    return need < cap ? need : cap;
 }
 
 // Launch the render kernel, bracketed by events on its stream when timing is on.
-cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStream_t stream) {
+cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStream_t stream, int ctas_per_sm) {
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (c->timing) {
         if (!c->ev_free.empty()) {
@@ -182,7 +204,7 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStr
         cudaError_t e = cudaEventRecord(ev.first, stream);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_trace(L, render, grid_for(c, L.total_items, render), stream);
+    cudaError_t e = launch_trace(L, render, grid_for(c, L.total_items, render, ctas_per_sm), stream);
     if (e != cudaSuccess) return e;
     if (c->timing) {
         e = cudaEventRecord(ev.second, stream);
@@ -409,7 +431,7 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     IL.total_blocks = n;
     IL.queue_reset = c->s_ctl + 0;
     PRDPT_CUDA(launch_instantiate(IL, st_));
-    const int k = choose_k(c, o->threads_per_pixel, n, o->width, o->height, o->spp, true);
+    const int px = choose_block(c, o->block_pixels, n, o->width, o->height, true);
     TraceLaunch TL{};
     TraceJob& J = TL.job0;
     J.scenes = c->s_scenes;
@@ -421,13 +443,14 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     J.rr_start = o->rr_start;
     J.R = n;
     J.D = s->D;
-    J.k = k;
-    tiles_for(k, o->width, o->height, &J.tiles_x, &J.tiles);
+    J.n_prims = s->host.n_prims;
+    J.n_mats = s->host.n_mats;
+    tiles_for(px, o->width, o->height, &J.bw, &J.bh, &J.tiles_x, &J.tiles);
     TL.total_items = n * J.tiles;
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, true, st_));
+    PRDPT_CUDA(timed_trace(c, TL, true, st_, o->ctas_per_sm));
     return PRDPT_OK;
 }
 
@@ -490,13 +513,15 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     if (prdpt_status st = check_grad_opts(o)) return st;
     PRDPT_CUDA(cudaSetDevice(c->device));
     const int R = 2 * o->pairs, D = s->D;
-    const int k = choose_k(c, o->threads_per_pixel, R, o->width, o->height, o->spp, false);
-    int tiles_x, tiles;
-    tiles_for(k, o->width, o->height, &tiles_x, &tiles);
+    const int px = choose_block(c, o->block_pixels, R, o->width, o->height, false);
+    int bw, bh, tiles_x, tiles;
+    tiles_for(px, o->width, o->height, &bw, &bh, &tiles_x, &tiles);
     if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)R)) return st;
     if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)R * D > (size_t)kMaxD ? (size_t)R * D : (size_t)kMaxD))
         return st;
     if (prdpt_status st = grow(c, &c->s_partials, &c->s_partials_n, (size_t)R * tiles)) return st;
+    if (prdpt_status st = grow(c, &c->s_losses, &c->s_losses_n, (size_t)R)) return st;
+    if (prdpt_status st = grow_zeroed(c, &c->s_rdone, &c->s_rdone_n, (size_t)kMaxRenders)) return st;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     InstLaunch IL{};
     fill_inst_grad(IL.job0, s, o);
@@ -512,7 +537,9 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     J.scenes = c->s_scenes;
     J.target = reinterpret_cast<const float4*>(target_dev);
     J.partials = c->s_partials;
+    J.render_done = c->s_rdone;
     J.done = c->s_ctl + 1;
+    J.losses = c->s_losses;
     J.w = c->s_w;
     J.grad_out = grad_dev;
     J.loss_out = losses_dev;
@@ -524,14 +551,17 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     J.R = R;
     J.D = D;
     J.antithetic = o->antithetic ? 1 : 0;
-    J.k = k;
+    J.bw = bw;
+    J.bh = bh;
     J.tiles_x = tiles_x;
     J.tiles = tiles;
+    J.n_prims = s->host.n_prims;
+    J.n_mats = s->host.n_mats;
     TL.total_items = R * tiles;
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, false, st_));
+    PRDPT_CUDA(timed_trace(c, TL, false, st_, o->ctas_per_sm));
     return PRDPT_OK;
 }
 
@@ -560,15 +590,17 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     j->D = s->D;
     j->R = 2 * o->pairs;
     const int D = j->D, R = j->R, W = o->width, H = o->height;
-    const int k = choose_k(c, o->threads_per_pixel, R, W, H, o->spp, false);
-    int tiles_x, tiles;
-    tiles_for(k, W, H, &tiles_x, &tiles);
+    const int px = choose_block(c, o->block_pixels, R, W, H, false);
+    int bw, bh, tiles_x, tiles;
+    tiles_for(px, W, H, &bw, &bh, &tiles_x, &tiles);
     j->tiles = tiles;
-    // one device block per job: small state first, then w, partials, scenes, target
-    const size_t small = 6 * sizeof(float) * kMaxD + sizeof(float) * kMaxRenders + 64;
+    j->ctas_per_sm = o->ctas_per_sm;
+    // one device block per job: small state first (zeroed), then w, partials, scenes, target
+    const size_t small = 6 * sizeof(float) * kMaxD + sizeof(float) * kMaxRenders + sizeof(double) * kMaxRenders +
+                         sizeof(unsigned) * kMaxRenders + 64;
     const size_t off_w = (small + 255) & ~size_t(255);
     const size_t off_p = (off_w + sizeof(float) * R * D + 255) & ~size_t(255);
-    const size_t off_s = (off_p + sizeof(float) * R * tiles + 255) & ~size_t(255);
+    const size_t off_s = (off_p + sizeof(double) * R * tiles + 255) & ~size_t(255);
     const size_t off_t = (off_s + sizeof(InstScene) * R + 255) & ~size_t(255);
     const size_t total = off_t + sizeof(float4) * (size_t)W * H;
     void* base = nullptr;
@@ -584,11 +616,13 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     j->sigma0 = j->v + kMaxD;
     j->grad = j->sigma0 + kMaxD;
     j->losses = j->grad + kMaxD;
-    j->step = reinterpret_cast<int*>(j->losses + kMaxRenders);
+    j->losses_d = reinterpret_cast<double*>(j->losses + kMaxRenders);
+    j->rdone = reinterpret_cast<unsigned*>(j->losses_d + kMaxRenders);
+    j->step = reinterpret_cast<int*>(j->rdone + kMaxRenders);
     j->done = reinterpret_cast<unsigned*>(j->step + 1);
     j->queue = j->done + 1;
     j->w = reinterpret_cast<float*>(b + off_w);
-    j->partials = reinterpret_cast<float*>(b + off_p);
+    j->partials = reinterpret_cast<double*>(b + off_p);
     j->scenes = reinterpret_cast<InstScene*>(b + off_s);
     j->target = reinterpret_cast<float4*>(b + off_t);
     cudaError_t e = cudaMemset(base, 0, off_w);
@@ -615,7 +649,9 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     T.scenes = j->scenes;
     T.target = j->target;
     T.partials = j->partials;
+    T.render_done = j->rdone;
     T.done = j->done;
+    T.losses = j->losses_d;
     T.w = j->w;
     T.grad_out = j->grad;
     T.loss_out = j->losses;
@@ -635,9 +671,12 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     T.R = R;
     T.D = D;
     T.antithetic = o->antithetic ? 1 : 0;
-    T.k = k;
+    T.bw = bw;
+    T.bh = bh;
     T.tiles_x = tiles_x;
     T.tiles = tiles;
+    T.n_prims = s->host.n_prims;
+    T.n_mats = s->host.n_mats;
     s->jobs++;
     c->jobs.push_back(j);
     *job_out = (int)c->jobs.size() - 1;
@@ -660,7 +699,7 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     TL.queue = j->queue;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, false, st_));
+    PRDPT_CUDA(timed_trace(c, TL, false, st_, j->ctas_per_sm));
     return PRDPT_OK;
 }
 
@@ -718,7 +757,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     TL.queue = c->s_ctl + 2;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, false, st_));
+    PRDPT_CUDA(timed_trace(c, TL, false, st_, 0));
     return PRDPT_OK;
 }
 

@@ -8,7 +8,7 @@
 //               constants precomputed (quad normals, reciprocal edge lengths, box
 //               corners, light areas) and the render's random-stream words. Each
 //               render CTA copies it into shared memory (~3.4 KB).
-//   partials    [R][tiles] FP32 tile sums of squared pixel errors.
+//   partials    [R][blocks] FP64 sums of squared pixel errors, one per warp work item.
 //   weights     [R][D] FP32 estimator weights d kappa / q of each render.
 //   per job     theta, Adam m and v, sigma0, gradient, losses, step counter, target.
 #pragma once
@@ -90,13 +90,16 @@ struct InstJob {
     int block_begin;          // first CTA index of this job in a packed launch
 };
 
-// Per-job description of one render launch.
+// Per-job description of one render launch. The image is cut into blocks of
+// bw x bh <= 32 pixels; one warp renders one (render, block) work item.
 struct TraceJob {
     const InstScene* scenes;  // [R]
     const float4* target;     // [H][W] (gradient mode) or null
     float4* images;           // [R][H][W] (render mode) or null
-    float* partials;          // [R][tiles]
-    unsigned* done;           // tiles finished (reset to 0 by the CTA that finalises)
+    double* partials;         // [R][tiles] sums of squared pixel errors per block
+    unsigned* render_done;    // [R] blocks finished per render (reset by the warp that completes the render)
+    unsigned* done;           // renders finished (reset by the warp that completes the job)
+    double* losses;           // [R] L_r
     const float* w;           // [R][D]
     float* grad_out;          // [D] or null
     float* loss_out;          // [R] or null
@@ -105,7 +108,9 @@ struct TraceJob {
     float* v;
     int* step_dev;
     float lr, b1, b2, eps;
-    int W, H, spp, depth, rr_start, R, D, antithetic, k, tiles_x, tiles;
+    int W, H, spp, depth, rr_start, R, D, antithetic;
+    int bw, bh, tiles_x, tiles;
+    int n_prims, n_mats;      // used primitive and material records (staging size)
     int item_begin;           // first work item of this job in a packed launch
 };
 
@@ -135,11 +140,10 @@ cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, uns
 // Resident CTAs per SM of the render kernel.
 int trace_blocks_per_sm(bool render_mode);
 
-// Tile shape of the render kernel for k threads per pixel: TW x TH pixels, TW*TH*k = kBlock.
-__host__ __device__ inline void tile_shape(int k, int* tw, int* th) {
-    int npix = kBlock / k;
-    *tw = (k <= 2) ? 16 : 8;
-    *th = npix / *tw;
+// Pixel block of one warp work item for 8, 16 or 32 pixels.
+inline void block_shape(int pixels, int* bw, int* bh) {
+    *bw = (pixels >= 16) ? 8 : 4;
+    *bh = pixels / *bw;
 }
 
 }  // namespace prdpt

@@ -3,18 +3,26 @@
 //   k_instantiate   one CTA per render: Philox draws -> perturbation tau and weight
 //                   w (Sec. 3.2, Eq. 11, Algorithm 1), theta +- tau bound into the
 //                   scene (Eq. 10's P(theta - tau_i)), derived constants precomputed.
-//   k_trace         persistent render kernel: CTAs pull (render, tile) items from a
-//                   work queue, stage the render's scene in shared memory, path-trace
-//                   every pixel of the tile (Eq. 1 / Eq. 3), and reduce the squared
-//                   pixel errors against the target to one tile partial (the image
-//                   never reaches HBM). The CTA that completes a job's last tile
-//                   forms L_r, the gradient of Eq. 10 and the Adam step.
+//   k_trace         persistent render kernel. Each warp pulls (render, pixel block)
+//                   work items from a queue, stages the render's scene in its own
+//                   shared-memory slot, and traces the block's pixels x samples as a
+//                   pool of path tasks: a lane whose path ends takes the next task
+//                   at once (ballot + popc), so live paths stay packed in the warp.
+//                   Radiance is accumulated per pixel in 2^-32 fixed point (integer
+//                   adds are order-independent, so results do not depend on which
+//                   lane traced which path). The pixel means, the squared error
+//                   against the target and the block's partial sum are formed in
+//                   FP64 in registers -- the perturbed image never reaches HBM.
+//                   The warp that completes a render's last block reduces L_r; the
+//                   warp that completes the job's last render forms the gradient of
+//                   Eq. 10 and applies Adam. No CTA-wide barriers, no spin waits.
 //   k_adam          standalone Adam update.
 //   k_philox        raw Philox words (for bit-exact checks of the random streams).
 //
-// FP32 throughout the tracer; loss partials are FP32 per tile and summed in FP64
-// in a fixed order, so every result is deterministic and independent of which CTA
-// processed which tile.
+// FP32 throughout the path tracer; every reduction is in a fixed order, so results
+// are deterministic and independent of the launch shape and of other jobs sharing
+// the launch.
+#include <cstddef>
 #include <cstdint>
 
 #include "internal.h"
@@ -36,6 +44,10 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 }
 __device__ __forceinline__ float3 normalized(float3 a) { return a * rsqrtf(dot3(a, a)); }
 __device__ __forceinline__ float maxc(float3 a) { return fmaxf(a.x, fmaxf(a.y, a.z)); }
+// Approximate reciprocal (MUFU.RCP, 1 ulp); +-0 gives +-inf as the slab test needs.
+__device__ __forceinline__ float3 rcp3(float3 d) {
+    return f3(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y), __fdividef(1.0f, d.z));
+}
 __device__ __forceinline__ int as_int(float f) { return __float_as_int(f); }
 
 // ---------------------------------------------------------------------------
@@ -98,7 +110,6 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     __shared__ float s_u[4 * 32];
     __shared__ float s_red[kInstBlock];
     __shared__ float s_theta[kMaxD];
-    __shared__ float s_w[kMaxD];
     __shared__ float s_scalar[2];
     __shared__ int s_job;
 
@@ -124,10 +135,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
 
     // ---- a1: perturbation and weight of render r --------------------------------
     if (J.render_mode) {
-        if (tid < D) {
-            s_theta[tid] = J.theta[r * D + tid];
-            s_w[tid] = 0.0f;
-        }
+        if (tid < D) s_theta[tid] = J.theta[r * D + tid];
     } else {
         const bool anti = J.antithetic && (r & 1);
         const unsigned index = J.antithetic ? unsigned(r >> 1) : unsigned(r);
@@ -201,7 +209,6 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
                 w = -w;
             }
             s_theta[tid] = J.theta[tid] + tau;  // FP32 sum: the parameters this render gets
-            s_w[tid] = w;
             if (J.tau_out) J.tau_out[r * D + tid] = tau;
             if (J.w_out) J.w_out[r * D + tid] = w;
         }
@@ -310,8 +317,8 @@ __device__ __forceinline__ float sphere_t(const InstScene& S, int i, float3 o, f
     const float b = dot3(oc, d);
     const float3 l = oc - d * b;  // centre offset from the ray line: better conditioned than b^2 - c
     const float disc = r2 - dot3(l, l);
-    if (disc < 0.0f) return INFINITY;
-    const float sq = sqrtf(disc);
+    if (!(disc > 0.0f)) return INFINITY;  // tangent rays (disc == 0) count as misses
+    const float sq = disc * rsqrtf(disc);
     float t = -b - sq;
     if (t <= kEps) t = -b + sq;
     return (t > kEps) ? t : INFINITY;
@@ -323,7 +330,7 @@ __device__ __forceinline__ float quad_t(const InstScene& S, int i, float3 o, flo
     const float den = dot3(n, d);
     if (fabsf(den) < 1e-12f) return INFINITY;
     const float3 co = xyz(a) - o;
-    const float t = dot3(n, co) / den;
+    const float t = __fdividef(dot3(n, co), den);
     if (!(t > kEps)) return INFINITY;
     const float3 q = d * t - co;  // hit point relative to the centre
     const float pa = dot3(q, xyz(uu)) * uu.w, pb = dot3(q, xyz(vv)) * vv.w;
@@ -393,7 +400,7 @@ __device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 
         if (t < h.t) { h.t = t; h.slot = i; h.type = kQuad; }
     }
     if (nb) {
-        const float3 inv = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+        const float3 inv = rcp3(d);
         for (int i = ns + nq; i < ns + nq + nb; ++i) {
             const float t = box_t(S, i, o, inv);
             if (t < h.t) { h.t = t; h.slot = i; h.type = kBox; }
@@ -418,7 +425,7 @@ __device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d,
         if (quad_t(S, i, o, d) < dist) return true;
     }
     if (nb) {
-        const float3 inv = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+        const float3 inv = rcp3(d);
         for (int i = ns + nq; i < ns + nq + nb; ++i) {
             if (i == skip) continue;
             if (kCount) ++cnt.box;
@@ -428,210 +435,238 @@ __device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d,
     return false;
 }
 
-__device__ __forceinline__ float4 path_uniforms(const InstScene& S, unsigned pixel, int s, int b, int slot,
-                                                uint4* words = nullptr) {
+__device__ __forceinline__ uint4 path_words(const InstScene& S, unsigned pixel, int s, int b, int slot) {
     const unsigned c1 = unsigned(s) | (unsigned(b) << 16) | (unsigned(slot) << 24);
-    const uint4 w = philox(make_uint4(pixel, c1, S.step, S.c3), S.seed_lo, S.seed_hi);
-    if (words) *words = w;
-    return make_float4(u01(w.x), u01(w.y), u01(w.z), u01(w.w));
+    return philox(make_uint4(pixel, c1, S.step, S.c3), S.seed_lo, S.seed_hi);
 }
 
 // Orthonormal basis around unit n (Duff et al. 2017).
 __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
     const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
-    const float a = -1.0f / (sg + n.z);
+    const float a = __fdividef(-1.0f, sg + n.z);
     const float b = n.x * n.y * a;
     t1 = f3(1.0f + sg * n.x * n.x * a, sg * b, -sg * n.x);
     t2 = f3(b, sg + n.y * n.y * a, -n.y);
 }
 
-// Radiance of one path sample through pixel (x, y): unidirectional path tracing
-// with next-event estimation on diffuse vertices (the Monte-Carlo estimate of
-// Eq. 1 whose pixel average is Eq. 3).
-template <bool kCount>
-__device__ float3 trace_path(const InstScene& S, int W, int H, int depth, int rr_start, int x, int y, int s,
-                             Counters& cnt) {
-    const unsigned pixel = unsigned(y * W + x);
-    const float4 jit = path_uniforms(S, pixel, s, 0, 2);
+// One live path sample (Eq. 1's integrand along one path; Eq. 3 averages them).
+struct Path {
+    float3 o, d, beta, L;
+    unsigned pixel;  // y * W + x
+    int s, b;        // sample index, vertex index
+    int slot;        // pixel slot inside the warp's block
+    bool specular;   // emission counts: camera rays and rays after specular bounces
+};
+
+// Camera ray of sample s through pixel (x, y): pinhole, box-filtered jitter (slot 2).
+__device__ __forceinline__ void start_path(const InstScene& S, int W, int H, int x, int y, int s, int slot,
+                                           Path& p) {
+    p.pixel = unsigned(y * W + x);
+    const uint4 jw = path_words(S, p.pixel, s, 0, 2);
     const float th = S.eye.w, aspect = S.fwd.w;
-    const float sx = (float(2 * x - W) + 2.0f * jit.x) * (aspect * th / float(W));
-    const float sy = (float(H - 2 * y) - 2.0f * jit.y) * (th / float(H));
-    float3 o = xyz(S.eye);
-    float3 d = normalized(xyz(S.fwd) + xyz(S.right) * sx + xyz(S.up) * sy);
-    float3 L = f3(0.f, 0.f, 0.f), beta = f3(1.f, 1.f, 1.f);
-    bool specular = true;
-    if (kCount) ++cnt.paths;
-    for (int b = 0; b < depth; ++b) {
-        const Hit h = closest_hit<kCount>(S, o, d, cnt);
-        if (h.slot < 0) {
-            L = L + beta * xyz(S.bg);
-            break;
-        }
-        if (kCount) ++cnt.vertices;
-        const float3 p = o + d * h.t;
-        float3 ng;
-        int mat;
-        if (h.type == kSphere) {
-            const float4 a = S.prim[h.slot][0];
-            ng = (p - xyz(a)) * S.prim[h.slot][1].y;
-            mat = as_int(S.prim[h.slot][1].z);
-        } else if (h.type == kQuad) {
-            ng = xyz(S.prim[h.slot][1]);
-            mat = as_int(S.prim[h.slot][0].w);
-        } else {
-            ng = box_normal(S, h.slot, o, d, f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z));
-            mat = as_int(S.prim[h.slot][0].w);
-        }
-        const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
-        const int mtype = as_int(m0.w);
-        const float3 albedo = xyz(m0), emission = xyz(m1);
-        if (specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(d, ng) < 0.0f)
-            L = L + beta * emission;
-        const bool last = (b + 1 >= depth);
-        float4 u;
-        if (mtype == kDiffuse) {
-            const float3 ns = dot3(ng, d) < 0.0f ? ng : ng * -1.0f;
-            const float3 po = p + ns * kEps;
-            if (S.n_lights > 0) {  // next-event estimation: one emitter, uniform area sample
-                uint4 words;
-                const float4 lu = path_uniforms(S, pixel, s, b, 1, &words);
-                int li = int((((words.z >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
-                li = min(li, S.n_lights - 1);
-                const int4 lt = S.light[li];
-                float3 yl, ny;
-                if (lt.x == kQuad) {
-                    const float3 uu = xyz(S.prim[lt.y][2]), vv = xyz(S.prim[lt.y][3]);
-                    yl = xyz(S.prim[lt.y][0]) + uu * (lu.x - 0.5f) + vv * (lu.y - 0.5f);
-                    ny = xyz(S.prim[lt.y][1]);
-                } else {
-                    const float z = 1.0f - 2.0f * lu.x;
-                    const float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-                    float sp, cp;
-                    sincospif(2.0f * lu.y, &sp, &cp);
-                    ny = f3(rr * cp, rr * sp, z);
-                    yl = xyz(S.prim[lt.y][0]) + ny * S.prim[lt.y][0].w;
-                }
-                const float3 dv = yl - po;
-                const float dist2 = dot3(dv, dv);
-                const float inv_dist = rsqrtf(dist2);
-                const float3 wi = dv * inv_dist;
-                const float cx = dot3(ns, wi), cl = -dot3(ny, wi);
-                if (cx > 0.0f && cl > 0.0f) {
-                    if (!occluded<kCount>(S, po, wi, dist2 * inv_dist, lt.y, cnt)) {
-                        const float g = cx * cl / dist2 * S.light_area[li] * float(S.n_lights) * 0.3183098861837907f;
-                        L = L + beta * albedo * xyz(S.mat[lt.w][1]) * g;
-                    }
-                }
-            }
-            if (last) break;
-            u = path_uniforms(S, pixel, s, b, 0);
-            const float rad = sqrtf(u.x);
-            float sp, cp;
-            sincospif(2.0f * u.y, &sp, &cp);
-            float3 t1, t2;
-            onb(ns, t1, t2);
-            const float3 wo = t1 * (rad * cp) + t2 * (rad * sp) + ns * sqrtf(fmaxf(0.0f, 1.0f - u.x));
-            beta = beta * albedo;
-            o = po;
-            d = normalized(wo);
-            specular = false;
-        } else if (mtype == kMirror) {
-            if (last) break;
-            u = path_uniforms(S, pixel, s, b, 0);
-            const float3 ns = dot3(ng, d) < 0.0f ? ng : ng * -1.0f;
-            d = normalized(d - ns * (2.0f * dot3(d, ns)));
-            o = p + ns * kEps;
-            beta = beta * albedo;
-            specular = true;
-        } else {  // smooth dielectric: exact unpolarised Fresnel, reflect or refract
-            if (last) break;
-            u = path_uniforms(S, pixel, s, b, 0);
-            float ci = -dot3(d, ng);
-            float eta;
-            float3 n;
-            if (ci > 0.0f) {
-                eta = 1.0f / m1.w;
-                n = ng;
-            } else {
-                eta = m1.w;
-                n = ng * -1.0f;
-                ci = -ci;
-            }
-            const float s2t = eta * eta * (1.0f - ci * ci);
-            float F, ct = 0.0f;
-            if (s2t >= 1.0f) {
-                F = 1.0f;
-            } else {
-                ct = sqrtf(1.0f - s2t);
-                const float rs = (eta * ci - ct) / (eta * ci + ct);
-                const float rp = (ci - eta * ct) / (ci + eta * ct);
-                F = 0.5f * (rs * rs + rp * rp);
-            }
-            if (u.z < F) {
-                d = normalized(d + n * (2.0f * ci));
-                o = p + n * kEps;
-            } else {
-                d = normalized(d * eta + n * (eta * ci - ct));
-                o = p - n * kEps;
-            }
-            beta = beta * albedo;
-            specular = true;
-        }
-        if (maxc(beta) <= 0.0f) break;
-        if (rr_start >= 0 && b >= rr_start) {  // Russian roulette on slot 0's fourth uniform
-            const float q = fminf(0.95f, maxc(beta));
-            if (u.w >= q) break;
-            beta = beta * (1.0f / q);
-        }
+    const float sx = (float(2 * x - W) + 2.0f * u01(jw.x)) * __fdividef(aspect * th, float(W));
+    const float sy = (float(H - 2 * y) - 2.0f * u01(jw.y)) * __fdividef(th, float(H));
+    p.o = xyz(S.eye);
+    p.d = normalized(xyz(S.fwd) + xyz(S.right) * sx + xyz(S.up) * sy);
+    p.L = f3(0.f, 0.f, 0.f);
+    p.beta = f3(1.f, 1.f, 1.f);
+    p.s = s;
+    p.b = 0;
+    p.slot = slot;
+    p.specular = true;
+}
+
+// One surface interaction of a path: unidirectional path tracing with next-event
+// estimation on diffuse vertices. Returns true when the path has ended.
+// Random slots of vertex b: slot 0 = (light point u, v, BSDF u1, u2); slot 1 =
+// (light choice, Russian roulette, dielectric choice), drawn only when needed.
+template <bool kCount>
+__device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt) {
+    const Hit h = closest_hit<kCount>(S, p.o, p.d, cnt);
+    if (h.slot < 0) {
+        p.L = p.L + p.beta * xyz(S.bg);
+        return true;
     }
-    return L;
+    if (kCount) ++cnt.vertices;
+    const float3 pt = p.o + p.d * h.t;
+    float3 ng;
+    int mat;
+    if (h.type == kSphere) {
+        const float4 a = S.prim[h.slot][0];
+        ng = (pt - xyz(a)) * S.prim[h.slot][1].y;
+        mat = as_int(S.prim[h.slot][1].z);
+    } else if (h.type == kQuad) {
+        ng = xyz(S.prim[h.slot][1]);
+        mat = as_int(S.prim[h.slot][0].w);
+    } else {
+        ng = box_normal(S, h.slot, p.o, p.d, rcp3(p.d));
+        mat = as_int(S.prim[h.slot][0].w);
+    }
+    const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
+    const int mtype = as_int(m0.w);
+    const float3 albedo = xyz(m0), emission = xyz(m1);
+    if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f)
+        p.L = p.L + p.beta * emission;
+    const bool last = (p.b + 1 >= depth);
+    const bool rr = !last && rr_start >= 0 && p.b >= rr_start;
+    uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
+    if (mtype == kDiffuse) {
+        const float3 ns = dot3(ng, p.d) < 0.0f ? ng : ng * -1.0f;
+        const float3 po = pt + ns * kEps;
+        const uint4 w0 = path_words(S, p.pixel, p.s, p.b, 0);
+        if (S.n_lights > 1 || rr) w1 = path_words(S, p.pixel, p.s, p.b, 1);
+        if (S.n_lights > 0) {  // next-event estimation: one emitter, uniform area sample
+            int li = int((((w1.x >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
+            li = min(li, S.n_lights - 1);
+            const int4 lt = S.light[li];
+            const float lu = u01(w0.x), lv = u01(w0.y);
+            float3 yl, ny;
+            if (lt.x == kQuad) {
+                const float3 uu = xyz(S.prim[lt.y][2]), vv = xyz(S.prim[lt.y][3]);
+                yl = xyz(S.prim[lt.y][0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
+                ny = xyz(S.prim[lt.y][1]);
+            } else {
+                const float z = 1.0f - 2.0f * lu;
+                const float rr2 = fmaxf(0.0f, 1.0f - z * z);
+                const float rr_ = rr2 * rsqrtf(fmaxf(rr2, 1e-30f));
+                float sp, cp;
+                sincospif(2.0f * lv, &sp, &cp);
+                ny = f3(rr_ * cp, rr_ * sp, z);
+                yl = xyz(S.prim[lt.y][0]) + ny * S.prim[lt.y][0].w;
+            }
+            const float3 dv = yl - po;
+            const float dist2 = dot3(dv, dv);
+            const float inv_dist = rsqrtf(dist2);
+            const float3 wi = dv * inv_dist;
+            const float cx = dot3(ns, wi), cl = -dot3(ny, wi);
+            if (cx > 0.0f && cl > 0.0f) {
+                if (!occluded<kCount>(S, po, wi, dist2 * inv_dist, lt.y, cnt)) {
+                    const float g = cx * cl * (inv_dist * inv_dist) * S.light_area[li] * float(S.n_lights) *
+                                    0.3183098861837907f;
+                    p.L = p.L + p.beta * albedo * xyz(S.mat[lt.w][1]) * g;
+                }
+            }
+        }
+        if (last) return true;
+        const float u1 = u01(w0.z), u2 = u01(w0.w);
+        const float rad = u1 * rsqrtf(u1);
+        float sp, cp;
+        sincospif(2.0f * u2, &sp, &cp);
+        float3 t1, t2;
+        onb(ns, t1, t2);
+        const float cz2 = fmaxf(0.0f, 1.0f - u1);
+        const float3 wo = t1 * (rad * cp) + t2 * (rad * sp) + ns * (cz2 * rsqrtf(fmaxf(cz2, 1e-30f)));
+        p.beta = p.beta * albedo;
+        p.o = po;
+        p.d = normalized(wo);
+        p.specular = false;
+    } else if (mtype == kMirror) {
+        if (last) return true;
+        if (rr) w1 = path_words(S, p.pixel, p.s, p.b, 1);
+        const float3 ns = dot3(ng, p.d) < 0.0f ? ng : ng * -1.0f;
+        p.d = normalized(p.d - ns * (2.0f * dot3(p.d, ns)));
+        p.o = pt + ns * kEps;
+        p.beta = p.beta * albedo;
+        p.specular = true;
+    } else {  // smooth dielectric: exact unpolarised Fresnel, reflect or refract
+        if (last) return true;
+        w1 = path_words(S, p.pixel, p.s, p.b, 1);
+        float ci = -dot3(p.d, ng);
+        float eta;
+        float3 n;
+        if (ci > 0.0f) {
+            eta = __fdividef(1.0f, m1.w);
+            n = ng;
+        } else {
+            eta = m1.w;
+            n = ng * -1.0f;
+            ci = -ci;
+        }
+        const float s2t = eta * eta * (1.0f - ci * ci);
+        float F, ct = 0.0f;
+        if (s2t >= 1.0f) {
+            F = 1.0f;
+        } else {
+            ct = sqrtf(1.0f - s2t);
+            const float rs = __fdividef(eta * ci - ct, eta * ci + ct);
+            const float rp = __fdividef(ci - eta * ct, ci + eta * ct);
+            F = 0.5f * (rs * rs + rp * rp);
+        }
+        if (u01(w1.z) < F) {
+            p.d = normalized(p.d + n * (2.0f * ci));
+            p.o = pt + n * kEps;
+        } else {
+            p.d = normalized(p.d * eta + n * (eta * ci - ct));
+            p.o = pt - n * kEps;
+        }
+        p.beta = p.beta * albedo;
+        p.specular = true;
+    }
+    if (maxc(p.beta) <= 0.0f) return true;
+    if (rr) {  // Russian roulette on slot 1's second uniform
+        const float q = fminf(0.95f, maxc(p.beta));
+        if (u01(w1.y) >= q) return true;
+        p.beta = p.beta * __fdividef(1.0f, q);
+    }
+    ++p.b;
+    return false;
 }
 
 // ---------------------------------------------------------------------------
 // k_trace: persistent render + fused loss/gradient/Adam epilogue
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+constexpr int kWarps = kBlock / 32;
+#ifndef PRDPT_TRACE_MIN_BLOCKS
+#define PRDPT_TRACE_MIN_BLOCKS 3  // <= 85 registers: 24 resident warps per SM
+#endif
+constexpr int kTraceMinBlocks = PRDPT_TRACE_MIN_BLOCKS;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kFix = 4294967296.0f;  // 2^32: fixed-point scale of the radiance accumulators
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 __device__ __forceinline__ unsigned warp_sum_u(unsigned v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
-// Loss of every render, the gradient of Eq. 10 and (for a resident job) the Adam
-// step. Run by the one CTA that finished the job's last tile.
-__device__ void finalize_job(const TraceJob& J, double* s_L) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double norm = 1.0 / (3.0 * double(J.W) * double(J.H));
-    for (int r = warp; r < J.R; r += kBlock / 32) {
-        double acc = 0.0;
-        for (int i = lane; i < J.tiles; i += 32) acc += double(__ldcg(J.partials + size_t(r) * J.tiles + i));
-        acc = warp_sum_d(acc);
-        if (lane == 0) s_L[r] = acc * norm;
-    }
-    __syncthreads();
-    if (J.loss_out)
-        for (int r = tid; r < J.R; r += kBlock) J.loss_out[r] = float(s_L[r]);
-    int t = 0;
-    if (J.step_dev) t = *J.step_dev;
-    __syncthreads();
-    if (tid < J.D) {
-        const int d = tid;
+// n / d for d >= 1 given m = ceil(2^32 / d) (m wraps to 0 for d = 1).
+__device__ __forceinline__ int div_magic(int n, int d, unsigned m) {
+    return d == 1 ? n : int(__umulhi(unsigned(n), m));
+}
+
+// Radiance to fixed point (2^-32 units): integer sums are exact and independent of
+// the order in which the warp's lanes finish their paths. The conversion is done
+// on the significand bits (a float -> int64 conversion would run on the FP64 pipe):
+// v * 2^32 = m * 2^(e + 9) for v = m * 2^(e - 23); values below 2^-9 are truncated.
+__device__ __forceinline__ unsigned long long to_fixed(float v) {
+    v = fminf(fmaxf(v, 0.0f), 2.0e9f);  // NaN -> 0
+    const unsigned bits = __float_as_uint(v);
+    const int e = int(bits >> 23) - 127;
+    if (e < -32) return 0ull;
+    const unsigned long long m = (bits & 0x7fffffu) | 0x800000u;
+    const int sh = e + 9;
+    return sh >= 0 ? (m << sh) : (m >> (-sh));
+}
+
+// Gradient of Eq. 10 from the per-render losses, then Adam; run by the one warp
+// that completed the job's last render.
+__device__ void finish_job(const TraceJob& J, int lane) {
+    __threadfence();
+    const int t = J.step_dev ? *J.step_dev : 0;
+    for (int d = lane; d < J.D; d += 32) {
         double g = 0.0;
         if (J.antithetic) {
             const int P = J.R / 2;
-            for (int p = 0; p < P; ++p) g += double(J.w[size_t(2 * p) * J.D + d]) * (s_L[2 * p] - s_L[2 * p + 1]);
+            for (int p = 0; p < P; ++p)
+                g += double(J.w[size_t(2 * p) * J.D + d]) * (__ldcg(J.losses + 2 * p) - __ldcg(J.losses + 2 * p + 1));
             g /= double(2 * P);
         } else {
-            for (int r = 0; r < J.R; ++r) g += double(J.w[size_t(r) * J.D + d]) * s_L[r];
+            for (int r = 0; r < J.R; ++r) g += double(J.w[size_t(r) * J.D + d]) * __ldcg(J.losses + r);
             g /= double(J.R);
         }
         const float gf = float(g);
@@ -647,136 +682,171 @@ __device__ void finalize_job(const TraceJob& J, double* s_L) {
             J.theta[d] = float(double(J.theta[d]) - double(J.lr) * mh / (sqrt(vh) + double(J.eps)));
         }
     }
-    if (tid == 0) {
+    __syncwarp();
+    if (lane == 0) {
         if (J.step_dev) *J.step_dev = t + 1;
         *J.done = 0u;  // ready for the next launch
     }
 }
 
-template <bool kRender, bool kCount>
-__global__ void __launch_bounds__(kBlock) k_trace(const TraceLaunch L) {
-    __shared__ InstScene s_scene;
-    __shared__ TraceJob s_job;
-    __shared__ float s_acc[3][kBlock];
-    __shared__ float s_red[kBlock / 32];
-    __shared__ double s_L[kMaxRenders];
-    __shared__ int s_item, s_jobi, s_last;
-    __shared__ unsigned s_cnt[kNumCounters][kBlock / 32];
+// L_r = (1/3HW) sum of render r's block partials (FP64, fixed order); run by the
+// warp that completed the render's last block.
+__device__ void finish_render(const TraceJob& J, int r, int lane) {
+    __threadfence();
+    double acc = 0.0;
+    for (int i = lane; i < J.tiles; i += 32) acc += __ldcg(J.partials + size_t(r) * J.tiles + i);
+    acc = warp_sum_d(acc);
+    unsigned last = 0;
+    if (lane == 0) {
+        const double Lr = acc / (3.0 * double(J.W) * double(J.H));
+        J.losses[r] = Lr;
+        if (J.loss_out) J.loss_out[r] = float(Lr);
+        J.render_done[r] = 0u;
+        __threadfence();
+        last = (atomicAdd(J.done, 1u) == unsigned(J.R - 1));
+    }
+    last = __shfl_sync(kFull, last, 0);
+    if (last) finish_job(J, lane);
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+template <bool kRender, bool kCount>
+__global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_constant__ TraceLaunch L) {
+    __shared__ InstScene s_scene[kWarps];
+    __shared__ TraceJob s_job[kWarps];
+    __shared__ unsigned long long s_acc[kWarps][3][32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    InstScene& S = s_scene[warp];
+    TraceJob& J = s_job[warp];
+    unsigned long long(&acc)[3][32] = s_acc[warp];
     int cur_job = -1, cur_r = -1;
     Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 
     for (;;) {
-        if (tid == 0) {
-            const int item = int(atomicAdd(L.queue, 1u));
-            s_item = item;
-            int j = 0;
-            if (item < L.total_items && L.jobs) {
+        // ---- pop one (job, render, block) work item for this warp ----------------
+        unsigned item = 0;
+        int j = 0;
+        if (lane == 0) {
+            item = atomicAdd(L.queue, 1u);
+            if (item < unsigned(L.total_items) && L.jobs) {
                 int lo = 0, hi = L.njobs - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) / 2;
-                    if (L.jobs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+                    if (L.jobs[mid].item_begin <= int(item)) lo = mid; else hi = mid - 1;
                 }
                 j = lo;
             }
-            s_jobi = j;
         }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= L.total_items) break;
-        const int j = s_jobi;
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= unsigned(L.total_items)) break;
+        j = __shfl_sync(kFull, j, 0);
         if (j != cur_job) {
-            if (tid == 0) s_job = L.jobs ? L.jobs[j] : L.job0;
-            __syncthreads();
+            const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + j : &L.job0);
+            unsigned* dst = reinterpret_cast<unsigned*>(&J);
+            for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
+            __syncwarp();
+            cur_job = j;
+            cur_r = -1;
         }
-        const TraceJob& J = s_job;
-        const int li = item - J.item_begin;
-        const int r = li % J.R, t = li / J.R;  // tile-major: consecutive items share pixels
+        const int li = int(item) - J.item_begin;
+        const int r = li % J.R, t = li / J.R;  // render-interleaved: neighbouring items share pixels
         if (r >= J.R || t >= J.tiles) {
-            if (tid == 0) atomicOr(L.status, kStatusBadItem);
+            if (lane == 0) atomicOr(L.status, kStatusBadItem);
             break;
         }
-        if (j != cur_job || r != cur_r) {  // stage the render's scene in shared memory
+        if (r != cur_r) {  // a2 -> shared memory: header, used materials, used primitives
             const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
-            float4* dst = reinterpret_cast<float4*>(&s_scene);
-            for (int i = tid; i < int(sizeof(InstScene) / 16); i += kBlock) dst[i] = __ldg(src + i);
-            cur_job = j;
+            float4* dst = reinterpret_cast<float4*>(&S);
+            constexpr int kHead = int(offsetof(InstScene, mat) / 16);
+            constexpr int kPrim = int(offsetof(InstScene, prim) / 16);
+            const int nm = 2 * J.n_mats, np = 4 * J.n_prims;
+            for (int i = lane; i < kHead + nm + np; i += 32) {
+                const int o = (i < kHead) ? i : (i < kHead + nm ? i : kPrim + (i - kHead - nm));
+                dst[o] = __ldg(src + o);
+            }
+            __syncwarp();
             cur_r = r;
-            __syncthreads();
         }
-        // tile geometry: k threads per pixel, warps cover 8x4 pixel blocks
-        int TW, TH;
-        tile_shape(J.k, &TW, &TH);
-        const int npix = kBlock / J.k;
-        const int q = tid % npix, c = tid / npix;
-        const int g = q >> 5, ql = q & 31;
-        const int gx = g % (TW / 8), gy = g / (TW / 8);
-        const int px = (t % J.tiles_x) * TW + gx * 8 + (ql & 7);
-        const int py = (t / J.tiles_x) * TH + gy * 4 + (ql >> 3);
-        const bool inside = px < J.W && py < J.H;
 
-        float3 rad = f3(0.f, 0.f, 0.f);
-        if (inside)
-            for (int s = c; s < J.spp; s += J.k)
-                rad = rad + trace_path<kCount>(s_scene, J.W, J.H, J.depth, J.rr_start, px, py, s, cnt);
-        if (J.k > 1) {  // combine the k sample chunks of each pixel in chunk order
-            s_acc[0][tid] = rad.x;
-            s_acc[1][tid] = rad.y;
-            s_acc[2][tid] = rad.z;
-            __syncthreads();
-            if (c == 0) {
-                for (int cc = 1; cc < J.k; ++cc) {
-                    rad.x += s_acc[0][q + cc * npix];
-                    rad.y += s_acc[1][q + cc * npix];
-                    rad.z += s_acc[2][q + cc * npix];
+        // ---- a3: trace the block's pixels x samples as a pool of path tasks --------
+        const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
+        const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
+        const int npx = vw * vh, ntasks = npx * J.spp;
+        // task -> (pixel slot, sample) by multiply-high with m = ceil(2^32 / d): exact for
+        // n < 2^32 / d (here n < 2^21, d <= 32); d = 1 has no 32-bit m and is special-cased
+        const unsigned magic = 0xffffffffu / unsigned(npx) + 1u, magic_w = 0xffffffffu / unsigned(vw) + 1u;
+        acc[0][lane] = 0ull;
+        acc[1][lane] = 0ull;
+        acc[2][lane] = 0ull;
+        __syncwarp();
+        Path p;
+        int task = lane;
+        bool alive = task < ntasks;
+        if (alive) {
+            const int smp = div_magic(task, npx, magic), slot = task - smp * npx;
+            const int row = div_magic(slot, vw, magic_w);
+            start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+            if (kCount) ++cnt.paths;
+        }
+        int next = 32;
+        while (__any_sync(kFull, alive)) {
+            bool ended = false;
+            if (alive) ended = advance<kCount>(S, J.depth, J.rr_start, p, cnt);
+            if (ended) {
+                atomicAdd(&acc[0][p.slot], to_fixed(p.L.x));
+                atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
+                atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
+            }
+            const unsigned need = __ballot_sync(kFull, ended);  // lanes whose path ended take new tasks
+            if (ended) {
+                task = next + __popc(need & lt_mask);
+                alive = task < ntasks;
+                if (alive) {
+                    const int smp = div_magic(task, npx, magic), slot = task - smp * npx;
+                    const int row = div_magic(slot, vw, magic_w);
+                    start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+                    if (kCount) ++cnt.paths;
                 }
             }
+            next += __popc(need);
         }
-        const float inv_spp = 1.0f / float(J.spp);
-        const float3 I = rad * inv_spp;
-        if (kRender) {
-            if (c == 0 && inside)
-                J.images[(size_t(r) * J.H + py) * J.W + px] = make_float4(I.x, I.y, I.z, 0.0f);
-            __syncthreads();
-        } else {
-            float e = 0.0f;
-            if (c == 0 && inside) {  // a4: squared error of the pixel mean against the target
+        __syncwarp();
+
+        // ---- a4/a5: pixel means, squared error, block partial ----------------------
+        double e = 0.0;
+        const int px = x0 + lane % vw, py = y0 + lane / vw;
+        if (lane < npx && px < J.W && py < J.H) {
+            const double inv = 1.0 / (double(J.spp) * double(kFix));
+            const double Ix = double(acc[0][lane]) * inv, Iy = double(acc[1][lane]) * inv,
+                         Iz = double(acc[2][lane]) * inv;
+            if (kRender) {
+                J.images[(size_t(r) * J.H + py) * J.W + px] = make_float4(float(Ix), float(Iy), float(Iz), 0.0f);
+            } else {
                 const float4 T = __ldg(J.target + size_t(py) * J.W + px);
-                const float ex = I.x - T.x, ey = I.y - T.y, ez = I.z - T.z;
+                const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
                 e = ex * ex + ey * ey + ez * ez;
             }
-            e = warp_sum(e);  // a5: warp shuffle, then CTA, then one partial per tile
-            if (lane == 0) s_red[warp] = e;
-            __syncthreads();
-            if (tid == 0) {
-                float tot = 0.0f;
-                for (int w = 0; w < kBlock / 32; ++w) tot += s_red[w];
-                J.partials[size_t(r) * J.tiles + t] = tot;
-                __threadfence();
-                const unsigned prev = atomicAdd(J.done, 1u);
-                s_last = (prev == unsigned(J.R * J.tiles - 1));
-            }
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                finalize_job(J, s_L);
-                __syncthreads();
-            }
         }
+        if (!kRender) {
+            e = warp_sum_d(e);
+            unsigned rlast = 0;
+            if (lane == 0) {
+                J.partials[size_t(r) * J.tiles + t] = e;
+                __threadfence();
+                rlast = (atomicAdd(J.render_done + r, 1u) == unsigned(J.tiles - 1));
+            }
+            rlast = __shfl_sync(kFull, rlast, 0);
+            if (rlast) finish_render(J, r, lane);  // a5/a6/a7 for the last block of a render
+        }
+        __syncwarp();
     }
     if (kCount) {
         const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
                                           warp_sum_u(cnt.paths), warp_sum_u(cnt.vertices), warp_sum_u(cnt.shadow),
                                           warp_sum_u(cnt.rays), 0u};
         if (lane == 0)
-            for (int i = 0; i < kNumCounters; ++i) s_cnt[i][warp] = v[i];
-        __syncthreads();
-        if (tid < kNumCounters) {
-            unsigned long long tot = 0;
-            for (int w = 0; w < kBlock / 32; ++w) tot += s_cnt[tid][w];
-            atomicAdd(L.counters + tid, tot);
-        }
+            for (int i = 0; i < kNumCounters; ++i) atomicAdd(L.counters + i, (unsigned long long)v[i]);
     }
 }
 

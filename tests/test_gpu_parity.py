@@ -74,13 +74,13 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("k", [1, 4])
+@pytest.mark.parametrize("k", [32, 8])
 def test_render_matches_oracle(ctx, name, k):
     wl = CASES[name]()
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     thetas = np.stack([wl.theta_ref, wl.theta0, wl.theta0 + 0.03]).astype(np.float32)
     img = scene.render_batch(_t(thetas), wl.width, wl.height, wl.spp, wl.depth, wl.rr_start, seed=wl.seed, step=3,
-                             tag=2, crn=0, threads_per_pixel=k)
+                             tag=2, crn=0, block_pixels=k)
     torch.cuda.synchronize()
     img = img.cpu().numpy()
     ref = oracle.render(wl.scene, wl.bindings, thetas, wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
@@ -92,10 +92,10 @@ def test_render_matches_oracle(ctx, name, k):
 def test_render_edge_sizes(ctx):
     wl = workloads.config_occlusion()
     scene = ctx.upload_scene(wl.scene, wl.bindings)
-    for (W, H, spp) in [(1, 1, 1), (7, 3, 2), (17, 33, 1), (33, 17, 3)]:
-        for k in (1, 2, 8):
+    for (W, H, spp) in [(1, 1, 1), (7, 3, 2), (17, 33, 1), (33, 17, 3), (5, 9, 40)]:
+        for k in (8, 16, 32):
             img = scene.render_batch(_t(wl.theta_ref[None]), W, H, spp, wl.depth, wl.rr_start, seed=1, step=0,
-                                     tag=3, crn=1, threads_per_pixel=k).cpu().numpy()
+                                     tag=3, crn=1, block_pixels=k).cpu().numpy()
             ref = oracle.render(wl.scene, wl.bindings, wl.theta_ref[None], W, H, spp, wl.depth, wl.rr_start, 1, 0, 3,
                                 1)
             diff = np.abs(img[..., :3] - ref)
@@ -106,7 +106,7 @@ def test_render_edge_sizes(ctx):
 def _grad_case(ctx, wl, step=0, k=0):
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     target = oracle.render_target(wl)
-    opts = scene.grad_opts(wl, step=step, threads_per_pixel=k)
+    opts = scene.grad_opts(wl, step=step, block_pixels=k)
     g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
     torch.cuda.synchronize()
     ref = oracle.smoothed_grad(wl, target=target, step=step)
@@ -134,7 +134,7 @@ def test_gradient_estimator_variants(ctx, sampler, antithetic, crn):
 
 def test_gradient_full_size_small_config(ctx):
     wl = workloads.config_small()
-    for k in (1, 2, 8):
+    for k in (8, 16, 32):
         g, L, ref = _grad_case(ctx, wl, step=0, k=k)
         assert grad_rel_error(g, ref["grad"], ref["weights"], ref["losses"]) <= GRAD_REL, k
 
@@ -155,8 +155,8 @@ def test_invisible_parameter_exact_zero_on_gpu(ctx):
 def test_deterministic_across_launch_shapes(ctx):
     wl = CASES["occlusion"]()
     wl.pairs = 4
-    g1, L1, _ = _grad_case(ctx, wl, k=1)
-    g1b, L1b, _ = _grad_case(ctx, wl, k=1)
+    g1, L1, _ = _grad_case(ctx, wl, k=32)
+    g1b, L1b, _ = _grad_case(ctx, wl, k=32)
     assert np.array_equal(g1, g1b) and np.array_equal(L1, L1b)  # bitwise reproducible
-    g4, L4, ref = _grad_case(ctx, wl, k=4)
-    assert np.allclose(L4, L1, rtol=1e-6)
+    g4, L4, ref = _grad_case(ctx, wl, k=8)
+    assert np.allclose(L4, L1, rtol=1e-12)  # block shape changes only the FP64 summation grouping
