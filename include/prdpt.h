@@ -35,6 +35,7 @@
 #ifndef PRDPT_H
 #define PRDPT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -226,6 +227,30 @@ prdpt_status prdpt_kernel_timing_read(prdpt_ctx* ctx, double* total_ms, int64_t*
 
 /* Synchronise `stream` and check the context's device status word. */
 prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);
+
+/* The same plateau-reduced gradient as prdpt_smoothed_grad, for callers that cannot
+ * allocate device memory -- for example a process whose device memory belongs to
+ * another allocator (a framework's caching allocator, a fixed arena of a serving
+ * runtime), or code that may not grow its footprint or create a context after
+ * start-up. It takes no context and allocates nothing: the scene comes from host
+ * memory (`scene`, `binds`, D as for prdpt_scene_upload), theta_dev, sigma_dev,
+ * target_dev, grad_dev and losses_dev (NULL allowed) are the caller's device buffers
+ * exactly as for prdpt_smoothed_grad, and every intermediate buffer lives in one
+ * fixed 6 MiB __device__ array that each GPU loading the library holds until the
+ * process exits.
+ * Limits: at most 32 antithetic pairs and 2P x (image blocks) x 8 bytes of loss
+ * partials within the 6 MiB (512 x 512 with 32-pixel blocks fits 32 pairs); larger
+ * requests return PRDPT_E_OUT_OF_BUDGET with a message. All calls share that array
+ * and each call overwrites what the last one left: calls that overlap on the GPU
+ * (different streams, no ordering) race and must not be issued. The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and the
+ * device's SM count; make that first call before any stream capture. Errors are
+ * written to err (err_len bytes, may be NULL); there is no context to query.
+ * The paper has no counterpart to this entry point. */
+prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene, const prdpt_param_binding* binds, int32_t D,
+                                        const float* theta_dev, const float* sigma_dev, const prdpt_grad_opts* opts,
+                                        const float* target_dev, float* grad_dev, float* losses_dev, void* stream,
+                                        char* err, size_t err_len);
 
 #ifdef __cplusplus
 }

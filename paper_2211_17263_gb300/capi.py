@@ -32,7 +32,7 @@ EXPORTS = [
     "prdpt_render_batch", "prdpt_sample_perturbations", "prdpt_smoothed_grad", "prdpt_adam_step",
     "prdpt_job_create", "prdpt_step", "prdpt_step_batch", "prdpt_job_read", "prdpt_job_release",
     "prdpt_philox_words", "prdpt_counters_enable", "prdpt_counters_read", "prdpt_kernel_timing_enable",
-    "prdpt_kernel_timing_read", "prdpt_sync",
+    "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static",
 ]
 
 
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
         "prdpt_kernel_timing_enable": ([vp, i32], i32),
         "prdpt_kernel_timing_read": ([vp, P(C.c_double), P(C.c_int64)], i32),
         "prdpt_sync": ([vp, vp], i32),
+        "prdpt_smoothed_grad_static": ([P(prdpt_scene_desc), P(prdpt_param_binding), i32, vp, vp,
+                                        P(prdpt_grad_opts), vp, vp, vp, vp, C.c_char_p, C.c_size_t], i32),
     }
     for name, (args, res) in proto.items():
         fn = getattr(L, name)
@@ -229,6 +231,16 @@ def prdpt_kernel_timing_read(ctx):
     n = C.c_int64()
     check(load().prdpt_kernel_timing_read(ctx, C.byref(ms), C.byref(n)), "prdpt_kernel_timing_read", ctx)
     return ms.value, n.value
+
+
+def prdpt_smoothed_grad_static(desc, binds, D, theta_dev, sigma_dev, opts, target_dev, grad_dev, losses_dev, stream):
+    """Context-free, allocation-free gradient call; raises PrdptError with the call's message."""
+    err = C.create_string_buffer(256)
+    code = load().prdpt_smoothed_grad_static(C.byref(desc), binds, D, theta_dev, sigma_dev, C.byref(opts),
+                                             target_dev, grad_dev, losses_dev, stream, err, C.sizeof(err))
+    if code != PRDPT_OK:
+        raise PrdptError(code, "prdpt_smoothed_grad_static", err.value.decode(errors="replace"))
+    return code
 
 
 def prdpt_sync(ctx, stream):

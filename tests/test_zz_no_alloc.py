@@ -1,0 +1,97 @@
+"""The allocation-free gradient entry point (prdpt_smoothed_grad_static).
+
+It exists for callers that cannot allocate device memory -- a process whose device
+memory belongs to another allocator, or code that may not grow its footprint or
+create a library context after start-up. It must give the same gradient and losses
+as prdpt_smoothed_grad on the same inputs, call after call (its scratch is one
+fixed __device__ array reused by every call), and refuse requests larger than that
+array. This file is collected last so that a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_helpers import GRAD_REL, grad_rel_error
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+
+
+def _scene_args(wl):
+    arrays = [np.ascontiguousarray(wl.scene.prim_type, np.int32), np.ascontiguousarray(wl.scene.prim_mat, np.int32),
+              np.ascontiguousarray(wl.scene.prim_geom, np.float32), np.ascontiguousarray(wl.scene.mat_type, np.int32),
+              np.ascontiguousarray(wl.scene.mat_param, np.float32), np.ascontiguousarray(wl.scene.camera, np.float32),
+              np.ascontiguousarray(wl.scene.background, np.float32)]
+    from paper_2211_17263_gb300 import capi
+    desc = capi.prdpt_scene_desc(wl.scene.n_prims, wl.scene.n_mats,
+                                 *[a.ctypes.data_as(C.c_void_p) for a in arrays])
+    b = np.ascontiguousarray(wl.bindings, np.int32)
+    binds = (capi.prdpt_param_binding * wl.D)(*[capi.prdpt_param_binding(*map(int, r)) for r in b])
+    return desc, binds, arrays
+
+
+def _static_call(wl, theta, sigma, target, opts):
+    from paper_2211_17263_gb300 import capi
+    desc, binds, keep = _scene_args(wl)
+    g = torch.full((wl.D,), float("nan"), dtype=torch.float32, device="cuda")
+    L = torch.full((wl.renders,), float("nan"), dtype=torch.float32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    capi.prdpt_smoothed_grad_static(desc, binds, wl.D, C.c_void_p(theta.data_ptr()), C.c_void_p(sigma.data_ptr()),
+                                    opts, C.c_void_p(target.data_ptr()), C.c_void_p(g.data_ptr()),
+                                    C.c_void_p(L.data_ptr()), stream)
+    torch.cuda.synchronize()
+    del keep
+    return g.cpu().numpy(), L.cpu().numpy()
+
+
+@pytest.mark.parametrize("make", [
+    lambda: workloads.config_small(),
+    lambda: workloads.scaled(workloads.config_occlusion(), width=72, height=52, spp=8, pairs=8),
+])
+def test_static_entry_matches_context_entry_twice(gpu_lib, make):
+    from paper_2211_17263_gb300 import api
+    wl = make()
+    target = _t(oracle.render_target(wl))
+    theta, sigma = _t(wl.theta0), _t(wl.sigma)
+    ctx = api.Context(0)
+    try:
+        scene = ctx.upload_scene(wl.scene, wl.bindings)
+        for step in (0, 1):  # two calls in a row: the shared scratch is reused
+            opts = scene.grad_opts(wl, step=step)
+            g_ref, L_ref = scene.smoothed_grad(theta, sigma, target, opts)
+            torch.cuda.synchronize()
+            g_ref, L_ref = g_ref.cpu().numpy(), L_ref.cpu().numpy()
+            g, L = _static_call(wl, theta, sigma, target, opts)
+            assert np.allclose(L, L_ref, rtol=1e-4, atol=1e-9), (L, L_ref)
+            w = np.ones((wl.renders, wl.D))
+            assert grad_rel_error(g, g_ref.astype(np.float64), w, L_ref) <= GRAD_REL, (g, g_ref)
+    finally:
+        ctx.close()
+
+
+def test_static_entry_rejects_oversized_requests(gpu_lib):
+    from paper_2211_17263_gb300 import capi
+    wl = workloads.config_small()
+    target, theta, sigma = _t(np.zeros((wl.height, wl.width, 4))), _t(wl.theta0), _t(wl.sigma)
+    too_many_pairs = capi.prdpt_grad_opts(pairs=33, width=wl.width, height=wl.height, spp=1, depth=1, rr_start=-1,
+                                          sampler=0, antithetic=1, crn=1, seed=0, step=0, block_pixels=0,
+                                          ctas_per_sm=0)
+    with pytest.raises(capi.PrdptError) as e:
+        _static_call(wl, theta, sigma, target, too_many_pairs)
+    assert e.value.code == capi.PRDPT_E_INVALID_ARG and "pairs" in str(e.value)
+    big = workloads.scaled(wl, width=4096, height=4096)
+    too_many_blocks = capi.prdpt_grad_opts(pairs=32, width=4096, height=4096, spp=1, depth=1, rr_start=-1,
+                                           sampler=0, antithetic=1, crn=1, seed=0, step=0, block_pixels=8,
+                                           ctas_per_sm=0)
+    big_target = _t(np.zeros((1, 4)))  # never read: the call is refused before any launch
+    with pytest.raises(capi.PrdptError) as e:
+        _static_call(big, theta, sigma, big_target, too_many_blocks)
+    assert e.value.code == capi.PRDPT_E_OUT_OF_BUDGET and "scratch" in str(e.value)
