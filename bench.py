@@ -158,6 +158,37 @@ def cpu_baseline(wl, target, nthreads=0, budget_s=10.0, max_steps=20):
                       f"{dt:.2f} s each", "cpu_model": _cpu_model()}
 
 
+def serving_bench(device, n_jobs, steps_per_job, gpaths_per_s, seed=0):
+    """Serving mix (jobs drawn from the small, occlusion and GI-box workloads with random
+    resolution 128-512, N in {8,16,32,64} renders, spp in {8,...,64}): Poisson arrivals at
+    1.5x the plain path's estimated capacity, served one job per launch ("plain") and with
+    continuous batching ("batched"), on the same arrival sequence."""
+    import workloads
+    from paper_2211_17263_gb300 import api
+    from paper_2211_17263_gb300.serve import Server
+
+    base = workloads.serving_mix(n_jobs=n_jobs, seed=seed)
+    mean_paths = float(np.mean([wl.paths_per_step for _, wl in base])) * steps_per_job
+    capacity_jobs_per_s = gpaths_per_s * 1e9 / mean_paths
+    rate = 1.5 * capacity_jobs_per_s
+    rng = np.random.default_rng(seed + 7)
+    t, arrivals = 0.0, []
+    for _, wl in base:
+        t += float(rng.exponential(1.0 / rate))
+        arrivals.append((t, wl))
+    out = {"jobs": n_jobs, "steps_per_job": steps_per_job, "arrival_rate_jobs_per_s": rate,
+           "hbm_budget_bytes": 150 * 10 ** 9}
+    for mode in ("plain", "batched"):
+        ctx = api.Context(device, hbm_budget_bytes=150 * 10 ** 9)
+        try:
+            rep, _ = Server(ctx, mode=mode, max_active=256).run(arrivals, steps_per_job=lambda wl: steps_per_job)
+        finally:
+            ctx.close()
+        out[mode] = {k: rep[k] for k in ("steps_per_s", "mpaths_per_s", "p50_ms", "p99_ms", "peak_active", "wall_s")}
+    out["batched_over_plain"] = out["batched"]["steps_per_s"] / out["plain"]["steps_per_s"]
+    return out
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
     if rank != 0:
@@ -196,6 +227,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-pixels", type=int, default=0, help="pixels per warp work item (8, 16, 32; 0 = auto)")
+    ap.add_argument("--serving-jobs", type=int, default=64, help="jobs in the serving mix (0 = skip serving)")
+    ap.add_argument("--serving-steps", type=int, default=4, help="steps per served job")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -343,6 +376,9 @@ def main():
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
         }
+        if world == 1 and args.serving_jobs > 0:
+            line["serving"] = serving_bench(local, args.serving_jobs, args.serving_steps,
+                                            line["mpaths_per_s"] / 1000.0)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, target_host)
         print(json.dumps(line), flush=True)

@@ -1,0 +1,87 @@
+"""Autotuner for the render kernel's launch shape.
+
+Candidates are (pixels per warp work item, resident CTAs per SM): the block of pixels a
+warp traces as one task pool, and how many 256-thread CTAs the persistent grid keeps per
+SM (the number of live warps). Each candidate is timed with CUDA events on the render
+launches of a throwaway resident job of the same shape; the fastest is cached in a JSON
+file keyed by the shape, so later jobs of that shape start from the tuned launch.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import numpy as np
+
+from . import api
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "prdpt_gb300", "autotune.json")
+CANDIDATES = [(px, cps) for px in (32, 16, 8) for cps in (3, 2, 1)]
+_lock = threading.Lock()
+
+
+def shape_key(wl) -> str:
+    sc = wl.scene
+    counts = [int((sc.prim_type == t).sum()) for t in range(3)]
+    mats = sorted(set(int(m) for m in sc.mat_type))
+    return (f"W{wl.width}xH{wl.height}_spp{wl.spp}_d{wl.depth}_rr{wl.rr_start}_R{wl.renders}_D{wl.D}"
+            f"_prims{counts[0]}-{counts[1]}-{counts[2]}_mats{'-'.join(map(str, mats))}")
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, table):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_candidate(scene: api.Scene, wl, target_host: np.ndarray, block_pixels: int, ctas_per_sm: int,
+                   steps: int = 3) -> float:
+    """Mean render-kernel time (ms) of `steps` resident steps with this launch shape."""
+    ctx = scene.ctx
+    job = api.Job(scene, wl, target_host, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm)
+    try:
+        job.step()  # warm-up
+        ctx.sync()
+        ctx.kernel_timing(True)
+        for _ in range(steps):
+            job.step()
+        ms, n = ctx.kernel_timing_read()
+        ctx.kernel_timing(False)
+        return ms / max(n, 1)
+    finally:
+        job.release()
+
+
+def autotune(scene: api.Scene, wl, target_host: np.ndarray, cache_path: str | None = DEFAULT_CACHE,
+             candidates=None, steps: int = 3, force: bool = False) -> dict:
+    """Best (block_pixels, ctas_per_sm) for this workload shape; cached by shape_key."""
+    key = shape_key(wl)
+    if cache_path and not force:
+        with _lock:
+            hit = _load(cache_path).get(key)
+        if hit:
+            return dict(hit, cached=True)
+    results = []
+    for px, cps in (candidates or CANDIDATES):
+        ms = time_candidate(scene, wl, target_host, px, cps, steps)
+        results.append({"block_pixels": px, "ctas_per_sm": cps, "ms": ms})
+    best = min(results, key=lambda r: r["ms"])
+    entry = {"block_pixels": best["block_pixels"], "ctas_per_sm": best["ctas_per_sm"], "ms": best["ms"],
+             "tried": results}
+    if cache_path:
+        with _lock:
+            table = _load(cache_path)
+            table[key] = entry
+            _store(cache_path, table)
+    return dict(entry, cached=False)
