@@ -120,6 +120,8 @@ typedef struct {
     uint32_t step;             /* optimiser step: Philox counter word 2 of every draw */
     int32_t block_pixels;      /* pixels per warp work item (8, 16 or 32); 0 = automatic */
     int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
+    int32_t no_path_sharing;   /* 0: with crn = 1, trace paths that no perturbation can touch once for
+                                  all renders (same result, bit for bit); 1: trace every render */
 } prdpt_grad_opts;
 
 /* A resident optimisation job: scene parameters, Adam state and target stay on
@@ -224,6 +226,9 @@ prdpt_status prdpt_counters_read(prdpt_ctx* ctx, uint64_t* counts_host);
  * count, then forgets them. Not for use inside CUDA-graph capture. */
 prdpt_status prdpt_kernel_timing_enable(prdpt_ctx* ctx, int32_t enable);
 prdpt_status prdpt_kernel_timing_read(prdpt_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Device memory the context currently holds (scenes, jobs, scratch), in bytes. */
+prdpt_status prdpt_memory_used(prdpt_ctx* ctx, uint64_t* bytes_out);
 
 /* Synchronise `stream` and check the context's device status word. */
 prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);

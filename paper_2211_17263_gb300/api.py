@@ -65,6 +65,9 @@ class Context:
     def kernel_timing_read(self):
         return capi.prdpt_kernel_timing_read(self.handle)
 
+    def memory_used(self) -> int:
+        return capi.prdpt_memory_used(self.handle)
+
     def sync(self, stream=None):
         capi.prdpt_sync(self.handle, _stream_ptr(stream))
 
@@ -118,12 +121,13 @@ class Scene:
         return out
 
     def grad_opts(self, wl, step=0, pairs=None, sampler=None, antithetic=None, crn=None, block_pixels=0,
-                  ctas_per_sm=0):
+                  ctas_per_sm=0, no_path_sharing=0):
         return capi.prdpt_grad_opts(
             pairs=wl.pairs if pairs is None else pairs, width=wl.width, height=wl.height, spp=wl.spp,
             depth=wl.depth, rr_start=wl.rr_start, sampler=wl.sampler if sampler is None else sampler,
             antithetic=wl.antithetic if antithetic is None else antithetic, crn=wl.crn if crn is None else crn,
-            seed=wl.seed, step=step, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm)
+            seed=wl.seed, step=step, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm,
+            no_path_sharing=no_path_sharing)
 
     def smoothed_grad(self, theta: torch.Tensor, sigma: torch.Tensor, target: torch.Tensor, opts,
                       grad: torch.Tensor | None = None, losses: torch.Tensor | None = None, stream=None):
@@ -140,7 +144,7 @@ class Job:
     """A resident optimisation job: parameters, Adam state and target live on the device."""
 
     def __init__(self, scene: Scene, wl, target_host: np.ndarray, step0=0, block_pixels=0, ctas_per_sm=0,
-                 anneal=None, lr=None, sampler=None):
+                 anneal=None, lr=None, sampler=None, no_path_sharing=0):
         self.scene = scene
         self.D = scene.D
         self.R = 2 * wl.pairs
@@ -151,7 +155,7 @@ class Job:
             raise ValueError("target must be [H, W, 4] float32")
         desc = capi.prdpt_job_desc(
             grad=scene.grad_opts(wl, step=step0, sampler=sampler, block_pixels=block_pixels,
-                                 ctas_per_sm=ctas_per_sm),
+                                 ctas_per_sm=ctas_per_sm, no_path_sharing=no_path_sharing),
             theta0_host=_np_ptr(self._theta0), sigma0_host=_np_ptr(self._sigma0), target_host=_np_ptr(self._target),
             lr=wl.lr if lr is None else lr, beta1=0.9, beta2=0.999, eps=1e-8, sigma_min=wl.sigma_min,
             anneal=wl.anneal if anneal is None else anneal, total_steps=wl.steps)

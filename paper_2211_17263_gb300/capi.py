@@ -32,7 +32,7 @@ EXPORTS = [
     "prdpt_render_batch", "prdpt_sample_perturbations", "prdpt_smoothed_grad", "prdpt_adam_step",
     "prdpt_job_create", "prdpt_step", "prdpt_step_batch", "prdpt_job_read", "prdpt_job_release",
     "prdpt_philox_words", "prdpt_counters_enable", "prdpt_counters_read", "prdpt_kernel_timing_enable",
-    "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static",
+    "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static", "prdpt_memory_used",
 ]
 
 
@@ -61,7 +61,7 @@ class prdpt_grad_opts(C.Structure):
         ("pairs", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32),
         ("depth", C.c_int32), ("rr_start", C.c_int32), ("sampler", C.c_int32), ("antithetic", C.c_int32),
         ("crn", C.c_int32), ("seed", C.c_uint64), ("step", C.c_uint32), ("block_pixels", C.c_int32),
-        ("ctas_per_sm", C.c_int32),
+        ("ctas_per_sm", C.c_int32), ("no_path_sharing", C.c_int32),
     ]
 
 
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
         "prdpt_kernel_timing_enable": ([vp, i32], i32),
         "prdpt_kernel_timing_read": ([vp, P(C.c_double), P(C.c_int64)], i32),
         "prdpt_sync": ([vp, vp], i32),
+        "prdpt_memory_used": ([vp, P(u64)], i32),
         "prdpt_smoothed_grad_static": ([P(prdpt_scene_desc), P(prdpt_param_binding), i32, vp, vp,
                                         P(prdpt_grad_opts), vp, vp, vp, vp, C.c_char_p, C.c_size_t], i32),
     }
@@ -241,6 +242,12 @@ def prdpt_smoothed_grad_static(desc, binds, D, theta_dev, sigma_dev, opts, targe
     if code != PRDPT_OK:
         raise PrdptError(code, "prdpt_smoothed_grad_static", err.value.decode(errors="replace"))
     return code
+
+
+def prdpt_memory_used(ctx) -> int:
+    n = C.c_uint64()
+    check(load().prdpt_memory_used(ctx, C.byref(n)), "prdpt_memory_used", ctx)
+    return n.value
 
 
 def prdpt_sync(ctx, stream):

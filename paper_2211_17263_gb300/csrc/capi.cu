@@ -46,10 +46,12 @@ struct Job {
     // device buffers
     float *theta = nullptr, *m = nullptr, *v = nullptr, *sigma0 = nullptr, *grad = nullptr, *losses = nullptr;
     float* w = nullptr;
+    unsigned long long* share = nullptr;
+    int* aff = nullptr;
     double *partials = nullptr, *losses_d = nullptr;
     unsigned* rdone = nullptr;
     int* step = nullptr;
-    unsigned *done = nullptr, *queue = nullptr;
+    unsigned *done = nullptr, *queue = nullptr, *share_ctl = nullptr;
     InstScene* scenes = nullptr;
     float4* target = nullptr;
     InstJob inst{};
@@ -81,7 +83,11 @@ struct prdpt_ctx {
     size_t s_losses_n = 0;
     unsigned* s_rdone = nullptr;  // per-render block counters (all zero between launches)
     size_t s_rdone_n = 0;
-    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2] batch queue
+    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2] batch queue, [4..5] sharing counters
+    unsigned long long* s_share = nullptr;  // path sharing: [tiles][96] radiance then [tiles][32] masks
+    size_t s_share_n = 0;
+    int* s_aff = nullptr;         // path sharing: list of blocks with affected paths
+    size_t s_aff_n = 0;
     // packed launches
     std::vector<int> batch_ids;
     InstJob* d_inst = nullptr;
@@ -206,6 +212,10 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStr
     }
     cudaError_t e = launch_trace(L, render, grid_for(c, L.total_items, render, ctas_per_sm), stream);
     if (e != cudaSuccess) return e;
+    if (!render && !L.jobs && L.job0.share) {  // per-render pass over the blocks with affected paths
+        e = launch_trace_affected(L, grid_for(c, 1 << 30, false, ctas_per_sm), stream);
+        if (e != cudaSuccess) return e;
+    }
     if (c->timing) {
         e = cudaEventRecord(ev.second, stream);
         if (e != cudaSuccess) return e;
@@ -397,6 +407,34 @@ prdpt_status prdpt_scene_release(prdpt_ctx* c, int32_t scene_id) {
     return PRDPT_OK;
 }
 
+// Path sharing across renders is exact when all renders share their path samples (crn)
+// and only geometry is perturbed: emitters and their materials must stay fixed, at most
+// kMaxVariant primitives move, and a pixel's samples fit one 64-bit mask.
+static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o) {
+    J.share = 0;
+    J.n_var = 0;
+    J.var_prims = 0u;
+    J.var_mats = 0u;
+    if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp) return;
+    bool var_prim[kMaxPrims] = {};
+    for (int d = 0; d < B.D; ++d) {
+        const int k = B.bind_kind[d], idx = B.bind_index[d];
+        if (k == kBindEmission) return;
+        if (k == kBindAlbedo) J.var_mats |= 1u << idx;
+        if (k == kBindPos || k == kBindRadius) var_prim[idx] = true;
+    }
+    for (int i = 0; i < B.n_prims; ++i) {
+        const float* mp = B.mat_param[B.prim_mat[i]];
+        const bool emitter = mp[3] > 0.f || mp[4] > 0.f || mp[5] > 0.f;
+        if (emitter && (var_prim[i] || ((J.var_mats >> B.prim_mat[i]) & 1u))) return;
+        if (!var_prim[i]) continue;
+        if (J.n_var == kMaxVariant) return;
+        J.var_slot[J.n_var++] = B.prim_slot[i];
+        J.var_prims |= 1u << B.prim_slot[i];
+    }
+    J.share = 1;
+}
+
 static void fill_inst_common(InstJob& J, const Scene* s, int R, int D, int W, int H) {
     std::memset(&J, 0, sizeof(J));
     J.base = s->dev;
@@ -513,9 +551,15 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     if (prdpt_status st = check_grad_opts(o)) return st;
     PRDPT_CUDA(cudaSetDevice(c->device));
     const int R = 2 * o->pairs, D = s->D;
-    const int px = choose_block(c, o->block_pixels, R, o->width, o->height, false);
+    TraceJob probe{};
+    fill_share(probe, s->host, o);  // path sharing: items are blocks, not (render, block)
+    const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, o->width, o->height, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, o->width, o->height, &bw, &bh, &tiles_x, &tiles);
+    if (probe.share) {
+        if (prdpt_status st = grow(c, &c->s_share, &c->s_share_n, (size_t)tiles * 128)) return st;
+        if (prdpt_status st = grow(c, &c->s_aff, &c->s_aff_n, (size_t)tiles)) return st;
+    }
     if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)R)) return st;
     if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)R * D > (size_t)kMaxD ? (size_t)R * D : (size_t)kMaxD))
         return st;
@@ -531,6 +575,7 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     IL.job0.w_out = c->s_w;
     IL.total_blocks = R;
     IL.queue_reset = c->s_ctl + 0;
+    IL.share_reset = probe.share ? c->s_ctl + 4 : nullptr;
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
     TraceJob& J = TL.job0;
@@ -557,7 +602,15 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     J.tiles = tiles;
     J.n_prims = s->host.n_prims;
     J.n_mats = s->host.n_mats;
-    TL.total_items = R * tiles;
+    fill_share(J, s->host, o);
+    if (J.share) {
+        J.share_acc = c->s_share;
+        J.share_mask = c->s_share + (size_t)tiles * 96;
+        J.aff_tiles = c->s_aff;
+        J.aff_count = c->s_ctl + 4;
+        J.queue_b = c->s_ctl + 5;
+    }
+    TL.total_items = J.share ? tiles : R * tiles;
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
@@ -590,7 +643,9 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     j->D = s->D;
     j->R = 2 * o->pairs;
     const int D = j->D, R = j->R, W = o->width, H = o->height;
-    const int px = choose_block(c, o->block_pixels, R, W, H, false);
+    TraceJob probe{};
+    fill_share(probe, s->host, o);
+    const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, W, H, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, W, H, &bw, &bh, &tiles_x, &tiles);
     j->tiles = tiles;
@@ -602,7 +657,9 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const size_t off_p = (off_w + sizeof(float) * R * D + 255) & ~size_t(255);
     const size_t off_s = (off_p + sizeof(double) * R * tiles + 255) & ~size_t(255);
     const size_t off_t = (off_s + sizeof(InstScene) * R + 255) & ~size_t(255);
-    const size_t total = off_t + sizeof(float4) * (size_t)W * H;
+    const size_t off_sh = (off_t + sizeof(float4) * (size_t)W * H + 255) & ~size_t(255);
+    const size_t off_af = off_sh + (probe.share ? sizeof(unsigned long long) * 128 * (size_t)tiles : 0);
+    const size_t total = off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0);
     void* base = nullptr;
     if (prdpt_status st = dev_alloc(c, &base, total)) {
         delete j;
@@ -621,10 +678,15 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     j->step = reinterpret_cast<int*>(j->rdone + kMaxRenders);
     j->done = reinterpret_cast<unsigned*>(j->step + 1);
     j->queue = j->done + 1;
+    unsigned* share_ctl = j->queue + 1;  // [0] affected-block count, [1] second-pass queue
     j->w = reinterpret_cast<float*>(b + off_w);
     j->partials = reinterpret_cast<double*>(b + off_p);
     j->scenes = reinterpret_cast<InstScene*>(b + off_s);
     j->target = reinterpret_cast<float4*>(b + off_t);
+    if (probe.share) {
+        j->share = reinterpret_cast<unsigned long long*>(b + off_sh);
+        j->aff = reinterpret_cast<int*>(b + off_af);
+    }
     cudaError_t e = cudaMemset(base, 0, off_w);
     if (e == cudaSuccess) e = cudaMemcpy(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
@@ -677,6 +739,15 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     T.tiles = tiles;
     T.n_prims = s->host.n_prims;
     T.n_mats = s->host.n_mats;
+    fill_share(T, s->host, o);
+    if (T.share) {
+        T.share_acc = j->share;
+        T.share_mask = j->share + (size_t)tiles * 96;
+        T.aff_tiles = j->aff;
+        T.aff_count = share_ctl;
+        T.queue_b = share_ctl + 1;
+        j->share_ctl = share_ctl;
+    }
     s->jobs++;
     c->jobs.push_back(j);
     *job_out = (int)c->jobs.size() - 1;
@@ -692,10 +763,11 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     IL.job0 = j->inst;
     IL.total_blocks = j->R;
     IL.queue_reset = j->queue;
+    IL.share_reset = j->trace.share ? j->share_ctl : nullptr;
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
     TL.job0 = j->trace;
-    TL.total_items = j->R * j->tiles;
+    TL.total_items = j->trace.share ? j->tiles : j->R * j->tiles;
     TL.queue = j->queue;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
@@ -721,6 +793,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             inst[i].block_begin = blocks;
             blocks += j->R;
             trace[i] = j->trace;
+            trace[i].share = 0;  // packed launches trace every render of every job
             trace[i].item_begin = items;
             items += j->R * j->tiles;
         }
@@ -850,6 +923,13 @@ prdpt_status prdpt_kernel_timing_read(prdpt_ctx* c, double* total_ms, int64_t* l
     *launches = (int64_t)c->ev_used.size();
     for (auto& ev : c->ev_used) c->ev_free.push_back(ev);
     c->ev_used.clear();
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_memory_used(prdpt_ctx* c, uint64_t* bytes_out) {
+    if (!c || !bytes_out) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    *bytes_out = c->used;
     return PRDPT_OK;
 }
 

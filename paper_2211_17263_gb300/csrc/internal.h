@@ -112,7 +112,21 @@ struct TraceJob {
     int bw, bh, tiles_x, tiles;
     int n_prims, n_mats;      // used primitive and material records (staging size)
     int item_begin;           // first work item of this job in a packed launch
+    // Path sharing across renders (common random numbers, geometry-only bindings): a work
+    // item is one pixel block of all R renders. share = 0 disables it.
+    int share;
+    unsigned long long* share_acc;   // [tiles][3][32] shared radiance of blocks with affected paths
+    unsigned long long* share_mask;  // [tiles][32] affected samples per pixel slot
+    int* aff_tiles;           // [tiles] blocks with affected paths (appended by the shared pass)
+    unsigned* aff_count;      // number of entries in aff_tiles (zeroed by the instantiation launch)
+    unsigned* queue_b;        // work queue of the per-render pass (zeroed by the instantiation launch)
+    int n_var;                // perturbed primitives (<= kMaxVariant)
+    int var_slot[4];          // their record slots
+    unsigned var_prims;       // record-slot bitmask of perturbed primitives
+    unsigned var_mats;        // bitmask of materials whose parameters are bound
 };
+constexpr int kMaxVariant = 4;
+constexpr int kMaxShareSpp = 64;  // one 64-bit sample mask per pixel
 
 struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)
@@ -128,11 +142,14 @@ struct InstLaunch {
     const InstJob* jobs;
     int njobs, total_blocks;
     unsigned* queue_reset;    // zeroed by CTA 0
+    unsigned* share_reset;    // [2] zeroed by CTA 0 (path-sharing list count and second queue) or null
 };
 
 // Launchers (kernels.cu). All enqueue on `stream` and return the launch error.
 cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream);
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream);
+// Second pass of a path-sharing job: the affected paths of the listed blocks, per render.
+cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t stream);
 cudaError_t launch_adam(int D, float* theta, float* m, float* v, const float* g, int t, float lr, float b1,
                         float b2, float eps, cudaStream_t stream);
 cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, unsigned c2, unsigned c3, int n,

@@ -114,7 +114,13 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     __shared__ int s_job;
 
     const int tid = threadIdx.x;
-    if (blockIdx.x == 0 && tid == 0 && L.queue_reset) *L.queue_reset = 0u;
+    if (blockIdx.x == 0 && tid == 0) {
+        if (L.queue_reset) *L.queue_reset = 0u;
+        if (L.share_reset) {
+            L.share_reset[0] = 0u;
+            L.share_reset[1] = 0u;
+        }
+    }
     if (tid == 0) {
         int j = 0;
         if (L.jobs) {
@@ -381,27 +387,33 @@ struct Hit {
     int type;
 };
 
-template <bool kCount>
-__device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 d, Counters& cnt) {
+// Closest hit over all primitives, grouped by type. With kSkip, primitives whose
+// record slot is set in `skip` are left out (the perturbed ones, in shared mode).
+template <bool kCount, bool kSkip>
+__device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 d, Counters& cnt, unsigned skip) {
     Hit h{INFINITY, -1, 0};
     const int ns = S.n_sph, nq = S.n_quad, nb = S.n_box;
     if (kCount) {
-        cnt.sph += ns;
-        cnt.quad += nq;
-        cnt.box += nb;
+        const unsigned sk = kSkip ? skip : 0u;
+        cnt.sph += ns - __popc(sk & ((1u << ns) - 1u));
+        cnt.quad += nq - __popc((sk >> ns) & ((1u << nq) - 1u));
+        cnt.box += nb - __popc((sk >> (ns + nq)) & ((1u << nb) - 1u));
         ++cnt.rays;
     }
     for (int i = 0; i < ns; ++i) {
+        if (kSkip && ((skip >> i) & 1u)) continue;
         const float t = sphere_t(S, i, o, d);
         if (t < h.t) { h.t = t; h.slot = i; h.type = kSphere; }
     }
     for (int i = ns; i < ns + nq; ++i) {
+        if (kSkip && ((skip >> i) & 1u)) continue;
         const float t = quad_t(S, i, o, d);
         if (t < h.t) { h.t = t; h.slot = i; h.type = kQuad; }
     }
     if (nb) {
         const float3 inv = rcp3(d);
         for (int i = ns + nq; i < ns + nq + nb; ++i) {
+            if (kSkip && ((skip >> i) & 1u)) continue;
             const float t = box_t(S, i, o, inv);
             if (t < h.t) { h.t = t; h.slot = i; h.type = kBox; }
         }
@@ -409,30 +421,59 @@ __device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 
     return h;
 }
 
-// Is anything but primitive slot `skip` hit closer than dist?
-template <bool kCount>
-__device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d, float dist, int skip, Counters& cnt) {
+// Is anything but primitive slot `light` (and, with kSkip, the slots in `skip`) hit
+// closer than dist?
+template <bool kCount, bool kSkip>
+__device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d, float dist, int light,
+                                         Counters& cnt, unsigned skip) {
     const int ns = S.n_sph, nq = S.n_quad, nb = S.n_box;
     if (kCount) ++cnt.shadow;
     for (int i = 0; i < ns; ++i) {
-        if (i == skip) continue;
+        if (i == light || (kSkip && ((skip >> i) & 1u))) continue;
         if (kCount) ++cnt.sph;
         if (sphere_t(S, i, o, d) < dist) return true;
     }
     for (int i = ns; i < ns + nq; ++i) {
-        if (i == skip) continue;
+        if (i == light || (kSkip && ((skip >> i) & 1u))) continue;
         if (kCount) ++cnt.quad;
         if (quad_t(S, i, o, d) < dist) return true;
     }
     if (nb) {
         const float3 inv = rcp3(d);
         for (int i = ns + nq; i < ns + nq + nb; ++i) {
-            if (i == skip) continue;
+            if (i == light || (kSkip && ((skip >> i) & 1u))) continue;
             if (kCount) ++cnt.box;
             if (box_t(S, i, o, inv) < dist) return true;
         }
     }
     return false;
+}
+
+// Union boxes of the perturbed primitives over all R renders (shared mode), inflated so
+// that the test below is conservative against the exact per-render intersection tests.
+struct VarBoxes {
+    float4 lo[kMaxVariant], hi[kMaxVariant];
+    int n;
+    unsigned skip, mats;
+};
+
+// Does the segment o + t d, 0 <= t <= tmax, touch any union box?
+template <bool kCount>
+__device__ __forceinline__ bool touches_variant(const VarBoxes& V, float3 o, float3 d, float tmax, Counters& cnt) {
+    const float3 inv = rcp3(d);
+    const float tm = tmax * 1.0001f + 1e-3f;
+    bool hit = false;
+    for (int k = 0; k < V.n; ++k) {
+        const float3 lo = xyz(V.lo[k]), hi = xyz(V.hi[k]);
+        const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+        const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+        const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+        const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+        const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tm));
+        hit = hit || (tn <= tf);
+    }
+    if (kCount) cnt.box += V.n;
+    return hit;
 }
 
 __device__ __forceinline__ uint4 path_words(const InstScene& S, unsigned pixel, int s, int b, int slot) {
@@ -477,15 +518,25 @@ __device__ __forceinline__ void start_path(const InstScene& S, int W, int H, int
 }
 
 // One surface interaction of a path: unidirectional path tracing with next-event
-// estimation on diffuse vertices. Returns true when the path has ended.
+// estimation on diffuse vertices. Returns kEnded when the path has ended.
 // Random slots of vertex b: slot 0 = (light point u, v, BSDF u1, u2); slot 1 =
 // (light choice, Russian roulette, dielectric choice), drawn only when needed.
-template <bool kCount>
-__device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt) {
-    const Hit h = closest_hit<kCount>(S, p.o, p.d, cnt);
+//
+// With kShared (path sharing across renders), the scene is the invariant part only and
+// the function returns kAffected, abandoning the path, as soon as a ray segment touches a
+// perturbed primitive's union box or the path hits a material whose parameters are bound:
+// such paths are traced again per render. Otherwise the path is exactly what every render
+// traces, because all renders share its random numbers.
+constexpr int kLive = 0, kEnded = 1, kAffected = 2;
+
+template <bool kCount, bool kShared>
+__device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt,
+                                       const VarBoxes* V = nullptr) {
+    const Hit h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
+    if (kShared && touches_variant<kCount>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, cnt)) return kAffected;
     if (h.slot < 0) {
         p.L = p.L + p.beta * xyz(S.bg);
-        return true;
+        return kEnded;
     }
     if (kCount) ++cnt.vertices;
     const float3 pt = p.o + p.d * h.t;
@@ -502,6 +553,7 @@ __device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_st
         ng = box_normal(S, h.slot, p.o, p.d, rcp3(p.d));
         mat = as_int(S.prim[h.slot][0].w);
     }
+    if (kShared && ((V->mats >> mat) & 1u)) return kAffected;
     const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
     const int mtype = as_int(m0.w);
     const float3 albedo = xyz(m0), emission = xyz(m1);
@@ -540,14 +592,16 @@ __device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_st
             const float3 wi = dv * inv_dist;
             const float cx = dot3(ns, wi), cl = -dot3(ny, wi);
             if (cx > 0.0f && cl > 0.0f) {
-                if (!occluded<kCount>(S, po, wi, dist2 * inv_dist, lt.y, cnt)) {
+                const float dist = dist2 * inv_dist;
+                if (!occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u)) {
+                    if (kShared && touches_variant<kCount>(*V, po, wi, dist, cnt)) return kAffected;
                     const float g = cx * cl * (inv_dist * inv_dist) * S.light_area[li] * float(S.n_lights) *
                                     0.3183098861837907f;
                     p.L = p.L + p.beta * albedo * xyz(S.mat[lt.w][1]) * g;
                 }
             }
         }
-        if (last) return true;
+        if (last) return kEnded;
         const float u1 = u01(w0.z), u2 = u01(w0.w);
         const float rad = u1 * rsqrtf(u1);
         float sp, cp;
@@ -561,7 +615,7 @@ __device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_st
         p.d = normalized(wo);
         p.specular = false;
     } else if (mtype == kMirror) {
-        if (last) return true;
+        if (last) return kEnded;
         if (rr) w1 = path_words(S, p.pixel, p.s, p.b, 1);
         const float3 ns = dot3(ng, p.d) < 0.0f ? ng : ng * -1.0f;
         p.d = normalized(p.d - ns * (2.0f * dot3(p.d, ns)));
@@ -569,7 +623,7 @@ __device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_st
         p.beta = p.beta * albedo;
         p.specular = true;
     } else {  // smooth dielectric: exact unpolarised Fresnel, reflect or refract
-        if (last) return true;
+        if (last) return kEnded;
         w1 = path_words(S, p.pixel, p.s, p.b, 1);
         float ci = -dot3(p.d, ng);
         float eta;
@@ -602,14 +656,14 @@ __device__ __forceinline__ bool advance(const InstScene& S, int depth, int rr_st
         p.beta = p.beta * albedo;
         p.specular = true;
     }
-    if (maxc(p.beta) <= 0.0f) return true;
+    if (maxc(p.beta) <= 0.0f) return kEnded;
     if (rr) {  // Russian roulette on slot 1's second uniform
         const float q = fminf(0.95f, maxc(p.beta));
-        if (u01(w1.y) >= q) return true;
+        if (u01(w1.y) >= q) return kEnded;
         p.beta = p.beta * __fdividef(1.0f, q);
     }
     ++p.b;
-    return false;
+    return kLive;
 }
 
 // ---------------------------------------------------------------------------
@@ -709,22 +763,234 @@ __device__ void finish_render(const TraceJob& J, int r, int lane) {
     if (last) finish_job(J, lane);
 }
 
-template <bool kRender, bool kCount>
+// Per-warp shared-memory workspace of the render kernel.
+struct WarpSmem {
+    InstScene scene;                  // the render being traced (render 0 in shared phase A)
+    TraceJob job;
+    unsigned long long acc[3][32];    // radiance of the block's pixels, 2^-32 fixed point
+    unsigned long long accr[3][32];   // shared mode: per-render radiance of the affected paths
+    unsigned long long mask[32];      // shared mode: affected samples of each pixel slot
+    VarBoxes vb;                      // shared mode: union boxes of the perturbed primitives
+};
+
+// Copy render r's scene (header, used materials, used primitives) into the warp's slot.
+__device__ __forceinline__ void stage_scene(WarpSmem& W, const TraceJob& J, int r, int lane) {
+    const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
+    float4* dst = reinterpret_cast<float4*>(&W.scene);
+    constexpr int kHead = int(offsetof(InstScene, mat) / 16);
+    constexpr int kPrim = int(offsetof(InstScene, prim) / 16);
+    const int nm = 2 * J.n_mats, np = 4 * J.n_prims;
+    for (int i = lane; i < kHead + nm + np; i += 32) {
+        const int o = (i < kHead + nm) ? i : kPrim + (i - kHead - nm);
+        dst[o] = __ldg(src + o);
+    }
+    __syncwarp();
+}
+
+// Union boxes of each perturbed primitive over the job's R renders (shared mode).
+__device__ void build_var_boxes(WarpSmem& W, const TraceJob& J, int lane) {
+    for (int k = 0; k < J.n_var; ++k) {
+        const int slot = J.var_slot[k];
+        float3 lo = f3(INFINITY, INFINITY, INFINITY), hi = f3(-INFINITY, -INFINITY, -INFINITY);
+        for (int r = lane; r < J.R; r += 32) {
+            const float4* P = J.scenes[r].prim[slot];
+            float3 a, b;
+            if (slot < J.scenes[r].n_sph) {
+                const float4 c = __ldg(P);
+                const float rad = fabsf(c.w);
+                a = xyz(c) - f3(rad, rad, rad);
+                b = xyz(c) + f3(rad, rad, rad);
+            } else if (slot < J.scenes[r].n_sph + J.scenes[r].n_quad) {
+                const float3 c = xyz(__ldg(P)), u = xyz(__ldg(P + 2)), v = xyz(__ldg(P + 3));
+                const float3 e = f3(0.5f * (fabsf(u.x) + fabsf(v.x)), 0.5f * (fabsf(u.y) + fabsf(v.y)),
+                                    0.5f * (fabsf(u.z) + fabsf(v.z)));
+                a = c - e;
+                b = c + e;
+            } else {
+                a = xyz(__ldg(P));
+                b = xyz(__ldg(P + 1));
+            }
+            lo = f3(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z));
+            hi = f3(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+            lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+            lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+            hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+            hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+            hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+        }
+        if (lane == 0) {  // inflate: 1e-3 scene units plus 1e-5 relative
+            const float3 m = f3(1e-3f + 1e-5f * fmaxf(fabsf(lo.x), fabsf(hi.x)),
+                                1e-3f + 1e-5f * fmaxf(fabsf(lo.y), fabsf(hi.y)),
+                                1e-3f + 1e-5f * fmaxf(fabsf(lo.z), fabsf(hi.z)));
+            W.vb.lo[k] = make_float4(lo.x - m.x, lo.y - m.y, lo.z - m.z, 0.f);
+            W.vb.hi[k] = make_float4(hi.x + m.x, hi.y + m.y, hi.z + m.z, 0.f);
+        }
+    }
+    if (lane == 0) {
+        W.vb.n = J.n_var;
+        W.vb.skip = J.var_prims;
+        W.vb.mats = J.var_mats;
+    }
+    __syncwarp();
+}
+
+// k-th (0-based) set bit of m.
+__device__ __forceinline__ int nth_set_bit(unsigned long long m, int k) {
+    int pos = 0;
+    unsigned x = unsigned(m);
+    const int c = __popc(x);
+    if (k >= c) {
+        k -= c;
+        x = unsigned(m >> 32);
+        pos = 32;
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int cw = __popc(x & ((1u << w) - 1u));
+        if (k >= cw) {
+            k -= cw;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// Trace `ntasks` path tasks with the warp as a pool: each lane holds one live path and,
+// when it ends, takes the next task (ballot + popc). decode(task, slot, sample) maps a
+// task to its pixel slot and sample; every lane calls it (it may use warp shuffles).
+// Ended paths add their radiance to acc[.][slot]; in shared mode, affected paths set
+// their sample's bit in mask[slot] instead.
+template <bool kCount, bool kShared, class Decode>
+__device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, int ntasks, int x0, int y0, int vw,
+                                         unsigned magic_w, Decode decode, unsigned long long (&acc)[3][32],
+                                         unsigned long long* mask, const VarBoxes* V, Counters& cnt, int lane) {
+    const unsigned lt_mask = (1u << lane) - 1u;
+    Path p;
+    int task = lane;
+    bool alive = task < ntasks;
+    int slot, smp;
+    decode(alive ? task : 0, slot, smp);
+    if (alive) {
+        const int row = div_magic(slot, vw, magic_w);
+        start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+        if (kCount) ++cnt.paths;
+    }
+    int next = 32;
+    while (__any_sync(kFull, alive)) {
+        int st = kLive;
+        if (alive) st = advance<kCount, kShared>(S, J.depth, J.rr_start, p, cnt, V);
+        const bool ended = alive && st != kLive;
+        if (ended && st == kEnded) {
+            atomicAdd(&acc[0][p.slot], to_fixed(p.L.x));
+            atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
+            atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
+        }
+        if (kShared && ended && st == kAffected) atomicOr(mask + p.slot, 1ull << p.s);
+        const unsigned need = __ballot_sync(kFull, ended);
+        const int mine = next + __popc(need & lt_mask);
+        decode((ended && mine < ntasks) ? mine : 0, slot, smp);
+        if (ended) {
+            task = mine;
+            alive = task < ntasks;
+            if (alive) {
+                const int row = div_magic(slot, vw, magic_w);
+                start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+                if (kCount) ++cnt.paths;
+            }
+        }
+        next += __popc(need);
+    }
+    __syncwarp();
+}
+
+// Pixel means of render r's block (acc, plus accr in shared mode), then either the image
+// (render mode) or the squared error, the block partial and the render/job completion.
+template <bool kRender>
+__device__ __forceinline__ void block_epilogue(const TraceJob& J, int r, int t, const WarpSmem& W, bool with_accr,
+                                               int x0, int y0, int vw, int npx, int lane) {
+    double e = 0.0;
+    const int px = x0 + lane % vw, py = y0 + lane / vw;
+    if (lane < npx && px < J.W && py < J.H) {
+        const double inv = 1.0 / (double(J.spp) * double(kFix));
+        unsigned long long ax = W.acc[0][lane], ay = W.acc[1][lane], az = W.acc[2][lane];
+        if (with_accr) {
+            ax += W.accr[0][lane];
+            ay += W.accr[1][lane];
+            az += W.accr[2][lane];
+        }
+        const double Ix = double(ax) * inv, Iy = double(ay) * inv, Iz = double(az) * inv;
+        if (kRender) {
+            J.images[(size_t(r) * J.H + py) * J.W + px] = make_float4(float(Ix), float(Iy), float(Iz), 0.0f);
+        } else {
+            const float4 T = __ldg(J.target + size_t(py) * J.W + px);
+            const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
+            e = ex * ex + ey * ey + ez * ez;
+        }
+    }
+    if (!kRender) {
+        e = warp_sum_d(e);
+        unsigned rlast = 0;
+        if (lane == 0) {
+            J.partials[size_t(r) * J.tiles + t] = e;
+            __threadfence();
+            rlast = (atomicAdd(J.render_done + r, 1u) == unsigned(J.tiles - 1));
+        }
+        rlast = __shfl_sync(kFull, rlast, 0);
+        if (rlast) finish_render(J, r, lane);  // a5/a6/a7 for the last block of a render
+    }
+    __syncwarp();
+}
+
+// The same squared error for all R renders of a block whose paths are all shared:
+// R partials, one fence, R completion counts (lanes take one render each).
+__device__ __forceinline__ void shared_block_epilogue(const TraceJob& J, int t, const WarpSmem& W, int x0, int y0,
+                                                      int vw, int npx, int lane) {
+    double e = 0.0;
+    const int px = x0 + lane % vw, py = y0 + lane / vw;
+    if (lane < npx && px < J.W && py < J.H) {
+        const double inv = 1.0 / (double(J.spp) * double(kFix));
+        const double Ix = double(W.acc[0][lane]) * inv, Iy = double(W.acc[1][lane]) * inv,
+                     Iz = double(W.acc[2][lane]) * inv;
+        const float4 T = __ldg(J.target + size_t(py) * J.W + px);
+        const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
+        e = ex * ex + ey * ey + ez * ez;
+    }
+    e = warp_sum_d(e);
+    for (int r = lane; r < J.R; r += 32) J.partials[size_t(r) * J.tiles + t] = e;
+    __threadfence();
+    __syncwarp();
+    for (int r0 = 0; r0 < J.R; r0 += 32) {
+        const int r = r0 + lane;
+        const bool last = r < J.R && atomicAdd(J.render_done + r, 1u) == unsigned(J.tiles - 1);
+        unsigned lastmask = __ballot_sync(kFull, last);
+        while (lastmask) {  // renders this block completed
+            const int src = __ffs(lastmask) - 1;
+            lastmask &= lastmask - 1;
+            finish_render(J, r0 + src, lane);
+        }
+    }
+    __syncwarp();
+}
+
+// kShare: every item is a pixel block of all renders of a path-sharing job (single-job
+// launches only); otherwise every item is one render's block and job.share is ignored.
+template <bool kRender, bool kCount, bool kShare>
 __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_constant__ TraceLaunch L) {
-    __shared__ InstScene s_scene[kWarps];
-    __shared__ TraceJob s_job[kWarps];
-    __shared__ unsigned long long s_acc[kWarps][3][32];
+    __shared__ WarpSmem s_warp[kWarps];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    InstScene& S = s_scene[warp];
-    TraceJob& J = s_job[warp];
-    unsigned long long(&acc)[3][32] = s_acc[warp];
+    WarpSmem& W = s_warp[warp];
+    const TraceJob& J = W.job;
     int cur_job = -1, cur_r = -1;
     Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 
     for (;;) {
-        // ---- pop one (job, render, block) work item for this warp ----------------
+        // ---- pop one work item for this warp --------------------------------------
         unsigned item = 0;
         int j = 0;
         if (lane == 0) {
@@ -743,103 +1009,147 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_
         j = __shfl_sync(kFull, j, 0);
         if (j != cur_job) {
             const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + j : &L.job0);
-            unsigned* dst = reinterpret_cast<unsigned*>(&J);
+            unsigned* dst = reinterpret_cast<unsigned*>(&W.job);
             for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
             __syncwarp();
+            if (kShare) build_var_boxes(W, J, lane);
             cur_job = j;
             cur_r = -1;
         }
         const int li = int(item) - J.item_begin;
-        const int r = li % J.R, t = li / J.R;  // render-interleaved: neighbouring items share pixels
+        const int r = kShare ? 0 : li % J.R;  // render-interleaved: neighbouring items share pixels
+        const int t = kShare ? li : li / J.R;
         if (r >= J.R || t >= J.tiles) {
             if (lane == 0) atomicOr(L.status, kStatusBadItem);
             break;
         }
-        if (r != cur_r) {  // a2 -> shared memory: header, used materials, used primitives
-            const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
-            float4* dst = reinterpret_cast<float4*>(&S);
-            constexpr int kHead = int(offsetof(InstScene, mat) / 16);
-            constexpr int kPrim = int(offsetof(InstScene, prim) / 16);
-            const int nm = 2 * J.n_mats, np = 4 * J.n_prims;
-            for (int i = lane; i < kHead + nm + np; i += 32) {
-                const int o = (i < kHead) ? i : (i < kHead + nm ? i : kPrim + (i - kHead - nm));
-                dst[o] = __ldg(src + o);
-            }
-            __syncwarp();
+        if (r != cur_r) {  // a2 -> shared memory
+            stage_scene(W, J, r, lane);
             cur_r = r;
         }
 
-        // ---- a3: trace the block's pixels x samples as a pool of path tasks --------
+        // ---- block geometry and task decoding ------------------------------------------
         const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
         const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
         const int npx = vw * vh, ntasks = npx * J.spp;
         // task -> (pixel slot, sample) by multiply-high with m = ceil(2^32 / d): exact for
         // n < 2^32 / d (here n < 2^21, d <= 32); d = 1 has no 32-bit m and is special-cased
         const unsigned magic = 0xffffffffu / unsigned(npx) + 1u, magic_w = 0xffffffffu / unsigned(vw) + 1u;
-        acc[0][lane] = 0ull;
-        acc[1][lane] = 0ull;
-        acc[2][lane] = 0ull;
-        __syncwarp();
-        Path p;
-        int task = lane;
-        bool alive = task < ntasks;
-        if (alive) {
-            const int smp = div_magic(task, npx, magic), slot = task - smp * npx;
-            const int row = div_magic(slot, vw, magic_w);
-            start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
-            if (kCount) ++cnt.paths;
-        }
-        int next = 32;
-        while (__any_sync(kFull, alive)) {
-            bool ended = false;
-            if (alive) ended = advance<kCount>(S, J.depth, J.rr_start, p, cnt);
-            if (ended) {
-                atomicAdd(&acc[0][p.slot], to_fixed(p.L.x));
-                atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
-                atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
-            }
-            const unsigned need = __ballot_sync(kFull, ended);  // lanes whose path ended take new tasks
-            if (ended) {
-                task = next + __popc(need & lt_mask);
-                alive = task < ntasks;
-                if (alive) {
-                    const int smp = div_magic(task, npx, magic), slot = task - smp * npx;
-                    const int row = div_magic(slot, vw, magic_w);
-                    start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
-                    if (kCount) ++cnt.paths;
-                }
-            }
-            next += __popc(need);
-        }
+        auto dense = [&](int task, int& slot, int& smp) {
+            smp = div_magic(task, npx, magic);
+            slot = task - smp * npx;
+        };
+        W.acc[0][lane] = 0ull;
+        W.acc[1][lane] = 0ull;
+        W.acc[2][lane] = 0ull;
         __syncwarp();
 
-        // ---- a4/a5: pixel means, squared error, block partial ----------------------
-        double e = 0.0;
-        const int px = x0 + lane % vw, py = y0 + lane / vw;
-        if (lane < npx && px < J.W && py < J.H) {
-            const double inv = 1.0 / (double(J.spp) * double(kFix));
-            const double Ix = double(acc[0][lane]) * inv, Iy = double(acc[1][lane]) * inv,
-                         Iz = double(acc[2][lane]) * inv;
-            if (kRender) {
-                J.images[(size_t(r) * J.H + py) * J.W + px] = make_float4(float(Ix), float(Iy), float(Iz), 0.0f);
-            } else {
-                const float4 T = __ldg(J.target + size_t(py) * J.W + px);
-                const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
-                e = ex * ex + ey * ey + ez * ez;
-            }
+        if (!kShare) {
+            // ---- a3: every pixel x sample of this render ----------------------------------
+            run_pool<kCount, false>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, nullptr, nullptr, cnt,
+                                    lane);
+            block_epilogue<kRender>(J, r, t, W, false, x0, y0, vw, npx, lane);  // a4/a5
+            continue;
         }
-        if (!kRender) {
-            e = warp_sum_d(e);
-            unsigned rlast = 0;
-            if (lane == 0) {
-                J.partials[size_t(r) * J.tiles + t] = e;
-                __threadfence();
-                rlast = (atomicAdd(J.render_done + r, 1u) == unsigned(J.tiles - 1));
-            }
-            rlast = __shfl_sync(kFull, rlast, 0);
-            if (rlast) finish_render(J, r, lane);  // a5/a6/a7 for the last block of a render
-        }
+
+        // ---- shared pass: every path once in the invariant scene ---------------------------
+        W.mask[lane] = 0ull;
         __syncwarp();
+        run_pool<kCount, true>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, W.mask, &W.vb, cnt, lane);
+        const unsigned long long my_mask = (lane < npx) ? W.mask[lane] : 0ull;
+        if (__ballot_sync(kFull, my_mask != 0ull) == 0u) {  // every path is shared by all renders
+            shared_block_epilogue(J, t, W, x0, y0, vw, npx, lane);
+            continue;
+        }
+        // some paths differ between renders: keep the shared radiance and the affected
+        // samples for the per-render pass, and list the block
+        unsigned long long* dst = J.share_acc + size_t(t) * 96;
+        dst[lane] = W.acc[0][lane];
+        dst[32 + lane] = W.acc[1][lane];
+        dst[64 + lane] = W.acc[2][lane];
+        J.share_mask[size_t(t) * 32 + lane] = my_mask;
+        if (lane == 0) J.aff_tiles[atomicAdd(J.aff_count, 1u)] = t;
+        __syncwarp();
+    }
+    if (kCount) {
+        const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
+                                          warp_sum_u(cnt.paths), warp_sum_u(cnt.vertices), warp_sum_u(cnt.shadow),
+                                          warp_sum_u(cnt.rays), 0u};
+        if (lane == 0)
+            for (int i = 0; i < kNumCounters; ++i) atomicAdd(L.counters + i, (unsigned long long)v[i]);
+    }
+}
+
+// Per-render pass of a path-sharing job: items are (listed block, render); each traces
+// the block's affected paths in that render and adds them to the shared radiance.
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(const __grid_constant__ TraceLaunch L) {
+    __shared__ WarpSmem s_warp[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem& W = s_warp[warp];
+    const TraceJob& J = W.job;
+    {
+        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        unsigned* dst = reinterpret_cast<unsigned*>(&W.job);
+        for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
+        __syncwarp();
+    }
+    const unsigned n_items = (*J.aff_count) * unsigned(J.R);
+    int cur_r = -1;
+    Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(J.queue_b, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_items) break;
+        const int r = int(item % unsigned(J.R));  // consecutive items: same block, other renders
+        const int t = __ldcg(J.aff_tiles + item / unsigned(J.R));
+        if (t < 0 || t >= J.tiles) {
+            if (lane == 0) atomicOr(L.status, kStatusBadItem);
+            break;
+        }
+        if (r != cur_r) {
+            stage_scene(W, J, r, lane);
+            cur_r = r;
+        }
+        const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
+        const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
+        const int npx = vw * vh;
+        const unsigned magic_w = 0xffffffffu / unsigned(vw) + 1u;
+        const unsigned long long* src = J.share_acc + size_t(t) * 96;
+        W.acc[0][lane] = __ldcg(src + lane);
+        W.acc[1][lane] = __ldcg(src + 32 + lane);
+        W.acc[2][lane] = __ldcg(src + 64 + lane);
+        W.accr[0][lane] = 0ull;
+        W.accr[1][lane] = 0ull;
+        W.accr[2][lane] = 0ull;
+        const unsigned long long my_mask = __ldcg(J.share_mask + size_t(t) * 32 + lane);
+        __syncwarp();
+        const int kcount = __popcll(my_mask);
+        int incl = kcount;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - kcount;
+        const int n_affected = __shfl_sync(kFull, incl, 31);
+        auto affected = [&](int task, int& slot, int& smp) {
+            int lo = 0, hi = 31;  // last lane whose exclusive offset is <= task
+#pragma unroll
+            for (int it = 0; it < 5; ++it) {
+                const int mid = (lo + hi + 1) >> 1;
+                const int off = __shfl_sync(kFull, excl, mid);
+                if (off <= task) lo = mid; else hi = mid - 1;
+            }
+            slot = lo;
+            const int k = task - __shfl_sync(kFull, excl, lo);
+            const unsigned long long m = __shfl_sync(kFull, my_mask, lo);
+            smp = nth_set_bit(m, k);
+        };
+        run_pool<kCount, false>(W.scene, J, n_affected, x0, y0, vw, magic_w, affected, W.accr, nullptr, nullptr, cnt,
+                                lane);
+        block_epilogue<false>(J, r, t, W, true, x0, y0, vw, npx, lane);
     }
     if (kCount) {
         const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
@@ -886,23 +1196,36 @@ cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream) {
 int trace_blocks_per_sm(bool render_mode) {
     int n = 0;
     if (render_mode)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false>, kBlock, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false>, kBlock, 0);
     return n > 0 ? n : 1;
 }
 
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream) {
     if (L.total_items <= 0) return cudaSuccess;
     const bool count = L.counters != nullptr;
+    const bool share = !render_mode && !L.jobs && L.job0.share;
     if (render_mode && count)
-        k_trace<true, true><<<grid, kBlock, 0, stream>>>(L);
+        k_trace<true, true, false><<<grid, kBlock, 0, stream>>>(L);
     else if (render_mode)
-        k_trace<true, false><<<grid, kBlock, 0, stream>>>(L);
+        k_trace<true, false, false><<<grid, kBlock, 0, stream>>>(L);
+    else if (share && count)
+        k_trace<false, true, true><<<grid, kBlock, 0, stream>>>(L);
+    else if (share)
+        k_trace<false, false, true><<<grid, kBlock, 0, stream>>>(L);
     else if (count)
-        k_trace<false, true><<<grid, kBlock, 0, stream>>>(L);
+        k_trace<false, true, false><<<grid, kBlock, 0, stream>>>(L);
     else
-        k_trace<false, false><<<grid, kBlock, 0, stream>>>(L);
+        k_trace<false, false, false><<<grid, kBlock, 0, stream>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t stream) {
+    if (L.counters)
+        k_trace_affected<true><<<grid, kBlock, 0, stream>>>(L);
+    else
+        k_trace_affected<false><<<grid, kBlock, 0, stream>>>(L);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,7 @@ class Server:
         pending = list(jobs)
         active: list[ServedJob] = []
         peak_active = 0
+        peak_bytes = self.ctx.memory_used()
         ticks = 0
         t0 = time.perf_counter()
         ev_start = torch.cuda.Event(enable_timing=True)
@@ -105,6 +106,7 @@ class Server:
                     time.sleep(max(0.0, min(pending[0].arrival - now, 0.01)))
                 continue
             peak_active = max(peak_active, len(active))
+            peak_bytes = max(peak_bytes, self.ctx.memory_used())
             ev_start.record(self.stream)
             if self.mode == "batched":
                 ev_end = torch.cuda.Event(enable_timing=True)
@@ -144,6 +146,6 @@ class Server:
             "mpaths_per_s": paths / wall / 1e6 if wall > 0 else 0.0,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
-            "peak_active": peak_active,
+            "peak_active": peak_active, "peak_hbm_bytes": peak_bytes,
         }
         return report, jobs

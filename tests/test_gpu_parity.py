@@ -160,3 +160,20 @@ def test_deterministic_across_launch_shapes(ctx):
     assert np.array_equal(g1, g1b) and np.array_equal(L1, L1b)  # bitwise reproducible
     g4, L4, ref = _grad_case(ctx, wl, k=8)
     assert np.allclose(L4, L1, rtol=1e-12)  # block shape changes only the FP64 summation grouping
+
+
+@pytest.mark.parametrize("make", [workloads.config_small, workloads.config_occlusion,
+                                  lambda: workloads.scaled(workloads.config_occlusion(), width=45, height=37, spp=7)])
+def test_path_sharing_is_bit_identical(ctx, make):
+    """With common random numbers, paths that no perturbed instance can touch are traced
+    once for all renders; the gradient and losses must equal tracing every render."""
+    wl = make()
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = _t(oracle.render_target(wl))
+    res = []
+    for no_share in (0, 1):
+        opts = scene.grad_opts(wl, step=5, no_path_sharing=no_share)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
+        torch.cuda.synchronize()
+        res.append((g.cpu().numpy(), L.cpu().numpy()))
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][0], res[1][0])

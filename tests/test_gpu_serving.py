@@ -20,12 +20,12 @@ torch = pytest.importorskip("torch")
 def _mix():
     base = [workloads.config_small(seed=3), workloads.config_occlusion(seed=4), workloads.config_gi_box(seed=5),
             workloads.config_small(seed=6), workloads.config_occlusion(seed=7)]
-    sizes = [(40, 32, 2, 2, 4), (48, 40, 2, 3, 3), (32, 24, 2, 2, 5), (24, 24, 4, 1, 2), (56, 48, 1, 2, 4)]
+    sizes = [(40, 32, 2, 2, 60), (48, 40, 2, 3, 50), (32, 24, 2, 2, 70), (24, 24, 4, 1, 40), (56, 48, 1, 2, 60)]
     out = []
     for i, (wl, (w, h, spp, pairs, steps)) in enumerate(zip(base, sizes)):
         s = workloads.scaled(wl, width=w, height=h, spp=spp, pairs=pairs)
         s.steps = steps
-        out.append((0.004 * i, s))
+        out.append((0.0005 * i, s))  # later jobs arrive while the first ones are running
     return out
 
 
@@ -68,7 +68,22 @@ def test_budget_limits_admission(gpu_lib):
     from paper_2211_17263_gb300 import api
     from paper_2211_17263_gb300.serve import Server
     arrivals = [(0.0, a[1]) for a in _mix()]
-    ctx = api.Context(0, hbm_budget_bytes=160_000)
+    probe = api.Context(0)  # measure what each job holds, then allow roughly two at a time
+    try:
+        sizes, before = [], probe.memory_used()
+        for _, wl in arrivals:
+            _alone(probe, wl, 1)
+        srv = Server(probe, mode="batched")
+        for _, wl in arrivals:
+            from paper_2211_17263_gb300.serve import ServedJob
+            sj = ServedJob(wl=wl, arrival=0.0, steps=1)
+            srv._admit(sj)
+            sizes.append(probe.memory_used() - before)
+            srv._retire(sj, 0.0)
+    finally:
+        probe.close()
+    budget = 2 * max(sizes) + 64 * 1024  # plus the context's own scratch (control words, descriptors)
+    ctx = api.Context(0, hbm_budget_bytes=budget)
     try:
         report, jobs = Server(ctx, mode="batched").run(arrivals, real_time=False)
         assert all(sj.result is not None and sj.result["steps"] == sj.steps for sj in jobs)
