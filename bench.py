@@ -302,6 +302,26 @@ def main():
         step_ms = float(t.item())
     state = job.read()
 
+    # the per-render kernel on the same workload (path sharing off): its own roofline
+    plain_job = api.Job(scene, wl, target_host, block_pixels=args.block_pixels, no_path_sharing=1)
+    for _ in range(3):
+        plain_job.step(stream)
+    ctx.counters_enable(True)
+    plain_job.step(stream)
+    pcounts = ctx.counters_read()
+    ctx.counters_enable(False)
+    torch.cuda.synchronize()
+    ctx.kernel_timing(True)
+    n_plain = min(args.steps, 100)
+    for _ in range(n_plain):
+        flush.zero_()
+        plain_job.step(stream)
+    p_ms, p_launches = ctx.kernel_timing_read()
+    ctx.kernel_timing(False)
+    plain_job.release()
+    pflops = (pcounts[0] * FLOPS["sphere_test"] + pcounts[1] * FLOPS["quad_test"] + pcounts[2] * FLOPS["box_test"]
+              + pcounts[3] * FLOPS["path"] + pcounts[4] * FLOPS["vertex"])
+
     # end to end through the C ABI with host buffers: H2D inputs, gradient, Adam, D2H results
     e2e = None
     theta_h = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32)).pin_memory()
@@ -353,6 +373,8 @@ def main():
         fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
         trace_avg_ms = trace_ms / max(launches, 1)
         achieved = flops_step / (trace_avg_ms * 1e-3) / 1e12
+        p_avg_ms = p_ms / max(p_launches, 1)
+        p_achieved = pflops / (p_avg_ms * 1e-3) / 1e12
         value = world * 1000.0 / step_ms
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -369,10 +391,16 @@ def main():
                               "closest_hit_rays": counts[6]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": _profiled_traffic(wl.name),
-                         "kernel": "k_trace", "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
-                                                            f" x 2 flop x {sm_max:.0f} MHz"},
+                         "kernel": "render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue,"
+                                   " k_finalize)",
+                         "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
+                                       f" x 2 flop x {sm_max:.0f} MHz"},
+            "roofline_per_render_kernel": {
+                "bound": "alu", "achieved": p_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": p_achieved / fp32_peak, "kernel": "k_trace (path sharing off) + k_finalize",
+                "ms_per_step": p_avg_ms, "paths_per_step": pcounts[3]},
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (5 if counts[3] < wl.paths_per_step else 3) * args.steps,
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
         }

@@ -47,6 +47,8 @@ struct Job {
     float *theta = nullptr, *m = nullptr, *v = nullptr, *sigma0 = nullptr, *grad = nullptr, *losses = nullptr;
     float* w = nullptr;
     unsigned long long* share = nullptr;
+    unsigned long long* accaff = nullptr;
+    unsigned* codes = nullptr;
     int* aff = nullptr;
     double *partials = nullptr, *losses_d = nullptr;
     unsigned* rdone = nullptr;
@@ -81,13 +83,15 @@ struct prdpt_ctx {
     size_t s_partials_n = 0;
     double* s_losses = nullptr;
     size_t s_losses_n = 0;
-    unsigned* s_rdone = nullptr;  // per-render block counters (all zero between launches)
-    size_t s_rdone_n = 0;
     unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2] batch queue, [4..5] sharing counters
-    unsigned long long* s_share = nullptr;  // path sharing: [tiles][96] radiance then [tiles][32] masks
+    unsigned long long* s_share = nullptr;  // path sharing: [tiles][96] shared radiance
     size_t s_share_n = 0;
     int* s_aff = nullptr;         // path sharing: list of blocks with affected paths
     size_t s_aff_n = 0;
+    unsigned long long* s_accaff = nullptr;  // path sharing: [R][H*W][3] affected radiance (kept zero)
+    size_t s_accaff_n = 0;
+    unsigned* s_codes = nullptr;  // path sharing: affected (pixel, sample) codes
+    size_t s_codes_n = 0;
     // packed launches
     std::vector<int> batch_ids;
     InstJob* d_inst = nullptr;
@@ -212,8 +216,14 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStr
     }
     cudaError_t e = launch_trace(L, render, grid_for(c, L.total_items, render, ctas_per_sm), stream);
     if (e != cudaSuccess) return e;
-    if (!render && !L.jobs && L.job0.share) {  // per-render pass over the blocks with affected paths
+    if (!render && !L.jobs && L.job0.share) {  // affected paths per render, then their blocks' errors
         e = launch_trace_affected(L, grid_for(c, 1 << 30, false, ctas_per_sm), stream);
+        if (e != cudaSuccess) return e;
+        e = launch_shared_epilogue(L, grid_for(c, 1 << 30, false, 0), stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (!render) {  // per-render losses, gradient, Adam
+        e = launch_finalize(L, L.jobs ? L.fin_total : L.job0.R, stream);
         if (e != cudaSuccess) return e;
     }
     if (c->timing) {
@@ -416,6 +426,8 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
     J.var_prims = 0u;
     J.var_mats = 0u;
     if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp) return;
+    // per-render radiance buffers of the affected paths: 24 bytes per render and pixel
+    if (24.0 * 2.0 * o->pairs * double(o->width) * double(o->height) > double(size_t(512) << 20)) return;
     bool var_prim[kMaxPrims] = {};
     for (int d = 0; d < B.D; ++d) {
         const int k = B.bind_kind[d], idx = B.bind_index[d];
@@ -557,15 +569,17 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     int bw, bh, tiles_x, tiles;
     tiles_for(px, o->width, o->height, &bw, &bh, &tiles_x, &tiles);
     if (probe.share) {
-        if (prdpt_status st = grow(c, &c->s_share, &c->s_share_n, (size_t)tiles * 128)) return st;
+        const size_t pix = (size_t)o->width * o->height;
+        if (prdpt_status st = grow(c, &c->s_share, &c->s_share_n, (size_t)tiles * 96)) return st;
         if (prdpt_status st = grow(c, &c->s_aff, &c->s_aff_n, (size_t)tiles)) return st;
+        if (prdpt_status st = grow_zeroed(c, &c->s_accaff, &c->s_accaff_n, (size_t)R * pix * 3)) return st;
+        if (prdpt_status st = grow(c, &c->s_codes, &c->s_codes_n, pix * o->spp)) return st;
     }
     if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)R)) return st;
     if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)R * D > (size_t)kMaxD ? (size_t)R * D : (size_t)kMaxD))
         return st;
     if (prdpt_status st = grow(c, &c->s_partials, &c->s_partials_n, (size_t)R * tiles)) return st;
     if (prdpt_status st = grow(c, &c->s_losses, &c->s_losses_n, (size_t)R)) return st;
-    if (prdpt_status st = grow_zeroed(c, &c->s_rdone, &c->s_rdone_n, (size_t)kMaxRenders)) return st;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     InstLaunch IL{};
     fill_inst_grad(IL.job0, s, o);
@@ -582,7 +596,6 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     J.scenes = c->s_scenes;
     J.target = reinterpret_cast<const float4*>(target_dev);
     J.partials = c->s_partials;
-    J.render_done = c->s_rdone;
     J.done = c->s_ctl + 1;
     J.losses = c->s_losses;
     J.w = c->s_w;
@@ -605,10 +618,10 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     fill_share(J, s->host, o);
     if (J.share) {
         J.share_acc = c->s_share;
-        J.share_mask = c->s_share + (size_t)tiles * 96;
+        J.acc_aff = c->s_accaff;
+        J.aff_codes = c->s_codes;
         J.aff_tiles = c->s_aff;
-        J.aff_count = c->s_ctl + 4;
-        J.queue_b = c->s_ctl + 5;
+        J.share_ctl = c->s_ctl + 4;
     }
     TL.total_items = J.share ? tiles : R * tiles;
     TL.queue = c->s_ctl + 0;
@@ -657,8 +670,13 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const size_t off_p = (off_w + sizeof(float) * R * D + 255) & ~size_t(255);
     const size_t off_s = (off_p + sizeof(double) * R * tiles + 255) & ~size_t(255);
     const size_t off_t = (off_s + sizeof(InstScene) * R + 255) & ~size_t(255);
-    const size_t off_sh = (off_t + sizeof(float4) * (size_t)W * H + 255) & ~size_t(255);
-    const size_t off_af = off_sh + (probe.share ? sizeof(unsigned long long) * 128 * (size_t)tiles : 0);
+    const size_t pix = (size_t)W * H;
+    const size_t off_sh = (off_t + sizeof(float4) * pix + 255) & ~size_t(255);
+    const size_t off_aa = (off_sh + (probe.share ? sizeof(unsigned long long) * 96 * (size_t)tiles : 0) + 255) &
+                          ~size_t(255);
+    const size_t off_cd = (off_aa + (probe.share ? sizeof(unsigned long long) * 3 * (size_t)R * pix : 0) + 255) &
+                          ~size_t(255);
+    const size_t off_af = (off_cd + (probe.share ? sizeof(unsigned) * pix * o->spp : 0) + 255) & ~size_t(255);
     const size_t total = off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0);
     void* base = nullptr;
     if (prdpt_status st = dev_alloc(c, &base, total)) {
@@ -678,19 +696,22 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     j->step = reinterpret_cast<int*>(j->rdone + kMaxRenders);
     j->done = reinterpret_cast<unsigned*>(j->step + 1);
     j->queue = j->done + 1;
-    unsigned* share_ctl = j->queue + 1;  // [0] affected-block count, [1] second-pass queue
+    unsigned* share_ctl = j->queue + 1;  // path-sharing counters: listed blocks, paths, two queues
     j->w = reinterpret_cast<float*>(b + off_w);
     j->partials = reinterpret_cast<double*>(b + off_p);
     j->scenes = reinterpret_cast<InstScene*>(b + off_s);
     j->target = reinterpret_cast<float4*>(b + off_t);
     if (probe.share) {
         j->share = reinterpret_cast<unsigned long long*>(b + off_sh);
+        j->accaff = reinterpret_cast<unsigned long long*>(b + off_aa);
+        j->codes = reinterpret_cast<unsigned*>(b + off_cd);
         j->aff = reinterpret_cast<int*>(b + off_af);
     }
     cudaError_t e = cudaMemset(base, 0, off_w);
     if (e == cudaSuccess) e = cudaMemcpy(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(j->target, d->target_host, sizeof(float4) * (size_t)W * H, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && probe.share) e = cudaMemset(j->accaff, 0, sizeof(unsigned long long) * 3 * (size_t)R * pix);
     if (e != cudaSuccess) {
         dev_free(c, base);
         delete j;
@@ -711,7 +732,6 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     T.scenes = j->scenes;
     T.target = j->target;
     T.partials = j->partials;
-    T.render_done = j->rdone;
     T.done = j->done;
     T.losses = j->losses_d;
     T.w = j->w;
@@ -742,10 +762,10 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     fill_share(T, s->host, o);
     if (T.share) {
         T.share_acc = j->share;
-        T.share_mask = j->share + (size_t)tiles * 96;
+        T.acc_aff = j->accaff;
+        T.aff_codes = j->codes;
         T.aff_tiles = j->aff;
-        T.aff_count = share_ctl;
-        T.queue_b = share_ctl + 1;
+        T.share_ctl = share_ctl;
         j->share_ctl = share_ctl;
     }
     s->jobs++;
@@ -795,6 +815,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             trace[i] = j->trace;
             trace[i].share = 0;  // packed launches trace every render of every job
             trace[i].item_begin = items;
+            trace[i].fin_begin = blocks - j->R;  // same prefix as the instantiation CTAs
             items += j->R * j->tiles;
         }
         PRDPT_CUDA(cudaStreamSynchronize(st_));  // the old descriptors may still be in use
@@ -826,6 +847,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     TraceLaunch TL{};
     TL.jobs = c->d_trace;
     TL.njobs = n;
+    TL.fin_total = c->batch_blocks;
     TL.total_items = c->batch_items;
     TL.queue = c->s_ctl + 2;
     TL.counters = c->counting ? c->counters : nullptr;

@@ -9,6 +9,7 @@
 //               corners, light areas) and the render's random-stream words. Each
 //               render CTA copies it into shared memory (~3.4 KB).
 //   partials    [R][blocks] FP64 sums of squared pixel errors, one per warp work item.
+//               k_finalize reduces them per render in a fixed order.
 //   weights     [R][D] FP32 estimator weights d kappa / q of each render.
 //   per job     theta, Adam m and v, sigma0, gradient, losses, step counter, target.
 #pragma once
@@ -97,8 +98,7 @@ struct TraceJob {
     const float4* target;     // [H][W] (gradient mode) or null
     float4* images;           // [R][H][W] (render mode) or null
     double* partials;         // [R][tiles] sums of squared pixel errors per block
-    unsigned* render_done;    // [R] blocks finished per render (reset by the warp that completes the render)
-    unsigned* done;           // renders finished (reset by the warp that completes the job)
+    unsigned* done;           // renders finalised (reset by the CTA that completes the job)
     double* losses;           // [R] L_r
     const float* w;           // [R][D]
     float* grad_out;          // [D] or null
@@ -112,14 +112,16 @@ struct TraceJob {
     int bw, bh, tiles_x, tiles;
     int n_prims, n_mats;      // used primitive and material records (staging size)
     int item_begin;           // first work item of this job in a packed launch
+    int fin_begin;            // first finalisation CTA of this job in a packed launch
     // Path sharing across renders (common random numbers, geometry-only bindings): a work
     // item is one pixel block of all R renders. share = 0 disables it.
     int share;
     unsigned long long* share_acc;   // [tiles][3][32] shared radiance of blocks with affected paths
-    unsigned long long* share_mask;  // [tiles][32] affected samples per pixel slot
+    unsigned long long* acc_aff;     // [R][H*W][3] per-render radiance of affected paths (kept zero between steps)
+    unsigned* aff_codes;      // [H*W*spp] affected paths as (pixel << 6) | sample
     int* aff_tiles;           // [tiles] blocks with affected paths (appended by the shared pass)
-    unsigned* aff_count;      // number of entries in aff_tiles (zeroed by the instantiation launch)
-    unsigned* queue_b;        // work queue of the per-render pass (zeroed by the instantiation launch)
+    unsigned* share_ctl;      // [0] listed blocks, [1] affected paths, [2] per-render queue, [3] epilogue
+                              // queue; zeroed by the instantiation launch
     int n_var;                // perturbed primitives (<= kMaxVariant)
     int var_slot[4];          // their record slots
     unsigned var_prims;       // record-slot bitmask of perturbed primitives
@@ -132,6 +134,7 @@ struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)
     const TraceJob* jobs;     // packed launch: [njobs] in device memory
     int njobs, total_items;
+    int fin_total;            // packed launch: finalisation CTAs (sum of R over jobs)
     unsigned* queue;          // work-queue head, zeroed by the instantiation launch
     unsigned long long* counters;  // [8] or null (null: the uncounted kernel variant runs)
     int* status;
@@ -142,14 +145,19 @@ struct InstLaunch {
     const InstJob* jobs;
     int njobs, total_blocks;
     unsigned* queue_reset;    // zeroed by CTA 0
-    unsigned* share_reset;    // [2] zeroed by CTA 0 (path-sharing list count and second queue) or null
+    unsigned* share_reset;    // [4] path-sharing counters zeroed by CTA 0, or null
 };
 
 // Launchers (kernels.cu). All enqueue on `stream` and return the launch error.
 cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream);
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream);
-// Second pass of a path-sharing job: the affected paths of the listed blocks, per render.
+// Second and third passes of a path-sharing job: the affected paths per render, then the
+// per-render errors of the blocks that had affected paths.
 cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t stream);
+cudaError_t launch_shared_epilogue(const TraceLaunch& L, int grid, cudaStream_t stream);
+// Per-render losses, gradient and Adam: one CTA per render of every job in the launch.
+cudaError_t launch_finalize(const TraceLaunch& L, int n_renders, cudaStream_t stream);
+constexpr int kAffChunk = 256;  // affected paths per work item of the per-render pass
 cudaError_t launch_adam(int D, float* theta, float* m, float* v, const float* g, int t, float lr, float b1,
                         float b2, float eps, cudaStream_t stream);
 cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, unsigned c2, unsigned c3, int n,

@@ -13,9 +13,11 @@
 //                   lane traced which path). The pixel means, the squared error
 //                   against the target and the block's partial sum are formed in
 //                   FP64 in registers -- the perturbed image never reaches HBM.
-//                   The warp that completes a render's last block reduces L_r; the
-//                   warp that completes the job's last render forms the gradient of
-//                   Eq. 10 and applies Adam. No CTA-wide barriers, no spin waits.
+//                   Each block's partial is a plain store; no CTA-wide barriers, no
+//                   fences or atomics per item, no spin waits.
+//   k_finalize      one CTA per render: L_r from the block partials (fixed order); the
+//                   CTA completing a job's last render forms the gradient of Eq. 10
+//                   and applies Adam.
 //   k_adam          standalone Adam update.
 //   k_philox        raw Philox words (for bit-exact checks of the random streams).
 //
@@ -116,10 +118,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     const int tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) {
         if (L.queue_reset) *L.queue_reset = 0u;
-        if (L.share_reset) {
-            L.share_reset[0] = 0u;
-            L.share_reset[1] = 0u;
-        }
+        if (L.share_reset)
+            for (int i = 0; i < 4; ++i) L.share_reset[i] = 0u;
     }
     if (tid == 0) {
         int j = 0;
@@ -707,62 +707,6 @@ __device__ __forceinline__ unsigned long long to_fixed(float v) {
     return sh >= 0 ? (m << sh) : (m >> (-sh));
 }
 
-// Gradient of Eq. 10 from the per-render losses, then Adam; run by the one warp
-// that completed the job's last render.
-__device__ void finish_job(const TraceJob& J, int lane) {
-    __threadfence();
-    const int t = J.step_dev ? *J.step_dev : 0;
-    for (int d = lane; d < J.D; d += 32) {
-        double g = 0.0;
-        if (J.antithetic) {
-            const int P = J.R / 2;
-            for (int p = 0; p < P; ++p)
-                g += double(J.w[size_t(2 * p) * J.D + d]) * (__ldcg(J.losses + 2 * p) - __ldcg(J.losses + 2 * p + 1));
-            g /= double(2 * P);
-        } else {
-            for (int r = 0; r < J.R; ++r) g += double(J.w[size_t(r) * J.D + d]) * __ldcg(J.losses + r);
-            g /= double(J.R);
-        }
-        const float gf = float(g);
-        if (J.grad_out) J.grad_out[d] = gf;
-        if (J.theta) {  // Adam (Kingma & Ba), state in FP32, arithmetic in FP64
-            const int tt = t + 1;
-            const double m = double(J.b1) * J.m[d] + (1.0 - double(J.b1)) * double(gf);
-            const double v = double(J.b2) * J.v[d] + (1.0 - double(J.b2)) * double(gf) * double(gf);
-            const double mh = m / (1.0 - pow(double(J.b1), tt));
-            const double vh = v / (1.0 - pow(double(J.b2), tt));
-            J.m[d] = float(m);
-            J.v[d] = float(v);
-            J.theta[d] = float(double(J.theta[d]) - double(J.lr) * mh / (sqrt(vh) + double(J.eps)));
-        }
-    }
-    __syncwarp();
-    if (lane == 0) {
-        if (J.step_dev) *J.step_dev = t + 1;
-        *J.done = 0u;  // ready for the next launch
-    }
-}
-
-// L_r = (1/3HW) sum of render r's block partials (FP64, fixed order); run by the
-// warp that completed the render's last block.
-__device__ void finish_render(const TraceJob& J, int r, int lane) {
-    __threadfence();
-    double acc = 0.0;
-    for (int i = lane; i < J.tiles; i += 32) acc += __ldcg(J.partials + size_t(r) * J.tiles + i);
-    acc = warp_sum_d(acc);
-    unsigned last = 0;
-    if (lane == 0) {
-        const double Lr = acc / (3.0 * double(J.W) * double(J.H));
-        J.losses[r] = Lr;
-        if (J.loss_out) J.loss_out[r] = float(Lr);
-        J.render_done[r] = 0u;
-        __threadfence();
-        last = (atomicAdd(J.done, 1u) == unsigned(J.R - 1));
-    }
-    last = __shfl_sync(kFull, last, 0);
-    if (last) finish_job(J, lane);
-}
-
 // Per-warp shared-memory workspace of the render kernel.
 struct WarpSmem {
     InstScene scene;                  // the render being traced (render 0 in shared phase A)
@@ -890,7 +834,18 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
             atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
             atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
         }
-        if (kShared && ended && st == kAffected) atomicOr(mask + p.slot, 1ull << p.s);
+        if (kShared) {  // affected paths: append (pixel, sample) to the job's list
+            const unsigned am = __ballot_sync(kFull, ended && st == kAffected);
+            if (am) {
+                unsigned base = 0;
+                if (lane == __ffs(am) - 1) base = atomicAdd(J.share_ctl + 1, unsigned(__popc(am)));
+                base = __shfl_sync(kFull, base, __ffs(am) - 1);
+                if (ended && st == kAffected) {
+                    J.aff_codes[base + __popc(am & lt_mask)] = (p.pixel << 6) | unsigned(p.s);
+                    if (mask) mask[0] = 1ull;  // the block has affected paths
+                }
+            }
+        }
         const unsigned need = __ballot_sync(kFull, ended);
         const int mine = next + __popc(need & lt_mask);
         decode((ended && mine < ntasks) ? mine : 0, slot, smp);
@@ -934,20 +889,12 @@ __device__ __forceinline__ void block_epilogue(const TraceJob& J, int r, int t, 
     }
     if (!kRender) {
         e = warp_sum_d(e);
-        unsigned rlast = 0;
-        if (lane == 0) {
-            J.partials[size_t(r) * J.tiles + t] = e;
-            __threadfence();
-            rlast = (atomicAdd(J.render_done + r, 1u) == unsigned(J.tiles - 1));
-        }
-        rlast = __shfl_sync(kFull, rlast, 0);
-        if (rlast) finish_render(J, r, lane);  // a5/a6/a7 for the last block of a render
+        if (lane == 0) J.partials[size_t(r) * J.tiles + t] = e;  // a5: one partial per block
     }
     __syncwarp();
 }
 
-// The same squared error for all R renders of a block whose paths are all shared:
-// R partials, one fence, R completion counts (lanes take one render each).
+// The same squared error for all R renders of a block whose paths are all shared.
 __device__ __forceinline__ void shared_block_epilogue(const TraceJob& J, int t, const WarpSmem& W, int x0, int y0,
                                                       int vw, int npx, int lane) {
     double e = 0.0;
@@ -962,18 +909,6 @@ __device__ __forceinline__ void shared_block_epilogue(const TraceJob& J, int t, 
     }
     e = warp_sum_d(e);
     for (int r = lane; r < J.R; r += 32) J.partials[size_t(r) * J.tiles + t] = e;
-    __threadfence();
-    __syncwarp();
-    for (int r0 = 0; r0 < J.R; r0 += 32) {
-        const int r = r0 + lane;
-        const bool last = r < J.R && atomicAdd(J.render_done + r, 1u) == unsigned(J.tiles - 1);
-        unsigned lastmask = __ballot_sync(kFull, last);
-        while (lastmask) {  // renders this block completed
-            const int src = __ffs(lastmask) - 1;
-            lastmask &= lastmask - 1;
-            finish_render(J, r0 + src, lane);
-        }
-    }
     __syncwarp();
 }
 
@@ -1053,22 +988,20 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_
         }
 
         // ---- shared pass: every path once in the invariant scene ---------------------------
-        W.mask[lane] = 0ull;
+        if (lane == 0) W.mask[0] = 0ull;
         __syncwarp();
         run_pool<kCount, true>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, W.mask, &W.vb, cnt, lane);
-        const unsigned long long my_mask = (lane < npx) ? W.mask[lane] : 0ull;
-        if (__ballot_sync(kFull, my_mask != 0ull) == 0u) {  // every path is shared by all renders
+        if (W.mask[0] == 0ull) {  // every path is shared by all renders
             shared_block_epilogue(J, t, W, x0, y0, vw, npx, lane);
             continue;
         }
-        // some paths differ between renders: keep the shared radiance and the affected
-        // samples for the per-render pass, and list the block
+        // some paths differ between renders: keep the shared radiance for the epilogue pass
+        // and list the block; its affected paths are already in the job's list
         unsigned long long* dst = J.share_acc + size_t(t) * 96;
         dst[lane] = W.acc[0][lane];
         dst[32 + lane] = W.acc[1][lane];
         dst[64 + lane] = W.acc[2][lane];
-        J.share_mask[size_t(t) * 32 + lane] = my_mask;
-        if (lane == 0) J.aff_tiles[atomicAdd(J.aff_count, 1u)] = t;
+        if (lane == 0) J.aff_tiles[atomicAdd(J.share_ctl + 0, 1u)] = t;
         __syncwarp();
     }
     if (kCount) {
@@ -1080,76 +1013,82 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_
     }
 }
 
-// Per-render pass of a path-sharing job: items are (listed block, render); each traces
-// the block's affected paths in that render and adds them to the shared radiance.
+// Per-render pass of a path-sharing job. Items are (render, chunk of kAffChunk affected
+// paths), so work is even however the affected paths cluster; radiance goes to the
+// render's image-sized fixed-point buffer with global atomic adds (order-independent).
 template <bool kCount>
 __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(const __grid_constant__ TraceLaunch L) {
-    __shared__ WarpSmem s_warp[kWarps];
+    __shared__ InstScene s_scene[kWarps];
+    __shared__ TraceJob s_job[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem& W = s_warp[warp];
-    const TraceJob& J = W.job;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    InstScene& S = s_scene[warp];
+    TraceJob& J = s_job[warp];
     {
         const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
-        unsigned* dst = reinterpret_cast<unsigned*>(&W.job);
+        unsigned* dst = reinterpret_cast<unsigned*>(&J);
         for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
         __syncwarp();
     }
-    const unsigned n_items = (*J.aff_count) * unsigned(J.R);
+    const unsigned n_codes = __ldcg(J.share_ctl + 1);
+    const unsigned n_chunks = (n_codes + kAffChunk - 1) / kAffChunk;
+    const unsigned n_items = n_chunks * unsigned(J.R);
+    const unsigned magic_W = 0xffffffffu / unsigned(J.W) + 1u;
     int cur_r = -1;
     Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     for (;;) {
         unsigned item = 0;
-        if (lane == 0) item = atomicAdd(J.queue_b, 1u);
+        if (lane == 0) item = atomicAdd(J.share_ctl + 2, 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= n_items) break;
-        const int r = int(item % unsigned(J.R));  // consecutive items: same block, other renders
-        const int t = __ldcg(J.aff_tiles + item / unsigned(J.R));
-        if (t < 0 || t >= J.tiles) {
-            if (lane == 0) atomicOr(L.status, kStatusBadItem);
-            break;
-        }
+        const int r = int(item / n_chunks);  // render-major: a warp's next item usually keeps its scene
+        const unsigned c0 = (item % n_chunks) * kAffChunk;
+        const int ntasks = int(min(unsigned(kAffChunk), n_codes - c0));
         if (r != cur_r) {
-            stage_scene(W, J, r, lane);
+            const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
+            float4* dst = reinterpret_cast<float4*>(&S);
+            constexpr int kHead = int(offsetof(InstScene, mat) / 16);
+            constexpr int kPrim = int(offsetof(InstScene, prim) / 16);
+            const int nm = 2 * J.n_mats, np = 4 * J.n_prims;
+            for (int i = lane; i < kHead + nm + np; i += 32) {
+                const int o = (i < kHead + nm) ? i : kPrim + (i - kHead - nm);
+                dst[o] = __ldg(src + o);
+            }
+            __syncwarp();
             cur_r = r;
         }
-        const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
-        const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
-        const int npx = vw * vh;
-        const unsigned magic_w = 0xffffffffu / unsigned(vw) + 1u;
-        const unsigned long long* src = J.share_acc + size_t(t) * 96;
-        W.acc[0][lane] = __ldcg(src + lane);
-        W.acc[1][lane] = __ldcg(src + 32 + lane);
-        W.acc[2][lane] = __ldcg(src + 64 + lane);
-        W.accr[0][lane] = 0ull;
-        W.accr[1][lane] = 0ull;
-        W.accr[2][lane] = 0ull;
-        const unsigned long long my_mask = __ldcg(J.share_mask + size_t(t) * 32 + lane);
-        __syncwarp();
-        const int kcount = __popcll(my_mask);
-        int incl = kcount;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int excl = incl - kcount;
-        const int n_affected = __shfl_sync(kFull, incl, 31);
-        auto affected = [&](int task, int& slot, int& smp) {
-            int lo = 0, hi = 31;  // last lane whose exclusive offset is <= task
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-                const int mid = (lo + hi + 1) >> 1;
-                const int off = __shfl_sync(kFull, excl, mid);
-                if (off <= task) lo = mid; else hi = mid - 1;
-            }
-            slot = lo;
-            const int k = task - __shfl_sync(kFull, excl, lo);
-            const unsigned long long m = __shfl_sync(kFull, my_mask, lo);
-            smp = nth_set_bit(m, k);
+        unsigned long long* acc = J.acc_aff + size_t(r) * J.W * J.H * 3;
+        Path p;
+        int task = lane;
+        bool alive = task < ntasks;
+        auto start = [&](int tk) {
+            const unsigned code = __ldcg(J.aff_codes + c0 + tk);
+            const int pixel = int(code >> 6), smp = int(code & 63u);
+            const int y = div_magic(pixel, J.W, magic_W);
+            start_path(S, J.W, J.H, pixel - y * J.W, y, smp, 0, p);
+            if (kCount) ++cnt.paths;
         };
-        run_pool<kCount, false>(W.scene, J, n_affected, x0, y0, vw, magic_w, affected, W.accr, nullptr, nullptr, cnt,
-                                lane);
-        block_epilogue<false>(J, r, t, W, true, x0, y0, vw, npx, lane);
+        if (alive) start(task);
+        int next = 32;
+        while (__any_sync(kFull, alive)) {
+            int st = kLive;
+            if (alive) st = advance<kCount, false>(S, J.depth, J.rr_start, p, cnt);
+            const bool ended = alive && st != kLive;
+            if (ended) {
+                unsigned long long* a = acc + size_t(p.pixel) * 3;
+                atomicAdd(a + 0, to_fixed(p.L.x));
+                atomicAdd(a + 1, to_fixed(p.L.y));
+                atomicAdd(a + 2, to_fixed(p.L.z));
+            }
+            const unsigned need = __ballot_sync(kFull, ended);
+            if (ended) {
+                task = next + __popc(need & lt_mask);
+                alive = task < ntasks;
+                if (alive) start(task);
+            }
+            next += __popc(need);
+        }
+        __syncwarp();
     }
     if (kCount) {
         const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
@@ -1157,6 +1096,167 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
                                           warp_sum_u(cnt.rays), 0u};
         if (lane == 0)
             for (int i = 0; i < kNumCounters; ++i) atomicAdd(L.counters + i, (unsigned long long)v[i]);
+    }
+}
+
+// Epilogue pass of a path-sharing job: one item per listed block, all renders. Lanes form
+// segments of `pw` lanes (one render each, one pixel per lane); a segment's error sum uses
+// the same shuffle tree as a full warp whose other lanes hold zeros, so the partial is
+// bit-identical to the per-render path. Clears the affected radiance it read, so the
+// buffers are zero for the next step.
+__global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constant__ TraceLaunch L) {
+    __shared__ TraceJob s_job[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TraceJob& J = s_job[warp];
+    {
+        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        unsigned* dst = reinterpret_cast<unsigned*>(&J);
+        for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
+        __syncwarp();
+    }
+    const unsigned n_items = __ldcg(J.share_ctl + 0);
+    const double inv = 1.0 / (double(J.spp) * double(kFix));
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(J.share_ctl + 3, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_items) break;
+        const int t = __ldcg(J.aff_tiles + item);
+        if (t < 0 || t >= J.tiles) {
+            if (lane == 0) atomicOr(L.status, kStatusBadItem);
+            break;
+        }
+        const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
+        const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
+        const int npx = vw * vh;
+        const int pw = npx <= 8 ? 8 : (npx <= 16 ? 16 : 32);  // lanes per render segment
+        const int G = 32 / pw, sub = lane / pw, pl = lane % pw;
+        const int px = x0 + pl % vw, py = y0 + pl / vw;
+        const bool pix_ok = pl < npx && px < J.W && py < J.H;
+        const unsigned long long* sh = J.share_acc + size_t(t) * 96;
+        const unsigned long long s0 = pix_ok ? __ldcg(sh + pl) : 0ull, s1 = pix_ok ? __ldcg(sh + 32 + pl) : 0ull,
+                                 s2 = pix_ok ? __ldcg(sh + 64 + pl) : 0ull;
+        const float4 T = pix_ok ? __ldg(J.target + size_t(py) * J.W + px) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t plane = size_t(J.W) * J.H * 3, pix3 = (size_t(py) * J.W + px) * 3;
+        constexpr int kBatch = 4;  // rounds whose loads are issued before any store
+        for (int rb = 0; rb < J.R; rb += kBatch * G) {
+            unsigned long long a[kBatch][3];
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q) {
+                const int r = rb + q * G + sub;
+                const bool ok = pix_ok && r < J.R;
+                const unsigned long long* af = J.acc_aff + size_t(ok ? r : 0) * plane + (ok ? pix3 : 0);
+                a[q][0] = ok ? __ldcg(af + 0) : 0ull;
+                a[q][1] = ok ? __ldcg(af + 1) : 0ull;
+                a[q][2] = ok ? __ldcg(af + 2) : 0ull;
+            }
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q) {
+                const int r = rb + q * G + sub;
+                double e = 0.0;
+                if (pix_ok && r < J.R) {
+                    const double Ix = double(s0 + a[q][0]) * inv;
+                    const double Iy = double(s1 + a[q][1]) * inv;
+                    const double Iz = double(s2 + a[q][2]) * inv;
+                    unsigned long long* af = J.acc_aff + size_t(r) * plane + pix3;
+                    af[0] = 0ull;
+                    af[1] = 0ull;
+                    af[2] = 0ull;
+                    const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
+                    e = ex * ex + ey * ey + ez * ez;
+                }
+                for (int o = pw / 2; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
+                if (pl == 0 && r < J.R) J.partials[size_t(r) * J.tiles + t] = e;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_finalize: a5 (per-render loss), a6 (gradient, Eq. 10), a7 (Adam)
+// ---------------------------------------------------------------------------
+// One 256-thread CTA per render of every job in the launch: L_r = (1/3HW) sum of the
+// render's block partials in a fixed order (strided per thread, four accumulators, then a
+// fixed shared-memory tree). The CTA that completes a job's last render forms the
+// gradient in FP64 and applies Adam (state in FP32, arithmetic in FP64).
+__global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ TraceLaunch L) {
+    __shared__ double s_red[kBlock];
+    __shared__ int s_job, s_last;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int j = 0;
+        if (L.jobs) {
+            int lo = 0, hi = L.njobs - 1;  // last job with fin_begin <= blockIdx.x
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (L.jobs[mid].fin_begin <= int(blockIdx.x)) lo = mid; else hi = mid - 1;
+            }
+            j = lo;
+        }
+        s_job = j;
+    }
+    __syncthreads();
+    const TraceJob& J = L.jobs ? L.jobs[s_job] : L.job0;
+    const int r = int(blockIdx.x) - J.fin_begin;
+    const double* src = J.partials + size_t(r) * J.tiles;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = tid;
+    for (; i + 3 * kBlock < J.tiles; i += 4 * kBlock) {
+        a0 += src[i];
+        a1 += src[i + kBlock];
+        a2 += src[i + 2 * kBlock];
+        a3 += src[i + 3 * kBlock];
+    }
+    for (int q = 0; i < J.tiles; i += kBlock, ++q) {
+        if (q == 0) a0 += src[i]; else if (q == 1) a1 += src[i]; else a2 += src[i];
+    }
+    s_red[tid] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    for (int o = kBlock / 2; o > 0; o >>= 1) {
+        if (tid < o) s_red[tid] += s_red[tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double Lr = s_red[0] / (3.0 * double(J.W) * double(J.H));
+        J.losses[r] = Lr;
+        if (J.loss_out) J.loss_out[r] = float(Lr);
+        __threadfence();
+        s_last = (atomicAdd(J.done, 1u) == unsigned(J.R - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int t = J.step_dev ? *J.step_dev : 0;
+    if (tid < J.D) {
+        const int d = tid;
+        double g = 0.0;
+        if (J.antithetic) {
+            const int P = J.R / 2;
+            for (int p = 0; p < P; ++p)
+                g += double(J.w[size_t(2 * p) * J.D + d]) * (__ldcg(J.losses + 2 * p) - __ldcg(J.losses + 2 * p + 1));
+            g /= double(2 * P);
+        } else {
+            for (int q = 0; q < J.R; ++q) g += double(J.w[size_t(q) * J.D + d]) * __ldcg(J.losses + q);
+            g /= double(J.R);
+        }
+        const float gf = float(g);
+        if (J.grad_out) J.grad_out[d] = gf;
+        if (J.theta) {
+            const int tt = t + 1;
+            const double m = double(J.b1) * J.m[d] + (1.0 - double(J.b1)) * double(gf);
+            const double v = double(J.b2) * J.v[d] + (1.0 - double(J.b2)) * double(gf) * double(gf);
+            const double mh = m / (1.0 - pow(double(J.b1), tt));
+            const double vh = v / (1.0 - pow(double(J.b2), tt));
+            J.m[d] = float(m);
+            J.v[d] = float(v);
+            J.theta[d] = float(double(J.theta[d]) - double(J.lr) * mh / (sqrt(vh) + double(J.eps)));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (J.step_dev) *J.step_dev = t + 1;
+        *J.done = 0u;  // ready for the next launch
     }
 }
 
@@ -1226,6 +1326,17 @@ cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t s
         k_trace_affected<true><<<grid, kBlock, 0, stream>>>(L);
     else
         k_trace_affected<false><<<grid, kBlock, 0, stream>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shared_epilogue(const TraceLaunch& L, int grid, cudaStream_t stream) {
+    k_shared_epilogue<<<grid, kBlock, 0, stream>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const TraceLaunch& L, int n_renders, cudaStream_t stream) {
+    if (n_renders <= 0) return cudaSuccess;
+    k_finalize<<<n_renders, kBlock, 0, stream>>>(L);
     return cudaGetLastError();
 }
 

@@ -239,7 +239,6 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     J.scenes = I.scenes;
     J.target = reinterpret_cast<const float4*>(target_dev);
     J.partials = reinterpret_cast<double*>(base + off_part);
-    J.render_done = rdone;
     J.done = ctl + 1;
     J.losses = reinterpret_cast<double*>(base + off_loss);
     J.w = I.w_out;
@@ -266,6 +265,7 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     const int cap = setup.sms * per_sm;
     const int want = (TL.total_items + kBlock / 32 - 1) / (kBlock / 32);
     e = launch_trace(TL, false, want < cap ? want : cap, st);
+    if (e == cudaSuccess) e = launch_finalize(TL, R, st);
     if (e != cudaSuccess) return report(err, err_len, PRDPT_E_CUDA, cudaGetErrorString(e));
     return PRDPT_OK;
 }
