@@ -83,7 +83,7 @@ struct prdpt_ctx {
     size_t s_partials_n = 0;
     double* s_losses = nullptr;
     size_t s_losses_n = 0;
-    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2] batch queue, [4..5] sharing counters
+    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2..3] batch queues, [4..7] sharing counters
     unsigned long long* s_share = nullptr;  // path sharing: [tiles][96] shared radiance
     size_t s_share_n = 0;
     int* s_aff = nullptr;         // path sharing: list of blocks with affected paths
@@ -98,6 +98,7 @@ struct prdpt_ctx {
     TraceJob* d_trace = nullptr;
     size_t batch_cap = 0;
     int batch_items = 0, batch_blocks = 0;
+    int batch_nshare = 0, batch_items_share = 0;  // path-sharing jobs come first in the packed arrays
     // optional CUDA-event timing of the render kernel, recorded on its launch stream
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -199,8 +200,13 @@ int grid_for(prdpt_ctx* c, int items, bool render, int ctas_per_sm) {
     return need < cap ? need : cap;
 }
 
-// Launch the render kernel, bracketed by events on its stream when timing is on.
-cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStream_t stream, int ctas_per_sm) {
+// Launch the render kernel(s), bracketed by events on their stream when timing is on.
+// Ls[0..nL): render-kernel launches (a packed step has one for its path-sharing jobs and
+// one for the rest); a launch with share = 1 is followed by the affected-path and block
+// epilogue passes over its jobs. fin (null when rendering only) covers every render of
+// every job for the per-render losses, gradient and Adam.
+cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch* Ls, int nL, const TraceLaunch* fin, bool render,
+                        cudaStream_t stream, int ctas_per_sm) {
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (c->timing) {
         if (!c->ev_free.empty()) {
@@ -214,16 +220,20 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch& L, bool render, cudaStr
         cudaError_t e = cudaEventRecord(ev.first, stream);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_trace(L, render, grid_for(c, L.total_items, render, ctas_per_sm), stream);
-    if (e != cudaSuccess) return e;
-    if (!render && !L.jobs && L.job0.share) {  // affected paths per render, then their blocks' errors
-        e = launch_trace_affected(L, grid_for(c, 1 << 30, false, ctas_per_sm), stream);
-        if (e != cudaSuccess) return e;
-        e = launch_shared_epilogue(L, grid_for(c, 1 << 30, false, 0), stream);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nL; ++i) {
+        e = launch_trace(Ls[i], render, grid_for(c, Ls[i].total_items, render, ctas_per_sm), stream);
         if (e != cudaSuccess) return e;
     }
-    if (!render) {  // per-render losses, gradient, Adam
-        e = launch_finalize(L, L.jobs ? L.fin_total : L.job0.R, stream);
+    for (int i = 0; i < nL && !render; ++i) {
+        if (!Ls[i].share) continue;  // affected paths per render, then their blocks' errors
+        e = launch_trace_affected(Ls[i], grid_for(c, 1 << 30, false, ctas_per_sm), stream);
+        if (e != cudaSuccess) return e;
+        e = launch_shared_epilogue(Ls[i], grid_for(c, 1 << 30, false, 0), stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (fin) {  // per-render losses, gradient, Adam
+        e = launch_finalize(*fin, fin->jobs ? fin->fin_total : fin->job0.R, stream);
         if (e != cudaSuccess) return e;
     }
     if (c->timing) {
@@ -500,7 +510,7 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, true, st_, o->ctas_per_sm));
+    PRDPT_CUDA(timed_trace(c, &TL, 1, nullptr, true, st_, o->ctas_per_sm));
     return PRDPT_OK;
 }
 
@@ -589,7 +599,7 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     IL.job0.w_out = c->s_w;
     IL.total_blocks = R;
     IL.queue_reset = c->s_ctl + 0;
-    IL.share_reset = probe.share ? c->s_ctl + 4 : nullptr;
+    IL.job0.share_reset = probe.share ? c->s_ctl + 4 : nullptr;
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
     TraceJob& J = TL.job0;
@@ -624,10 +634,11 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         J.share_ctl = c->s_ctl + 4;
     }
     TL.total_items = J.share ? tiles : R * tiles;
+    TL.share = J.share;
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, false, st_, o->ctas_per_sm));
+    PRDPT_CUDA(timed_trace(c, &TL, 1, &TL, false, st_, o->ctas_per_sm));
     return PRDPT_OK;
 }
 
@@ -767,6 +778,7 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         T.aff_tiles = j->aff;
         T.share_ctl = share_ctl;
         j->share_ctl = share_ctl;
+        I.share_reset = share_ctl;
     }
     s->jobs++;
     c->jobs.push_back(j);
@@ -783,15 +795,15 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     IL.job0 = j->inst;
     IL.total_blocks = j->R;
     IL.queue_reset = j->queue;
-    IL.share_reset = j->trace.share ? j->share_ctl : nullptr;
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
     TL.job0 = j->trace;
     TL.total_items = j->trace.share ? j->tiles : j->R * j->tiles;
+    TL.share = j->trace.share;
     TL.queue = j->queue;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, false, st_, j->ctas_per_sm));
+    PRDPT_CUDA(timed_trace(c, &TL, 1, &TL, false, st_, j->ctas_per_sm));
     return PRDPT_OK;
 }
 
@@ -801,22 +813,37 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     std::vector<int> ids(job_ids, job_ids + n);
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     if (ids != c->batch_ids) {
-        std::vector<InstJob> inst(n);
-        std::vector<TraceJob> trace(n);
-        int blocks = 0, items = 0;
+        // path-sharing jobs first (one render-kernel launch with items = pixel blocks), then
+        // the rest (items = (render, block)); the order of the jobs does not change results
+        std::vector<Job*> order;
         for (int i = 0; i < n; ++i) {
             Job* j = get_job(c, ids[i]);
             if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job in batch");
             for (int q = 0; q < i; ++q)
                 if (ids[q] == ids[i]) return fail(PRDPT_E_INVALID_ARG, "a job appears twice in a batch");
+        }
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i < n; ++i) {
+                Job* j = get_job(c, ids[i]);
+                if ((j->trace.share != 0) == (pass == 0)) order.push_back(j);
+            }
+        std::vector<InstJob> inst(n);
+        std::vector<TraceJob> trace(n);
+        int blocks = 0, items = 0, nshare = 0, items_share = 0;
+        for (int i = 0; i < n; ++i) {
+            Job* j = order[i];
+            if (i > 0 && !j->trace.share && order[i - 1]->trace.share) items = 0;  // second launch
             inst[i] = j->inst;
             inst[i].block_begin = blocks;
             blocks += j->R;
             trace[i] = j->trace;
-            trace[i].share = 0;  // packed launches trace every render of every job
             trace[i].item_begin = items;
-            trace[i].fin_begin = blocks - j->R;  // same prefix as the instantiation CTAs
-            items += j->R * j->tiles;
+            trace[i].fin_begin = blocks - j->R;  // same prefix as the sampler CTAs
+            items += j->trace.share ? j->tiles : j->R * j->tiles;
+            if (j->trace.share) {
+                nshare++;
+                items_share = items;
+            }
         }
         PRDPT_CUDA(cudaStreamSynchronize(st_));  // the old descriptors may still be in use
         if ((size_t)n > c->batch_cap) {
@@ -836,23 +863,44 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
         PRDPT_CUDA(cudaMemcpy(c->d_trace, trace.data(), sizeof(TraceJob) * n, cudaMemcpyHostToDevice));
         c->batch_ids = ids;
         c->batch_blocks = blocks;
-        c->batch_items = items;
+        c->batch_nshare = nshare;
+        c->batch_items_share = items_share;
+        c->batch_items = nshare < n ? items : 0;
     }
     InstLaunch IL{};
     IL.jobs = c->d_inst;
     IL.njobs = n;
     IL.total_blocks = c->batch_blocks;
     IL.queue_reset = c->s_ctl + 2;
+    IL.queue_reset2 = c->s_ctl + 3;
     PRDPT_CUDA(launch_instantiate(IL, st_));
-    TraceLaunch TL{};
-    TL.jobs = c->d_trace;
-    TL.njobs = n;
-    TL.fin_total = c->batch_blocks;
-    TL.total_items = c->batch_items;
-    TL.queue = c->s_ctl + 2;
-    TL.counters = c->counting ? c->counters : nullptr;
-    TL.status = c->status;
-    PRDPT_CUDA(timed_trace(c, TL, false, st_, 0));
+    TraceLaunch TL[2] = {};
+    int nL = 0;
+    if (c->batch_nshare > 0) {  // path-sharing jobs
+        TraceLaunch& T = TL[nL++];
+        T.jobs = c->d_trace;
+        T.njobs = c->batch_nshare;
+        T.total_items = c->batch_items_share;
+        T.share = 1;
+        T.queue = c->s_ctl + 2;
+    }
+    if (c->batch_nshare < n) {  // every render of the other jobs
+        TraceLaunch& T = TL[nL++];
+        T.jobs = c->d_trace + c->batch_nshare;
+        T.njobs = n - c->batch_nshare;
+        T.total_items = c->batch_items;
+        T.queue = c->s_ctl + 3;
+    }
+    for (int i = 0; i < nL; ++i) {
+        TL[i].counters = c->counting ? c->counters : nullptr;
+        TL[i].status = c->status;
+    }
+    TraceLaunch FL{};
+    FL.jobs = c->d_trace;
+    FL.njobs = n;
+    FL.fin_total = c->batch_blocks;
+    FL.status = c->status;
+    PRDPT_CUDA(timed_trace(c, TL, nL, &FL, false, st_, 0));
     return PRDPT_OK;
 }
 

@@ -89,6 +89,7 @@ struct InstJob {
     int anneal, total_steps;
     float sigma_min, c_radial;  // c_radial = sqrt(2) Gamma((D+1)/2) / Gamma(D/2)
     int block_begin;          // first CTA index of this job in a packed launch
+    unsigned* share_reset;    // [4] path-sharing counters of the job, zeroed by its first CTA, or null
 };
 
 // Per-job description of one render launch. The image is cut into blocks of
@@ -134,6 +135,7 @@ struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)
     const TraceJob* jobs;     // packed launch: [njobs] in device memory
     int njobs, total_items;
+    int share;                // 1: every job of the launch shares paths (selects the kernel variant)
     int fin_total;            // packed launch: finalisation CTAs (sum of R over jobs)
     unsigned* queue;          // work-queue head, zeroed by the instantiation launch
     unsigned long long* counters;  // [8] or null (null: the uncounted kernel variant runs)
@@ -145,7 +147,7 @@ struct InstLaunch {
     const InstJob* jobs;
     int njobs, total_blocks;
     unsigned* queue_reset;    // zeroed by CTA 0
-    unsigned* share_reset;    // [4] path-sharing counters zeroed by CTA 0, or null
+    unsigned* queue_reset2;   // zeroed by CTA 0 (second queue of a packed launch), or null
 };
 
 // Launchers (kernels.cu). All enqueue on `stream` and return the launch error.

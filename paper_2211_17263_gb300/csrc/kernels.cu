@@ -118,8 +118,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     const int tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) {
         if (L.queue_reset) *L.queue_reset = 0u;
-        if (L.share_reset)
-            for (int i = 0; i < 4; ++i) L.share_reset[i] = 0u;
+        if (L.queue_reset2) *L.queue_reset2 = 0u;
     }
     if (tid == 0) {
         int j = 0;
@@ -136,6 +135,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     __syncthreads();
     const InstJob& J = L.jobs ? L.jobs[s_job] : L.job0;
     const int r = blockIdx.x - J.block_begin;
+    if (r == 0 && tid == 0 && J.share_reset)
+        for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
     const int D = J.D;
     const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
 
@@ -1024,18 +1025,23 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
     const unsigned lt_mask = (1u << lane) - 1u;
     InstScene& S = s_scene[warp];
     TraceJob& J = s_job[warp];
+    Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    const int njobs = L.jobs ? L.njobs : 1;
+    for (int jb = 0; jb < njobs; ++jb) {  // the jobs of a packed launch one after another
     {
-        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + jb : &L.job0);
         unsigned* dst = reinterpret_cast<unsigned*>(&J);
         for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
         __syncwarp();
     }
+    const bool job_shares = J.share != 0;
+    __syncwarp();  // every lane has read the descriptor before the next copy may overwrite it
+    if (!job_shares) continue;
     const unsigned n_codes = __ldcg(J.share_ctl + 1);
     const unsigned n_chunks = (n_codes + kAffChunk - 1) / kAffChunk;
     const unsigned n_items = n_chunks * unsigned(J.R);
     const unsigned magic_W = 0xffffffffu / unsigned(J.W) + 1u;
     int cur_r = -1;
-    Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(J.share_ctl + 2, 1u);
@@ -1090,6 +1096,7 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
         }
         __syncwarp();
     }
+    }
     if (kCount) {
         const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
                                           warp_sum_u(cnt.paths), warp_sum_u(cnt.vertices), warp_sum_u(cnt.shadow),
@@ -1108,12 +1115,17 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
     __shared__ TraceJob s_job[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TraceJob& J = s_job[warp];
+    const int njobs = L.jobs ? L.njobs : 1;
+    for (int jb = 0; jb < njobs; ++jb) {  // the jobs of a packed launch one after another
     {
-        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + jb : &L.job0);
         unsigned* dst = reinterpret_cast<unsigned*>(&J);
         for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
         __syncwarp();
     }
+    const bool job_shares = J.share != 0;
+    __syncwarp();  // every lane has read the descriptor before the next copy may overwrite it
+    if (!job_shares) continue;
     const unsigned n_items = __ldcg(J.share_ctl + 0);
     const double inv = 1.0 / (double(J.spp) * double(kFix));
     for (;;) {
@@ -1170,6 +1182,7 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
             }
         }
         __syncwarp();
+    }
     }
 }
 
@@ -1305,7 +1318,7 @@ int trace_blocks_per_sm(bool render_mode) {
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream) {
     if (L.total_items <= 0) return cudaSuccess;
     const bool count = L.counters != nullptr;
-    const bool share = !render_mode && !L.jobs && L.job0.share;
+    const bool share = !render_mode && L.share;
     if (render_mode && count)
         k_trace<true, true, false><<<grid, kBlock, 0, stream>>>(L);
     else if (render_mode)

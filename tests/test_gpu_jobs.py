@@ -69,6 +69,46 @@ def test_packed_steps_equal_alone(ctx):
         j.release()
 
 
+def test_packed_mixed_sharing_equal_alone(ctx):
+    """A batch mixing path-sharing jobs (items = pixel blocks, affected-path and epilogue
+    passes) and per-render jobs, listed in interleaved order: the packed step splits them
+    into two render launches over one sampler and one finalisation launch; every job
+    still matches its own single-job step bit for bit, as do different batch orders."""
+    from paper_2211_17263_gb300 import api
+    cfgs = [(workloads.config_occlusion(seed=11), 72, 56, 4, 3, 1),  # per-render (sharing off)
+            (workloads.config_occlusion(seed=12), 64, 48, 8, 4, 0),  # path sharing
+            (workloads.config_gi_box(seed=13), 40, 40, 4, 2, 1),
+            (workloads.config_small(seed=14), 56, 40, 4, 2, 0),
+            (workloads.config_gi_box(seed=15), 48, 40, 2, 3, 0)]
+    wls, flags = [], []
+    for wl, w, h, spp, pairs, off in cfgs:
+        wls.append(workloads.scaled(wl, width=w, height=h, spp=spp, pairs=pairs))
+        flags.append(off)
+    targets = [oracle.render_target(w) for w in wls]
+
+    def make(i):
+        scene = ctx.upload_scene(wls[i].scene, wls[i].bindings)
+        return api.Job(scene, wls[i], targets[i], no_path_sharing=flags[i])
+
+    alone = []
+    for i in range(len(wls)):
+        j = make(i)
+        for _ in range(3):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    for order in ([0, 1, 2, 3, 4], [4, 2, 3, 0, 1]):
+        jobs = {i: make(i) for i in order}
+        for _ in range(3):
+            api.step_batch(ctx, [jobs[i] for i in order])
+        for i in order:
+            b = jobs[i].read()
+            assert b["steps"] == 3
+            for key in ("theta", "grad", "losses"):
+                assert np.array_equal(alone[i][key], b[key]), (order, i, key)
+            jobs[i].release()
+
+
 def test_job_release_and_reuse_of_batch(ctx):
     from paper_2211_17263_gb300 import api
     wl = workloads.scaled(workloads.config_small(), width=16, height=16, spp=1, pairs=1)
