@@ -33,6 +33,8 @@ UNIT = "steps/s"
 # Algorithmic FP32 operations (add/sub/mul = 1, fma = 2, div/sqrt/rsqrt = 1; compares
 # and min/max not counted) per unit of work of the path tracer.
 FLOPS = {"sphere_test": 22, "quad_test": 32, "box_test": 12, "path": 27, "vertex": 120}
+WORKLOADS = {"small": "config_small", "occlusion": "config_occlusion", "gi_box": "config_gi_box",
+             "caustic": "config_caustic"}
 
 
 def _env_int(name, default):
@@ -143,19 +145,30 @@ def _profiled_traffic(workload_name):
         return None
 
 
+CPU_SAMPLE_MAX_PATHS = 40_000_000  # larger steps are sampled (one pair, 4 spp) and scaled
+
+
 def cpu_baseline(wl, target, nthreads=0, budget_s=10.0, max_steps=20):
     """The FP64 oracle on whole steps of the same workload, repeated until about
-    `budget_s` seconds of wall time have passed (bounded by `max_steps`)."""
+    `budget_s` seconds of wall time have passed (bounded by `max_steps`). A step of
+    more than CPU_SAMPLE_MAX_PATHS paths is sampled instead: one antithetic pair at
+    4 spp, its time scaled by the ratio of path counts."""
     import oracle
+    import workloads
     cores = nthreads or os.cpu_count() or 1
+    run, scale, what = wl, 1.0, "whole steps"
+    if wl.paths_per_step > CPU_SAMPLE_MAX_PATHS:
+        run = workloads.scaled(wl, spp=4, pairs=1)
+        scale = wl.paths_per_step / run.paths_per_step
+        what = f"sampled steps (1 pair, 4 spp; time x{scale:.0f} by path count)"
     n, t0 = 0, time.perf_counter()
     while n < max_steps and (n == 0 or time.perf_counter() - t0 < budget_s):
-        oracle.smoothed_grad(wl, target=target, nthreads=cores, step=n)
+        oracle.smoothed_grad(run, target=target, nthreads=cores, step=n)
         n += 1
-    dt = (time.perf_counter() - t0) / n
+    dt = (time.perf_counter() - t0) / n * scale
     return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} whole steps ({wl.renders} renders at {wl.width}x{wl.height}, {wl.spp} spp), "
-                      f"{dt:.2f} s each", "cpu_model": _cpu_model()}
+            "sample": f"{n} {what} ({wl.renders} renders at {wl.width}x{wl.height}, {wl.spp} spp), "
+                      f"{dt:.2f} s per full step", "cpu_model": _cpu_model()}
 
 
 def serving_bench(device, n_jobs, steps_per_job, gpaths_per_s, seed=0):
@@ -229,6 +242,8 @@ def main():
     ap.add_argument("--block-pixels", type=int, default=0, help="pixels per warp work item (8, 16, 32; 0 = auto)")
     ap.add_argument("--serving-jobs", type=int, default=64, help="jobs in the serving mix (0 = skip serving)")
     ap.add_argument("--serving-steps", type=int, default=4, help="steps per served job")
+    ap.add_argument("--workload", default="occlusion", choices=sorted(WORKLOADS),
+                    help="occlusion is the headline workload; the others are measured on request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -253,8 +268,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    wl = workloads.config_occlusion(seed=rank)  # one independent replica per rank
+    wl = getattr(workloads, WORKLOADS[args.workload])(seed=rank)  # one independent replica per rank
     ctx = api.Context(local)
+    probe_tflops, probe_ms = ctx.fp32_peak_probe()  # FMA-chain launch: confirms the FP32 peak
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=f"cuda:{local}")  # noqa: E731
     target = scene.render_batch(dev(wl.theta_ref[None]), wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
@@ -399,12 +415,14 @@ def main():
                 "bound": "alu", "achieved": p_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": p_achieved / fp32_peak, "kernel": "k_trace (path sharing off) + k_finalize",
                 "ms_per_step": p_avg_ms, "paths_per_step": pcounts[3]},
+            "fp32_probe": {"achieved_tflops": probe_tflops, "ms": probe_ms,
+                           "frac_of_peak": probe_tflops / fp32_peak},
             "e2e": e2e,
             "gpu_launches": (5 if counts[3] < wl.paths_per_step else 3) * args.steps,
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
         }
-        if world == 1 and args.serving_jobs > 0:
+        if world == 1 and args.serving_jobs > 0 and args.workload == "occlusion":
             line["serving"] = serving_bench(local, args.serving_jobs, args.serving_steps,
                                             line["mpaths_per_s"] / 1000.0)
         if world == 1 and not args.no_cpu_baseline:

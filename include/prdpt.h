@@ -230,6 +230,15 @@ prdpt_status prdpt_kernel_timing_read(prdpt_ctx* ctx, double* total_ms, int64_t*
 /* Device memory the context currently holds (scenes, jobs, scratch), in bytes. */
 prdpt_status prdpt_memory_used(prdpt_ctx* ctx, uint64_t* bytes_out);
 
+/* FP32 issue-rate probe (a measurement utility; the paper has no counterpart): one
+ * full-occupancy launch on every SM in which each thread runs independent fused
+ * multiply-add chains for `iters` iterations (16 flop per thread per iteration), timed
+ * with CUDA events after a short warm-up launch on a stream of its own. Writes the
+ * achieved FP32 TFLOP/s, the denominator of the render kernels' roofline, and the
+ * launch's duration in ms (ms_out may be NULL). Synchronous; allocates and frees a
+ * small device buffer. */
+prdpt_status prdpt_fp32_peak_probe(prdpt_ctx* ctx, int32_t iters, double* tflops_out, double* ms_out);
+
 /* Synchronise `stream` and check the context's device status word. */
 prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);
 

@@ -68,6 +68,10 @@ class Context:
     def memory_used(self) -> int:
         return capi.prdpt_memory_used(self.handle)
 
+    def fp32_peak_probe(self, iters: int = 1 << 19) -> tuple[float, float]:
+        """Achieved FP32 FMA TFLOP/s of a full-occupancy FMA-chain launch, and its ms."""
+        return capi.prdpt_fp32_peak_probe(self.handle, iters)
+
     def sync(self, stream=None):
         capi.prdpt_sync(self.handle, _stream_ptr(stream))
 

@@ -33,6 +33,7 @@ EXPORTS = [
     "prdpt_job_create", "prdpt_step", "prdpt_step_batch", "prdpt_job_read", "prdpt_job_release",
     "prdpt_philox_words", "prdpt_counters_enable", "prdpt_counters_read", "prdpt_kernel_timing_enable",
     "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static", "prdpt_memory_used",
+    "prdpt_fp32_peak_probe",
 ]
 
 
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True):
         "prdpt_kernel_timing_read": ([vp, P(C.c_double), P(C.c_int64)], i32),
         "prdpt_sync": ([vp, vp], i32),
         "prdpt_memory_used": ([vp, P(u64)], i32),
+        "prdpt_fp32_peak_probe": ([vp, i32, P(C.c_double), P(C.c_double)], i32),
         "prdpt_smoothed_grad_static": ([P(prdpt_scene_desc), P(prdpt_param_binding), i32, vp, vp,
                                         P(prdpt_grad_opts), vp, vp, vp, vp, C.c_char_p, C.c_size_t], i32),
     }
@@ -242,6 +244,13 @@ def prdpt_smoothed_grad_static(desc, binds, D, theta_dev, sigma_dev, opts, targe
     if code != PRDPT_OK:
         raise PrdptError(code, "prdpt_smoothed_grad_static", err.value.decode(errors="replace"))
     return code
+
+
+def prdpt_fp32_peak_probe(ctx, iters: int = 1 << 19) -> tuple[float, float]:
+    """(achieved FP32 TFLOP/s, launch ms) of the FMA-chain probe."""
+    tf, ms = C.c_double(), C.c_double()
+    check(load().prdpt_fp32_peak_probe(ctx, int(iters), C.byref(tf), C.byref(ms)), "prdpt_fp32_peak_probe", ctx)
+    return tf.value, ms.value
 
 
 def prdpt_memory_used(ctx) -> int:

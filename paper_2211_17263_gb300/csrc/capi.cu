@@ -48,7 +48,9 @@ struct Job {
     float* w = nullptr;
     unsigned long long* share = nullptr;
     unsigned long long* accaff = nullptr;
-    unsigned* codes = nullptr;
+    void* afflist = nullptr;
+    float4* varbox = nullptr;
+    unsigned* cursor = nullptr;
     int* aff = nullptr;
     double *partials = nullptr, *losses_d = nullptr;
     unsigned* rdone = nullptr;
@@ -90,8 +92,12 @@ struct prdpt_ctx {
     size_t s_aff_n = 0;
     unsigned long long* s_accaff = nullptr;  // path sharing: [R][H*W][3] affected radiance (kept zero)
     size_t s_accaff_n = 0;
-    unsigned* s_codes = nullptr;  // path sharing: affected (pixel, sample) codes
-    size_t s_codes_n = 0;
+    unsigned char* s_afflist = nullptr;  // path sharing: recorded paths (masks, codes, radiance)
+    size_t s_afflist_n = 0;
+    float4* s_varbox = nullptr;   // path sharing: [R][kMaxVariant][2] per-render bounds
+    size_t s_varbox_n = 0;
+    unsigned* s_cursor = nullptr; // path sharing: [R] per-render cursors
+    size_t s_cursor_n = 0;
     // packed launches
     std::vector<int> batch_ids;
     InstJob* d_inst = nullptr;
@@ -430,14 +436,49 @@ prdpt_status prdpt_scene_release(prdpt_ctx* c, int32_t scene_id) {
 // Path sharing across renders is exact when all renders share their path samples (crn)
 // and only geometry is perturbed: emitters and their materials must stay fixed, at most
 // kMaxVariant primitives move, and a pixel's samples fit one 64-bit mask.
-static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o) {
+// Recorded-path list of a path-sharing job with room for n paths: codes and segment
+// words (u32) and shared-pass radiance (3 floats), then the touching-segment pool
+// (2 float4 per slot, kSeg slots per path for one path in 16; a path that finds the
+// pool full is traced again by every render).
+static size_t seg_slots(size_t n) {
+    const size_t paths = n / 16 > 4096 ? n / 16 : 4096;
+    return paths * kSeg;
+}
+
+static size_t afflist_bytes(size_t n) {
+    return 2 * ((sizeof(unsigned) * n + 255) & ~size_t(255)) + ((sizeof(float) * 3 * n + 255) & ~size_t(255)) +
+           sizeof(float4) * 2 * seg_slots(n);
+}
+
+static void afflist_carve(TraceJob& J, void* base, size_t n) {
+    char* b = static_cast<char*>(base);
+    J.aff_codes = reinterpret_cast<unsigned*>(b);
+    b += (sizeof(unsigned) * n + 255) & ~size_t(255);
+    J.aff_segw = reinterpret_cast<unsigned*>(b);
+    b += (sizeof(unsigned) * n + 255) & ~size_t(255);
+    J.aff_lsh = reinterpret_cast<float*>(b);
+    b += (sizeof(float) * 3 * n + 255) & ~size_t(255);
+    J.seg_pool = reinterpret_cast<float4*>(b);
+    J.seg_cap = unsigned(seg_slots(n));
+}
+
+// Decide whether a gradient job shares paths across its renders and, if so, record its
+// perturbed primitives in J (and in I, whose launch writes their per-render bounds).
+static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o, InstJob* I = nullptr) {
     J.share = 0;
     J.n_var = 0;
     J.var_prims = 0u;
     J.var_mats = 0u;
+    if (I) {
+        I->n_var = 0;
+        I->var_box = nullptr;
+    }
     if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp) return;
-    // per-render radiance buffers of the affected paths: 24 bytes per render and pixel
-    if (24.0 * 2.0 * o->pairs * double(o->width) * double(o->height) > double(size_t(512) << 20)) return;
+    // per-render radiance buffers (24 bytes per render and pixel) and the recorded-path
+    // list (20 bytes per path plus the segment pool) each within 512 MB
+    const double pix = double(o->width) * double(o->height);
+    if (24.0 * 2.0 * o->pairs * pix > double(size_t(512) << 20)) return;
+    if (double(afflist_bytes(size_t(pix) * o->spp)) > double(size_t(512) << 20)) return;
     bool var_prim[kMaxPrims] = {};
     for (int d = 0; d < B.D; ++d) {
         const int k = B.bind_kind[d], idx = B.bind_index[d];
@@ -445,16 +486,22 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
         if (k == kBindAlbedo) J.var_mats |= 1u << idx;
         if (k == kBindPos || k == kBindRadius) var_prim[idx] = true;
     }
+    int prims[kMaxVariant];
     for (int i = 0; i < B.n_prims; ++i) {
         const float* mp = B.mat_param[B.prim_mat[i]];
         const bool emitter = mp[3] > 0.f || mp[4] > 0.f || mp[5] > 0.f;
         if (emitter && (var_prim[i] || ((J.var_mats >> B.prim_mat[i]) & 1u))) return;
         if (!var_prim[i]) continue;
         if (J.n_var == kMaxVariant) return;
+        prims[J.n_var] = i;
         J.var_slot[J.n_var++] = B.prim_slot[i];
         J.var_prims |= 1u << B.prim_slot[i];
     }
     J.share = 1;
+    if (I) {
+        I->n_var = J.n_var;
+        for (int k = 0; k < J.n_var; ++k) I->var_prim[k] = prims[k];
+    }
 }
 
 static void fill_inst_common(InstJob& J, const Scene* s, int R, int D, int W, int H) {
@@ -583,7 +630,9 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         if (prdpt_status st = grow(c, &c->s_share, &c->s_share_n, (size_t)tiles * 96)) return st;
         if (prdpt_status st = grow(c, &c->s_aff, &c->s_aff_n, (size_t)tiles)) return st;
         if (prdpt_status st = grow_zeroed(c, &c->s_accaff, &c->s_accaff_n, (size_t)R * pix * 3)) return st;
-        if (prdpt_status st = grow(c, &c->s_codes, &c->s_codes_n, pix * o->spp)) return st;
+        if (prdpt_status st = grow(c, &c->s_afflist, &c->s_afflist_n, afflist_bytes(pix * o->spp))) return st;
+        if (prdpt_status st = grow(c, &c->s_varbox, &c->s_varbox_n, (size_t)R * kMaxVariant * 2)) return st;
+        if (prdpt_status st = grow(c, &c->s_cursor, &c->s_cursor_n, (size_t)R)) return st;
     }
     if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)R)) return st;
     if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)R * D > (size_t)kMaxD ? (size_t)R * D : (size_t)kMaxD))
@@ -600,6 +649,11 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     IL.total_blocks = R;
     IL.queue_reset = c->s_ctl + 0;
     IL.job0.share_reset = probe.share ? c->s_ctl + 4 : nullptr;
+    fill_share(probe, s->host, o, &IL.job0);
+    if (probe.share) {
+        IL.job0.var_box = c->s_varbox;
+        IL.job0.aff_cursor = c->s_cursor;
+    }
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
     TraceJob& J = TL.job0;
@@ -629,7 +683,9 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     if (J.share) {
         J.share_acc = c->s_share;
         J.acc_aff = c->s_accaff;
-        J.aff_codes = c->s_codes;
+        afflist_carve(J, c->s_afflist, (size_t)o->width * o->height * o->spp);
+        J.var_box = c->s_varbox;
+        J.aff_cursor = c->s_cursor;
         J.aff_tiles = c->s_aff;
         J.share_ctl = c->s_ctl + 4;
     }
@@ -687,7 +743,10 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
                           ~size_t(255);
     const size_t off_cd = (off_aa + (probe.share ? sizeof(unsigned long long) * 3 * (size_t)R * pix : 0) + 255) &
                           ~size_t(255);
-    const size_t off_af = (off_cd + (probe.share ? sizeof(unsigned) * pix * o->spp : 0) + 255) & ~size_t(255);
+    const size_t off_vb = (off_cd + (probe.share ? afflist_bytes(pix * o->spp) : 0) + 255) & ~size_t(255);
+    const size_t off_cu = (off_vb + (probe.share ? sizeof(float4) * 2 * kMaxVariant * (size_t)R : 0) + 255) &
+                          ~size_t(255);
+    const size_t off_af = (off_cu + (probe.share ? sizeof(unsigned) * (size_t)R : 0) + 255) & ~size_t(255);
     const size_t total = off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0);
     void* base = nullptr;
     if (prdpt_status st = dev_alloc(c, &base, total)) {
@@ -715,7 +774,9 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     if (probe.share) {
         j->share = reinterpret_cast<unsigned long long*>(b + off_sh);
         j->accaff = reinterpret_cast<unsigned long long*>(b + off_aa);
-        j->codes = reinterpret_cast<unsigned*>(b + off_cd);
+        j->afflist = b + off_cd;
+        j->varbox = reinterpret_cast<float4*>(b + off_vb);
+        j->cursor = reinterpret_cast<unsigned*>(b + off_cu);
         j->aff = reinterpret_cast<int*>(b + off_af);
     }
     cudaError_t e = cudaMemset(base, 0, off_w);
@@ -770,11 +831,15 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     T.tiles = tiles;
     T.n_prims = s->host.n_prims;
     T.n_mats = s->host.n_mats;
-    fill_share(T, s->host, o);
+    fill_share(T, s->host, o, &I);
     if (T.share) {
         T.share_acc = j->share;
         T.acc_aff = j->accaff;
-        T.aff_codes = j->codes;
+        afflist_carve(T, j->afflist, pix * o->spp);
+        T.var_box = j->varbox;
+        I.var_box = j->varbox;
+        T.aff_cursor = j->cursor;
+        I.aff_cursor = j->cursor;
         T.aff_tiles = j->aff;
         T.share_ctl = share_ctl;
         j->share_ctl = share_ctl;
@@ -1000,6 +1065,38 @@ prdpt_status prdpt_memory_used(prdpt_ctx* c, uint64_t* bytes_out) {
     if (!c || !bytes_out) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
     *bytes_out = c->used;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_fp32_peak_probe(prdpt_ctx* c, int32_t iters, double* tflops_out, double* ms_out) {
+    if (!c || !tflops_out || iters < 1) return fail(PRDPT_E_INVALID_ARG, "bad argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    int per_sm = 0;
+    PRDPT_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, c->device));
+    const int blocks = c->sms * (per_sm / kBlock > 0 ? per_sm / kBlock : 1);
+    void* out = nullptr;
+    if (prdpt_status st = dev_alloc(c, &out, sizeof(float) * (size_t)blocks * kBlock)) return st;
+    cudaStream_t st_ = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    cudaError_t e = cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch_ffma_probe(static_cast<float*>(out), blocks, iters / 8 + 1, st_);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st_);
+    if (e == cudaSuccess) e = launch_ffma_probe(static_cast<float*>(out), blocks, iters, st_);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st_);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st_) cudaStreamDestroy(st_);
+    dev_free(c, out);
+    if (e != cudaSuccess) return fail(PRDPT_E_CUDA, std::string("fp32 peak probe: ") + cudaGetErrorString(e));
+    const double flops = double(blocks) * kBlock * double(iters) * ffma_probe_flops_per_thread_iter();
+    *tflops_out = flops / (double(ms) * 1e-3) / 1e12;
+    if (ms_out) *ms_out = ms;
     return PRDPT_OK;
 }
 

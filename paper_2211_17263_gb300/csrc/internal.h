@@ -29,6 +29,9 @@ constexpr int kMaxRenders = 2 * kMaxPairs;
 constexpr int kBlock = 256;      // render CTA size
 constexpr int kInstBlock = 64;   // instantiation CTA size (one thread per parameter)
 constexpr float kEps = 1e-4f;    // ray t_min and surface offset (scene units)
+constexpr int kMaxVariant = 4;   // path sharing: perturbed primitives
+constexpr int kMaxShareSpp = 64; // path sharing: samples per pixel (6 bits of a path code)
+constexpr int kSeg = 4;          // path sharing: touching segments kept per path
 
 constexpr unsigned kTagPerturb = 1u;
 constexpr unsigned kTagPath = 2u;
@@ -90,6 +93,12 @@ struct InstJob {
     float sigma_min, c_radial;  // c_radial = sqrt(2) Gamma((D+1)/2) / Gamma(D/2)
     int block_begin;          // first CTA index of this job in a packed launch
     unsigned* share_reset;    // [4] path-sharing counters of the job, zeroed by its first CTA, or null
+    // path sharing: bounds of each perturbed primitive in each render, [R][kMaxVariant][2]
+    // (min, max corner, inflated), written by the render's CTA; null when not sharing
+    float4* var_box;
+    unsigned* aff_cursor;     // [R] per-render cursors of the per-render pass, zeroed by the render's CTA
+    int n_var;
+    int var_prim[kMaxVariant];  // the perturbed primitives (natural order indices)
 };
 
 // Per-job description of one render launch. The image is cut into blocks of
@@ -118,19 +127,24 @@ struct TraceJob {
     // item is one pixel block of all R renders. share = 0 disables it.
     int share;
     unsigned long long* share_acc;   // [tiles][3][32] shared radiance of blocks with affected paths
-    unsigned long long* acc_aff;     // [R][H*W][3] per-render radiance of affected paths (kept zero between steps)
-    unsigned* aff_codes;      // [H*W*spp] affected paths as (pixel << 6) | sample
+    unsigned long long* acc_aff;     // [R][H*W][3] per-render radiance corrections of recorded paths, 2^-32
+                                     // fixed point modulo 2^64 (kept zero between steps)
+    // recorded paths (a ray touched a union box of the perturbed primitives): [H*W*spp] capacity
+    unsigned* aff_codes;      // (pixel << 6) | sample
+    unsigned* aff_segw;       // segment word: where its touching segments are kept, or "every render"
+    float* aff_lsh;           // [3] radiance of the path in the shared pass
+    float4* seg_pool;         // [seg_cap][2] touching segments (o, tmax), (d, 0), kSeg slots per path
+    unsigned seg_cap;
+    const float4* var_box;    // [R][kMaxVariant][2] per-render bounds of the perturbed primitives
+    unsigned* aff_cursor;     // [R] next list entry of each render in the per-render pass
     int* aff_tiles;           // [tiles] blocks with affected paths (appended by the shared pass)
-    unsigned* share_ctl;      // [0] listed blocks, [1] affected paths, [2] per-render queue, [3] epilogue
-                              // queue; zeroed by the instantiation launch
+    unsigned* share_ctl;      // [0] listed blocks, [1] recorded paths, [2] segment slots claimed,
+                              // [3] epilogue queue; zeroed by the instantiation launch
     int n_var;                // perturbed primitives (<= kMaxVariant)
-    int var_slot[4];          // their record slots
+    int var_slot[kMaxVariant];  // their record slots
     unsigned var_prims;       // record-slot bitmask of perturbed primitives
     unsigned var_mats;        // bitmask of materials whose parameters are bound
 };
-constexpr int kMaxVariant = 4;
-constexpr int kMaxShareSpp = 64;  // one 64-bit sample mask per pixel
-
 struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)
     const TraceJob* jobs;     // packed launch: [njobs] in device memory
@@ -159,9 +173,12 @@ cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t s
 cudaError_t launch_shared_epilogue(const TraceLaunch& L, int grid, cudaStream_t stream);
 // Per-render losses, gradient and Adam: one CTA per render of every job in the launch.
 cudaError_t launch_finalize(const TraceLaunch& L, int n_renders, cudaStream_t stream);
-constexpr int kAffChunk = 256;  // affected paths per work item of the per-render pass
 cudaError_t launch_adam(int D, float* theta, float* m, float* v, const float* g, int t, float lr, float b1,
                         float b2, float eps, cudaStream_t stream);
+// FP32 FMA throughput probe: `blocks` CTAs of kBlock threads, each thread 2 x kFfmaChains
+// x iters flop; out holds blocks x kBlock floats.
+cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t stream);
+int ffma_probe_flops_per_thread_iter();
 cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, unsigned c2, unsigned c3, int n,
                           uint32_t* out, cudaStream_t stream);
 // Resident CTAs per SM of the render kernel.

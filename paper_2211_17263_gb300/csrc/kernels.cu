@@ -31,6 +31,8 @@
 
 namespace prdpt {
 
+constexpr unsigned kFull = 0xffffffffu;  // all lanes of a warp
+
 // ---------------------------------------------------------------------------
 // small vector helpers
 // ---------------------------------------------------------------------------
@@ -105,6 +107,31 @@ __device__ __forceinline__ float sigma_at(const InstJob& J, int d, int t) {
     return s0 - frac * (s0 - J.sigma_min);
 }
 
+// Axis-aligned bounds of a primitive record, inflated by 1e-3 scene units plus 1e-5
+// relative, so that a slab test against them is conservative for the exact FP32
+// intersection tests of the primitive (path sharing).
+__device__ __forceinline__ void prim_bounds(const float4* P, int type, float3& lo, float3& hi) {
+    if (type == kSphere) {
+        const float4 c = P[0];
+        const float rad = fabsf(c.w);
+        lo = f3(c.x - rad, c.y - rad, c.z - rad);
+        hi = f3(c.x + rad, c.y + rad, c.z + rad);
+    } else if (type == kQuad) {
+        const float3 c = xyz(P[0]), u = xyz(P[2]), v = xyz(P[3]);
+        const float3 e = f3(0.5f * (fabsf(u.x) + fabsf(v.x)), 0.5f * (fabsf(u.y) + fabsf(v.y)),
+                            0.5f * (fabsf(u.z) + fabsf(v.z)));
+        lo = c - e;
+        hi = c + e;
+    } else {
+        lo = xyz(P[0]);
+        hi = xyz(P[1]);
+    }
+    const float3 m = f3(1e-3f + 1e-5f * fmaxf(fabsf(lo.x), fabsf(hi.x)), 1e-3f + 1e-5f * fmaxf(fabsf(lo.y), fabsf(hi.y)),
+                        1e-3f + 1e-5f * fmaxf(fabsf(lo.z), fabsf(hi.z)));
+    lo = lo - m;
+    hi = hi + m;
+}
+
 // ---------------------------------------------------------------------------
 // k_instantiate: one CTA (kInstBlock threads) per render
 // ---------------------------------------------------------------------------
@@ -137,6 +164,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     const int r = blockIdx.x - J.block_begin;
     if (r == 0 && tid == 0 && J.share_reset)
         for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
+    if (tid == 0 && J.aff_cursor) J.aff_cursor[r] = 0u;
     const int D = J.D;
     const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
 
@@ -270,6 +298,13 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         S.mat[i][1] = make_float4(p[3], p[4], p[5], p[6]);
     }
     __syncthreads();
+    if (J.var_box && tid < J.n_var) {  // path sharing: this render's bounds of a perturbed primitive
+        const int i = J.var_prim[tid];
+        float3 lo, hi;
+        prim_bounds(S.prim[B.prim_slot[i]], B.prim_type[i], lo, hi);
+        J.var_box[(size_t(r) * kMaxVariant + tid) * 2 + 0] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+        J.var_box[(size_t(r) * kMaxVariant + tid) * 2 + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+    }
     if (tid == 0) {
         S.n_sph = B.n_sph;
         S.n_quad = B.n_quad;
@@ -450,31 +485,63 @@ __device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d,
     return false;
 }
 
-// Union boxes of the perturbed primitives over all R renders (shared mode), inflated so
-// that the test below is conservative against the exact per-render intersection tests.
+// Union over the job's R renders of the perturbed primitives' bounds (shared mode; each
+// render's bounds are inflated so that a slab test is conservative against the exact
+// intersection tests), and the pool that keeps the segments touching them.
 struct VarBoxes {
-    float4 lo[kMaxVariant], hi[kMaxVariant];
+    float4 lo[kMaxVariant], hi[kMaxVariant];  // union over renders
+    float4* seg_pool;                         // touching segments, kSeg slots per path
+    unsigned* seg_ctr;                        // slots claimed
+    unsigned seg_cap;                         // slots available
     int n;
     unsigned skip, mats;
 };
 
-// Does the segment o + t d, 0 <= t <= tmax, touch any union box?
+// Does the segment o + t inv^-1, 0 <= t <= tm, touch the box [lo, hi]?
+__device__ __forceinline__ bool slab_touch(float3 lo, float3 hi, float3 o, float3 inv, float tm) {
+    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tm));
+    return tn <= tf;
+}
+
+// Touching segments of a shared-pass path: the path's segment word is 0 (no segment
+// touched a union box), kSegFull (every render traces the path again: a bound material
+// was hit, or the path touched more than kSeg times, or the pool ran out) or
+// ((first slot / kSeg + 1) << 3 | count) for count <= kSeg segments kept in the pool as
+// (o, tmax), (d, 0). The per-render pass tests them against each render's own bounds.
+constexpr unsigned kSegFull = 0xffffffffu;
+
 template <bool kCount>
-__device__ __forceinline__ bool touches_variant(const VarBoxes& V, float3 o, float3 d, float tmax, Counters& cnt) {
+__device__ __forceinline__ void note_touch(const VarBoxes& V, float3 o, float3 d, float tmax, unsigned& seg,
+                                           Counters& cnt) {
     const float3 inv = rcp3(d);
     const float tm = tmax * 1.0001f + 1e-3f;
     bool hit = false;
-    for (int k = 0; k < V.n; ++k) {
-        const float3 lo = xyz(V.lo[k]), hi = xyz(V.hi[k]);
-        const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
-        const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
-        const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
-        const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-        const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tm));
-        hit = hit || (tn <= tf);
-    }
+    for (int k = 0; k < V.n; ++k) hit = hit || slab_touch(xyz(V.lo[k]), xyz(V.hi[k]), o, inv, tm);
     if (kCount) cnt.box += V.n;
-    return hit;
+    if (!hit || seg == kSegFull) return;
+    unsigned base, n;
+    if (seg == 0u) {
+        base = atomicAdd(V.seg_ctr, unsigned(kSeg));
+        n = 0u;
+        if (base + unsigned(kSeg) > V.seg_cap) {
+            seg = kSegFull;
+            return;
+        }
+    } else {
+        base = ((seg >> 3) - 1u) * unsigned(kSeg);
+        n = seg & 7u;
+        if (n == unsigned(kSeg)) {
+            seg = kSegFull;
+            return;
+        }
+    }
+    V.seg_pool[2 * size_t(base + n) + 0] = make_float4(o.x, o.y, o.z, tmax);
+    V.seg_pool[2 * size_t(base + n) + 1] = make_float4(d.x, d.y, d.z, 0.0f);
+    seg = ((base / unsigned(kSeg) + 1u) << 3) | (n + 1u);
 }
 
 __device__ __forceinline__ uint4 path_words(const InstScene& S, unsigned pixel, int s, int b, int slot) {
@@ -496,8 +563,9 @@ struct Path {
     float3 o, d, beta, L;
     unsigned pixel;  // y * W + x
     int s, b;        // sample index, vertex index
-    int slot;        // pixel slot inside the warp's block
+    int slot;        // pixel slot inside the warp's block (per-render pass: the path's record)
     bool specular;   // emission counts: camera rays and rays after specular bounces
+    unsigned seg;    // shared pass: touching-segment word (see note_touch)
 };
 
 // Camera ray of sample s through pixel (x, y): pinhole, box-filtered jitter (slot 2).
@@ -523,18 +591,22 @@ __device__ __forceinline__ void start_path(const InstScene& S, int W, int H, int
 // Random slots of vertex b: slot 0 = (light point u, v, BSDF u1, u2); slot 1 =
 // (light choice, Russian roulette, dielectric choice), drawn only when needed.
 //
-// With kShared (path sharing across renders), the scene is the invariant part only and
-// the function returns kAffected, abandoning the path, as soon as a ray segment touches a
-// perturbed primitive's union box or the path hits a material whose parameters are bound:
-// such paths are traced again per render. Otherwise the path is exactly what every render
-// traces, because all renders share its random numbers.
+// With kShared (path sharing across renders), the scene is the invariant part only. A
+// render whose perturbed primitives no ray segment of the path can meet traces exactly
+// this path, because all renders share its random numbers. Segments that touch a union
+// box are kept (note_touch) for the per-render pass, which traces the path again in the
+// renders whose own bounds a kept segment touches. A path that hits a material whose
+// parameters are bound, or that every render must trace again, returns kAffected.
 constexpr int kLive = 0, kEnded = 1, kAffected = 2;
 
 template <bool kCount, bool kShared>
 __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt,
                                        const VarBoxes* V = nullptr) {
     const Hit h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
-    if (kShared && touches_variant<kCount>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, cnt)) return kAffected;
+    if (kShared) {
+        note_touch<kCount>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, p.seg, cnt);
+        if (p.seg == kSegFull) return kAffected;
+    }
     if (h.slot < 0) {
         p.L = p.L + p.beta * xyz(S.bg);
         return kEnded;
@@ -554,7 +626,10 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
         ng = box_normal(S, h.slot, p.o, p.d, rcp3(p.d));
         mat = as_int(S.prim[h.slot][0].w);
     }
-    if (kShared && ((V->mats >> mat) & 1u)) return kAffected;
+    if (kShared && ((V->mats >> mat) & 1u)) {
+        p.seg = kSegFull;
+        return kAffected;
+    }
     const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
     const int mtype = as_int(m0.w);
     const float3 albedo = xyz(m0), emission = xyz(m1);
@@ -595,7 +670,10 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
             if (cx > 0.0f && cl > 0.0f) {
                 const float dist = dist2 * inv_dist;
                 if (!occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u)) {
-                    if (kShared && touches_variant<kCount>(*V, po, wi, dist, cnt)) return kAffected;
+                    if (kShared) {
+                        note_touch<kCount>(*V, po, wi, dist, p.seg, cnt);
+                        if (p.seg == kSegFull) return kAffected;
+                    }
                     const float g = cx * cl * (inv_dist * inv_dist) * S.light_area[li] * float(S.n_lights) *
                                     0.3183098861837907f;
                     p.L = p.L + p.beta * albedo * xyz(S.mat[lt.w][1]) * g;
@@ -675,7 +753,6 @@ constexpr int kWarps = kBlock / 32;
 #define PRDPT_TRACE_MIN_BLOCKS 3  // <= 85 registers: 24 resident warps per SM
 #endif
 constexpr int kTraceMinBlocks = PRDPT_TRACE_MIN_BLOCKS;
-constexpr unsigned kFull = 0xffffffffu;
 constexpr float kFix = 4294967296.0f;  // 2^32: fixed-point scale of the radiance accumulators
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -713,9 +790,9 @@ struct WarpSmem {
     InstScene scene;                  // the render being traced (render 0 in shared phase A)
     TraceJob job;
     unsigned long long acc[3][32];    // radiance of the block's pixels, 2^-32 fixed point
-    unsigned long long accr[3][32];   // shared mode: per-render radiance of the affected paths
-    unsigned long long mask[32];      // shared mode: affected samples of each pixel slot
-    VarBoxes vb;                      // shared mode: union boxes of the perturbed primitives
+    unsigned recorded;                // shared mode: the block has recorded paths
+    VarBoxes vb;                      // shared mode: bounds of the perturbed primitives
+
 };
 
 // Copy render r's scene (header, used materials, used primitives) into the warp's slot.
@@ -732,31 +809,15 @@ __device__ __forceinline__ void stage_scene(WarpSmem& W, const TraceJob& J, int 
     __syncwarp();
 }
 
-// Union boxes of each perturbed primitive over the job's R renders (shared mode).
+// Union over the job's R renders of each perturbed primitive's bounds (shared mode).
 __device__ void build_var_boxes(WarpSmem& W, const TraceJob& J, int lane) {
     for (int k = 0; k < J.n_var; ++k) {
-        const int slot = J.var_slot[k];
         float3 lo = f3(INFINITY, INFINITY, INFINITY), hi = f3(-INFINITY, -INFINITY, -INFINITY);
         for (int r = lane; r < J.R; r += 32) {
-            const float4* P = J.scenes[r].prim[slot];
-            float3 a, b;
-            if (slot < J.scenes[r].n_sph) {
-                const float4 c = __ldg(P);
-                const float rad = fabsf(c.w);
-                a = xyz(c) - f3(rad, rad, rad);
-                b = xyz(c) + f3(rad, rad, rad);
-            } else if (slot < J.scenes[r].n_sph + J.scenes[r].n_quad) {
-                const float3 c = xyz(__ldg(P)), u = xyz(__ldg(P + 2)), v = xyz(__ldg(P + 3));
-                const float3 e = f3(0.5f * (fabsf(u.x) + fabsf(v.x)), 0.5f * (fabsf(u.y) + fabsf(v.y)),
-                                    0.5f * (fabsf(u.z) + fabsf(v.z)));
-                a = c - e;
-                b = c + e;
-            } else {
-                a = xyz(__ldg(P));
-                b = xyz(__ldg(P + 1));
-            }
+            const float4* b = J.var_box + (size_t(r) * kMaxVariant + k) * 2;
+            const float3 a = xyz(__ldg(b)), c = xyz(__ldg(b + 1));
             lo = f3(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z));
-            hi = f3(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z));
+            hi = f3(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -767,15 +828,15 @@ __device__ void build_var_boxes(WarpSmem& W, const TraceJob& J, int lane) {
             hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
             hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
         }
-        if (lane == 0) {  // inflate: 1e-3 scene units plus 1e-5 relative
-            const float3 m = f3(1e-3f + 1e-5f * fmaxf(fabsf(lo.x), fabsf(hi.x)),
-                                1e-3f + 1e-5f * fmaxf(fabsf(lo.y), fabsf(hi.y)),
-                                1e-3f + 1e-5f * fmaxf(fabsf(lo.z), fabsf(hi.z)));
-            W.vb.lo[k] = make_float4(lo.x - m.x, lo.y - m.y, lo.z - m.z, 0.f);
-            W.vb.hi[k] = make_float4(hi.x + m.x, hi.y + m.y, hi.z + m.z, 0.f);
+        if (lane == 0) {
+            W.vb.lo[k] = make_float4(lo.x, lo.y, lo.z, 0.f);
+            W.vb.hi[k] = make_float4(hi.x, hi.y, hi.z, 0.f);
         }
     }
     if (lane == 0) {
+        W.vb.seg_pool = J.seg_pool;
+        W.vb.seg_ctr = J.share_ctl + 2;
+        W.vb.seg_cap = J.seg_cap;
         W.vb.n = J.n_var;
         W.vb.skip = J.var_prims;
         W.vb.mats = J.var_mats;
@@ -808,12 +869,13 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, int k) {
 // Trace `ntasks` path tasks with the warp as a pool: each lane holds one live path and,
 // when it ends, takes the next task (ballot + popc). decode(task, slot, sample) maps a
 // task to its pixel slot and sample; every lane calls it (it may use warp shuffles).
-// Ended paths add their radiance to acc[.][slot]; in shared mode, affected paths set
-// their sample's bit in mask[slot] instead.
+// Ended paths add their radiance to acc[.][slot]. In shared mode a path that touched a
+// perturbed primitive's union box is also recorded -- its code, segment word and
+// shared-pass radiance -- in the job's list, and *recorded is set.
 template <bool kCount, bool kShared, class Decode>
 __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, int ntasks, int x0, int y0, int vw,
                                          unsigned magic_w, Decode decode, unsigned long long (&acc)[3][32],
-                                         unsigned long long* mask, const VarBoxes* V, Counters& cnt, int lane) {
+                                         unsigned* recorded, const VarBoxes* V, Counters& cnt, int lane) {
     const unsigned lt_mask = (1u << lane) - 1u;
     Path p;
     int task = lane;
@@ -823,6 +885,7 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
     if (alive) {
         const int row = div_magic(slot, vw, magic_w);
         start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+        if (kShared) p.seg = 0u;
         if (kCount) ++cnt.paths;
     }
     int next = 32;
@@ -830,21 +893,29 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
         int st = kLive;
         if (alive) st = advance<kCount, kShared>(S, J.depth, J.rr_start, p, cnt, V);
         const bool ended = alive && st != kLive;
-        if (ended && st == kEnded) {
+        // every ended path counts in the shared radiance; the per-render pass later adds,
+        // for each render in a recorded path's mask, its own radiance minus this value
+        if (ended) {
             atomicAdd(&acc[0][p.slot], to_fixed(p.L.x));
             atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
             atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
         }
-        if (kShared) {  // affected paths: append (pixel, sample) to the job's list
-            const unsigned am = __ballot_sync(kFull, ended && st == kAffected);
+        if (kShared) {  // record the paths some render must trace itself
+            const bool rec = ended && p.seg != 0u;
+            const unsigned am = __ballot_sync(kFull, rec);
             if (am) {
                 unsigned base = 0;
                 if (lane == __ffs(am) - 1) base = atomicAdd(J.share_ctl + 1, unsigned(__popc(am)));
                 base = __shfl_sync(kFull, base, __ffs(am) - 1);
-                if (ended && st == kAffected) {
-                    J.aff_codes[base + __popc(am & lt_mask)] = (p.pixel << 6) | unsigned(p.s);
-                    if (mask) mask[0] = 1ull;  // the block has affected paths
+                if (rec) {
+                    const unsigned e = base + __popc(am & lt_mask);
+                    J.aff_codes[e] = (p.pixel << 6) | unsigned(p.s);
+                    J.aff_segw[e] = p.seg;
+                    J.aff_lsh[3 * size_t(e) + 0] = p.L.x;
+                    J.aff_lsh[3 * size_t(e) + 1] = p.L.y;
+                    J.aff_lsh[3 * size_t(e) + 2] = p.L.z;
                 }
+                if (lane == 0) *recorded = 1u;
             }
         }
         const unsigned need = __ballot_sync(kFull, ended);
@@ -856,6 +927,7 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
             if (alive) {
                 const int row = div_magic(slot, vw, magic_w);
                 start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+                if (kShared) p.seg = 0u;
                 if (kCount) ++cnt.paths;
             }
         }
@@ -864,21 +936,16 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
     __syncwarp();
 }
 
-// Pixel means of render r's block (acc, plus accr in shared mode), then either the image
-// (render mode) or the squared error, the block partial and the render/job completion.
+// Pixel means of render r's block, then either the image (render mode) or the squared
+// error and the block partial.
 template <bool kRender>
-__device__ __forceinline__ void block_epilogue(const TraceJob& J, int r, int t, const WarpSmem& W, bool with_accr,
-                                               int x0, int y0, int vw, int npx, int lane) {
+__device__ __forceinline__ void block_epilogue(const TraceJob& J, int r, int t, const WarpSmem& W, int x0, int y0,
+                                               int vw, int npx, int lane) {
     double e = 0.0;
     const int px = x0 + lane % vw, py = y0 + lane / vw;
     if (lane < npx && px < J.W && py < J.H) {
         const double inv = 1.0 / (double(J.spp) * double(kFix));
-        unsigned long long ax = W.acc[0][lane], ay = W.acc[1][lane], az = W.acc[2][lane];
-        if (with_accr) {
-            ax += W.accr[0][lane];
-            ay += W.accr[1][lane];
-            az += W.accr[2][lane];
-        }
+        const unsigned long long ax = W.acc[0][lane], ay = W.acc[1][lane], az = W.acc[2][lane];
         const double Ix = double(ax) * inv, Iy = double(ay) * inv, Iz = double(az) * inv;
         if (kRender) {
             J.images[(size_t(r) * J.H + py) * J.W + px] = make_float4(float(Ix), float(Iy), float(Iz), 0.0f);
@@ -984,15 +1051,15 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_
             // ---- a3: every pixel x sample of this render ----------------------------------
             run_pool<kCount, false>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, nullptr, nullptr, cnt,
                                     lane);
-            block_epilogue<kRender>(J, r, t, W, false, x0, y0, vw, npx, lane);  // a4/a5
+            block_epilogue<kRender>(J, r, t, W, x0, y0, vw, npx, lane);  // a4/a5
             continue;
         }
 
         // ---- shared pass: every path once in the invariant scene ---------------------------
-        if (lane == 0) W.mask[0] = 0ull;
+        if (lane == 0) W.recorded = 0u;
         __syncwarp();
-        run_pool<kCount, true>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, W.mask, &W.vb, cnt, lane);
-        if (W.mask[0] == 0ull) {  // every path is shared by all renders
+        run_pool<kCount, true>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, &W.recorded, &W.vb, cnt, lane);
+        if (W.recorded == 0u) {  // every path is shared by all renders
             shared_block_epilogue(J, t, W, x0, y0, vw, npx, lane);
             continue;
         }
@@ -1014,17 +1081,29 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_
     }
 }
 
-// Per-render pass of a path-sharing job. Items are (render, chunk of kAffChunk affected
-// paths), so work is even however the affected paths cluster; radiance goes to the
-// render's image-sized fixed-point buffer with global atomic adds (order-independent).
+// Per-render pass of a path-sharing job: render r traces again each recorded path one of
+// whose kept segments touches render r's bounds of a perturbed primitive, and adds its radiance minus the shared-pass radiance (2^-32 fixed point,
+// modulo 2^64) to the render's image-sized buffer with global atomic adds -- integer
+// sums, so the order does not matter and the block sums equal those of tracing every
+// path in every render.
+// Work distribution: warp g starts on render g mod R and streams that render's paths.
+// Batches of 32 list entries are claimed from the render's cursor, the entries that
+// render r must trace are compacted into a per-warp ring, and a lane whose path ends takes the
+// next ring entry at once, so the warp's pool only drains when the render's list is
+// used up; the warp then moves on to the next render with entries left.
+constexpr int kAffRing = 64;  // ring entries per warp (the ring never holds more than 63)
+
 template <bool kCount>
 __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(const __grid_constant__ TraceLaunch L) {
     __shared__ InstScene s_scene[kWarps];
     __shared__ TraceJob s_job[kWarps];
+    __shared__ unsigned s_ring[kWarps][kAffRing];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     InstScene& S = s_scene[warp];
     TraceJob& J = s_job[warp];
+    unsigned* ring = s_ring[warp];
+    const int gwarp = int(blockIdx.x) * kWarps + warp;
     Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     const int njobs = L.jobs ? L.njobs : 1;
     for (int jb = 0; jb < njobs; ++jb) {  // the jobs of a packed launch one after another
@@ -1038,19 +1117,14 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
     __syncwarp();  // every lane has read the descriptor before the next copy may overwrite it
     if (!job_shares) continue;
     const unsigned n_codes = __ldcg(J.share_ctl + 1);
-    const unsigned n_chunks = (n_codes + kAffChunk - 1) / kAffChunk;
-    const unsigned n_items = n_chunks * unsigned(J.R);
     const unsigned magic_W = 0xffffffffu / unsigned(J.W) + 1u;
-    int cur_r = -1;
-    for (;;) {
-        unsigned item = 0;
-        if (lane == 0) item = atomicAdd(J.share_ctl + 2, 1u);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= n_items) break;
-        const int r = int(item / n_chunks);  // render-major: a warp's next item usually keeps its scene
-        const unsigned c0 = (item % n_chunks) * kAffChunk;
-        const int ntasks = int(min(unsigned(kAffChunk), n_codes - c0));
-        if (r != cur_r) {
+    for (int k = 0; k < J.R; ++k) {
+        const int r = (gwarp + k) % J.R;
+        unsigned* cursor = J.aff_cursor + r;
+        unsigned seen = 0;
+        if (lane == 0) seen = __ldcg(cursor);
+        if (__shfl_sync(kFull, seen, 0) >= n_codes) continue;  // nothing left for this render
+        {  // stage render r's scene
             const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
             float4* dst = reinterpret_cast<float4*>(&S);
             constexpr int kHead = int(offsetof(InstScene, mat) / 16);
@@ -1061,38 +1135,69 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
                 dst[o] = __ldg(src + o);
             }
             __syncwarp();
-            cur_r = r;
         }
         unsigned long long* acc = J.acc_aff + size_t(r) * J.W * J.H * 3;
+        unsigned head = 0, tail = 0;  // ring positions, the same in every lane
+        bool src_done = false, alive = false;
         Path p;
-        int task = lane;
-        bool alive = task < ntasks;
-        auto start = [&](int tk) {
-            const unsigned code = __ldcg(J.aff_codes + c0 + tk);
-            const int pixel = int(code >> 6), smp = int(code & 63u);
-            const int y = div_magic(pixel, J.W, magic_W);
-            start_path(S, J.W, J.H, pixel - y * J.W, y, smp, 0, p);
-            if (kCount) ++cnt.paths;
-        };
-        if (alive) start(task);
-        int next = 32;
-        while (__any_sync(kFull, alive)) {
+        for (;;) {
+            while (!src_done && tail - head < 32u) {  // claim 32 entries, keep render r's
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(cursor, 32u);
+                base = __shfl_sync(kFull, base, 0);
+                if (base >= n_codes) {
+                    src_done = true;
+                    break;
+                }
+                const unsigned e = base + unsigned(lane);
+                bool need = false;
+                if (e < n_codes) {  // does a kept segment of the path touch render r's bounds?
+                    const unsigned sw = __ldcg(J.aff_segw + e);
+                    need = sw == kSegFull;
+                    const unsigned s0 = ((sw >> 3) - 1u) * unsigned(kSeg), ns = need ? 0u : (sw & 7u);
+                    for (unsigned q = 0; q < ns && !need; ++q) {
+                        const float4 A = __ldcg(J.seg_pool + 2 * size_t(s0 + q));
+                        const float4 B = __ldcg(J.seg_pool + 2 * size_t(s0 + q) + 1);
+                        const float3 o = xyz(A), inv = rcp3(xyz(B));
+                        const float tm = A.w * 1.0001f + 1e-3f;
+                        for (int k = 0; k < J.n_var && !need; ++k) {
+                            const float4* bx = J.var_box + (size_t(r) * kMaxVariant + k) * 2;
+                            need = slab_touch(xyz(__ldg(bx)), xyz(__ldg(bx + 1)), o, inv, tm);
+                        }
+                    }
+                }
+                const unsigned nb = __ballot_sync(kFull, need);
+                if (need) ring[(tail + __popc(nb & lt_mask)) % kAffRing] = e;
+                tail += unsigned(__popc(nb));
+            }
+            __syncwarp();
+            const unsigned fr = __ballot_sync(kFull, !alive);  // lanes free for a new path
+            const unsigned avail = tail - head, rank = unsigned(__popc(fr & lt_mask));
+            if (!alive && rank < avail) {
+                const unsigned e = ring[(head + rank) % kAffRing];
+                const unsigned code = __ldcg(J.aff_codes + e);
+                const int pixel = int(code >> 6), smp = int(code & 63u);
+                const int y = div_magic(pixel, J.W, magic_W);
+                start_path(S, J.W, J.H, pixel - y * J.W, y, smp, int(e), p);
+                if (kCount) ++cnt.paths;
+                alive = true;
+            }
+            head += min(avail, unsigned(__popc(fr)));
+            __syncwarp();
+            if (!__any_sync(kFull, alive)) break;  // ring empty and the render's list used up
             int st = kLive;
             if (alive) st = advance<kCount, false>(S, J.depth, J.rr_start, p, cnt);
-            const bool ended = alive && st != kLive;
-            if (ended) {
+            if (alive && st != kLive) {
                 unsigned long long* a = acc + size_t(p.pixel) * 3;
-                atomicAdd(a + 0, to_fixed(p.L.x));
-                atomicAdd(a + 1, to_fixed(p.L.y));
-                atomicAdd(a + 2, to_fixed(p.L.z));
+                const float* ls = J.aff_lsh + 3 * size_t(p.slot);
+                const unsigned long long dx = to_fixed(p.L.x) - to_fixed(__ldcg(ls + 0));
+                const unsigned long long dy = to_fixed(p.L.y) - to_fixed(__ldcg(ls + 1));
+                const unsigned long long dz = to_fixed(p.L.z) - to_fixed(__ldcg(ls + 2));
+                if (dx) atomicAdd(a + 0, dx);
+                if (dy) atomicAdd(a + 1, dy);
+                if (dz) atomicAdd(a + 2, dz);
+                alive = false;
             }
-            const unsigned need = __ballot_sync(kFull, ended);
-            if (ended) {
-                task = next + __popc(need & lt_mask);
-                alive = task < ntasks;
-                if (alive) start(task);
-            }
-            next += __popc(need);
         }
         __syncwarp();
     }
@@ -1363,6 +1468,36 @@ cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, uns
                           uint32_t* out, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     k_philox<<<(n + 255) / 256, 256, 0, stream>>>(seed, c0, c1, c2, c3, n, reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 issue-rate probe: the denominator of the render kernels' roofline
+// ---------------------------------------------------------------------------
+// Every thread runs kFfmaChains independent fused multiply-add chains, so each warp
+// always has an FMA ready; a full-occupancy grid then issues FFMA on every FP32 lane
+// of every SM each cycle, up to the loop's few integer instructions.
+constexpr int kFfmaChains = 8;
+
+__global__ void __launch_bounds__(kBlock) k_ffma_probe(float* out, int iters, float b, float c) {
+    float a[kFfmaChains];
+#pragma unroll
+    for (int i = 0; i < kFfmaChains; ++i) a[i] = float(threadIdx.x) * 1e-7f + float(i);
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll 16
+        for (int i = 0; i < kFfmaChains; ++i) a[i] = fmaf(a[i], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kFfmaChains; ++i) s += a[i];
+    out[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = s;
+}
+
+int ffma_probe_flops_per_thread_iter() { return 2 * kFfmaChains; }
+
+cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t stream) {
+    if (blocks <= 0 || iters <= 0) return cudaErrorInvalidValue;
+    k_ffma_probe<<<blocks, kBlock, 0, stream>>>(out, iters, 0.9999999f, 1e-7f);
     return cudaGetLastError();
 }
 

@@ -163,10 +163,18 @@ def test_deterministic_across_launch_shapes(ctx):
 
 
 @pytest.mark.parametrize("make", [workloads.config_small, workloads.config_occlusion,
-                                  lambda: workloads.scaled(workloads.config_occlusion(), width=45, height=37, spp=7)])
+                                  lambda: workloads.scaled(workloads.config_occlusion(), width=45, height=37, spp=7),
+                                  # 64 renders: the render mask uses all 64 bits
+                                  lambda: workloads.scaled(workloads.config_occlusion(), width=64, height=48, spp=4,
+                                                           pairs=32),
+                                  # 80 renders: a touched path is traced again by every render
+                                  lambda: workloads.scaled(workloads.config_occlusion(), width=40, height=40, spp=4,
+                                                           pairs=40)])
 def test_path_sharing_is_bit_identical(ctx, make):
-    """With common random numbers, paths that no perturbed instance can touch are traced
-    once for all renders; the gradient and losses must equal tracing every render."""
+    """With common random numbers, a path is traced once in the scene without the
+    perturbed primitives; only the renders whose own primitives one of its rays may meet
+    trace it again, and add their radiance minus the shared one. The gradient and losses
+    must equal tracing every path in every render."""
     wl = make()
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     target = _t(oracle.render_target(wl))
