@@ -191,14 +191,16 @@ def serving_bench(device, n_jobs, steps_per_job, gpaths_per_s, seed=0):
         arrivals.append((t, wl))
     out = {"jobs": n_jobs, "steps_per_job": steps_per_job, "arrival_rate_jobs_per_s": rate,
            "hbm_budget_bytes": 150 * 10 ** 9}
-    for mode in ("plain", "batched"):
+    for mode in ("plain", "batched", "graphed"):
         ctx = api.Context(device, hbm_budget_bytes=150 * 10 ** 9)
         try:
             rep, _ = Server(ctx, mode=mode, max_active=256).run(arrivals, steps_per_job=lambda wl: steps_per_job)
         finally:
             ctx.close()
-        out[mode] = {k: rep[k] for k in ("steps_per_s", "mpaths_per_s", "p50_ms", "p99_ms", "peak_active", "wall_s")}
+        out[mode] = {k: rep[k] for k in ("steps_per_s", "mpaths_per_s", "p50_ms", "p99_ms", "peak_active", "wall_s",
+                                         "graph_replays")}
     out["batched_over_plain"] = out["batched"]["steps_per_s"] / out["plain"]["steps_per_s"]
+    out["graphed_over_plain"] = out["graphed"]["steps_per_s"] / out["plain"]["steps_per_s"]
     return out
 
 

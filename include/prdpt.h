@@ -176,8 +176,8 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* ctx, int32_t scene_id, const float* 
                                  const prdpt_grad_opts* opts, const float* target_dev, float* grad_dev,
                                  float* losses_dev, void* stream);
 
-/* One Adam update (PyTorch defaults' formula; t is the 1-based step) of D
- * parameters in place: theta_dev, m_dev, v_dev [D], grad_dev [D]. */
+/* One Adam update (Sec. 3.4; PyTorch's formula, FP32 arithmetic as its FP32 Adam; t is
+ * the 1-based step) of D parameters in place: theta_dev, m_dev, v_dev [D], grad_dev [D]. */
 prdpt_status prdpt_adam_step(prdpt_ctx* ctx, int32_t D, float* theta_dev, float* m_dev, float* v_dev,
                              const float* grad_dev, int32_t t, float lr, float beta1, float beta2, float eps,
                              void* stream);

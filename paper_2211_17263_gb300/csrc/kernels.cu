@@ -33,6 +33,15 @@ namespace prdpt {
 
 constexpr unsigned kFull = 0xffffffffu;  // all lanes of a warp
 
+// Programmatic dependent launch: the kernels of a step are launched so that the next one
+// may be scheduled while the previous one drains. Each kernel first waits until every
+// kernel before it in the stream has completed and its writes are visible (a no-op for a
+// launch without the attribute), then lets the next kernel be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // small vector helpers
 // ---------------------------------------------------------------------------
@@ -136,6 +145,7 @@ __device__ __forceinline__ void prim_bounds(const float4* P, int type, float3& l
 // k_instantiate: one CTA (kInstBlock threads) per render
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) {
+    pdl_enter();
     __shared__ float s_u[4 * 32];
     __shared__ float s_red[kInstBlock];
     __shared__ float s_theta[kMaxD];
@@ -785,6 +795,27 @@ __device__ __forceinline__ unsigned long long to_fixed(float v) {
     return sh >= 0 ? (m << sh) : (m >> (-sh));
 }
 
+// Squared error of one pixel against the target, summed over RGB (a4). The pixel's sums
+// are 2^-32 fixed point over spp samples; acc - T * spp * 2^32 is formed exactly in 64-bit
+// integers (T truncated to 2^-32), so the difference suffers no cancellation, and is then
+// scaled to the mean and squared in FP32. Only the sums over pixels are FP64.
+__device__ __forceinline__ float fixed_diff(unsigned long long a, float t, unsigned spp, float inv) {
+    const long long D = (long long)(a - to_fixed(t) * (unsigned long long)spp);
+    const unsigned long long m = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
+    const float f = fmaf(float(unsigned(m >> 32)), 4294967296.0f, float(unsigned(m)));
+    return (D < 0 ? -f : f) * inv;
+}
+
+__device__ __forceinline__ double pixel_sq_error(unsigned long long ax, unsigned long long ay, unsigned long long az,
+                                                 float4 T, unsigned spp, float inv) {
+    const float dx = fixed_diff(ax, T.x, spp, inv), dy = fixed_diff(ay, T.y, spp, inv),
+                dz = fixed_diff(az, T.z, spp, inv);
+    return double(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+}
+
+// 1 / (spp * 2^32): scale of a pixel's fixed-point sum to its mean.
+__device__ __forceinline__ float mean_scale(int spp) { return 1.0f / (float(spp) * 4294967296.0f); }
+
 // Per-warp shared-memory workspace of the render kernel.
 struct WarpSmem {
     InstScene scene;                  // the render being traced (render 0 in shared phase A)
@@ -944,15 +975,14 @@ __device__ __forceinline__ void block_epilogue(const TraceJob& J, int r, int t, 
     double e = 0.0;
     const int px = x0 + lane % vw, py = y0 + lane / vw;
     if (lane < npx && px < J.W && py < J.H) {
-        const double inv = 1.0 / (double(J.spp) * double(kFix));
         const unsigned long long ax = W.acc[0][lane], ay = W.acc[1][lane], az = W.acc[2][lane];
-        const double Ix = double(ax) * inv, Iy = double(ay) * inv, Iz = double(az) * inv;
         if (kRender) {
-            J.images[(size_t(r) * J.H + py) * J.W + px] = make_float4(float(Ix), float(Iy), float(Iz), 0.0f);
+            const double inv = 1.0 / (double(J.spp) * double(kFix));
+            J.images[(size_t(r) * J.H + py) * J.W + px] =
+                make_float4(float(double(ax) * inv), float(double(ay) * inv), float(double(az) * inv), 0.0f);
         } else {
-            const float4 T = __ldg(J.target + size_t(py) * J.W + px);
-            const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
-            e = ex * ex + ey * ey + ez * ez;
+            e = pixel_sq_error(ax, ay, az, __ldg(J.target + size_t(py) * J.W + px), unsigned(J.spp),
+                               mean_scale(J.spp));
         }
     }
     if (!kRender) {
@@ -968,12 +998,8 @@ __device__ __forceinline__ void shared_block_epilogue(const TraceJob& J, int t, 
     double e = 0.0;
     const int px = x0 + lane % vw, py = y0 + lane / vw;
     if (lane < npx && px < J.W && py < J.H) {
-        const double inv = 1.0 / (double(J.spp) * double(kFix));
-        const double Ix = double(W.acc[0][lane]) * inv, Iy = double(W.acc[1][lane]) * inv,
-                     Iz = double(W.acc[2][lane]) * inv;
-        const float4 T = __ldg(J.target + size_t(py) * J.W + px);
-        const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
-        e = ex * ex + ey * ey + ez * ez;
+        e = pixel_sq_error(W.acc[0][lane], W.acc[1][lane], W.acc[2][lane], __ldg(J.target + size_t(py) * J.W + px),
+                           unsigned(J.spp), mean_scale(J.spp));
     }
     e = warp_sum_d(e);
     for (int r = lane; r < J.R; r += 32) J.partials[size_t(r) * J.tiles + t] = e;
@@ -984,6 +1010,7 @@ __device__ __forceinline__ void shared_block_epilogue(const TraceJob& J, int t, 
 // launches only); otherwise every item is one render's block and job.share is ignored.
 template <bool kRender, bool kCount, bool kShare>
 __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_constant__ TraceLaunch L) {
+    pdl_enter();
     __shared__ WarpSmem s_warp[kWarps];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1095,6 +1122,7 @@ constexpr int kAffRing = 64;  // ring entries per warp (the ring never holds mor
 
 template <bool kCount>
 __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(const __grid_constant__ TraceLaunch L) {
+    pdl_enter();
     __shared__ InstScene s_scene[kWarps];
     __shared__ TraceJob s_job[kWarps];
     __shared__ unsigned s_ring[kWarps][kAffRing];
@@ -1217,6 +1245,7 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
 // bit-identical to the per-render path. Clears the affected radiance it read, so the
 // buffers are zero for the next step.
 __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constant__ TraceLaunch L) {
+    pdl_enter();
     __shared__ TraceJob s_job[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TraceJob& J = s_job[warp];
@@ -1232,7 +1261,7 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
     __syncwarp();  // every lane has read the descriptor before the next copy may overwrite it
     if (!job_shares) continue;
     const unsigned n_items = __ldcg(J.share_ctl + 0);
-    const double inv = 1.0 / (double(J.spp) * double(kFix));
+    const float inv = mean_scale(J.spp);
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(J.share_ctl + 3, 1u);
@@ -1272,15 +1301,11 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
                 const int r = rb + q * G + sub;
                 double e = 0.0;
                 if (pix_ok && r < J.R) {
-                    const double Ix = double(s0 + a[q][0]) * inv;
-                    const double Iy = double(s1 + a[q][1]) * inv;
-                    const double Iz = double(s2 + a[q][2]) * inv;
                     unsigned long long* af = J.acc_aff + size_t(r) * plane + pix3;
                     af[0] = 0ull;
                     af[1] = 0ull;
                     af[2] = 0ull;
-                    const double ex = Ix - T.x, ey = Iy - T.y, ez = Iz - T.z;
-                    e = ex * ex + ey * ey + ez * ez;
+                    e = pixel_sq_error(s0 + a[q][0], s1 + a[q][1], s2 + a[q][2], T, unsigned(J.spp), inv);
                 }
                 for (int o = pw / 2; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
                 if (pl == 0 && r < J.R) J.partials[size_t(r) * J.tiles + t] = e;
@@ -1291,15 +1316,28 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
     }
 }
 
+// One Adam update (Sec. 3.4: Adam with PyTorch's default betas and eps) of one parameter
+// in FP32, as PyTorch's FP32 Adam. The bias corrections 1 - beta^t are formed as
+// -expm1(t log1p(beta - 1)), which keeps their relative accuracy while beta^t is near 1.
+__device__ __forceinline__ void adam_update(float& th, float& m, float& v, float g, int t, float lr, float b1,
+                                            float b2, float eps) {
+    m = fmaf(b1, m, (1.0f - b1) * g);
+    v = fmaf(b2, v, (1.0f - b2) * g * g);
+    const float bc1 = -expm1f(float(t) * log1pf(b1 - 1.0f));
+    const float bc2 = -expm1f(float(t) * log1pf(b2 - 1.0f));
+    th -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
 // ---------------------------------------------------------------------------
 // k_finalize: a5 (per-render loss), a6 (gradient, Eq. 10), a7 (Adam)
 // ---------------------------------------------------------------------------
 // One 256-thread CTA per render of every job in the launch: L_r = (1/3HW) sum of the
-// render's block partials in a fixed order (strided per thread, four accumulators, then a
-// fixed shared-memory tree). The CTA that completes a job's last render forms the
-// gradient in FP64 and applies Adam (state in FP32, arithmetic in FP64).
+// render's block partials in a fixed order (strided per thread into eight accumulators, a
+// warp shuffle tree, then the eight warp sums in order). The CTA that completes a job's
+// last render forms the gradient in FP64 (one warp per parameter) and applies Adam.
 __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ TraceLaunch L) {
-    __shared__ double s_red[kBlock];
+    pdl_enter();
+    __shared__ double s_red[kBlock / 32];
     __shared__ int s_job, s_last;
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -1318,25 +1356,23 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
     const TraceJob& J = L.jobs ? L.jobs[s_job] : L.job0;
     const int r = int(blockIdx.x) - J.fin_begin;
     const double* src = J.partials + size_t(r) * J.tiles;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = 0.0;
     int i = tid;
-    for (; i + 3 * kBlock < J.tiles; i += 4 * kBlock) {
-        a0 += src[i];
-        a1 += src[i + kBlock];
-        a2 += src[i + 2 * kBlock];
-        a3 += src[i + 3 * kBlock];
+    for (; i + 7 * kBlock < J.tiles; i += 8 * kBlock) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] += __ldcg(src + i + q * kBlock);
     }
-    for (int q = 0; i < J.tiles; i += kBlock, ++q) {
-        if (q == 0) a0 += src[i]; else if (q == 1) a1 += src[i]; else a2 += src[i];
-    }
-    s_red[tid] = (a0 + a1) + (a2 + a3);
+    for (; i < J.tiles; i += kBlock) a[0] += __ldcg(src + i);
+    double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    v = warp_sum_d(v);
+    if ((tid & 31) == 0) s_red[tid >> 5] = v;
     __syncthreads();
-    for (int o = kBlock / 2; o > 0; o >>= 1) {
-        if (tid < o) s_red[tid] += s_red[tid + o];
-        __syncthreads();
-    }
     if (tid == 0) {
-        const double Lr = s_red[0] / (3.0 * double(J.W) * double(J.H));
+        double sum = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) sum += s_red[w];
+        const double Lr = sum / (3.0 * double(J.W) * double(J.H));
         J.losses[r] = Lr;
         if (J.loss_out) J.loss_out[r] = float(Lr);
         __threadfence();
@@ -1345,30 +1381,24 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int t = J.step_dev ? *J.step_dev : 0;
-    if (tid < J.D) {
-        const int d = tid;
+    // a6: one warp per parameter, lanes over pairs (fixed order), FP64; a7: Adam in FP32
+    const int t = J.step_dev ? __ldcg(J.step_dev) : 0;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int d = warp; d < J.D; d += kBlock / 32) {
         double g = 0.0;
         if (J.antithetic) {
             const int P = J.R / 2;
-            for (int p = 0; p < P; ++p)
+            for (int p = lane; p < P; p += 32)
                 g += double(J.w[size_t(2 * p) * J.D + d]) * (__ldcg(J.losses + 2 * p) - __ldcg(J.losses + 2 * p + 1));
-            g /= double(2 * P);
+            g = warp_sum_d(g) / double(2 * P);
         } else {
-            for (int q = 0; q < J.R; ++q) g += double(J.w[size_t(q) * J.D + d]) * __ldcg(J.losses + q);
-            g /= double(J.R);
+            for (int q = lane; q < J.R; q += 32) g += double(J.w[size_t(q) * J.D + d]) * __ldcg(J.losses + q);
+            g = warp_sum_d(g) / double(J.R);
         }
-        const float gf = float(g);
-        if (J.grad_out) J.grad_out[d] = gf;
-        if (J.theta) {
-            const int tt = t + 1;
-            const double m = double(J.b1) * J.m[d] + (1.0 - double(J.b1)) * double(gf);
-            const double v = double(J.b2) * J.v[d] + (1.0 - double(J.b2)) * double(gf) * double(gf);
-            const double mh = m / (1.0 - pow(double(J.b1), tt));
-            const double vh = v / (1.0 - pow(double(J.b2), tt));
-            J.m[d] = float(m);
-            J.v[d] = float(v);
-            J.theta[d] = float(double(J.theta[d]) - double(J.lr) * mh / (sqrt(vh) + double(J.eps)));
+        if (lane == 0) {
+            const float gf = float(g);
+            if (J.grad_out) J.grad_out[d] = gf;
+            if (J.theta) adam_update(J.theta[d], J.m[d], J.v[d], gf, t + 1, J.lr, J.b1, J.b2, J.eps);
         }
     }
     __syncthreads();
@@ -1385,14 +1415,7 @@ __global__ void k_adam(int D, float* theta, float* m, float* v, const float* g, 
                        float eps) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= D) return;
-    const double gd = g[d];
-    const double mm = double(b1) * m[d] + (1.0 - double(b1)) * gd;
-    const double vv = double(b2) * v[d] + (1.0 - double(b2)) * gd * gd;
-    const double mh = mm / (1.0 - pow(double(b1), t));
-    const double vh = vv / (1.0 - pow(double(b2), t));
-    m[d] = float(mm);
-    v[d] = float(vv);
-    theta[d] = float(double(theta[d]) - double(lr) * mh / (sqrt(vh) + double(eps)));
+    adam_update(theta[d], m[d], v[d], g[d], t, lr, b1, b2, eps);
 }
 
 __global__ void k_philox(unsigned long long seed, unsigned c0, unsigned c1, unsigned c2, unsigned c3, int n,
@@ -1405,10 +1428,25 @@ __global__ void k_philox(unsigned long long seed, unsigned c0, unsigned c1, unsi
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Launch with the programmatic-stream-serialisation attribute (see pdl_enter).
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, int block, cudaStream_t stream, const Args&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(block));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream) {
     if (L.total_blocks <= 0) return cudaSuccess;
-    k_instantiate<<<L.total_blocks, kInstBlock, 0, stream>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(k_instantiate, L.total_blocks, kInstBlock, stream, L);
 }
 
 int trace_blocks_per_sm(bool render_mode) {
@@ -1424,38 +1462,24 @@ cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaS
     if (L.total_items <= 0) return cudaSuccess;
     const bool count = L.counters != nullptr;
     const bool share = !render_mode && L.share;
-    if (render_mode && count)
-        k_trace<true, true, false><<<grid, kBlock, 0, stream>>>(L);
-    else if (render_mode)
-        k_trace<true, false, false><<<grid, kBlock, 0, stream>>>(L);
-    else if (share && count)
-        k_trace<false, true, true><<<grid, kBlock, 0, stream>>>(L);
-    else if (share)
-        k_trace<false, false, true><<<grid, kBlock, 0, stream>>>(L);
-    else if (count)
-        k_trace<false, true, false><<<grid, kBlock, 0, stream>>>(L);
-    else
-        k_trace<false, false, false><<<grid, kBlock, 0, stream>>>(L);
-    return cudaGetLastError();
+    if (render_mode) return launch_pdl(count ? k_trace<true, true, false> : k_trace<true, false, false>, grid, kBlock,
+                                       stream, L);
+    if (share) return launch_pdl(count ? k_trace<false, true, true> : k_trace<false, false, true>, grid, kBlock,
+                                 stream, L);
+    return launch_pdl(count ? k_trace<false, true, false> : k_trace<false, false, false>, grid, kBlock, stream, L);
 }
 
 cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t stream) {
-    if (L.counters)
-        k_trace_affected<true><<<grid, kBlock, 0, stream>>>(L);
-    else
-        k_trace_affected<false><<<grid, kBlock, 0, stream>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(L.counters ? k_trace_affected<true> : k_trace_affected<false>, grid, kBlock, stream, L);
 }
 
 cudaError_t launch_shared_epilogue(const TraceLaunch& L, int grid, cudaStream_t stream) {
-    k_shared_epilogue<<<grid, kBlock, 0, stream>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(k_shared_epilogue, grid, kBlock, stream, L);
 }
 
 cudaError_t launch_finalize(const TraceLaunch& L, int n_renders, cudaStream_t stream) {
     if (n_renders <= 0) return cudaSuccess;
-    k_finalize<<<n_renders, kBlock, 0, stream>>>(L);
-    return cudaGetLastError();
+    return launch_pdl(k_finalize, n_renders, kBlock, stream, L);
 }
 
 cudaError_t launch_adam(int D, float* theta, float* m, float* v, const float* g, int t, float lr, float b1,

@@ -7,9 +7,13 @@ as soon as a slot and the context's HBM budget allow (a job that does not fit wa
 until a finished job frees its memory). Each tick advances every active job by one
 plateau-reduced gradient step:
 
-  mode "batched": all active jobs' renders are packed into one sampler launch and one
-                  persistent render launch (prdpt_step_batch);
-  mode "plain":   one job per launch pair (prdpt_step), jobs one after another.
+  mode "batched": all active jobs' steps are packed into shared launches
+                  (prdpt_step_batch: one sampler launch, one render launch per kind of job,
+                  the path-sharing passes, one finalisation launch);
+  mode "graphed": as "batched", but once the set of active jobs has stayed the same for
+                  a tick, the packed step is captured as a CUDA graph and replayed (one
+                  graph launch per tick) until the set changes;
+  mode "plain":   one job per launch sequence (prdpt_step), jobs one after another.
 
 Per-step latency is measured with CUDA events from the start of the tick (when the
 step becomes runnable) to the completion of that job's step. The report gives p50/p99
@@ -43,13 +47,37 @@ class ServedJob:
 
 class Server:
     def __init__(self, ctx: api.Context, mode: str = "batched", max_active: int = 256, block_pixels: int = 0):
-        if mode not in ("batched", "plain"):
-            raise ValueError("mode must be 'batched' or 'plain'")
+        if mode not in ("batched", "graphed", "plain"):
+            raise ValueError("mode must be 'batched', 'graphed' or 'plain'")
         self.ctx = ctx
         self.mode = mode
         self.max_active = max_active
         self.block_pixels = block_pixels
         self.stream = torch.cuda.current_stream()
+        self._graph = None       # captured packed step of self._graph_ids
+        self._graph_ids = None
+        self._last_ids = None    # active set of the previous tick
+        self.graph_replays = 0
+        self.graph_captures = 0
+
+    def _graphed_step(self, active):
+        ids = tuple(sj.job.id for sj in active)
+        if self._graph is not None and ids == self._graph_ids:
+            self._graph.replay()
+            self.graph_replays += 1
+            return
+        jobs = [sj.job for sj in active]
+        api.step_batch(self.ctx, jobs, stream=self.stream)  # this tick's step (updates the descriptors)
+        if ids == self._last_ids:  # stable set: capture the packed step for the next ticks
+            self.stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                api.step_batch(self.ctx, jobs, stream=torch.cuda.current_stream())
+            self._graph, self._graph_ids = g, ids
+            self.graph_captures += 1
+        else:
+            self._graph, self._graph_ids = None, None
+        self._last_ids = ids
 
     def _admit(self, sj: ServedJob) -> bool:
         wl = sj.wl
@@ -108,9 +136,12 @@ class Server:
             peak_active = max(peak_active, len(active))
             peak_bytes = max(peak_bytes, self.ctx.memory_used())
             ev_start.record(self.stream)
-            if self.mode == "batched":
+            if self.mode in ("batched", "graphed"):
                 ev_end = torch.cuda.Event(enable_timing=True)
-                api.step_batch(self.ctx, [sj.job for sj in active], stream=self.stream)
+                if self.mode == "graphed":
+                    self._graphed_step(active)
+                else:
+                    api.step_batch(self.ctx, [sj.job for sj in active], stream=self.stream)
                 ev_end.record(self.stream)
                 ev_end.synchronize()
                 dt = ev_start.elapsed_time(ev_end)
@@ -147,5 +178,6 @@ class Server:
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "peak_active": peak_active, "peak_hbm_bytes": peak_bytes,
+            "graph_replays": self.graph_replays, "graph_captures": self.graph_captures,
         }
         return report, jobs

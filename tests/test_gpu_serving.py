@@ -1,8 +1,9 @@
 """GPU tests of the serving loop and the launch-shape autotuner.
 
 * Continuous batching: jobs arriving while others run are admitted and packed into the
-  same launches; every job's final parameters, gradient and losses are bit-identical to
-  running it alone (and to the one-job-per-launch mode).
+  same launches (also replayed as captured CUDA graphs); every job's final parameters,
+  gradient and losses are bit-identical to running it alone (and to the
+  one-job-per-launch mode).
 * HBM-budget admission: with a budget that fits only a few jobs, the rest wait and are
   admitted as finished jobs free their memory; all complete.
 * The autotuner returns one of its candidates, caches it, and the tuned launch gives the
@@ -44,7 +45,7 @@ def _alone(ctx, wl, steps):
     return res
 
 
-@pytest.mark.parametrize("mode", ["batched", "plain"])
+@pytest.mark.parametrize("mode", ["batched", "graphed", "plain"])
 def test_served_results_equal_alone(gpu_lib, mode):
     from paper_2211_17263_gb300 import api
     from paper_2211_17263_gb300.serve import Server
@@ -58,8 +59,10 @@ def test_served_results_equal_alone(gpu_lib, mode):
             assert sj.result["steps"] == sj.steps == alone["steps"]
             for key in ("theta", "grad", "losses"):
                 assert np.array_equal(sj.result[key], alone[key]), (mode, sj.wl.name, key)
-        if mode == "batched":
+        if mode != "plain":
             assert report["peak_active"] >= 2  # arrivals overlapped on the device
+        if mode == "graphed":
+            assert report["graph_replays"] > 0  # stable stretches ran as graph replays
     finally:
         ctx.close()
 
