@@ -125,9 +125,11 @@ def _kernel_source_sha():
 
 
 def _profiled_traffic(workload_name):
-    """DRAM bytes per render launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "k_trace_occlusion-256x256_ncu.md")
+    """DRAM bytes of one step's render kernels from the committed ncu summary of the
+    occlusion workload, if it was taken on the current kernel source; else None."""
+    if not workload_name.startswith("occlusion"):
+        return None
+    path = os.path.join(ROOT, "profiles", "render_pipeline_occlusion-256x256_ncu.md")
     try:
         text = open(path).read()
     except OSError:
@@ -140,7 +142,7 @@ def _profiled_traffic(workload_name):
     if vals.get("kernel_source_sha") != _kernel_source_sha():
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_size"])
+        return float(vals["dram_bytes_per_step"])
     except (KeyError, ValueError):
         return None
 
@@ -402,6 +404,10 @@ def main():
                        "height": wl.height, "spp": wl.spp, "depth": wl.depth, "D": wl.D,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "mpaths_per_s": world * wl.paths_per_step / (step_ms * 1e-3) / 1e6,
+            # ray segments (closest-hit rays + shadow rays) traced per second: as executed
+            # (shared pass + re-traced paths) and as the method defines them (every render)
+            "msegments_per_s": world * (counts[5] + counts[6]) / (step_ms * 1e-3) / 1e6,
+            "msegments_per_s_method": world * (pcounts[5] + pcounts[6]) / (step_ms * 1e-3) / 1e6,
             "wall_s": wall,
             "render_kernel_ms": trace_avg_ms,
             "work_per_step": {"sphere_tests": counts[0], "quad_tests": counts[1], "box_tests": counts[2],
