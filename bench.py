@@ -124,9 +124,9 @@ def _kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload_name):
-    """DRAM bytes of one step's render kernels from the committed ncu summary of the
-    occlusion workload, if it was taken on the current kernel source; else None."""
+def _profiled(workload_name, key):
+    """A per-step figure of the occlusion workload's render kernels from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
     if not workload_name.startswith("occlusion"):
         return None
     path = os.path.join(ROOT, "profiles", "render_pipeline_occlusion-256x256_ncu.md")
@@ -138,16 +138,29 @@ def _profiled_traffic(workload_name):
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
+            vals[k.strip()] = v.strip().split("`")[1] if "`" in v else v.strip()
     if vals.get("kernel_source_sha") != _kernel_source_sha():
         return None
     try:
-        return float(vals["dram_bytes_per_step"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
 
 CPU_SAMPLE_MAX_PATHS = 40_000_000  # larger steps are sampled (one pair, 4 spp) and scaled
+
+
+def _issue_rate(workload_name, sms, sm_mhz, pipeline_ms, per_render_ms):
+    peak = 4.0 * sms * sm_mhz * 1e6 / 1e9  # G warp instructions / s
+    out = {"unit": "G warp instr/s", "peak": peak}
+    for key, ms, name in (("warp_instructions_per_step", pipeline_ms, "pipeline"),
+                          ("warp_instructions_per_step_no_sharing", per_render_ms, "per_render_kernel")):
+        n = _profiled(workload_name, key)
+        if n is None or not ms:
+            return None
+        out[name] = n / (ms * 1e-3) / 1e9
+        out[name + "_frac"] = out[name] / peak
+    return out
 
 
 def cpu_baseline(wl, target, nthreads=0, budget_s=10.0, max_steps=20):
@@ -414,7 +427,7 @@ def main():
                               "paths": counts[3], "vertices": counts[4], "shadow_rays": counts[5],
                               "closest_hit_rays": counts[6]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": _profiled_traffic(wl.name),
+                         "frac": achieved / fp32_peak, "traffic": _profiled(wl.name, "dram_bytes_per_step"),
                          "kernel": "render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue,"
                                    " k_finalize)",
                          "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
@@ -423,6 +436,9 @@ def main():
                 "bound": "alu", "achieved": p_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": p_achieved / fp32_peak, "kernel": "k_trace (path sharing off) + k_finalize",
                 "ms_per_step": p_avg_ms, "paths_per_step": pcounts[3]},
+            # diagnostic beside the algorithmic roofline: warp instructions issued per second
+            # (ncu count per step from the committed summary) against 4 schedulers x SMs x clock
+            "issue_rate": _issue_rate(wl.name, props.multi_processor_count, sm_max, trace_avg_ms, p_avg_ms),
             "fp32_probe": {"achieved_tflops": probe_tflops, "ms": probe_ms,
                            "frac_of_peak": probe_tflops / fp32_peak},
             "e2e": e2e,
