@@ -13,6 +13,8 @@ Path Tracing"):
 * `render`, `render_pixels` -- the Monte-Carlo forward model P(theta) of Eq. 1 / Eq. 3
 * `mse`                 -- the image loss of Sec. 4.1
 * `smoothed_grad`       -- Eq. 10 with the antithetic pairs of Algorithm 1
+* `render_tangent`, `kdp_grad` -- Eq. 9: pathwise derivatives of the render for albedo and
+                          emission parameters, and their mean over Gaussian perturbations
 * `adam`                -- the optimiser of Sec. 3.4
 * `sigma_schedule`      -- the linear bandwidth decay of Sec. 3.3
 
@@ -76,6 +78,11 @@ def lib():
         L.orc_estimate.argtypes = [i32, i32, i32, vp, vp, i32, u64, u32, _LOSS_CB, vp, vp, vp, vp, vp]
         L.orc_estimate.restype = i32
         L.orc_sample_unit_batch.argtypes = [i32, i32, i32, vp, vp, vp]
+        L.orc_render_tangent.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, vp, vp, i32]
+        L.orc_render_tangent.restype = i32
+        L.orc_kdp_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, u64, u32, vp,
+                                   vp, vp, vp, vp, i32]
+        L.orc_kdp_grad.restype = i32
         L.orc_adam.argtypes = [i32, vp, vp, vp, vp, i32, dbl, dbl, dbl, dbl]
         L.orc_sigma_schedule.argtypes = [dbl, dbl, i32, i32]
         L.orc_sigma_schedule.restype = dbl
@@ -250,6 +257,49 @@ def smoothed_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, m
     if rc:
         raise ValueError(f"oracle smoothed_grad failed ({rc})")
     return {"grad": grad, "losses": losses, "taus": taus, "weights": weights}
+
+
+def render_tangent(scene, bindings, theta, width, height, spp, depth, rr_start=-1, seed=0, step=0, tag=TAG_PATH,
+                   render_field=0, nthreads=0):
+    """One render at theta and its pathwise tangents (Eq. 9's dP/dtheta) for albedo and
+    emission bindings: (image [H, W, 3], dimage [H, W, D]); dimage[..., d] is the
+    derivative of channel bindings[d][2] of the pixel mean with respect to theta_d."""
+    h = _SceneHandle(scene)
+    binds = np.ascontiguousarray(bindings, np.int32)
+    th = np.ascontiguousarray(theta, np.float32)
+    D = th.shape[0]
+    img = np.zeros((height, width, 3), np.float64)
+    dimg = np.zeros((height, width, D), np.float64)
+    rc = lib().orc_render_tangent(h.ref, _ptr(binds), D, _ptr(th), render_field, width, height, spp, depth,
+                                  rr_start, seed, step, tag, _ptr(img), _ptr(dimg), nthreads)
+    if rc:
+        raise ValueError(f"oracle render_tangent failed ({rc})")
+    return img, dimg
+
+
+def kdp_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, antithetic=None, crn=None, nthreads=0):
+    """Eq. 9 estimate at theta (Gaussian draws, pathwise render gradients) for workload `wl`
+    whose bindings are all albedo or emission ones. Returns dict(grad, losses, taus, rgrads)."""
+    h = _SceneHandle(wl.scene)
+    binds = np.ascontiguousarray(wl.bindings, np.int32)
+    th = np.ascontiguousarray(wl.theta0 if theta is None else theta, np.float32)
+    sg = np.ascontiguousarray(wl.sigma if sigma is None else sigma, np.float32)
+    P = wl.pairs if pairs is None else pairs
+    D = th.shape[0]
+    tg = np.ascontiguousarray(target, np.float32)
+    if tg.shape != (wl.height, wl.width, 4):
+        raise ValueError("target must be [H, W, 4] float32")
+    grad = np.zeros(D, np.float64)
+    losses = np.zeros(2 * P, np.float64)
+    taus = np.zeros((2 * P, D), np.float32)
+    rgrads = np.zeros((2 * P, D), np.float64)
+    rc = lib().orc_kdp_grad(
+        h.ref, _ptr(binds), D, _ptr(th), _ptr(sg), P, wl.antithetic if antithetic is None else antithetic,
+        wl.crn if crn is None else crn, wl.width, wl.height, wl.spp, wl.depth, wl.rr_start, wl.seed, step,
+        _ptr(tg), _ptr(grad), _ptr(losses), _ptr(taus), _ptr(rgrads), nthreads)
+    if rc:
+        raise ValueError(f"oracle kdp_grad failed ({rc})")
+    return {"grad": grad, "losses": losses, "taus": taus, "rgrads": rgrads}
 
 
 def render_target(wl, nthreads=0) -> np.ndarray:

@@ -473,10 +473,39 @@ static void path_uniforms(const orc_trace_opts* o, uint32_t pixel, int s, int b,
     uniforms4(o->seed, pixel, c1, o->step, c3, u);
 }
 
-/* Radiance of one path sample through pixel (x, y). */
-static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y, int s) {
+/* Forward-mode tangents of a path sample for Eq. 9's pathwise derivative dP/dtheta with
+ * respect to n bound material parameters: kind 2 (albedo) or 3 (emission) of material
+ * mat, colour channel c; dclamp is the derivative of the clamp applied at instantiation
+ * (1 inside the valid range, 0 where the value was clamped). The discrete choices of the
+ * path (light choice, Fresnel choice, Russian-roulette survival) are held fixed, and the
+ * Russian-roulette probability is a constant of the derivative: dividing by it keeps the
+ * derivative estimate unbiased, as it keeps the radiance estimate unbiased. */
+typedef struct {
+    int n;
+    int kind[ORC_MAX_D], mat[ORC_MAX_D], c[ORC_MAX_D];
+    double dclamp[ORC_MAX_D];
+} orc_tangent_spec;
+
+/* beta <- beta * albedo (material mat): product rule on each tangent's channel. */
+static void scatter_tangents(const orc_tangent_spec* ts, double* dB, v3 beta, v3 albedo, int mat) {
+    if (!ts) return;
+    for (int k = 0; k < ts->n; ++k) {
+        int c = ts->c[k];
+        double d = dB[k] * comp(albedo, c);
+        if (ts->kind[k] == 2 && ts->mat[k] == mat) d += comp(beta, c) * ts->dclamp[k];
+        dB[k] = d;
+    }
+}
+
+/* Radiance of one path sample through pixel (x, y); with ts, also the derivative of
+ * channel ts->c[k] of the radiance with respect to each parameter k, in dL[k]. */
+static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int y, int s,
+                       const orc_tangent_spec* ts, double* dL) {
     uint32_t pixel = (uint32_t)(y * o->width + x);
     double u[4];
+    int nt = ts ? ts->n : 0;
+    double dB[ORC_MAX_D]; /* d(beta channel c_k) / d theta_k */
+    for (int k = 0; k < nt; ++k) { dB[k] = 0.0; dL[k] = 0.0; }
 
     /* pinhole camera, box-filtered jitter inside the pixel */
     v3 f = normalize(sub(sc->look, sc->eye));
@@ -499,12 +528,20 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
         int hit = closest_hit(sc, org, dir, &t, &ng);
         if (hit < 0) {
             L = add(L, hmul(beta, sc->background));
+            for (int k = 0; k < nt; ++k) dL[k] += dB[k] * comp(sc->background, ts->c[k]);
             break;
         }
         const orc_prim* pr = &sc->prim[hit];
         const orc_mat* m = &sc->mat[pr->mat];
         v3 p = add(org, mul(dir, t));
-        if (specular && is_emissive(m) && dot(dir, ng) < 0.0) L = add(L, hmul(beta, m->emission));
+        if (specular && is_emissive(m) && dot(dir, ng) < 0.0) {
+            L = add(L, hmul(beta, m->emission));
+            for (int k = 0; k < nt; ++k) {
+                int c = ts->c[k];
+                dL[k] += dB[k] * comp(m->emission, c);
+                if (ts->kind[k] == 3 && ts->mat[k] == pr->mat) dL[k] += comp(beta, c) * ts->dclamp[k];
+            }
+        }
         int last = (b + 1 >= o->depth);
         path_uniforms(o, pixel, s, b, 0, u);
         path_uniforms(o, pixel, s, b, 1, u1);
@@ -540,6 +577,14 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
                     double g = cx * cl / dist2 * area * sc->n_lights / M_PI;
                     v3 le = sc->mat[lp->mat].emission;
                     L = add(L, mul(hmul(hmul(beta, m->albedo), le), g));
+                    for (int k = 0; k < nt; ++k) { /* product rule on beta * albedo * Le */
+                        int c = ts->c[k];
+                        double bc = comp(beta, c), rc = comp(m->albedo, c), ec = comp(le, c);
+                        double d = dB[k] * rc * ec;
+                        if (ts->kind[k] == 2 && ts->mat[k] == pr->mat) d += bc * ts->dclamp[k] * ec;
+                        if (ts->kind[k] == 3 && ts->mat[k] == lp->mat) d += bc * rc * ts->dclamp[k];
+                        dL[k] += d * g;
+                    }
                 }
             }
             if (last) break;
@@ -547,6 +592,7 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
             v3 t1, t2;
             onb(ns, &t1, &t2);
             v3 wo = add(add(mul(t1, rad * cos(phi)), mul(t2, rad * sin(phi))), mul(ns, sqrt(fmax(0.0, 1.0 - u[2]))));
+            scatter_tangents(ts, dB, beta, m->albedo, pr->mat);
             beta = hmul(beta, m->albedo);
             org = po;
             dir = normalize(wo);
@@ -556,6 +602,7 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
             v3 ns = dot(ng, dir) < 0.0 ? ng : mul(ng, -1.0);
             dir = normalize(sub(dir, mul(ns, 2.0 * dot(dir, ns))));
             org = add(p, mul(ns, ORC_EPS));
+            scatter_tangents(ts, dB, beta, m->albedo, pr->mat);
             beta = hmul(beta, m->albedo);
             specular = 1;
         } else { /* smooth dielectric: exact unpolarised Fresnel, reflect or refract */
@@ -582,6 +629,7 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
                 dir = normalize(add(mul(dir, eta), mul(n, eta * ci - ct)));
                 org = sub(p, mul(n, ORC_EPS));
             }
+            scatter_tangents(ts, dB, beta, m->albedo, pr->mat);
             beta = hmul(beta, m->albedo);
             specular = 1;
         }
@@ -590,9 +638,14 @@ static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y,
             double q = fmin(0.95, maxc(beta));
             if (u1[1] >= q) break;
             beta = mul(beta, 1.0 / q);
+            for (int k = 0; k < nt; ++k) dB[k] /= q;
         }
     }
     return L;
+}
+
+static v3 trace_path(const orc_scene* sc, const orc_trace_opts* o, int x, int y, int s) {
+    return trace_path_t(sc, o, x, y, s, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -606,6 +659,8 @@ typedef struct {
     int n, width, height;
     int next_row;
     pthread_mutex_t lock;
+    const orc_tangent_spec* ts; /* one per scene, or NULL */
+    double* dimages;            /* [n][H][W][ts->n] pixel-mean tangents, or NULL */
 } render_job;
 
 static void* render_worker(void* arg) {
@@ -617,12 +672,21 @@ static void* render_worker(void* arg) {
         if (row >= j->n * j->height) break;
         int i = row / j->height, y = row % j->height;
         const orc_trace_opts* o = &j->opts[i];
+        const orc_tangent_spec* ts = j->ts ? &j->ts[i] : NULL;
+        int nt = ts ? ts->n : 0;
         for (int x = 0; x < j->width; ++x) {
             v3 acc = V(0, 0, 0);
-            for (int s = 0; s < o->spp; ++s) acc = add(acc, trace_path(&j->scenes[i], o, x, y, s));
+            double dacc[ORC_MAX_D], dl[ORC_MAX_D];
+            for (int k = 0; k < nt; ++k) dacc[k] = 0.0;
+            for (int s = 0; s < o->spp; ++s) {
+                acc = add(acc, trace_path_t(&j->scenes[i], o, x, y, s, ts, dl));
+                for (int k = 0; k < nt; ++k) dacc[k] += dl[k];
+            }
             acc = mul(acc, 1.0 / o->spp);
-            double* px = j->images + (((size_t)i * j->height + y) * j->width + x) * 3;
+            size_t pix = ((size_t)i * j->height + y) * j->width + x;
+            double* px = j->images + pix * 3;
             px[0] = acc.x; px[1] = acc.y; px[2] = acc.z;
+            for (int k = 0; k < nt; ++k) j->dimages[pix * nt + k] = dacc[k] / o->spp;
         }
     }
     return NULL;
@@ -634,9 +698,11 @@ static int resolve_threads(int nthreads) {
     return n > 0 ? (int)n : 1;
 }
 
-static void render_scenes(const orc_scene* scenes, const orc_trace_opts* opts, int n, double* images, int nthreads) {
+static void render_scenes_t(const orc_scene* scenes, const orc_trace_opts* opts, int n, double* images,
+                            const orc_tangent_spec* ts, double* dimages, int nthreads) {
     render_job j;
     j.scenes = scenes; j.opts = opts; j.images = images; j.n = n;
+    j.ts = ts; j.dimages = dimages;
     j.width = opts[0].width; j.height = opts[0].height; j.next_row = 0;
     pthread_mutex_init(&j.lock, NULL);
     int nt = resolve_threads(nthreads);
@@ -645,6 +711,10 @@ static void render_scenes(const orc_scene* scenes, const orc_trace_opts* opts, i
     for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, render_worker, &j);
     for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
     pthread_mutex_destroy(&j.lock);
+}
+
+static void render_scenes(const orc_scene* scenes, const orc_trace_opts* opts, int n, double* images, int nthreads) {
+    render_scenes_t(scenes, opts, n, images, NULL, NULL, nthreads);
 }
 
 /* Render n scenes at parameter vectors thetas[n][D]; render i uses the path
@@ -777,6 +847,100 @@ int orc_smoothed_grad(const orc_scene_arrays* a, const int32_t* binds, int D, co
     int rc = orc_estimate(mode, antithetic, D, theta, sigma, pairs, seed, step, render_loss, &c, grad, losses, taus,
                           weights);
     free(c.image);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The kappa-dP estimator (Eq. 9) for albedo and emission parameters.       */
+/* ------------------------------------------------------------------------ */
+/* Tangent spec of all D bindings at parameters theta; every binding must be an albedo
+ * or emission one. Returns 0 on success. */
+static int tangent_spec(const int32_t* binds, int D, const float* theta, orc_tangent_spec* ts) {
+    if (D < 1 || D > ORC_MAX_D) return 1;
+    ts->n = D;
+    for (int d = 0; d < D; ++d) {
+        int kind = binds[3 * d], idx = binds[3 * d + 1], c = binds[3 * d + 2];
+        if (kind != 2 && kind != 3) return 5;
+        double t = (double)theta[d];
+        ts->kind[d] = kind;
+        ts->mat[d] = idx;
+        ts->c[d] = c;
+        ts->dclamp[d] = (kind == 2) ? ((t >= 0.0 && t <= 1.0) ? 1.0 : 0.0) : (t >= 0.0 ? 1.0 : 0.0);
+    }
+    return 0;
+}
+
+/* One render at theta (path stream field `render_field`) with its pathwise tangents:
+ * image [H][W][3] pixel means and dimage [H][W][D], the derivative of the pixel mean's
+ * channel c_d with respect to theta_d. */
+int orc_render_tangent(const orc_scene_arrays* a, const int32_t* binds, int D, const float* theta, int render_field,
+                       int width, int height, int spp, int depth, int rr_start, uint64_t seed, uint32_t step,
+                       uint32_t tag, double* image, double* dimage, int nthreads) {
+    orc_scene sc;
+    orc_tangent_spec ts;
+    int rc = orc_instantiate(a, binds, D, theta, &sc);
+    if (rc) return rc;
+    rc = tangent_spec(binds, D, theta, &ts);
+    if (rc) return rc;
+    orc_trace_opts o = {width, height, spp, depth, rr_start, seed, step, tag, (uint32_t)render_field};
+    render_scenes_t(&sc, &o, 1, image, &ts, dimage, nthreads);
+    return 0;
+}
+
+/* Gradient of the image loss (1/3HW) sum (I - T)^2 from a render and its tangents:
+ * dL/dtheta_d = (2/3HW) sum_px (I_c - T_c) dI_c/dtheta_d with c = c_d. */
+static void loss_gradient(const double* image, const double* dimage, const float* target, const int32_t* binds,
+                          int D, int width, int height, double* g) {
+    for (int d = 0; d < D; ++d) g[d] = 0.0;
+    for (int i = 0; i < width * height; ++i)
+        for (int d = 0; d < D; ++d) {
+            int c = binds[3 * d + 2];
+            g[d] += (image[3 * i + c] - (double)target[4 * i + c]) * dimage[(size_t)i * D + d];
+        }
+    for (int d = 0; d < D; ++d) g[d] *= 2.0 / (3.0 * width * height);
+}
+
+/*
+ * Eq. 9 with the Gaussian kernel sampled exactly (tau ~ N(0, sigma^2), so the kernel
+ * weight over the sampling density is 1): g = (1/R) sum_r dL/dtheta (theta + tau_r), the
+ * mean over the R = 2P renders of each render's pathwise loss gradient. Draws and pairing
+ * are those of the gauss sampler of orc_smoothed_grad (antithetic: tau_p, -tau_p); render
+ * r uses path-stream field (crn ? 0 : r + 1). Outputs grad[D], losses[2P], taus[2P][D]
+ * (FP32) and the per-render gradients rgrads[2P][D].
+ */
+int orc_kdp_grad(const orc_scene_arrays* a, const int32_t* binds, int D, const float* theta, const float* sigma,
+                 int pairs, int antithetic, int crn, int width, int height, int spp, int depth, int rr_start,
+                 uint64_t seed, uint32_t step, const float* target, double* grad, double* losses, float* taus,
+                 double* rgrads, int nthreads) {
+    const int mode = 2; /* Gaussian draws */
+    int R = 2 * pairs;
+    if (D < 1 || D > ORC_MAX_D || pairs < 1) return 1;
+    double* image = (double*)malloc(sizeof(double) * (size_t)width * height * 3);
+    double* dimage = (double*)malloc(sizeof(double) * (size_t)width * height * D);
+    if (!image || !dimage) { free(image); free(dimage); return 9; }
+    for (int d = 0; d < D; ++d) grad[d] = 0.0;
+    int rc = 0;
+    for (int r = 0; r < R && !rc; ++r) {
+        double tau[ORC_MAX_D], w[ORC_MAX_D];
+        float tf[ORC_MAX_D], th[ORC_MAX_D];
+        int anti = antithetic && (r % 2 == 1);
+        uint32_t index = antithetic ? (uint32_t)(r / 2) : (uint32_t)r;
+        orc_sample(mode, D, sigma, seed, step, index, tau, tf, w);
+        for (int d = 0; d < D; ++d) {
+            float t = anti ? -tf[d] : tf[d];
+            th[d] = theta[d] + t; /* FP32 sum */
+            taus[(size_t)r * D + d] = t;
+        }
+        rc = orc_render_tangent(a, binds, D, th, crn ? 0 : r + 1, width, height, spp, depth, rr_start, seed, step,
+                                TAG_PATH, image, dimage, nthreads);
+        if (rc) break;
+        losses[r] = orc_mse(image, target, width, height);
+        loss_gradient(image, dimage, target, binds, D, width, height, rgrads + (size_t)r * D);
+        for (int d = 0; d < D; ++d) grad[d] += rgrads[(size_t)r * D + d];
+    }
+    for (int d = 0; d < D; ++d) grad[d] /= R;
+    free(image);
+    free(dimage);
     return rc;
 }
 

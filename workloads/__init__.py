@@ -13,6 +13,6 @@ from .scenes import (  # noqa: F401
     BIND_PRIM_POS, BIND_SPHERE_RADIUS, BIND_MAT_ALBEDO, BIND_MAT_EMISSION,
     SAMPLER_RADIAL, SAMPLER_PERDIM, SAMPLER_GAUSS,
     Scene, Workload, SceneBuilder,
-    config_small, config_occlusion, config_gi_box, config_caustic,
+    config_small, config_occlusion, config_gi_box, config_caustic, config_small_albedo, config_gi_albedo,
     all_configs, scaled, serving_mix,
 )

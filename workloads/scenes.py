@@ -125,6 +125,7 @@ class Workload:
     crn: int = 1
     sigma_min: float = 0.01
     anneal: int = 0          # 1 = linear sigma decay after a warm start at 50 % of `steps`
+    estimator: int = 0       # 0 = Eq. 10 (kernel-gradient weights), 1 = Eq. 9 (pathwise render gradients)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -254,6 +255,43 @@ def config_caustic(seed: int = 0) -> Workload:
         width=512, height=512, spp=64, depth=12, rr_start=3, pairs=32, seed=seed,
         lr=1e-2, steps=500,
     )
+
+
+def config_small_albedo(seed: int = 0) -> Workload:
+    """The small scene with material parameters instead: theta = sphere albedo RGB, ground
+    albedo G and light emission R (D = 5); Gaussian perturbations (sigma 0.05 on the
+    albedos, 2 on the emission) for the pathwise estimator of Eq. 9."""
+    wl = config_small(seed)
+    b = SceneBuilder()
+    m_ground = b.material(MAT_DIFFUSE, (0.8, 0.8, 0.8))
+    m_sphere = b.material(MAT_DIFFUSE, (0.8, 0.8, 0.8))
+    m_light = b.material(MAT_DIFFUSE, (0.0, 0.0, 0.0), emission=(40.0, 40.0, 40.0))
+    b.quad((0, 0, 0), (8, 0, 0), (0, 8, 0), m_ground)
+    b.sphere((0.0, 0.0, 0.5), 0.5, m_sphere)
+    b.quad((1.5, 1.5, 2.5), (0.5, 0, 0), (0, -0.5, 0), m_light)
+    b.look_at((0, 0, 5), (0, 0, 0), (0, 1, 0), 40.0)
+    rng = np.random.default_rng(seed + 5)
+    theta_ref = np.array([0.7, 0.3, 0.4, 0.6, 30.0])
+    theta0 = np.concatenate([rng.uniform(0.3, 0.9, size=4), [45.0]])
+    binds = [[BIND_MAT_ALBEDO, m_sphere, c] for c in range(3)]
+    binds += [[BIND_MAT_ALBEDO, m_ground, 1], [BIND_MAT_EMISSION, m_light, 0]]
+    return Workload(
+        name="small-64x64-albedo-emission", scene=b.build(), bindings=np.array(binds, np.int32),
+        theta_ref=_f32(theta_ref), theta0=_f32(theta0), sigma=_f32([0.05, 0.05, 0.05, 0.05, 2.0]),
+        width=wl.width, height=wl.height, spp=wl.spp, depth=wl.depth, rr_start=-1, pairs=4, seed=seed,
+        lr=2e-2, steps=200, sampler=SAMPLER_GAUSS, estimator=1,
+    )
+
+
+def config_gi_albedo(seed: int = 0) -> Workload:
+    """The GI box (512x512, depth 8 with Russian roulette from the 4th vertex, 32 spp,
+    P = 16) with theta = left and right wall RGB albedo (D = 6), sigma = 0.125, for the
+    pathwise estimator of Eq. 9 (Gaussian perturbations)."""
+    wl = config_gi_box(seed)
+    sl = slice(3, 9)
+    return replace(wl, name="gi-box-512x512-walls-albedo", bindings=wl.bindings[sl].copy(),
+                   theta_ref=wl.theta_ref[sl].copy(), theta0=wl.theta0[sl].copy(), sigma=wl.sigma[sl].copy(),
+                   sampler=SAMPLER_GAUSS, estimator=1)
 
 
 def all_configs():
