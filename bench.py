@@ -34,7 +34,9 @@ UNIT = "steps/s"
 # and min/max not counted) per unit of work of the path tracer.
 FLOPS = {"sphere_test": 22, "quad_test": 32, "box_test": 12, "path": 27, "vertex": 120}
 WORKLOADS = {"small": "config_small", "occlusion": "config_occlusion", "gi_box": "config_gi_box",
-             "caustic": "config_caustic"}
+             "caustic": "config_caustic",
+             # the pathwise estimator (Eq. 9) on material parameters
+             "small_albedo": "config_small_albedo", "gi_albedo": "config_gi_albedo"}
 
 
 def _env_int(name, default):
@@ -176,9 +178,10 @@ def cpu_baseline(wl, target, nthreads=0, budget_s=10.0, max_steps=20):
         run = workloads.scaled(wl, spp=4, pairs=1)
         scale = wl.paths_per_step / run.paths_per_step
         what = f"sampled steps (1 pair, 4 spp; time x{scale:.0f} by path count)"
+    estimate = oracle.kdp_grad if getattr(wl, "estimator", 0) == 1 else oracle.smoothed_grad
     n, t0 = 0, time.perf_counter()
     while n < max_steps and (n == 0 or time.perf_counter() - t0 < budget_s):
-        oracle.smoothed_grad(run, target=target, nthreads=cores, step=n)
+        estimate(run, target=target, nthreads=cores, step=n)
         n += 1
     dt = (time.perf_counter() - t0) / n * scale
     return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -415,6 +418,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "renders": wl.renders, "pairs": wl.pairs, "width": wl.width,
                        "height": wl.height, "spp": wl.spp, "depth": wl.depth, "D": wl.D,
+                       "estimator": "Eq. 9 (pathwise)" if getattr(wl, "estimator", 0) == 1 else "Eq. 10",
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "mpaths_per_s": world * wl.paths_per_step / (step_ms * 1e-3) / 1e6,
             # ray segments (closest-hit rays + shadow rays) traced per second: as executed

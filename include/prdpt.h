@@ -109,7 +109,7 @@ typedef struct {
     int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
 } prdpt_render_opts;
 
-/* Gradient-estimator options (Eq. 10, Algorithm 1). R = 2 * pairs renders. */
+/* Gradient-estimator options (Eq. 10 / Eq. 9, Algorithm 1). R = 2 * pairs renders. */
 typedef struct {
     int32_t pairs;             /* P antithetic pairs (Algorithm 1's N = 2P) */
     int32_t width, height, spp, depth, rr_start;
@@ -122,7 +122,13 @@ typedef struct {
     int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
     int32_t no_path_sharing;   /* 0: with crn = 1, trace paths that no perturbation can touch once for
                                   all renders (same result, bit for bit); 1: trace every render */
+    int32_t estimator;         /* PRDPT_ESTIMATOR_*: 0 = Eq. 10 (kernel-gradient weights times render
+                                  losses); 1 = Eq. 9 (mean over the renders of each render's pathwise
+                                  loss gradient: requires sampler = GAUSS, every binding an albedo or
+                                  emission one, D <= 8; no path sharing; single-job steps only) */
 } prdpt_grad_opts;
+#define PRDPT_ESTIMATOR_KERNEL_GRADIENT 0 /* Eq. 10: sum_r w_r L_r */
+#define PRDPT_ESTIMATOR_PATHWISE 1        /* Eq. 9: mean_r dL/dtheta (theta + tau_r) */
 
 /* A resident optimisation job: scene parameters, Adam state and target stay on
  * the device between steps (Adam, Sec. 3.4; bandwidth schedule, Sec. 3.3). */
@@ -260,7 +266,8 @@ prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);
  * a device looks up the array's device address (cudaGetSymbolAddress) and the
  * device's SM count; make that first call before any stream capture. Errors are
  * written to err (err_len bytes, may be NULL); there is no context to query.
- * The paper has no counterpart to this entry point. */
+ * Only the Eq. 10 estimator (opts->estimator = 0). The paper has no counterpart to this
+ * entry point. */
 prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene, const prdpt_param_binding* binds, int32_t D,
                                         const float* theta_dev, const float* sigma_dev, const prdpt_grad_opts* opts,
                                         const float* target_dev, float* grad_dev, float* losses_dev, void* stream,

@@ -67,7 +67,7 @@ struct Job {
 struct prdpt_ctx {
     int device = 0;
     int sms = 0;
-    int occ_grad = 1, occ_render = 1;
+    int occ_grad = 1, occ_render = 1, occ_diff = 1;
     uint64_t budget = 0, used = 0;
     std::map<void*, size_t> allocs;
     std::vector<Scene*> scenes;
@@ -98,6 +98,10 @@ struct prdpt_ctx {
     size_t s_varbox_n = 0;
     unsigned* s_cursor = nullptr; // path sharing: [R] per-render cursors
     size_t s_cursor_n = 0;
+    double* s_gpart = nullptr;    // pathwise estimator: [R][tiles][D] gradient partials
+    size_t s_gpart_n = 0;
+    double* s_rgrads = nullptr;   // pathwise estimator: [R][kMaxDiff] per-render gradients
+    size_t s_rgrads_n = 0;
     // packed launches
     std::vector<int> batch_ids;
     InstJob* d_inst = nullptr;
@@ -206,6 +210,14 @@ int grid_for(prdpt_ctx* c, int items, bool render, int ctas_per_sm) {
     return need < cap ? need : cap;
 }
 
+// Persistent grid of the pathwise-estimator render kernel (CTAs of kDiffBlock threads).
+int grid_for_diff(prdpt_ctx* c, int items, int ctas_per_sm) {
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < c->occ_diff) ? ctas_per_sm : c->occ_diff;
+    const int cap = c->sms * per_sm;
+    const int need = (items + kDiffBlock / 32 - 1) / (kDiffBlock / 32);
+    return need < cap ? need : cap;
+}
+
 // Launch the render kernel(s), bracketed by events on their stream when timing is on.
 // Ls[0..nL): render-kernel launches (a packed step has one for its path-sharing jobs and
 // one for the rest); a launch with share = 1 is followed by the affected-path and block
@@ -228,7 +240,9 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch* Ls, int nL, const Trace
     }
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < nL; ++i) {
-        e = launch_trace(Ls[i], render, grid_for(c, Ls[i].total_items, render, ctas_per_sm), stream);
+        const int grid = Ls[i].diff_nd ? grid_for_diff(c, Ls[i].total_items, ctas_per_sm)
+                                       : grid_for(c, Ls[i].total_items, render, ctas_per_sm);
+        e = launch_trace(Ls[i], render, grid, stream);
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < nL && !render; ++i) {
@@ -275,6 +289,7 @@ prdpt_status prdpt_create(prdpt_ctx** out, int32_t device, uint64_t hbm_budget_b
     c->sms = prop.multiProcessorCount;
     c->occ_grad = trace_blocks_per_sm(false);
     c->occ_render = trace_blocks_per_sm(true);
+    c->occ_diff = trace_diff_blocks_per_sm();
     void* p = nullptr;
     prdpt_status st = dev_alloc(c, &p, 128);  // status word, then 8 counters
     if (st) {
@@ -473,7 +488,8 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
         I->n_var = 0;
         I->var_box = nullptr;
     }
-    if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp) return;
+    if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT)
+        return;
     // per-render radiance buffers (24 bytes per render and pixel) and the recorded-path
     // list (20 bytes per path plus the segment pool) each within 512 MB
     const double pix = double(o->width) * double(o->height);
@@ -564,11 +580,38 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
 static prdpt_status check_grad_opts(const prdpt_grad_opts* o) {
     if (o->pairs < 1 || o->pairs > kMaxPairs) return fail(PRDPT_E_INVALID_ARG, "pairs must be in 1..256");
     if (o->sampler < 0 || o->sampler > 2) return fail(PRDPT_E_INVALID_ARG, "unknown sampler");
+    if (o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT && o->estimator != PRDPT_ESTIMATOR_PATHWISE)
+        return fail(PRDPT_E_INVALID_ARG, "unknown estimator");
+    if (o->estimator == PRDPT_ESTIMATOR_PATHWISE && o->sampler != PRDPT_SAMPLER_GAUSS)
+        return fail(PRDPT_E_INVALID_ARG, "the pathwise estimator (Eq. 9) samples the Gaussian kernel: sampler must be GAUSS");
     return check_common(o->width, o->height, o->spp, o->depth, o->rr_start);
 }
 
+// Pathwise estimator (Eq. 9): every binding must be an albedo or emission one (their
+// tangents are exact pathwise derivatives; geometry would need boundary terms).
+static prdpt_status fill_diff(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o) {
+    J.diff = 0;
+    J.diff_n = 0;
+    if (o->estimator != PRDPT_ESTIMATOR_PATHWISE) return PRDPT_OK;
+    if (B.D > kMaxDiff) return fail(PRDPT_E_INVALID_ARG, "the pathwise estimator takes at most 8 parameters");
+    for (int d = 0; d < B.D; ++d) {
+        const int kind = B.bind_kind[d];
+        if (kind != kBindAlbedo && kind != kBindEmission)
+            return fail(PRDPT_E_INVALID_ARG, "the pathwise estimator differentiates albedo and emission bindings only");
+        J.diff_mat[d] = B.bind_index[d];
+        J.diff_comp[d] = B.bind_comp[d];
+        J.diff_kind[d] = kind;
+    }
+    J.diff = 1;
+    J.diff_n = B.D;
+    return PRDPT_OK;
+}
+
+static int diff_slots(const TraceJob& J) { return J.diff ? (J.diff_n <= 4 ? 4 : 8) : 0; }
+
 static void fill_inst_grad(InstJob& J, const Scene* s, const prdpt_grad_opts* o) {
     fill_inst_common(J, s, 2 * o->pairs, s->D, o->width, o->height);
+    J.diff = o->estimator == PRDPT_ESTIMATOR_PATHWISE ? 1 : 0;
     J.seed = o->seed;
     J.step = o->step;
     J.tag = kTagPath;
@@ -621,6 +664,7 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     PRDPT_CUDA(cudaSetDevice(c->device));
     const int R = 2 * o->pairs, D = s->D;
     TraceJob probe{};
+    if (prdpt_status st = fill_diff(probe, s->host, o)) return st;
     fill_share(probe, s->host, o);  // path sharing: items are blocks, not (render, block)
     const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, o->width, o->height, false);
     int bw, bh, tiles_x, tiles;
@@ -639,6 +683,10 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         return st;
     if (prdpt_status st = grow(c, &c->s_partials, &c->s_partials_n, (size_t)R * tiles)) return st;
     if (prdpt_status st = grow(c, &c->s_losses, &c->s_losses_n, (size_t)R)) return st;
+    if (probe.diff) {
+        if (prdpt_status st = grow(c, &c->s_gpart, &c->s_gpart_n, (size_t)R * tiles * D)) return st;
+        if (prdpt_status st = grow(c, &c->s_rgrads, &c->s_rgrads_n, (size_t)R * kMaxDiff)) return st;
+    }
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     InstLaunch IL{};
     fill_inst_grad(IL.job0, s, o);
@@ -689,6 +737,12 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         J.aff_tiles = c->s_aff;
         J.share_ctl = c->s_ctl + 4;
     }
+    fill_diff(J, s->host, o);
+    if (J.diff) {
+        J.gpartials = c->s_gpart;
+        J.rgrads = c->s_rgrads;
+    }
+    TL.diff_nd = diff_slots(J);
     TL.total_items = J.share ? tiles : R * tiles;
     TL.share = J.share;
     TL.queue = c->s_ctl + 0;
@@ -718,13 +772,14 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const prdpt_grad_opts* o = &d->grad;
     if (prdpt_status st = check_grad_opts(o)) return st;
     PRDPT_CUDA(cudaSetDevice(c->device));
+    TraceJob probe{};
+    if (prdpt_status st = fill_diff(probe, s->host, o)) return st;
+    fill_share(probe, s->host, o);
     Job* j = new Job();
     j->scene = scene_id;
     j->D = s->D;
     j->R = 2 * o->pairs;
     const int D = j->D, R = j->R, W = o->width, H = o->height;
-    TraceJob probe{};
-    fill_share(probe, s->host, o);
     const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, W, H, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, W, H, &bw, &bh, &tiles_x, &tiles);
@@ -747,7 +802,9 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const size_t off_cu = (off_vb + (probe.share ? sizeof(float4) * 2 * kMaxVariant * (size_t)R : 0) + 255) &
                           ~size_t(255);
     const size_t off_af = (off_cu + (probe.share ? sizeof(unsigned) * (size_t)R : 0) + 255) & ~size_t(255);
-    const size_t total = off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0);
+    const size_t off_gp = (off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0) + 255) & ~size_t(255);
+    const size_t off_rg = (off_gp + (probe.diff ? sizeof(double) * (size_t)R * tiles * D : 0) + 255) & ~size_t(255);
+    const size_t total = off_rg + (probe.diff ? sizeof(double) * (size_t)R * kMaxDiff : 0);
     void* base = nullptr;
     if (prdpt_status st = dev_alloc(c, &base, total)) {
         delete j;
@@ -831,6 +888,11 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     T.tiles = tiles;
     T.n_prims = s->host.n_prims;
     T.n_mats = s->host.n_mats;
+    fill_diff(T, s->host, o);
+    if (T.diff) {
+        T.gpartials = reinterpret_cast<double*>(b + off_gp);
+        T.rgrads = reinterpret_cast<double*>(b + off_rg);
+    }
     fill_share(T, s->host, o, &I);
     if (T.share) {
         T.share_acc = j->share;
@@ -865,6 +927,7 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     TL.job0 = j->trace;
     TL.total_items = j->trace.share ? j->tiles : j->R * j->tiles;
     TL.share = j->trace.share;
+    TL.diff_nd = diff_slots(j->trace);
     TL.queue = j->queue;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
@@ -886,6 +949,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job in batch");
             for (int q = 0; q < i; ++q)
                 if (ids[q] == ids[i]) return fail(PRDPT_E_INVALID_ARG, "a job appears twice in a batch");
+            if (j->trace.diff) return fail(PRDPT_E_INVALID_ARG, "pathwise-estimator jobs step alone (prdpt_step)");
         }
         for (int pass = 0; pass < 2; ++pass)
             for (int i = 0; i < n; ++i) {

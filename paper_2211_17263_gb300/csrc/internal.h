@@ -32,6 +32,7 @@ constexpr float kEps = 1e-4f;    // ray t_min and surface offset (scene units)
 constexpr int kMaxVariant = 4;   // path sharing: perturbed primitives
 constexpr int kMaxShareSpp = 64; // path sharing: samples per pixel (6 bits of a path code)
 constexpr int kSeg = 4;          // path sharing: touching segments kept per path
+constexpr int kMaxDiff = 8;      // pathwise estimator (Eq. 9): differentiated parameters
 
 constexpr unsigned kTagPerturb = 1u;
 constexpr unsigned kTagPath = 2u;
@@ -72,6 +73,7 @@ struct __align__(16) InstScene {
     float4 bg;     // background radiance, 0
     int4 light[kMaxLights];
     float light_area[kMaxLights];
+    float dclamp[kMaxDiff];  // pathwise estimator: derivative of each parameter's clamp (1 or 0)
     float4 mat[kMaxMats][2];
     float4 prim[kMaxPrims][4];
 };
@@ -92,6 +94,7 @@ struct InstJob {
     int anneal, total_steps;
     float sigma_min, c_radial;  // c_radial = sqrt(2) Gamma((D+1)/2) / Gamma(D/2)
     int block_begin;          // first CTA index of this job in a packed launch
+    int diff;                 // pathwise estimator: write each render's clamp derivatives
     unsigned* share_reset;    // [4] path-sharing counters of the job, zeroed by its first CTA, or null
     // path sharing: bounds of each perturbed primitive in each render, [R][kMaxVariant][2]
     // (min, max corner, inflated), written by the render's CTA; null when not sharing
@@ -140,6 +143,14 @@ struct TraceJob {
     int* aff_tiles;           // [tiles] blocks with affected paths (appended by the shared pass)
     unsigned* share_ctl;      // [0] listed blocks, [1] recorded paths, [2] segment slots claimed,
                               // [3] epilogue queue; zeroed by the instantiation launch
+    // Pathwise estimator (Eq. 9): diff_n parameters, all albedo (kind 2) or emission (kind 3)
+    // of material diff_mat, channel diff_comp; each block writes its partial sums of
+    // (I - T) dI/dtheta_k to gpartials [R][tiles][diff_n]; k_finalize reduces them per render
+    // into rgrads [R][kMaxDiff] and forms the mean over renders.
+    int diff, diff_n;
+    int diff_mat[kMaxDiff], diff_comp[kMaxDiff], diff_kind[kMaxDiff];
+    double* gpartials;
+    double* rgrads;
     int n_var;                // perturbed primitives (<= kMaxVariant)
     int var_slot[kMaxVariant];  // their record slots
     unsigned var_prims;       // record-slot bitmask of perturbed primitives
@@ -150,6 +161,7 @@ struct TraceLaunch {
     const TraceJob* jobs;     // packed launch: [njobs] in device memory
     int njobs, total_items;
     int share;                // 1: every job of the launch shares paths (selects the kernel variant)
+    int diff_nd;              // pathwise estimator: tangent slots of the kernel variant (0, 4 or 8)
     int fin_total;            // packed launch: finalisation CTAs (sum of R over jobs)
     unsigned* queue;          // work-queue head, zeroed by the instantiation launch
     unsigned long long* counters;  // [8] or null (null: the uncounted kernel variant runs)
@@ -181,8 +193,11 @@ cudaError_t launch_ffma_probe(float* out, int blocks, int iters, cudaStream_t st
 int ffma_probe_flops_per_thread_iter();
 cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, unsigned c2, unsigned c3, int n,
                           uint32_t* out, cudaStream_t stream);
-// Resident CTAs per SM of the render kernel.
+// Resident CTAs per SM of the render kernel; the pathwise-estimator variant runs CTAs of
+// kDiffBlock threads.
 int trace_blocks_per_sm(bool render_mode);
+constexpr int kDiffBlock = 128;
+int trace_diff_blocks_per_sm();
 
 // Pixel block of one warp work item for 8, 16 or 32 pixels.
 inline void block_shape(int pixels, int* bw, int* bh) {

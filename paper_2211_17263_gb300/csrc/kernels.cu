@@ -264,6 +264,14 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     // ---- a2: bind theta_r into the scene -----------------------------------------
     const BaseScene& B = *J.base;
     InstScene& S = J.scenes[r];
+    if (tid < kMaxDiff) {  // pathwise estimator: derivative of each parameter's clamp
+        float dc = 0.0f;
+        if (J.diff && tid < D) {
+            const float t = s_theta[tid];
+            dc = B.bind_kind[tid] == kBindAlbedo ? ((t >= 0.0f && t <= 1.0f) ? 1.0f : 0.0f) : (t >= 0.0f ? 1.0f : 0.0f);
+        }
+        S.dclamp[tid] = dc;
+    }
     if (tid < B.n_prims) {
         const int i = tid;
         const int type = B.prim_type[i], mat = B.prim_mat[i], slot = B.prim_slot[i];
@@ -609,15 +617,85 @@ __device__ __forceinline__ void start_path(const InstScene& S, int W, int H, int
 // parameters are bound, or that every render must trace again, returns kAffected.
 constexpr int kLive = 0, kEnded = 1, kAffected = 2;
 
-template <bool kCount, bool kShared>
+// Forward-mode tangents of one path for the pathwise estimator (Eq. 9): dL[k] is the
+// derivative of radiance channel c_k with respect to parameter k (an albedo or emission of
+// material m_k), dB[k] that of the throughput's channel c_k. The path's discrete choices
+// are held fixed and the Russian-roulette probability is a constant of the derivative,
+// which keeps the derivative estimate unbiased as it keeps the radiance unbiased.
+template <int kND>
+struct Tangents {
+    float dB[kND > 0 ? kND : 1], dL[kND > 0 ? kND : 1];
+};
+
+__device__ __forceinline__ float comp3(float3 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
+
+template <int kND>
+__device__ __forceinline__ void tan_reset(Tangents<kND>& t) {
+#pragma unroll
+    for (int k = 0; k < kND; ++k) t.dB[k] = t.dL[k] = 0.0f;
+}
+
+// L += beta * E (background or emitter seen on a camera or specular ray); E may be bound.
+template <int kND>
+__device__ __forceinline__ void tan_emit(Tangents<kND>& t, const TraceJob& J, const InstScene& S, float3 beta,
+                                         float3 E, int mat) {
+#pragma unroll
+    for (int k = 0; k < kND; ++k) {
+        if (k >= J.diff_n) break;
+        const int c = J.diff_comp[k];
+        float d = t.dB[k] * comp3(E, c);
+        if (J.diff_kind[k] == kBindEmission && J.diff_mat[k] == mat) d = fmaf(comp3(beta, c), S.dclamp[k], d);
+        t.dL[k] += d;
+    }
+}
+
+// L += beta * albedo * Le * g (next-event estimation at a vertex of material mat).
+template <int kND>
+__device__ __forceinline__ void tan_nee(Tangents<kND>& t, const TraceJob& J, const InstScene& S, float3 beta,
+                                        float3 albedo, int mat, float3 Le, int lmat, float g) {
+#pragma unroll
+    for (int k = 0; k < kND; ++k) {
+        if (k >= J.diff_n) break;
+        const int c = J.diff_comp[k];
+        const float bc = comp3(beta, c), rc = comp3(albedo, c), ec = comp3(Le, c);
+        float d = t.dB[k] * rc * ec;
+        if (J.diff_kind[k] == kBindAlbedo && J.diff_mat[k] == mat) d = fmaf(bc * S.dclamp[k], ec, d);
+        if (J.diff_kind[k] == kBindEmission && J.diff_mat[k] == lmat) d = fmaf(bc * rc, S.dclamp[k], d);
+        t.dL[k] = fmaf(d, g, t.dL[k]);
+    }
+}
+
+// beta <- beta * albedo (scattering at a vertex of material mat); beta is the old value.
+template <int kND>
+__device__ __forceinline__ void tan_scatter(Tangents<kND>& t, const TraceJob& J, const InstScene& S, float3 beta,
+                                            float3 albedo, int mat) {
+#pragma unroll
+    for (int k = 0; k < kND; ++k) {
+        if (k >= J.diff_n) break;
+        const int c = J.diff_comp[k];
+        float d = t.dB[k] * comp3(albedo, c);
+        if (J.diff_kind[k] == kBindAlbedo && J.diff_mat[k] == mat) d = fmaf(comp3(beta, c), S.dclamp[k], d);
+        t.dB[k] = d;
+    }
+}
+
+template <int kND>
+__device__ __forceinline__ void tan_rr(Tangents<kND>& t, float inv_q) {
+#pragma unroll
+    for (int k = 0; k < kND; ++k) t.dB[k] *= inv_q;
+}
+
+template <bool kCount, bool kShared, int kND = 0>
 __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt,
-                                       const VarBoxes* V = nullptr) {
+                                       const VarBoxes* V = nullptr, Tangents<kND>* tn = nullptr,
+                                       const TraceJob* Jd = nullptr) {
     const Hit h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
     if (kShared) {
         note_touch<kCount>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, p.seg, cnt);
         if (p.seg == kSegFull) return kAffected;
     }
     if (h.slot < 0) {
+        if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, xyz(S.bg), -1);
         p.L = p.L + p.beta * xyz(S.bg);
         return kEnded;
     }
@@ -643,8 +721,10 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
     const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
     const int mtype = as_int(m0.w);
     const float3 albedo = xyz(m0), emission = xyz(m1);
-    if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f)
+    if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f) {
+        if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, emission, mat);
         p.L = p.L + p.beta * emission;
+    }
     const bool last = (p.b + 1 >= depth);
     const bool rr = !last && rr_start >= 0 && p.b >= rr_start;
     uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
@@ -686,6 +766,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
                     }
                     const float g = cx * cl * (inv_dist * inv_dist) * S.light_area[li] * float(S.n_lights) *
                                     0.3183098861837907f;
+                    if (kND > 0) tan_nee(*tn, *Jd, S, p.beta, albedo, mat, xyz(S.mat[lt.w][1]), lt.w, g);
                     p.L = p.L + p.beta * albedo * xyz(S.mat[lt.w][1]) * g;
                 }
             }
@@ -699,6 +780,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
         onb(ns, t1, t2);
         const float cz2 = fmaxf(0.0f, 1.0f - u1);
         const float3 wo = t1 * (rad * cp) + t2 * (rad * sp) + ns * (cz2 * rsqrtf(fmaxf(cz2, 1e-30f)));
+        if (kND > 0) tan_scatter(*tn, *Jd, S, p.beta, albedo, mat);
         p.beta = p.beta * albedo;
         p.o = po;
         p.d = normalized(wo);
@@ -709,6 +791,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
         const float3 ns = dot3(ng, p.d) < 0.0f ? ng : ng * -1.0f;
         p.d = normalized(p.d - ns * (2.0f * dot3(p.d, ns)));
         p.o = pt + ns * kEps;
+        if (kND > 0) tan_scatter(*tn, *Jd, S, p.beta, albedo, mat);
         p.beta = p.beta * albedo;
         p.specular = true;
     } else {  // smooth dielectric: exact unpolarised Fresnel, reflect or refract
@@ -742,6 +825,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
             p.d = normalized(p.d * eta + n * (eta * ci - ct));
             p.o = pt - n * kEps;
         }
+        if (kND > 0) tan_scatter(*tn, *Jd, S, p.beta, albedo, mat);
         p.beta = p.beta * albedo;
         p.specular = true;
     }
@@ -749,7 +833,9 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
     if (rr) {  // Russian roulette on slot 1's second uniform
         const float q = fminf(0.95f, maxc(p.beta));
         if (u01(w1.y) >= q) return kEnded;
-        p.beta = p.beta * __fdividef(1.0f, q);
+        const float inv_q = __fdividef(1.0f, q);
+        if (kND > 0) tan_rr(*tn, inv_q);
+        p.beta = p.beta * inv_q;
     }
     ++p.b;
     return kLive;
@@ -763,6 +849,7 @@ constexpr int kWarps = kBlock / 32;
 #define PRDPT_TRACE_MIN_BLOCKS 3  // <= 85 registers: 24 resident warps per SM
 #endif
 constexpr int kTraceMinBlocks = PRDPT_TRACE_MIN_BLOCKS;
+constexpr int kDiffMinBlocks = 5;  // pathwise-estimator CTAs of kDiffBlock threads: <= 102 registers
 constexpr float kFix = 4294967296.0f;  // 2^32: fixed-point scale of the radiance accumulators
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -795,15 +882,25 @@ __device__ __forceinline__ unsigned long long to_fixed(float v) {
     return sh >= 0 ? (m << sh) : (m >> (-sh));
 }
 
+// Signed value to 2^-32 fixed point as a two's-complement 64-bit word (tangent sums).
+__device__ __forceinline__ unsigned long long to_fixed_signed(float v) {
+    return v >= 0.0f ? to_fixed(v) : 0ull - to_fixed(-v);
+}
+
+// Two's-complement 64-bit integer to float (magnitude split into 32-bit halves, so no
+// 64-bit conversion instruction is needed); relative rounding error below 2^-23.
+__device__ __forceinline__ float signed_word_to_float(long long D) {
+    const unsigned long long m = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
+    const float f = fmaf(float(unsigned(m >> 32)), 4294967296.0f, float(unsigned(m)));
+    return D < 0 ? -f : f;
+}
+
 // Squared error of one pixel against the target, summed over RGB (a4). The pixel's sums
 // are 2^-32 fixed point over spp samples; acc - T * spp * 2^32 is formed exactly in 64-bit
 // integers (T truncated to 2^-32), so the difference suffers no cancellation, and is then
 // scaled to the mean and squared in FP32. Only the sums over pixels are FP64.
 __device__ __forceinline__ float fixed_diff(unsigned long long a, float t, unsigned spp, float inv) {
-    const long long D = (long long)(a - to_fixed(t) * (unsigned long long)spp);
-    const unsigned long long m = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
-    const float f = fmaf(float(unsigned(m >> 32)), 4294967296.0f, float(unsigned(m)));
-    return (D < 0 ? -f : f) * inv;
+    return signed_word_to_float((long long)(a - to_fixed(t) * (unsigned long long)spp)) * inv;
 }
 
 __device__ __forceinline__ double pixel_sq_error(unsigned long long ax, unsigned long long ay, unsigned long long az,
@@ -903,12 +1000,14 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, int k) {
 // Ended paths add their radiance to acc[.][slot]. In shared mode a path that touched a
 // perturbed primitive's union box is also recorded -- its code, segment word and
 // shared-pass radiance -- in the job's list, and *recorded is set.
-template <bool kCount, bool kShared, class Decode>
+template <bool kCount, bool kShared, class Decode, int kND = 0>
 __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, int ntasks, int x0, int y0, int vw,
                                          unsigned magic_w, Decode decode, unsigned long long (&acc)[3][32],
-                                         unsigned* recorded, const VarBoxes* V, Counters& cnt, int lane) {
+                                         unsigned* recorded, const VarBoxes* V, Counters& cnt, int lane,
+                                         unsigned long long (*dacc)[32] = nullptr) {
     const unsigned lt_mask = (1u << lane) - 1u;
     Path p;
+    Tangents<kND> tn;
     int task = lane;
     bool alive = task < ntasks;
     int slot, smp;
@@ -917,12 +1016,13 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
         const int row = div_magic(slot, vw, magic_w);
         start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
         if (kShared) p.seg = 0u;
+        if (kND > 0) tan_reset(tn);
         if (kCount) ++cnt.paths;
     }
     int next = 32;
     while (__any_sync(kFull, alive)) {
         int st = kLive;
-        if (alive) st = advance<kCount, kShared>(S, J.depth, J.rr_start, p, cnt, V);
+        if (alive) st = advance<kCount, kShared, kND>(S, J.depth, J.rr_start, p, cnt, V, &tn, &J);
         const bool ended = alive && st != kLive;
         // every ended path counts in the shared radiance; the per-render pass later adds,
         // for each render in a recorded path's mask, its own radiance minus this value
@@ -930,6 +1030,9 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
             atomicAdd(&acc[0][p.slot], to_fixed(p.L.x));
             atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
             atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
+#pragma unroll
+            for (int k = 0; k < kND; ++k)  // tangents: signed fixed point, exact and order-free
+                if (k < J.diff_n) atomicAdd(&dacc[k][p.slot], to_fixed_signed(tn.dL[k]));
         }
         if (kShared) {  // record the paths some render must trace itself
             const bool rec = ended && p.seg != 0u;
@@ -959,6 +1062,7 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
                 const int row = div_magic(slot, vw, magic_w);
                 start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
                 if (kShared) p.seg = 0u;
+                if (kND > 0) tan_reset(tn);
                 if (kCount) ++cnt.paths;
             }
         }
@@ -1006,12 +1110,48 @@ __device__ __forceinline__ void shared_block_epilogue(const TraceJob& J, int t, 
     __syncwarp();
 }
 
+// Pathwise estimator (Eq. 9): the block's loss partial as in block_epilogue, and for each
+// parameter k the partial sum over its pixels of (I - T)_c dI_c/dtheta_k (c = c_k), where
+// dI is the tangent sum divided by spp; the 2 / (3HW) factor is applied in k_finalize.
+template <int kND>
+__device__ __forceinline__ void diff_epilogue(const TraceJob& J, int r, int t, const unsigned long long (&acc)[3][32],
+                                              const unsigned long long (*dacc)[32], int x0, int y0, int vw, int npx,
+                                              int lane) {
+    const int px = x0 + lane % vw, py = y0 + lane / vw;
+    const bool ok = lane < npx && px < J.W && py < J.H;
+    const float inv = mean_scale(J.spp);
+    float3 res = f3(0.f, 0.f, 0.f);
+    double e = 0.0;
+    if (ok) {
+        const float4 T = __ldg(J.target + size_t(py) * J.W + px);
+        res = f3(fixed_diff(acc[0][lane], T.x, unsigned(J.spp), inv), fixed_diff(acc[1][lane], T.y, unsigned(J.spp), inv),
+                 fixed_diff(acc[2][lane], T.z, unsigned(J.spp), inv));
+        e = double(fmaf(res.x, res.x, fmaf(res.y, res.y, res.z * res.z)));
+    }
+    e = warp_sum_d(e);
+    if (lane == 0) J.partials[size_t(r) * J.tiles + t] = e;
+#pragma unroll
+    for (int k = 0; k < kND; ++k) {
+        if (k >= J.diff_n) break;
+        double g = 0.0;
+        if (ok) g = double(comp3(res, J.diff_comp[k]) * (signed_word_to_float((long long)dacc[k][lane]) * inv));
+        g = warp_sum_d(g);
+        if (lane == 0) J.gpartials[(size_t(r) * J.tiles + t) * J.diff_n + k] = g;
+    }
+    __syncwarp();
+}
+
 // kShare: every item is a pixel block of all renders of a path-sharing job (single-job
 // launches only); otherwise every item is one render's block and job.share is ignored.
-template <bool kRender, bool kCount, bool kShare>
-__global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_constant__ TraceLaunch L) {
+// kND > 0: the pathwise estimator (Eq. 9) with tangents of up to kND parameters, in CTAs
+// of kDiffBlock threads (room for the per-pixel tangent sums in shared memory).
+template <bool kRender, bool kCount, bool kShare, int kND>
+__global__ void __launch_bounds__(kND > 0 ? kDiffBlock : kBlock, kND > 0 ? kDiffMinBlocks : kTraceMinBlocks)
+    k_trace(const __grid_constant__ TraceLaunch L) {
     pdl_enter();
-    __shared__ WarpSmem s_warp[kWarps];
+    constexpr int kW = (kND > 0 ? kDiffBlock : kBlock) / 32;
+    __shared__ WarpSmem s_warp[kW];
+    __shared__ unsigned long long s_dacc[kND > 0 ? kW : 1][kND > 0 ? kND : 1][32];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem& W = s_warp[warp];
@@ -1074,6 +1214,16 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace(const __grid_
         W.acc[2][lane] = 0ull;
         __syncwarp();
 
+        if (!kShare && kND > 0) {
+            // ---- pathwise estimator: radiance and tangents of every pixel x sample ----------
+#pragma unroll
+            for (int k = 0; k < (kND > 0 ? kND : 1); ++k) s_dacc[warp][k][lane] = 0ull;
+            __syncwarp();
+            run_pool<kCount, false, decltype(dense), kND>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc,
+                                                          nullptr, nullptr, cnt, lane, s_dacc[warp]);
+            diff_epilogue<kND>(J, r, t, W.acc, s_dacc[warp], x0, y0, vw, npx, lane);
+            continue;
+        }
         if (!kShare) {
             // ---- a3: every pixel x sample of this render ----------------------------------
             run_pool<kCount, false>(W.scene, J, ntasks, x0, y0, vw, magic_w, dense, W.acc, nullptr, nullptr, cnt,
@@ -1355,26 +1505,40 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
     __syncthreads();
     const TraceJob& J = L.jobs ? L.jobs[s_job] : L.job0;
     const int r = int(blockIdx.x) - J.fin_begin;
-    const double* src = J.partials + size_t(r) * J.tiles;
-    double a[8];
+    // fixed-order sum of src[i * stride], i < n: strided per thread into eight
+    // accumulators, a warp shuffle tree, then the eight warp sums in order (thread 0)
+    auto reduce = [&](const double* src, int n, int stride) -> double {
+        double a[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) a[q] = 0.0;
-    int i = tid;
-    for (; i + 7 * kBlock < J.tiles; i += 8 * kBlock) {
+        for (int q = 0; q < 8; ++q) a[q] = 0.0;
+        int i = tid;
+        for (; i + 7 * kBlock < n; i += 8 * kBlock) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] += __ldcg(src + i + q * kBlock);
-    }
-    for (; i < J.tiles; i += kBlock) a[0] += __ldcg(src + i);
-    double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    v = warp_sum_d(v);
-    if ((tid & 31) == 0) s_red[tid >> 5] = v;
-    __syncthreads();
-    if (tid == 0) {
+            for (int q = 0; q < 8; ++q) a[q] += __ldcg(src + size_t(i + q * kBlock) * stride);
+        }
+        for (; i < n; i += kBlock) a[0] += __ldcg(src + size_t(i) * stride);
+        double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        v = warp_sum_d(v);
+        if ((tid & 31) == 0) s_red[tid >> 5] = v;
+        __syncthreads();
         double sum = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) sum += s_red[w];
-        const double Lr = sum / (3.0 * double(J.W) * double(J.H));
+        if (tid == 0)
+            for (int w = 0; w < kBlock / 32; ++w) sum += s_red[w];
+        __syncthreads();
+        return sum;
+    };
+    const double lsum = reduce(J.partials + size_t(r) * J.tiles, J.tiles, 1);
+    if (tid == 0) {
+        const double Lr = lsum / (3.0 * double(J.W) * double(J.H));
         J.losses[r] = Lr;
         if (J.loss_out) J.loss_out[r] = float(Lr);
+    }
+    if (J.diff)  // pathwise estimator: render r's loss gradient (without the 2 / 3HW factor)
+        for (int k = 0; k < J.diff_n; ++k) {
+            const double gsum = reduce(J.gpartials + size_t(r) * J.tiles * J.diff_n + k, J.tiles, J.diff_n);
+            if (tid == 0) J.rgrads[size_t(r) * kMaxDiff + k] = gsum;
+        }
+    if (tid == 0) {
         __threadfence();
         s_last = (atomicAdd(J.done, 1u) == unsigned(J.R - 1));
     }
@@ -1386,7 +1550,10 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
     const int warp = tid >> 5, lane = tid & 31;
     for (int d = warp; d < J.D; d += kBlock / 32) {
         double g = 0.0;
-        if (J.antithetic) {
+        if (J.diff) {  // Eq. 9: mean over renders of the pathwise loss gradients
+            for (int q = lane; q < J.R; q += 32) g += __ldcg(J.rgrads + size_t(q) * kMaxDiff + d);
+            g = warp_sum_d(g) * (2.0 / (3.0 * double(J.W) * double(J.H))) / double(J.R);
+        } else if (J.antithetic) {
             const int P = J.R / 2;
             for (int p = lane; p < P; p += 32)
                 g += double(J.w[size_t(2 * p) * J.D + d]) * (__ldcg(J.losses + 2 * p) - __ldcg(J.losses + 2 * p + 1));
@@ -1449,12 +1616,18 @@ cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream) {
     return launch_pdl(k_instantiate, L.total_blocks, kInstBlock, stream, L);
 }
 
+int trace_diff_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, 8>, kDiffBlock, 0);
+    return n > 0 ? n : 1;
+}
+
 int trace_blocks_per_sm(bool render_mode) {
     int n = 0;
     if (render_mode)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false, 0>, kBlock, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, 0>, kBlock, 0);
     return n > 0 ? n : 1;
 }
 
@@ -1462,11 +1635,17 @@ cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaS
     if (L.total_items <= 0) return cudaSuccess;
     const bool count = L.counters != nullptr;
     const bool share = !render_mode && L.share;
-    if (render_mode) return launch_pdl(count ? k_trace<true, true, false> : k_trace<true, false, false>, grid, kBlock,
+    if (render_mode) return launch_pdl(count ? k_trace<true, true, false, 0> : k_trace<true, false, false, 0>, grid, kBlock,
                                        stream, L);
-    if (share) return launch_pdl(count ? k_trace<false, true, true> : k_trace<false, false, true>, grid, kBlock,
+    if (share) return launch_pdl(count ? k_trace<false, true, true, 0> : k_trace<false, false, true, 0>, grid, kBlock,
                                  stream, L);
-    return launch_pdl(count ? k_trace<false, true, false> : k_trace<false, false, false>, grid, kBlock, stream, L);
+    if (L.diff_nd == 4)
+        return launch_pdl(count ? k_trace<false, true, false, 4> : k_trace<false, false, false, 4>, grid, kDiffBlock,
+                          stream, L);
+    if (L.diff_nd == 8)
+        return launch_pdl(count ? k_trace<false, true, false, 8> : k_trace<false, false, false, 8>, grid, kDiffBlock,
+                          stream, L);
+    return launch_pdl(count ? k_trace<false, true, false, 0> : k_trace<false, false, false, 0>, grid, kBlock, stream, L);
 }
 
 cudaError_t launch_trace_affected(const TraceLaunch& L, int grid, cudaStream_t stream) {

@@ -145,6 +145,8 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     if (o->pairs < 1 || 2 * o->pairs > kStaticMaxRenders)
         return report(err, err_len, PRDPT_E_INVALID_ARG, "pairs must be in 1..32 for the allocation-free call");
     if (o->sampler < 0 || o->sampler > 2) return report(err, err_len, PRDPT_E_INVALID_ARG, "unknown sampler");
+    if (o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT)
+        return report(err, err_len, PRDPT_E_INVALID_ARG, "the allocation-free call computes Eq. 10 only");
     if (o->width < 1 || o->height < 1 || o->width > 8192 || o->height > 8192)
         return report(err, err_len, PRDPT_E_INVALID_ARG, "width/height must be in 1..8192");
     if (o->spp < 1 || o->spp > 65535) return report(err, err_len, PRDPT_E_INVALID_ARG, "spp must be in 1..65535");
