@@ -264,6 +264,9 @@ def main():
     ap.add_argument("--serving-steps", type=int, default=4, help="steps per served job")
     ap.add_argument("--workload", default="occlusion", choices=sorted(WORKLOADS),
                     help="occlusion is the headline workload; the others are measured on request")
+    ap.add_argument("--estimator", default="auto", choices=["auto", "kernel", "pathwise"],
+                    help="auto: the workload's own; kernel: Eq. 10 with the radial sampler; pathwise: Eq. 9 "
+                         "(Gaussian draws; material bindings only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -289,6 +292,10 @@ def main():
             dist.barrier()
 
     wl = getattr(workloads, WORKLOADS[args.workload])(seed=rank)  # one independent replica per rank
+    if args.estimator == "kernel":
+        wl.estimator, wl.sampler = 0, workloads.SAMPLER_RADIAL
+    elif args.estimator == "pathwise":
+        wl.estimator, wl.sampler = 1, workloads.SAMPLER_GAUSS
     ctx = api.Context(local)
     probe_tflops, probe_ms = ctx.fp32_peak_probe()  # FMA-chain launch: confirms the FP32 peak
     scene = ctx.upload_scene(wl.scene, wl.bindings)
