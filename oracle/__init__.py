@@ -90,6 +90,14 @@ def lib():
     return _lib
 
 
+def _param_dim(binds: np.ndarray) -> int:
+    """Parameters the bindings stand for: one per row, or 3 T^2 for a texture row (4, mat, T)."""
+    binds = np.asarray(binds).reshape(-1, 3)
+    if binds.shape[0] == 1 and int(binds[0, 0]) == 4:
+        return 3 * int(binds[0, 2]) ** 2
+    return binds.shape[0]
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -201,7 +209,7 @@ def render(scene, bindings, thetas, width, height, spp, depth, rr_start=-1, seed
     binds = np.ascontiguousarray(bindings, np.int32).reshape(-1, 3)
     th = np.ascontiguousarray(np.atleast_2d(thetas), np.float32)
     n, D = th.shape
-    if binds.shape[0] != D:
+    if _param_dim(binds) != D:
         raise ValueError("thetas and bindings disagree on D")
     out = np.zeros((n, height, width, 3), np.float64)
     rc = lib().orc_render(h.ref, _ptr(binds), D, _ptr(th), n, width, height, spp, depth, rr_start, seed, step, tag,

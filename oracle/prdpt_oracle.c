@@ -147,8 +147,8 @@ void orc_sample_unit(int mode, int D, const double* u, double* tau, double* w) {
         int extra = (D % 2 == 0) ? 1 : 0;
         double r2 = 0.0;
         for (int j = 0; j < n_exp; ++j) r2 += -2.0 * log(u[j]); /* chi^2 with 2 dof each */
-        double z[ORC_MAX_D + 2];
         int nz = D + extra;
+        double* z = (double*)malloc(sizeof(double) * (size_t)(nz + 1));
         for (int m = 0; 2 * m < nz; ++m) { /* Box-Muller pairs */
             double a = u[n_exp + 2 * m], b = u[n_exp + 2 * m + 1];
             double rad = sqrt(-2.0 * log(a));
@@ -165,6 +165,7 @@ void orc_sample_unit(int mode, int D, const double* u, double* tau, double* w) {
             tau[d] = r * dir;
             w[d] = c * dir;
         }
+        free(z);
         return;
     }
     if (mode == 1) {
@@ -200,15 +201,18 @@ void orc_sample_unit(int mode, int D, const double* u, double* tau, double* w) {
 void orc_sample(int mode, int D, const float* sigma, uint64_t seed, uint32_t step, uint32_t index,
                 double* tau, float* tau_f32, double* w) {
     int nu = orc_sampler_uniforms(mode, D);
-    double u[4 * ((2 * ORC_MAX_D + 8) / 4 + 1)];
+    double* u = (double*)malloc(sizeof(double) * (size_t)(4 * (nu / 4 + 1)));
+    double* tt = (double*)malloc(sizeof(double) * (size_t)D * 2);
+    double* wt = tt + D;
     for (int k = 0; 4 * k < nu; ++k) uniforms4(seed, index, (uint32_t)k, step, TAG_PERTURB << 28, u + 4 * k);
-    double tt[ORC_MAX_D], wt[ORC_MAX_D];
     orc_sample_unit(mode, D, u, tt, wt);
     for (int d = 0; d < D; ++d) {
         tau[d] = (double)sigma[d] * tt[d];
         tau_f32[d] = (float)tau[d];
         w[d] = wt[d] / (double)sigma[d];
     }
+    free(u);
+    free(tt);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -251,6 +255,11 @@ typedef struct {
     v3 eye, look, up;
     double vfov_deg;
     v3 background;
+    /* texture: the albedo of material tex_mat on quads is looked up in tex, tex_res x
+     * tex_res texels of RGB (row-major [t][s][3], texel (0,0) at the quad corner
+     * c - u/2 - v/2), clamped to [0,1] at lookup; tex_mat = -1: none */
+    int tex_mat, tex_res;
+    const float* tex;
 } orc_scene;
 
 /* Flat scene arrays exactly as the workloads package lays them out. */
@@ -272,8 +281,10 @@ static int is_emissive(const orc_mat* m) { return m->emission.x > 0 || m->emissi
  * 1 sphere radius, 2 material albedo (clamped to [0,1]), 3 material emission
  * (clamped to >= 0). Returns 0 on success. */
 int orc_instantiate(const orc_scene_arrays* a, const int32_t* binds, int D, const float* theta, orc_scene* s) {
-    if (a->n_prims > ORC_MAX_PRIMS || a->n_mats > ORC_MAX_MATS || D > ORC_MAX_D) return 1;
+    int texture = D > 0 && binds && binds[0] == 4;
+    if (a->n_prims > ORC_MAX_PRIMS || a->n_mats > ORC_MAX_MATS || (!texture && D > ORC_MAX_D)) return 1;
     memset(s, 0, sizeof(*s));
+    s->tex_mat = -1;
     s->n_prims = a->n_prims;
     s->n_mats = a->n_mats;
     for (int i = 0; i < a->n_prims; ++i) {
@@ -292,6 +303,14 @@ int orc_instantiate(const orc_scene_arrays* a, const int32_t* binds, int D, cons
         s->mat[i].albedo = V(q[0], q[1], q[2]);
         s->mat[i].emission = V(q[3], q[4], q[5]);
         s->mat[i].ior = q[6];
+    }
+    if (texture) { /* kind 4: one binding row (4, material, resolution) for all 3 res^2 parameters */
+        int idx = binds[1], res = binds[2];
+        if (idx < 0 || idx >= s->n_mats || res < 1 || D != 3 * res * res) return 2;
+        s->tex_mat = idx;
+        s->tex_res = res;
+        s->tex = theta;
+        D = 0;
     }
     for (int d = 0; d < D; ++d) {
         int kind = binds[3 * d], idx = binds[3 * d + 1], c = binds[3 * d + 2];
@@ -486,6 +505,20 @@ typedef struct {
     double dclamp[ORC_MAX_D];
 } orc_tangent_spec;
 
+/* Albedo of a textured quad at hit point p: texel (floor(s T), floor(t T)) with
+ * s = (p - c).u / |u|^2 + 1/2, t = (p - c).v / |v|^2 + 1/2, each clamped to [0, T-1];
+ * channels clamped to [0,1]. */
+static v3 tex_albedo(const orc_scene* sc, const orc_prim* pr, v3 p) {
+    v3 l = sub(p, pr->c);
+    double s = dot(l, pr->u) / dot(pr->u, pr->u) + 0.5, t = dot(l, pr->v) / dot(pr->v, pr->v) + 0.5;
+    int T = sc->tex_res;
+    int tx = (int)floor(s * T), ty = (int)floor(t * T);
+    tx = tx < 0 ? 0 : (tx > T - 1 ? T - 1 : tx);
+    ty = ty < 0 ? 0 : (ty > T - 1 ? T - 1 : ty);
+    const float* q = sc->tex + ((size_t)ty * T + tx) * 3;
+    return V(fmin(fmax(q[0], 0.0), 1.0), fmin(fmax(q[1], 0.0), 1.0), fmin(fmax(q[2], 0.0), 1.0));
+}
+
 /* beta <- beta * albedo (material mat): product rule on each tangent's channel. */
 static void scatter_tangents(const orc_tangent_spec* ts, double* dB, v3 beta, v3 albedo, int mat) {
     if (!ts) return;
@@ -534,6 +567,8 @@ static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int 
         const orc_prim* pr = &sc->prim[hit];
         const orc_mat* m = &sc->mat[pr->mat];
         v3 p = add(org, mul(dir, t));
+        v3 albedo = m->albedo;
+        if (pr->mat == sc->tex_mat && pr->type == P_QUAD) albedo = tex_albedo(sc, pr, p);
         if (specular && is_emissive(m) && dot(dir, ng) < 0.0) {
             L = add(L, hmul(beta, m->emission));
             for (int k = 0; k < nt; ++k) {
@@ -576,10 +611,10 @@ static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int 
                 if (cx > 0.0 && cl > 0.0 && !occluded(sc, po, wi, dist, sc->light[li])) {
                     double g = cx * cl / dist2 * area * sc->n_lights / M_PI;
                     v3 le = sc->mat[lp->mat].emission;
-                    L = add(L, mul(hmul(hmul(beta, m->albedo), le), g));
+                    L = add(L, mul(hmul(hmul(beta, albedo), le), g));
                     for (int k = 0; k < nt; ++k) { /* product rule on beta * albedo * Le */
                         int c = ts->c[k];
-                        double bc = comp(beta, c), rc = comp(m->albedo, c), ec = comp(le, c);
+                        double bc = comp(beta, c), rc = comp(albedo, c), ec = comp(le, c);
                         double d = dB[k] * rc * ec;
                         if (ts->kind[k] == 2 && ts->mat[k] == pr->mat) d += bc * ts->dclamp[k] * ec;
                         if (ts->kind[k] == 3 && ts->mat[k] == lp->mat) d += bc * rc * ts->dclamp[k];
@@ -592,8 +627,8 @@ static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int 
             v3 t1, t2;
             onb(ns, &t1, &t2);
             v3 wo = add(add(mul(t1, rad * cos(phi)), mul(t2, rad * sin(phi))), mul(ns, sqrt(fmax(0.0, 1.0 - u[2]))));
-            scatter_tangents(ts, dB, beta, m->albedo, pr->mat);
-            beta = hmul(beta, m->albedo);
+            scatter_tangents(ts, dB, beta, albedo, pr->mat);
+            beta = hmul(beta, albedo);
             org = po;
             dir = normalize(wo);
             specular = 0;
@@ -602,8 +637,8 @@ static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int 
             v3 ns = dot(ng, dir) < 0.0 ? ng : mul(ng, -1.0);
             dir = normalize(sub(dir, mul(ns, 2.0 * dot(dir, ns))));
             org = add(p, mul(ns, ORC_EPS));
-            scatter_tangents(ts, dB, beta, m->albedo, pr->mat);
-            beta = hmul(beta, m->albedo);
+            scatter_tangents(ts, dB, beta, albedo, pr->mat);
+            beta = hmul(beta, albedo);
             specular = 1;
         } else { /* smooth dielectric: exact unpolarised Fresnel, reflect or refract */
             if (last) break;
@@ -629,8 +664,8 @@ static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int 
                 dir = normalize(add(mul(dir, eta), mul(n, eta * ci - ct)));
                 org = sub(p, mul(n, ORC_EPS));
             }
-            scatter_tangents(ts, dB, beta, m->albedo, pr->mat);
-            beta = hmul(beta, m->albedo);
+            scatter_tangents(ts, dB, beta, albedo, pr->mat);
+            beta = hmul(beta, albedo);
             specular = 1;
         }
         if (maxc(beta) <= 0.0) break; /* nothing more can be added */
@@ -785,10 +820,13 @@ int orc_estimate(int mode, int antithetic, int D, const float* theta, const floa
                  uint32_t step, orc_loss_cb loss, void* user, double* grad, double* losses, float* taus,
                  double* weights) {
     int R = 2 * pairs;
-    if (D < 1 || D > ORC_MAX_D || pairs < 1) return 1;
+    if (D < 1 || pairs < 1) return 1;
+    double* tau = (double*)malloc(sizeof(double) * (size_t)D * 2);
+    float* tf = (float*)malloc(sizeof(float) * (size_t)D * 2);
+    if (!tau || !tf) { free(tau); free(tf); return 9; }
+    double* w = tau + D;
+    float* th = tf + D;
     for (int r = 0; r < R; ++r) {
-        double tau[ORC_MAX_D], w[ORC_MAX_D];
-        float tf[ORC_MAX_D], th[ORC_MAX_D];
         int anti = antithetic && (r % 2 == 1);
         uint32_t index = antithetic ? (uint32_t)(r / 2) : (uint32_t)r;
         orc_sample(mode, D, sigma, seed, step, index, tau, tf, w);
@@ -799,8 +837,10 @@ int orc_estimate(int mode, int antithetic, int D, const float* theta, const floa
             weights[(size_t)r * D + d] = anti ? -w[d] : w[d];
         }
         losses[r] = loss(th, D, r, user);
-        if (isnan(losses[r])) return 4;
+        if (isnan(losses[r])) { free(tau); free(tf); return 4; }
     }
+    free(tau);
+    free(tf);
     for (int d = 0; d < D; ++d) {
         double g = 0.0;
         if (antithetic) {

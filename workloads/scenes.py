@@ -34,6 +34,7 @@ import numpy as np
 PRIM_SPHERE, PRIM_QUAD, PRIM_BOX = 0, 1, 2
 MAT_DIFFUSE, MAT_MIRROR, MAT_DIELECTRIC = 0, 1, 2
 BIND_PRIM_POS, BIND_SPHERE_RADIUS, BIND_MAT_ALBEDO, BIND_MAT_EMISSION = 0, 1, 2, 3
+BIND_TEXTURE = 4  # one row (4, material, T) standing for the T x T x 3 texel albedos
 SAMPLER_RADIAL, SAMPLER_PERDIM, SAMPLER_GAUSS = 0, 1, 2
 
 
@@ -130,6 +131,8 @@ class Workload:
 
     @property
     def D(self) -> int:
+        if self.bindings.shape[0] == 1 and int(self.bindings[0, 0]) == BIND_TEXTURE:
+            return 3 * int(self.bindings[0, 2]) ** 2
         return int(self.bindings.shape[0])
 
     @property
@@ -292,6 +295,37 @@ def config_gi_albedo(seed: int = 0) -> Workload:
     return replace(wl, name="gi-box-512x512-walls-albedo", bindings=wl.bindings[sl].copy(),
                    theta_ref=wl.theta_ref[sl].copy(), theta0=wl.theta0[sl].copy(), sigma=wl.sigma[sl].copy(),
                    sampler=SAMPLER_GAUSS, estimator=1)
+
+
+def config_texture(res: int = 128, px_per_texel: int = 2, seed: int = 0) -> Workload:
+    """The paper's high-dimensional texture task (its supplemental "Compatibility"
+    section) as an analytic stand-in: a res x res RGB texture (D = 3 res^2; 49,152 for
+    res = 128) on a square diffuse plane seen straight from above under a uniform
+    environment (background radiance 1), depth 2 (the plane, then the sky). The camera
+    frames the plane exactly, px_per_texel pixels per texel side, so a pixel sees one
+    texel and its value is that texel's albedo. theta_ref is a seeded smooth pattern in
+    [0.2, 0.8], theta0 a uniform grey; sigma = 0.01 per texel; 8 pairs, 4 spp."""
+    b = SceneBuilder()
+    m_tex = b.material(MAT_DIFFUSE, (0.5, 0.5, 0.5))
+    b.quad((0, 0, 0), (2, 0, 0), (0, -2, 0), m_tex)  # s along +x, t along -y: texel rows follow image rows
+    b.look_at((0, 0, 1), (0, 0, 0), (0, 1, 0), 90.0)
+    b.background = np.array([1.0, 1.0, 1.0], np.float32)
+    rng = np.random.default_rng(seed + 11)
+    y, x = np.mgrid[0:res, 0:res] / res
+    ref = np.zeros((res, res, 3))
+    for c in range(3):
+        for _ in range(3):
+            fx, fy, ph = rng.uniform(1.0, 4.0), rng.uniform(1.0, 4.0), rng.uniform(0, 2 * np.pi)
+            ref[..., c] += np.sin(2 * np.pi * (fx * x + fy * y) + ph)
+    ref = 0.5 + 0.3 * ref / np.abs(ref).max()
+    D = 3 * res * res
+    W = res * px_per_texel
+    return Workload(
+        name=f"texture-{res}x{res}-rgb", scene=b.build(),
+        bindings=np.array([[BIND_TEXTURE, m_tex, res]], np.int32),
+        theta_ref=_f32(ref.reshape(-1)), theta0=_f32(np.full(D, 0.5)), sigma=_f32(np.full(D, 0.01)),
+        width=W, height=W, spp=4, depth=2, rr_start=-1, pairs=8, seed=seed, lr=1e-2, steps=300,
+    )
 
 
 def all_configs():
