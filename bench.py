@@ -36,7 +36,9 @@ FLOPS = {"sphere_test": 22, "quad_test": 32, "box_test": 12, "path": 27, "vertex
 WORKLOADS = {"small": "config_small", "occlusion": "config_occlusion", "gi_box": "config_gi_box",
              "caustic": "config_caustic",
              # the pathwise estimator (Eq. 9) on material parameters
-             "small_albedo": "config_small_albedo", "gi_albedo": "config_gi_albedo"}
+             "small_albedo": "config_small_albedo", "gi_albedo": "config_gi_albedo",
+             # the 128 x 128 RGB texture: 49,152 parameters
+             "texture": "config_texture"}
 
 
 def _env_int(name, default):
@@ -439,8 +441,8 @@ def main():
                               "closest_hit_rays": counts[6]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": _profiled(wl.name, "dram_bytes_per_step"),
-                         "kernel": "render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue,"
-                                   " k_finalize)",
+                         "kernel": ("render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue,"
+                                    " k_finalize)" if counts[3] < wl.paths_per_step else "k_trace + k_finalize"),
                          "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
                                        f" x 2 flop x {sm_max:.0f} MHz"},
             "roofline_per_render_kernel": {

@@ -108,8 +108,9 @@ class Scene:
                   np.ascontiguousarray(scene.background, np.float32)]
         desc = capi.prdpt_scene_desc(int(arrays[0].shape[0]), int(arrays[3].shape[0]), *[_np_ptr(a) for a in arrays])
         b = np.ascontiguousarray(bindings, np.int32).reshape(-1, 3)
-        self.D = int(b.shape[0])
-        binds = (capi.prdpt_param_binding * self.D)(*[capi.prdpt_param_binding(*map(int, row)) for row in b])
+        # a texture binding (4, material, T) is one row standing for 3 T^2 parameters
+        self.D = 3 * int(b[0, 2]) ** 2 if b.shape[0] == 1 and int(b[0, 0]) == 4 else int(b.shape[0])
+        binds = (capi.prdpt_param_binding * b.shape[0])(*[capi.prdpt_param_binding(*map(int, row)) for row in b])
         self.id = capi.prdpt_scene_upload(ctx.handle, desc, binds, self.D)
 
     def render_batch(self, thetas: torch.Tensor, width, height, spp, depth, rr_start=-1, seed=0, step=0, tag=2,

@@ -40,12 +40,16 @@ struct Scene {
 };
 
 struct Job {
+    void* base = nullptr;  // the job's one device allocation
     int scene = -1;
     int D = 0, R = 0, tiles = 0, ctas_per_sm = 0;
     size_t bytes = 0;
     // device buffers
     float *theta = nullptr, *m = nullptr, *v = nullptr, *sigma0 = nullptr, *grad = nullptr, *losses = nullptr;
     float* w = nullptr;
+    bool tex = false;              // texture scene: D > kMaxD parameters
+    float* tex_all = nullptr;      // [R][D] per-render textures
+    float2* norms = nullptr;       // [R] radial-sampler norms
     unsigned long long* share = nullptr;
     unsigned long long* accaff = nullptr;
     void* afflist = nullptr;
@@ -98,6 +102,10 @@ struct prdpt_ctx {
     size_t s_varbox_n = 0;
     unsigned* s_cursor = nullptr; // path sharing: [R] per-render cursors
     size_t s_cursor_n = 0;
+    float* s_tex = nullptr;       // texture scenes: [R][D] per-render textures
+    size_t s_tex_n = 0;
+    float2* s_norms = nullptr;    // texture scenes: [draws] radial-sampler norms
+    size_t s_norms_n = 0;
     double* s_gpart = nullptr;    // pathwise estimator: [R][tiles][D] gradient partials
     size_t s_gpart_n = 0;
     double* s_rgrads = nullptr;   // pathwise estimator: [R][kMaxDiff] per-render gradients
@@ -129,13 +137,13 @@ prdpt_status dev_alloc(prdpt_ctx* c, void** p, size_t bytes) {
     return PRDPT_OK;
 }
 
+// Free an allocation made by dev_alloc (other pointers are not the context's to free).
 void dev_free(prdpt_ctx* c, void* p) {
     if (!p) return;
     auto it = c->allocs.find(p);
-    if (it != c->allocs.end()) {
-        c->used -= it->second;
-        c->allocs.erase(it);
-    }
+    if (it == c->allocs.end()) return;
+    c->used -= it->second;
+    c->allocs.erase(it);
     cudaFree(p);
 }
 
@@ -337,7 +345,15 @@ prdpt_status prdpt_scene_upload(prdpt_ctx* c, const prdpt_scene_desc* sd, const 
     std::lock_guard<std::mutex> lk(c->mu);
     if (sd->n_prims < 1 || sd->n_prims > kMaxPrims) return fail(PRDPT_E_INVALID_ARG, "n_prims must be in 1..32");
     if (sd->n_mats < 1 || sd->n_mats > kMaxMats) return fail(PRDPT_E_INVALID_ARG, "n_mats must be in 1..32");
-    if (D < 1 || D > kMaxD) return fail(PRDPT_E_INVALID_ARG, "D must be in 1..64");
+    const bool texture = D >= 1 && binds[0].kind == kBindTexture;
+    if (texture) {  // one row (4, material, T) standing for the T x T x 3 texel albedos
+        const int m = binds[0].index, T = binds[0].component;
+        if (m < 0 || m >= sd->n_mats) return fail(PRDPT_E_INVALID_ARG, "texture binding: material index out of range");
+        if (T < 1 || T > kMaxTexRes) return fail(PRDPT_E_INVALID_ARG, "texture binding: resolution must be in 1..1024");
+        if (D != 3 * T * T) return fail(PRDPT_E_INVALID_ARG, "texture binding: D must be 3 * resolution^2");
+    } else if (D < 1 || D > kMaxD) {
+        return fail(PRDPT_E_INVALID_ARG, "D must be in 1..64 (or 3 T^2 for one texture binding)");
+    }
     if (!sd->prim_type || !sd->prim_mat || !sd->prim_geom || !sd->mat_type || !sd->mat_param || !sd->camera ||
         !sd->background)
         return fail(PRDPT_E_INVALID_ARG, "scene array is NULL");
@@ -346,13 +362,15 @@ prdpt_status prdpt_scene_upload(prdpt_ctx* c, const prdpt_scene_desc* sd, const 
     B.n_prims = sd->n_prims;
     B.n_mats = sd->n_mats;
     B.D = D;
+    B.tex_mat = texture ? binds[0].index : -1;
+    B.tex_res = texture ? binds[0].component : 0;
     for (int i = 0; i < sd->n_mats; ++i) {
         if (sd->mat_type[i] < 0 || sd->mat_type[i] > 2) return fail(PRDPT_E_INVALID_ARG, "bad material type");
         B.mat_type[i] = sd->mat_type[i];
         for (int q = 0; q < 8; ++q) B.mat_param[i][q] = sd->mat_param[8 * i + q];
     }
     std::vector<bool> emission_bound(sd->n_mats, false);
-    for (int d = 0; d < D; ++d) {
+    for (int d = 0; d < (texture ? 0 : D); ++d) {
         const int k = binds[d].kind, idx = binds[d].index, comp = binds[d].component;
         if (k == kBindPos || k == kBindRadius) {
             if (idx < 0 || idx >= sd->n_prims) return fail(PRDPT_E_INVALID_ARG, "binding: primitive index out of range");
@@ -488,7 +506,8 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
         I->n_var = 0;
         I->var_box = nullptr;
     }
-    if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT)
+    if (o->no_path_sharing || !o->crn || o->spp > kMaxShareSpp || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT ||
+        B.tex_mat >= 0)  // a texture changes every path that meets it
         return;
     // per-render radiance buffers (24 bytes per render and pixel) and the recorded-path
     // list (20 bytes per path plus the segment pool) each within 512 MB
@@ -551,6 +570,11 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     IL.job0.tag = o->tag;
     IL.job0.crn = o->crn;
     IL.job0.render_mode = 1;
+    if (s->host.tex_mat >= 0) {  // texture scenes: thetas [n][D] are the textures themselves
+        IL.job0.hd = 1;
+        IL.job0.tex_all = thetas_dev;
+        IL.job0.tex_D = s->D;
+    }
     IL.total_blocks = n;
     IL.queue_reset = c->s_ctl + 0;
     PRDPT_CUDA(launch_instantiate(IL, st_));
@@ -577,6 +601,25 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     return PRDPT_OK;
 }
 
+// Draws of a texture scene (D > kMaxD parameters) by the high-dimensional kernels.
+static HdDraws hd_draws(const Scene* s, const prdpt_grad_opts* o, const float* theta, const float* sigma,
+                        float2* norms, float* theta_out, float* w_out) {
+    HdDraws H{};
+    H.D = s->D;
+    H.R = 2 * o->pairs;
+    H.sampler = o->sampler;
+    H.antithetic = o->antithetic ? 1 : 0;
+    H.seed = o->seed;
+    H.step = o->step;
+    H.theta = theta;
+    H.sigma = sigma;
+    H.c_radial = float(radial_constant(s->D));
+    H.norms = norms;
+    H.theta_out = theta_out;
+    H.w_out = w_out;
+    return H;
+}
+
 static prdpt_status check_grad_opts(const prdpt_grad_opts* o) {
     if (o->pairs < 1 || o->pairs > kMaxPairs) return fail(PRDPT_E_INVALID_ARG, "pairs must be in 1..256");
     if (o->sampler < 0 || o->sampler > 2) return fail(PRDPT_E_INVALID_ARG, "unknown sampler");
@@ -593,6 +636,7 @@ static prdpt_status fill_diff(TraceJob& J, const BaseScene& B, const prdpt_grad_
     J.diff = 0;
     J.diff_n = 0;
     if (o->estimator != PRDPT_ESTIMATOR_PATHWISE) return PRDPT_OK;
+    if (B.tex_mat >= 0) return fail(PRDPT_E_INVALID_ARG, "the pathwise estimator does not take texture parameters");
     if (B.D > kMaxDiff) return fail(PRDPT_E_INVALID_ARG, "the pathwise estimator takes at most 8 parameters");
     for (int d = 0; d < B.D; ++d) {
         const int kind = B.bind_kind[d];
@@ -624,11 +668,28 @@ static void fill_inst_grad(InstJob& J, const Scene* s, const prdpt_grad_opts* o)
 prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* sigma_dev, const prdpt_grad_opts* o,
                                         float* tau_dev, float* w_dev, void* stream) {
     if (!c || !o || !sigma_dev || !tau_dev || !w_dev) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
-    if (D < 1 || D > kMaxD) return fail(PRDPT_E_INVALID_ARG, "D must be in 1..64");
+    if (D < 1 || D > 3 * kMaxTexRes * kMaxTexRes) return fail(PRDPT_E_INVALID_ARG, "D must be in 1..3 * 1024^2");
     if (o->pairs < 1 || o->pairs > kMaxPairs) return fail(PRDPT_E_INVALID_ARG, "pairs must be in 1..256");
     if (o->sampler < 0 || o->sampler > 2) return fail(PRDPT_E_INVALID_ARG, "unknown sampler");
     std::lock_guard<std::mutex> lk(c->mu);
     PRDPT_CUDA(cudaSetDevice(c->device));
+    if (D > kMaxD) {  // the high-dimensional kernels
+        if (prdpt_status st = grow(c, &c->s_norms, &c->s_norms_n, (size_t)2 * o->pairs)) return st;
+        HdDraws H{};
+        H.D = D;
+        H.R = 2 * o->pairs;
+        H.sampler = o->sampler;
+        H.antithetic = o->antithetic ? 1 : 0;
+        H.seed = o->seed;
+        H.step = o->step;
+        H.sigma = sigma_dev;
+        H.c_radial = float(radial_constant(D));
+        H.norms = c->s_norms;
+        H.tau_out = tau_dev;
+        H.w_out = w_dev;
+        PRDPT_CUDA(launch_hd_draws(H, static_cast<cudaStream_t>(stream)));
+        return PRDPT_OK;
+    }
     // reuse the theta slot for a zero vector: the draws do not depend on theta
     if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)kMaxD)) return st;
     PRDPT_CUDA(cudaMemsetAsync(c->s_w, 0, sizeof(float) * D, static_cast<cudaStream_t>(stream)));
@@ -687,13 +748,22 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         if (prdpt_status st = grow(c, &c->s_gpart, &c->s_gpart_n, (size_t)R * tiles * D)) return st;
         if (prdpt_status st = grow(c, &c->s_rgrads, &c->s_rgrads_n, (size_t)R * kMaxDiff)) return st;
     }
+    const bool tex = s->host.tex_mat >= 0;
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    if (tex) {  // a1 over the texture's D parameters: per-render textures and weights
+        if (prdpt_status st = grow(c, &c->s_tex, &c->s_tex_n, (size_t)R * D)) return st;
+        if (prdpt_status st = grow(c, &c->s_norms, &c->s_norms_n, (size_t)R)) return st;
+        PRDPT_CUDA(launch_hd_draws(hd_draws(s, o, theta_dev, sigma_dev, c->s_norms, c->s_tex, c->s_w), st_));
+    }
     InstLaunch IL{};
     fill_inst_grad(IL.job0, s, o);
     IL.job0.scenes = c->s_scenes;
     IL.job0.theta = theta_dev;
     IL.job0.sigma = sigma_dev;
     IL.job0.w_out = c->s_w;
+    IL.job0.hd = tex ? 1 : 0;
+    IL.job0.tex_all = tex ? c->s_tex : nullptr;
+    IL.job0.tex_D = D;
     IL.total_blocks = R;
     IL.queue_reset = c->s_ctl + 0;
     IL.job0.share_reset = probe.share ? c->s_ctl + 4 : nullptr;
@@ -742,6 +812,7 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         J.gpartials = c->s_gpart;
         J.rgrads = c->s_rgrads;
     }
+    J.hd = tex ? 1 : 0;
     TL.diff_nd = diff_slots(J);
     TL.total_items = J.share ? tiles : R * tiles;
     TL.share = J.share;
@@ -749,6 +820,16 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
     PRDPT_CUDA(timed_trace(c, &TL, 1, &TL, false, st_, o->ctas_per_sm));
+    if (tex) {  // a6: g = W^T dL / 2P over the texture's parameters
+        HdGrad G{};
+        G.D = D;
+        G.R = R;
+        G.antithetic = o->antithetic ? 1 : 0;
+        G.w = c->s_w;
+        G.losses = c->s_losses;
+        G.grad_out = grad_dev;
+        PRDPT_CUDA(launch_hd_grad(G, st_));
+    }
     return PRDPT_OK;
 }
 
@@ -804,13 +885,19 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const size_t off_af = (off_cu + (probe.share ? sizeof(unsigned) * (size_t)R : 0) + 255) & ~size_t(255);
     const size_t off_gp = (off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0) + 255) & ~size_t(255);
     const size_t off_rg = (off_gp + (probe.diff ? sizeof(double) * (size_t)R * tiles * D : 0) + 255) & ~size_t(255);
-    const size_t total = off_rg + (probe.diff ? sizeof(double) * (size_t)R * kMaxDiff : 0);
+    // texture scenes: theta, m, v, sigma0, grad of D entries; per-render textures; norms
+    const bool tex = s->host.tex_mat >= 0;
+    const size_t off_hs = (off_rg + (probe.diff ? sizeof(double) * (size_t)R * kMaxDiff : 0) + 255) & ~size_t(255);
+    const size_t off_tx = (off_hs + (tex ? sizeof(float) * 5 * (size_t)D : 0) + 255) & ~size_t(255);
+    const size_t off_nr = (off_tx + (tex ? sizeof(float) * (size_t)R * D : 0) + 255) & ~size_t(255);
+    const size_t total = off_nr + (tex ? sizeof(float2) * (size_t)R : 0);
     void* base = nullptr;
     if (prdpt_status st = dev_alloc(c, &base, total)) {
         delete j;
         return st;
     }
     j->bytes = total;
+    j->base = base;
     char* b = static_cast<char*>(base);
     j->theta = reinterpret_cast<float*>(b);
     j->m = j->theta + kMaxD;
@@ -836,7 +923,18 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         j->cursor = reinterpret_cast<unsigned*>(b + off_cu);
         j->aff = reinterpret_cast<int*>(b + off_af);
     }
+    j->tex = tex;
     cudaError_t e = cudaMemset(base, 0, off_w);
+    if (tex) {
+        j->theta = reinterpret_cast<float*>(b + off_hs);
+        j->m = j->theta + D;
+        j->v = j->m + D;
+        j->sigma0 = j->v + D;
+        j->grad = j->sigma0 + D;
+        j->tex_all = reinterpret_cast<float*>(b + off_tx);
+        j->norms = reinterpret_cast<float2*>(b + off_nr);
+        if (e == cudaSuccess) e = cudaMemset(j->theta, 0, sizeof(float) * 5 * (size_t)D);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(j->target, d->target_host, sizeof(float4) * (size_t)W * H, cudaMemcpyHostToDevice);
@@ -856,8 +954,12 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     I.anneal = d->anneal ? 1 : 0;
     I.total_steps = d->total_steps;
     I.sigma_min = d->sigma_min;
+    I.hd = tex ? 1 : 0;
+    I.tex_all = j->tex_all;
+    I.tex_D = D;
     TraceJob& T = j->trace;
     std::memset(&T, 0, sizeof(T));
+    T.hd = tex ? 1 : 0;
     T.scenes = j->scenes;
     T.target = j->target;
     T.partials = j->partials;
@@ -913,11 +1015,55 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     return PRDPT_OK;
 }
 
+// Draws of a texture job's step by the high-dimensional kernels (from its sampler setup).
+static HdDraws job_hd_draws(const Job* j) {
+    const InstJob& I = j->inst;
+    HdDraws H{};
+    H.D = j->D;
+    H.R = j->R;
+    H.sampler = I.sampler;
+    H.antithetic = I.antithetic;
+    H.seed = I.seed;
+    H.step = I.step;
+    H.step_dev = j->step;
+    H.theta = j->theta;
+    H.sigma = j->sigma0;
+    H.anneal = I.anneal;
+    H.total_steps = I.total_steps;
+    H.sigma_min = I.sigma_min;
+    H.c_radial = I.c_radial;
+    H.norms = j->norms;
+    H.theta_out = j->tex_all;
+    H.w_out = j->w;
+    return H;
+}
+
+static HdGrad job_hd_grad(const Job* j) {
+    const TraceJob& T = j->trace;
+    HdGrad G{};
+    G.D = j->D;
+    G.R = j->R;
+    G.antithetic = T.antithetic;
+    G.w = j->w;
+    G.losses = j->losses_d;
+    G.grad_out = j->grad;
+    G.theta = j->theta;
+    G.m = j->m;
+    G.v = j->v;
+    G.step_dev = j->step;
+    G.lr = T.lr;
+    G.b1 = T.b1;
+    G.b2 = T.b2;
+    G.eps = T.eps;
+    return G;
+}
+
 prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
     Job* j = get_job(c, job_id);
     if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    if (j->tex) PRDPT_CUDA(launch_hd_draws(job_hd_draws(j), st_));  // a1 over the texture
     InstLaunch IL{};
     IL.job0 = j->inst;
     IL.total_blocks = j->R;
@@ -932,6 +1078,7 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
     PRDPT_CUDA(timed_trace(c, &TL, 1, &TL, false, st_, j->ctas_per_sm));
+    if (j->tex) PRDPT_CUDA(launch_hd_grad(job_hd_grad(j), st_));  // a6 + a7 over the texture
     return PRDPT_OK;
 }
 
@@ -950,6 +1097,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             for (int q = 0; q < i; ++q)
                 if (ids[q] == ids[i]) return fail(PRDPT_E_INVALID_ARG, "a job appears twice in a batch");
             if (j->trace.diff) return fail(PRDPT_E_INVALID_ARG, "pathwise-estimator jobs step alone (prdpt_step)");
+            if (j->tex) return fail(PRDPT_E_INVALID_ARG, "texture jobs step alone (prdpt_step)");
         }
         for (int pass = 0; pass < 2; ++pass)
             for (int i = 0; i < n; ++i) {
@@ -1061,7 +1209,7 @@ prdpt_status prdpt_job_release(prdpt_ctx* c, int32_t job_id) {
     Job* j = get_job(c, job_id);
     if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
     PRDPT_CUDA(cudaDeviceSynchronize());
-    dev_free(c, j->theta);
+    dev_free(c, j->base);
     Scene* s = get_scene(c, j->scene);
     if (s) s->jobs--;
     for (int q : c->batch_ids)

@@ -40,7 +40,8 @@ constexpr unsigned kTagTarget = 3u;
 
 enum : int { kSphere = 0, kQuad = 1, kBox = 2 };
 enum : int { kDiffuse = 0, kMirror = 1, kDielectric = 2 };
-enum : int { kBindPos = 0, kBindRadius = 1, kBindAlbedo = 2, kBindEmission = 3 };
+enum : int { kBindPos = 0, kBindRadius = 1, kBindAlbedo = 2, kBindEmission = 3, kBindTexture = 4 };
+constexpr int kMaxTexRes = 1024;  // texture parameters: up to 3 x 1024^2
 enum : int { kRadial = 0, kPerDim = 1, kGauss = 2 };
 
 // Device status word bits.
@@ -55,6 +56,7 @@ struct BaseScene {
     int bind_kind[kMaxD], bind_index[kMaxD], bind_comp[kMaxD];
     float eye[3], fwd[3], right[3], up[3], tan_half;
     float bg[3];
+    int tex_mat, tex_res;  // texture binding: material tex_mat's albedo on quads, tex_res^2 RGB texels; -1: none
 };
 
 // Primitive records (4 x float4, grouped: spheres, quads, boxes):
@@ -74,6 +76,8 @@ struct __align__(16) InstScene {
     int4 light[kMaxLights];
     float light_area[kMaxLights];
     float dclamp[kMaxDiff];  // pathwise estimator: derivative of each parameter's clamp (1 or 0)
+    const float* tex;        // this render's texture [tex_res][tex_res][3] (texture scenes), or null
+    int tex_mat, tex_res;    // material whose quads are textured (-1: none), resolution
     float4 mat[kMaxMats][2];
     float4 prim[kMaxPrims][4];
 };
@@ -95,6 +99,9 @@ struct InstJob {
     float sigma_min, c_radial;  // c_radial = sqrt(2) Gamma((D+1)/2) / Gamma(D/2)
     int block_begin;          // first CTA index of this job in a packed launch
     int diff;                 // pathwise estimator: write each render's clamp derivatives
+    int hd;                   // high-dimensional parameters: draws made by k_perturb_hd, skip a1 here
+    const float* tex_all;     // texture scenes: [R][tex_D] per-render textures, or null
+    int tex_D;
     unsigned* share_reset;    // [4] path-sharing counters of the job, zeroed by its first CTA, or null
     // path sharing: bounds of each perturbed primitive in each render, [R][kMaxVariant][2]
     // (min, max corner, inflated), written by the render's CTA; null when not sharing
@@ -147,6 +154,7 @@ struct TraceJob {
     // of material diff_mat, channel diff_comp; each block writes its partial sums of
     // (I - T) dI/dtheta_k to gpartials [R][tiles][diff_n]; k_finalize reduces them per render
     // into rgrads [R][kMaxDiff] and forms the mean over renders.
+    int hd;                   // high-dimensional parameters: gradient and Adam by k_grad_adam_hd
     int diff, diff_n;
     int diff_mat[kMaxDiff], diff_comp[kMaxDiff], diff_kind[kMaxDiff];
     double* gpartials;
@@ -176,7 +184,36 @@ struct InstLaunch {
     unsigned* queue_reset2;   // zeroed by CTA 0 (second queue of a packed launch), or null
 };
 
+// High-dimensional parameter draws (texture scenes, D > kMaxD): norms per draw, then
+// per (render, parameter) perturbation, weight and perturbed parameter.
+struct HdDraws {
+    int D, R, sampler, antithetic;
+    unsigned long long seed;
+    unsigned step;
+    const int* step_dev;      // resident job: device step counter added to `step`, else null
+    const float* theta;       // [D] centre
+    const float* sigma;       // [D] bandwidth (sigma0 when annealing)
+    int anneal, total_steps;
+    float sigma_min, c_radial;
+    float2* norms;            // [draws] (|z|, radius) of the radial sampler
+    float* theta_out;         // [R][D] theta + tau (per-render texture), or null
+    float* tau_out;           // [R][D] or null
+    float* w_out;             // [R][D] or null
+};
+// The gradient of Eq. 10 over D > kMaxD parameters (g = W^T dL / 2P) and Adam.
+struct HdGrad {
+    int D, R, antithetic;
+    const float* w;           // [R][D]
+    const double* losses;     // [R]
+    float* grad_out;          // [D] or null
+    float *theta, *m, *v;     // Adam state, or null (no optimiser step)
+    const int* step_dev;      // incremented by k_finalize before this kernel runs: Adam's 1-based t
+    float lr, b1, b2, eps;
+};
+
 // Launchers (kernels.cu). All enqueue on `stream` and return the launch error.
+cudaError_t launch_hd_draws(const HdDraws& H, cudaStream_t stream);
+cudaError_t launch_hd_grad(const HdGrad& G, cudaStream_t stream);
 cudaError_t launch_instantiate(const InstLaunch& L, cudaStream_t stream);
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream);
 // Second and third passes of a path-sharing job: the affected paths per render, then the

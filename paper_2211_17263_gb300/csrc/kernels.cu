@@ -106,14 +106,18 @@ __device__ __forceinline__ float bm_normal(const float* u, int base, int j) {
 }
 
 // Bandwidth at step t: constant, or the warm-started linear decay (Sec. 3.3).
-__device__ __forceinline__ float sigma_at(const InstJob& J, int d, int t) {
-    const float s0 = J.sigma[d];
-    if (!J.anneal) return s0;
-    const int w = J.total_steps / 2;
-    if (t < w || J.total_steps - w <= 0) return s0;
-    float frac = float(t - w) / float(J.total_steps - w);
+__device__ __forceinline__ float sigma_sched(const float* sigma, int anneal, int total_steps, float sigma_min, int d,
+                                             int t) {
+    const float s0 = sigma[d];
+    if (!anneal) return s0;
+    const int w = total_steps / 2;
+    if (t < w || total_steps - w <= 0) return s0;
+    float frac = float(t - w) / float(total_steps - w);
     frac = fminf(frac, 1.0f);
-    return s0 - frac * (s0 - J.sigma_min);
+    return s0 - frac * (s0 - sigma_min);
+}
+__device__ __forceinline__ float sigma_at(const InstJob& J, int d, int t) {
+    return sigma_sched(J.sigma, J.anneal, J.total_steps, J.sigma_min, d, t);
 }
 
 // Axis-aligned bounds of a primitive record, inflated by 1e-3 scene units plus 1e-5
@@ -179,7 +183,10 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
 
     // ---- a1: perturbation and weight of render r --------------------------------
-    if (J.render_mode) {
+    // (texture scenes: the draws are made by the high-dimensional kernels, k_hd_*)
+    const bool texscene = J.base && J.base->tex_mat >= 0;
+    if (texscene) {
+    } else if (J.render_mode) {
         if (tid < D) s_theta[tid] = J.theta[r * D + tid];
     } else {
         const bool anti = J.antithetic && (r & 1);
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     InstScene& S = J.scenes[r];
     if (tid < kMaxDiff) {  // pathwise estimator: derivative of each parameter's clamp
         float dc = 0.0f;
-        if (J.diff && tid < D) {
+        if (J.diff && !texscene && tid < D) {
             const float t = s_theta[tid];
             dc = B.bind_kind[tid] == kBindAlbedo ? ((t >= 0.0f && t <= 1.0f) ? 1.0f : 0.0f) : (t >= 0.0f ? 1.0f : 0.0f);
         }
@@ -278,7 +285,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         float g[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) g[q] = B.prim_geom[i][q];
-        for (int d = 0; d < D; ++d) {
+        for (int d = 0; d < (texscene ? 0 : D); ++d) {
             if (B.bind_index[d] != i) continue;
             if (B.bind_kind[d] == kBindPos) g[B.bind_comp[d]] = s_theta[d];
             if (B.bind_kind[d] == kBindRadius && type == kSphere) g[3] = fabsf(s_theta[d]);
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         float p[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) p[q] = B.mat_param[i][q];
-        for (int d = 0; d < D; ++d) {
+        for (int d = 0; d < (texscene ? 0 : D); ++d) {
             if (B.bind_index[d] != i) continue;
             if (B.bind_kind[d] == kBindAlbedo) p[B.bind_comp[d]] = s_theta[d];
             if (B.bind_kind[d] == kBindEmission) p[3 + B.bind_comp[d]] = s_theta[d];
@@ -324,6 +331,9 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         J.var_box[(size_t(r) * kMaxVariant + tid) * 2 + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     }
     if (tid == 0) {
+        S.tex = texscene ? J.tex_all + size_t(r) * size_t(J.tex_D) : nullptr;
+        S.tex_mat = texscene ? B.tex_mat : -1;
+        S.tex_res = texscene ? B.tex_res : 0;
         S.n_sph = B.n_sph;
         S.n_quad = B.n_quad;
         S.n_box = B.n_box;
@@ -576,6 +586,21 @@ __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
     t2 = f3(b, sg + n.y * n.y * a, -n.y);
 }
 
+// Albedo of a textured quad at hit point pt: texel (floor(s T), floor(t T)) with
+// s = (pt - c).u / |u|^2 + 1/2, t = (pt - c).v / |v|^2 + 1/2 (each clamped to [0, T-1]) of
+// the render's texture [T][T][3]; channels clamped to [0, 1].
+__device__ __forceinline__ float3 tex_albedo(const InstScene& S, int slot, float3 pt) {
+    const float4 c = S.prim[slot][0], u = S.prim[slot][2], v = S.prim[slot][3];
+    const float3 l = pt - xyz(c);
+    const float s = fmaf(dot3(l, xyz(u)), u.w, 0.5f), t = fmaf(dot3(l, xyz(v)), v.w, 0.5f);
+    const int T = S.tex_res;
+    const int tx = min(max(int(floorf(s * float(T))), 0), T - 1);
+    const int ty = min(max(int(floorf(t * float(T))), 0), T - 1);
+    const float* q = S.tex + (size_t(ty) * T + tx) * 3;
+    return f3(fminf(fmaxf(__ldg(q), 0.0f), 1.0f), fminf(fmaxf(__ldg(q + 1), 0.0f), 1.0f),
+              fminf(fmaxf(__ldg(q + 2), 0.0f), 1.0f));
+}
+
 // One live path sample (Eq. 1's integrand along one path; Eq. 3 averages them).
 struct Path {
     float3 o, d, beta, L;
@@ -720,7 +745,9 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
     }
     const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
     const int mtype = as_int(m0.w);
-    const float3 albedo = xyz(m0), emission = xyz(m1);
+    const float3 emission = xyz(m1);
+    float3 albedo = xyz(m0);
+    if (mat == S.tex_mat && h.type == kQuad) albedo = tex_albedo(S, h.slot, pt);
     if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f) {
         if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, emission, mat);
         p.L = p.L + p.beta * emission;
@@ -1548,7 +1575,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
     // a6: one warp per parameter, lanes over pairs (fixed order), FP64; a7: Adam in FP32
     const int t = J.step_dev ? __ldcg(J.step_dev) : 0;
     const int warp = tid >> 5, lane = tid & 31;
-    for (int d = warp; d < J.D; d += kBlock / 32) {
+    for (int d = warp; d < (J.hd ? 0 : J.D); d += kBlock / 32) {  // hd: k_hd_grad
         double g = 0.0;
         if (J.diff) {  // Eq. 9: mean over renders of the pathwise loss gradients
             for (int q = lane; q < J.R; q += 32) g += __ldcg(J.rgrads + size_t(q) * kMaxDiff + d);
@@ -1672,6 +1699,140 @@ cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, uns
     if (n <= 0) return cudaSuccess;
     k_philox<<<(n + 255) / 256, 256, 0, stream>>>(seed, c0, c1, c2, c3, n, reinterpret_cast<uint4*>(out));
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// High-dimensional parameters (texture scenes): a1 and a6/a7 over D > kMaxD
+// ---------------------------------------------------------------------------
+// Uniform number k of draw `index` (stream PERTURB): word k mod 4 of Philox block k / 4,
+// the same counter layout as the small-D sampler of k_instantiate.
+__device__ __forceinline__ float perturb_uniform(const HdDraws& H, unsigned index, unsigned step, int k) {
+    const uint4 w = philox(make_uint4(index, unsigned(k >> 2), step, kTagPerturb << 28), unsigned(H.seed),
+                           unsigned(H.seed >> 32));
+    const unsigned x = (k & 3) == 0 ? w.x : ((k & 3) == 1 ? w.y : ((k & 3) == 2 ? w.z : w.w));
+    return u01(x);
+}
+
+// Box-Muller normal j of a draw whose pairs start at uniform `base` (as bm_normal).
+__device__ __forceinline__ float hd_normal(const HdDraws& H, unsigned index, unsigned step, int base, int j) {
+    const float a = perturb_uniform(H, index, step, base + 2 * (j / 2));
+    const float b = perturb_uniform(H, index, step, base + 2 * (j / 2) + 1);
+    const float rad = sqrtf(-2.0f * logf(a));
+    float sn, cs;
+    sincospif(2.0f * b, &sn, &cs);
+    return rad * ((j & 1) ? sn : cs);
+}
+
+__device__ __forceinline__ unsigned hd_step(const HdDraws& H) {
+    return H.step + (H.step_dev ? unsigned(*H.step_dev) : 0u);
+}
+
+// Radial sampler (Sec. 3.2, reading R1) in D dimensions, one CTA per draw: the norm of
+// the D Box-Muller normals and the chi_{D+1} radius (sum of (D+1)/2 exponentials, plus
+// one more squared normal when D is even), each summed in FP64 in a fixed order.
+__global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
+    pdl_enter();
+    __shared__ double s_z[kBlock / 32], s_r[kBlock / 32];
+    const unsigned index = blockIdx.x, step = hd_step(H);
+    const int D = H.D, n_exp = (D + 1) / 2, nz = D + (D % 2 == 0 ? 1 : 0);
+    double zs = 0.0, rs = 0.0;
+    for (int j = threadIdx.x; j < nz; j += kBlock) {
+        const float z = hd_normal(H, index, step, n_exp, j);
+        if (j < D) zs += double(z * z); else rs += double(z * z);
+    }
+    for (int j = threadIdx.x; j < n_exp; j += kBlock) rs += double(-2.0f * logf(perturb_uniform(H, index, step, j)));
+    zs = warp_sum_d(zs);
+    rs = warp_sum_d(rs);
+    if ((threadIdx.x & 31) == 0) {
+        s_z[threadIdx.x >> 5] = zs;
+        s_r[threadIdx.x >> 5] = rs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double z = 0.0, r = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            z += s_z[w];
+            r += s_r[w];
+        }
+        H.norms[index] = make_float2(float(sqrt(z)), float(sqrt(r)));
+    }
+}
+
+// One thread per (render, parameter): tau, w and theta + tau of every sampler (as the
+// small-D sampler, per dimension), antithetic renders negated.
+__global__ void __launch_bounds__(kBlock) k_hd_perturb(const HdDraws H) {
+    pdl_enter();
+    const size_t i = size_t(blockIdx.x) * kBlock + threadIdx.x;
+    if (i >= size_t(H.R) * size_t(H.D)) return;
+    const int r = int(i / size_t(H.D)), d = int(i - size_t(r) * size_t(H.D));
+    const bool anti = H.antithetic && (r & 1);
+    const unsigned index = H.antithetic ? unsigned(r >> 1) : unsigned(r), step = hd_step(H);
+    float tt, wt;
+    if (H.sampler == kRadial) {
+        const float z = hd_normal(H, index, step, (H.D + 1) / 2, d);
+        const float2 nr = H.norms[index];
+        const float dir = z / nr.x;
+        tt = nr.y * dir;
+        wt = H.c_radial * dir;
+    } else if (H.sampler == kPerDim) {
+        const float xi = perturb_uniform(H, index, step, d);
+        const float c1 = 0.7978845608028654f;  // sqrt(2/pi)
+        if (xi < 0.5f) {
+            tt = -sqrtf(-2.0f * logf(2.0f * xi));
+            wt = -c1;
+        } else {
+            tt = sqrtf(-2.0f * logf(2.0f * (1.0f - xi)));
+            wt = c1;
+        }
+    } else {
+        tt = hd_normal(H, index, step, 0, d);
+        wt = tt;
+    }
+    const float sg = sigma_sched(H.sigma, H.anneal, H.total_steps, H.sigma_min, d, int(step));
+    float tau = sg * tt, w = wt / sg;
+    if (anti) {
+        tau = -tau;
+        w = -w;
+    }
+    if (H.theta_out) H.theta_out[i] = H.theta[d] + tau;  // FP32 sum: the parameters this render gets
+    if (H.tau_out) H.tau_out[i] = tau;
+    if (H.w_out) H.w_out[i] = w;
+}
+
+// a6 + a7 over D parameters: g_d = (1/2P) sum_p w_{2p,d} (L_2p - L_2p+1) (a skinny GEMV,
+// W^T dL, fixed order over p in FP64), then Adam with t = the already advanced step.
+__global__ void __launch_bounds__(kBlock) k_hd_grad(const HdGrad G) {
+    pdl_enter();
+    const int d = int(blockIdx.x) * kBlock + int(threadIdx.x);
+    if (d >= G.D) return;
+    double g = 0.0;
+    if (G.antithetic) {
+        const int P = G.R / 2;
+        for (int p = 0; p < P; ++p)
+            g += double(G.w[size_t(2 * p) * G.D + d]) * (__ldcg(G.losses + 2 * p) - __ldcg(G.losses + 2 * p + 1));
+        g /= double(2 * P);
+    } else {
+        for (int q = 0; q < G.R; ++q) g += double(G.w[size_t(q) * G.D + d]) * __ldcg(G.losses + q);
+        g /= double(G.R);
+    }
+    const float gf = float(g);
+    if (G.grad_out) G.grad_out[d] = gf;
+    if (G.theta) adam_update(G.theta[d], G.m[d], G.v[d], gf, __ldcg(G.step_dev), G.lr, G.b1, G.b2, G.eps);
+}
+
+cudaError_t launch_hd_draws(const HdDraws& H, cudaStream_t stream) {
+    if (H.D <= 0 || H.R <= 0) return cudaSuccess;
+    if (H.sampler == kRadial) {
+        const cudaError_t e = launch_pdl(k_hd_norms, H.antithetic ? H.R / 2 : H.R, kBlock, stream, H);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t n = size_t(H.R) * size_t(H.D);
+    return launch_pdl(k_hd_perturb, int((n + kBlock - 1) / kBlock), kBlock, stream, H);
+}
+
+cudaError_t launch_hd_grad(const HdGrad& G, cudaStream_t stream) {
+    if (G.D <= 0) return cudaSuccess;
+    return launch_pdl(k_hd_grad, (G.D + kBlock - 1) / kBlock, kBlock, stream, G);
 }
 
 // ---------------------------------------------------------------------------

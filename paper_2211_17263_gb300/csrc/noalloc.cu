@@ -61,6 +61,7 @@ bool build_base_scene(const prdpt_scene_desc* sd, const prdpt_param_binding* bin
         !sd->background)
         return *why = "scene array is NULL", false;
     std::memset(B, 0, sizeof(*B));
+    B->tex_mat = -1;  // no texture parameters in this entry point
     B->n_prims = sd->n_prims;
     B->n_mats = sd->n_mats;
     B->D = D;
