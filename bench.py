@@ -455,7 +455,10 @@ def main():
             "fp32_probe": {"achieved_tflops": probe_tflops, "ms": probe_ms,
                            "frac_of_peak": probe_tflops / fp32_peak},
             "e2e": e2e,
-            "gpu_launches": (5 if counts[3] < wl.paths_per_step else 3) * args.steps,
+            # sampler, render kernel(s), finalisation; path sharing adds the per-render and
+            # epilogue passes; texture scenes add the D-dimensional draws and gradient kernels
+            "gpu_launches": ((5 if counts[3] < wl.paths_per_step else 3)
+                             + ((3 if wl.sampler == workloads.SAMPLER_RADIAL else 2) if wl.D > 64 else 0)) * args.steps,
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
         }
