@@ -41,13 +41,6 @@ WORKLOADS = {"small": "config_small", "occlusion": "config_occlusion", "gi_box":
              "texture": "config_texture"}
 
 
-def _env_int(name, default):
-    try:
-        return int(os.environ.get(name, default))
-    except ValueError:
-        return default
-
-
 def _cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -272,7 +265,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    from paper_2211_17263_gb300 import dist as pdist
+    rank, world, local = pdist.env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -290,8 +284,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        pdist.barrier(world)
 
     wl = getattr(workloads, WORKLOADS[args.workload])(seed=rank)  # one independent replica per rank
     if args.estimator == "kernel":
@@ -340,11 +333,8 @@ def main():
     clocks = sampler.stop()
     trace_ms, launches = ctx.kernel_timing_read()
     ctx.kernel_timing(False)
-    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = pdist.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, world,
+                                   device=f"cuda:{local}")
     state = job.read()
 
     # the per-render kernel on the same workload (path sharing off): its own roofline
@@ -404,11 +394,7 @@ def main():
         e2e_step(k)
     torch.cuda.synchronize()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = pdist.max_over_ranks((time.perf_counter() - t0) / args.steps, world, device=f"cuda:{local}")
     e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank == 0:

@@ -126,6 +126,10 @@ typedef struct {
                                   losses); 1 = Eq. 9 (mean over the renders of each render's pathwise
                                   loss gradient: requires sampler = GAUSS, every binding an albedo or
                                   emission one, D <= 8; no path sharing; single-job steps only) */
+    int32_t pair_begin;        /* first pair of a shard of a larger estimate (0 normally): this call
+                                  computes pairs [pair_begin, pair_begin + pairs) with their global
+                                  draw indices (and, with crn = 0, global path-stream fields), and
+                                  returns their mean; shards combine as g = sum_s (P_s / P) g_s */
 } prdpt_grad_opts;
 #define PRDPT_ESTIMATOR_KERNEL_GRADIENT 0 /* Eq. 10: sum_r w_r L_r */
 #define PRDPT_ESTIMATOR_PATHWISE 1        /* Eq. 9: mean_r dL/dtheta (theta + tau_r) */

@@ -72,16 +72,16 @@ def lib():
         L.orc_render_pixels.restype = i32
         L.orc_mse.argtypes = [vp, vp, i32, i32]
         L.orc_mse.restype = dbl
-        L.orc_smoothed_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64, u32,
-                                        vp, vp, vp, vp, vp, i32]
+        L.orc_smoothed_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64,
+                                        u32, vp, vp, vp, vp, vp, i32]
         L.orc_smoothed_grad.restype = i32
-        L.orc_estimate.argtypes = [i32, i32, i32, vp, vp, i32, u64, u32, _LOSS_CB, vp, vp, vp, vp, vp]
+        L.orc_estimate.argtypes = [i32, i32, i32, vp, vp, i32, i32, u64, u32, _LOSS_CB, vp, vp, vp, vp, vp]
         L.orc_estimate.restype = i32
         L.orc_sample_unit_batch.argtypes = [i32, i32, i32, vp, vp, vp]
         L.orc_render_tangent.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, vp, vp, i32]
         L.orc_render_tangent.restype = i32
-        L.orc_kdp_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, u64, u32, vp,
-                                   vp, vp, vp, vp, i32]
+        L.orc_kdp_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64, u32,
+                                   vp, vp, vp, vp, vp, i32]
         L.orc_kdp_grad.restype = i32
         L.orc_adam.argtypes = [i32, vp, vp, vp, vp, i32, dbl, dbl, dbl, dbl]
         L.orc_sigma_schedule.argtypes = [dbl, dbl, i32, i32]
@@ -160,7 +160,8 @@ def sample_unit_batch(mode: int, D: int, u: np.ndarray):
     return tau, w
 
 
-def estimate(loss, theta, sigma, pairs: int, mode: int = 0, antithetic: int = 1, seed: int = 0, step: int = 0):
+def estimate(loss, theta, sigma, pairs: int, mode: int = 0, antithetic: int = 1, seed: int = 0, step: int = 0,
+             pair_begin: int = 0):
     """Eq. 10 estimate for an arbitrary Python loss L(theta_r: float32[D]) -> float.
     Returns dict(grad, losses, taus, weights)."""
     th = np.ascontiguousarray(theta, np.float32)
@@ -175,7 +176,8 @@ def estimate(loss, theta, sigma, pairs: int, mode: int = 0, antithetic: int = 1,
     losses = np.zeros(2 * pairs, np.float64)
     taus = np.zeros((2 * pairs, D), np.float32)
     weights = np.zeros((2 * pairs, D), np.float64)
-    rc = lib().orc_estimate(mode, antithetic, D, _ptr(th), _ptr(sg), pairs, seed, step, cb, None, _ptr(grad),
+    rc = lib().orc_estimate(mode, antithetic, D, _ptr(th), _ptr(sg), pairs, pair_begin, seed, step, cb, None,
+                            _ptr(grad),
                             _ptr(losses), _ptr(taus), _ptr(weights))
     if rc:
         raise ValueError(f"oracle estimate failed ({rc})")
@@ -242,7 +244,7 @@ def mse(image: np.ndarray, target: np.ndarray) -> float:
 
 
 def smoothed_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, mode=None, antithetic=None,
-                  crn=None, nthreads=0):
+                  crn=None, nthreads=0, pair_begin=0):
     """Eq. 10 estimate at theta for workload `wl`. Returns dict(grad, losses, taus, weights)."""
     h = _SceneHandle(wl.scene)
     binds = np.ascontiguousarray(wl.bindings, np.int32)
@@ -258,7 +260,7 @@ def smoothed_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, m
     taus = np.zeros((2 * P, D), np.float32)
     weights = np.zeros((2 * P, D), np.float64)
     rc = lib().orc_smoothed_grad(
-        h.ref, _ptr(binds), D, _ptr(th), _ptr(sg), P, wl.sampler if mode is None else mode,
+        h.ref, _ptr(binds), D, _ptr(th), _ptr(sg), P, pair_begin, wl.sampler if mode is None else mode,
         wl.antithetic if antithetic is None else antithetic, wl.crn if crn is None else crn,
         wl.width, wl.height, wl.spp, wl.depth, wl.rr_start, wl.seed, step, _ptr(tg),
         _ptr(grad), _ptr(losses), _ptr(taus), _ptr(weights), nthreads)
@@ -285,7 +287,8 @@ def render_tangent(scene, bindings, theta, width, height, spp, depth, rr_start=-
     return img, dimg
 
 
-def kdp_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, antithetic=None, crn=None, nthreads=0):
+def kdp_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, antithetic=None, crn=None, nthreads=0,
+             pair_begin=0):
     """Eq. 9 estimate at theta (Gaussian draws, pathwise render gradients) for workload `wl`
     whose bindings are all albedo or emission ones. Returns dict(grad, losses, taus, rgrads)."""
     h = _SceneHandle(wl.scene)
@@ -302,7 +305,7 @@ def kdp_grad(wl, theta=None, sigma=None, target=None, step=0, pairs=None, antith
     taus = np.zeros((2 * P, D), np.float32)
     rgrads = np.zeros((2 * P, D), np.float64)
     rc = lib().orc_kdp_grad(
-        h.ref, _ptr(binds), D, _ptr(th), _ptr(sg), P, wl.antithetic if antithetic is None else antithetic,
+        h.ref, _ptr(binds), D, _ptr(th), _ptr(sg), P, pair_begin, wl.antithetic if antithetic is None else antithetic,
         wl.crn if crn is None else crn, wl.width, wl.height, wl.spp, wl.depth, wl.rr_start, wl.seed, step,
         _ptr(tg), _ptr(grad), _ptr(losses), _ptr(taus), _ptr(rgrads), nthreads)
     if rc:

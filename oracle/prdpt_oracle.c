@@ -811,14 +811,16 @@ double orc_mse(const double* image, const float* target, int width, int height) 
  *   theta+tau_p (evaluation 2p) and theta-tau_p (evaluation 2p+1), and
  *   g = (1/2P) sum_p w_p (L_2p - L_2p+1).
  * antithetic=0: R = 2P independent draws (counter index r), g = (1/R) sum_r w_r L_r.
+ * pair_begin: the first pair of a shard of a larger estimate: draw indices and the
+ *   render numbers handed to the loss are global (pair_begin + p, 2 pair_begin + r).
  * The perturbed parameters are FP32 sums theta + tau_f32 (what a renderer gets).
  * Outputs: grad[D], losses[2P], taus[2P][D] (FP32), weights[2P][D].
  */
 typedef double (*orc_loss_cb)(const float* theta_r, int D, int r, void* user);
 
-int orc_estimate(int mode, int antithetic, int D, const float* theta, const float* sigma, int pairs, uint64_t seed,
-                 uint32_t step, orc_loss_cb loss, void* user, double* grad, double* losses, float* taus,
-                 double* weights) {
+int orc_estimate(int mode, int antithetic, int D, const float* theta, const float* sigma, int pairs, int pair_begin,
+                 uint64_t seed, uint32_t step, orc_loss_cb loss, void* user, double* grad, double* losses,
+                 float* taus, double* weights) {
     int R = 2 * pairs;
     if (D < 1 || pairs < 1) return 1;
     double* tau = (double*)malloc(sizeof(double) * (size_t)D * 2);
@@ -828,7 +830,8 @@ int orc_estimate(int mode, int antithetic, int D, const float* theta, const floa
     float* th = tf + D;
     for (int r = 0; r < R; ++r) {
         int anti = antithetic && (r % 2 == 1);
-        uint32_t index = antithetic ? (uint32_t)(r / 2) : (uint32_t)r;
+        uint32_t index = (antithetic ? (uint32_t)(r / 2) : (uint32_t)r) +
+                         (uint32_t)(antithetic ? pair_begin : 2 * pair_begin);
         orc_sample(mode, D, sigma, seed, step, index, tau, tf, w);
         for (int d = 0; d < D; ++d) {
             float t = anti ? -tf[d] : tf[d];
@@ -836,7 +839,7 @@ int orc_estimate(int mode, int antithetic, int D, const float* theta, const floa
             taus[(size_t)r * D + d] = t;
             weights[(size_t)r * D + d] = anti ? -w[d] : w[d];
         }
-        losses[r] = loss(th, D, r, user);
+        losses[r] = loss(th, D, 2 * pair_begin + r, user);
         if (isnan(losses[r])) { free(tau); free(tf); return 4; }
     }
     free(tau);
@@ -878,14 +881,15 @@ static double render_loss(const float* theta_r, int D, int r, void* user) {
 /* The plateau-reduced gradient of the image loss of a scene (path streams:
  * render r uses field (crn ? 0 : r + 1)). */
 int orc_smoothed_grad(const orc_scene_arrays* a, const int32_t* binds, int D, const float* theta,
-                      const float* sigma, int pairs, int mode, int antithetic, int crn, int width, int height,
-                      int spp, int depth, int rr_start, uint64_t seed, uint32_t step, const float* target,
-                      double* grad, double* losses, float* taus, double* weights, int nthreads) {
+                      const float* sigma, int pairs, int pair_begin, int mode, int antithetic, int crn, int width,
+                      int height, int spp, int depth, int rr_start, uint64_t seed, uint32_t step,
+                      const float* target, double* grad, double* losses, float* taus, double* weights,
+                      int nthreads) {
     render_loss_ctx c = {a, binds, target, width, height, spp, depth, rr_start, crn, nthreads, seed, step, NULL};
     c.image = (double*)malloc(sizeof(double) * (size_t)width * height * 3);
     if (!c.image) return 9;
-    int rc = orc_estimate(mode, antithetic, D, theta, sigma, pairs, seed, step, render_loss, &c, grad, losses, taus,
-                          weights);
+    int rc = orc_estimate(mode, antithetic, D, theta, sigma, pairs, pair_begin, seed, step, render_loss, &c, grad,
+                          losses, taus, weights);
     free(c.image);
     return rc;
 }
@@ -949,7 +953,8 @@ static void loss_gradient(const double* image, const double* dimage, const float
  * (FP32) and the per-render gradients rgrads[2P][D].
  */
 int orc_kdp_grad(const orc_scene_arrays* a, const int32_t* binds, int D, const float* theta, const float* sigma,
-                 int pairs, int antithetic, int crn, int width, int height, int spp, int depth, int rr_start,
+                 int pairs, int pair_begin, int antithetic, int crn, int width, int height, int spp, int depth,
+                 int rr_start,
                  uint64_t seed, uint32_t step, const float* target, double* grad, double* losses, float* taus,
                  double* rgrads, int nthreads) {
     const int mode = 2; /* Gaussian draws */
@@ -964,14 +969,16 @@ int orc_kdp_grad(const orc_scene_arrays* a, const int32_t* binds, int D, const f
         double tau[ORC_MAX_D], w[ORC_MAX_D];
         float tf[ORC_MAX_D], th[ORC_MAX_D];
         int anti = antithetic && (r % 2 == 1);
-        uint32_t index = antithetic ? (uint32_t)(r / 2) : (uint32_t)r;
+        uint32_t index = (antithetic ? (uint32_t)(r / 2) : (uint32_t)r) +
+                         (uint32_t)(antithetic ? pair_begin : 2 * pair_begin);
         orc_sample(mode, D, sigma, seed, step, index, tau, tf, w);
         for (int d = 0; d < D; ++d) {
             float t = anti ? -tf[d] : tf[d];
             th[d] = theta[d] + t; /* FP32 sum */
             taus[(size_t)r * D + d] = t;
         }
-        rc = orc_render_tangent(a, binds, D, th, crn ? 0 : r + 1, width, height, spp, depth, rr_start, seed, step,
+        rc = orc_render_tangent(a, binds, D, th, crn ? 0 : 2 * pair_begin + r + 1, width, height, spp, depth, rr_start,
+                                seed, step,
                                 TAG_PATH, image, dimage, nthreads);
         if (rc) break;
         losses[r] = orc_mse(image, target, width, height);

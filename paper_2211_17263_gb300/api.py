@@ -126,14 +126,14 @@ class Scene:
         return out
 
     def grad_opts(self, wl, step=0, pairs=None, sampler=None, antithetic=None, crn=None, block_pixels=0,
-                  ctas_per_sm=0, no_path_sharing=0, estimator=None):
+                  ctas_per_sm=0, no_path_sharing=0, estimator=None, pair_begin=0):
         return capi.prdpt_grad_opts(
             pairs=wl.pairs if pairs is None else pairs, width=wl.width, height=wl.height, spp=wl.spp,
             depth=wl.depth, rr_start=wl.rr_start, sampler=wl.sampler if sampler is None else sampler,
             antithetic=wl.antithetic if antithetic is None else antithetic, crn=wl.crn if crn is None else crn,
             seed=wl.seed, step=step, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm,
             no_path_sharing=no_path_sharing,
-            estimator=getattr(wl, "estimator", 0) if estimator is None else estimator)
+            estimator=getattr(wl, "estimator", 0) if estimator is None else estimator, pair_begin=pair_begin)
 
     def smoothed_grad(self, theta: torch.Tensor, sigma: torch.Tensor, target: torch.Tensor, opts,
                       grad: torch.Tensor | None = None, losses: torch.Tensor | None = None, stream=None):

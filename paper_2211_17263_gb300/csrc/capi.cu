@@ -609,6 +609,7 @@ static HdDraws hd_draws(const Scene* s, const prdpt_grad_opts* o, const float* t
     H.R = 2 * o->pairs;
     H.sampler = o->sampler;
     H.antithetic = o->antithetic ? 1 : 0;
+    H.draw_begin = o->antithetic ? o->pair_begin : 2 * o->pair_begin;
     H.seed = o->seed;
     H.step = o->step;
     H.theta = theta;
@@ -625,6 +626,7 @@ static prdpt_status check_grad_opts(const prdpt_grad_opts* o) {
     if (o->sampler < 0 || o->sampler > 2) return fail(PRDPT_E_INVALID_ARG, "unknown sampler");
     if (o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT && o->estimator != PRDPT_ESTIMATOR_PATHWISE)
         return fail(PRDPT_E_INVALID_ARG, "unknown estimator");
+    if (o->pair_begin < 0 || o->pair_begin > (1 << 26)) return fail(PRDPT_E_INVALID_ARG, "pair_begin must be in 0..2^26");
     if (o->estimator == PRDPT_ESTIMATOR_PATHWISE && o->sampler != PRDPT_SAMPLER_GAUSS)
         return fail(PRDPT_E_INVALID_ARG, "the pathwise estimator (Eq. 9) samples the Gaussian kernel: sampler must be GAUSS");
     return check_common(o->width, o->height, o->spp, o->depth, o->rr_start);
@@ -656,6 +658,7 @@ static int diff_slots(const TraceJob& J) { return J.diff ? (J.diff_n <= 4 ? 4 : 
 static void fill_inst_grad(InstJob& J, const Scene* s, const prdpt_grad_opts* o) {
     fill_inst_common(J, s, 2 * o->pairs, s->D, o->width, o->height);
     J.diff = o->estimator == PRDPT_ESTIMATOR_PATHWISE ? 1 : 0;
+    J.pair_begin = o->pair_begin;
     J.seed = o->seed;
     J.step = o->step;
     J.tag = kTagPath;
@@ -680,6 +683,7 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* si
         H.R = 2 * o->pairs;
         H.sampler = o->sampler;
         H.antithetic = o->antithetic ? 1 : 0;
+        H.draw_begin = o->antithetic ? o->pair_begin : 2 * o->pair_begin;
         H.seed = o->seed;
         H.step = o->step;
         H.sigma = sigma_dev;
@@ -708,6 +712,7 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* si
     IL.job0.step = o->step;
     IL.job0.sampler = o->sampler;
     IL.job0.antithetic = o->antithetic ? 1 : 0;
+    IL.job0.pair_begin = o->pair_begin;
     IL.total_blocks = 2 * o->pairs;  // scenes == null: draws only, no scene binding
     PRDPT_CUDA(launch_instantiate(IL, static_cast<cudaStream_t>(stream)));
     return PRDPT_OK;
@@ -1023,6 +1028,7 @@ static HdDraws job_hd_draws(const Job* j) {
     H.R = j->R;
     H.sampler = I.sampler;
     H.antithetic = I.antithetic;
+    H.draw_begin = I.antithetic ? I.pair_begin : 2 * I.pair_begin;
     H.seed = I.seed;
     H.step = I.step;
     H.step_dev = j->step;

@@ -98,6 +98,7 @@ struct InstJob {
     int anneal, total_steps;
     float sigma_min, c_radial;  // c_radial = sqrt(2) Gamma((D+1)/2) / Gamma(D/2)
     int block_begin;          // first CTA index of this job in a packed launch
+    int pair_begin;           // the job's first antithetic pair of a sharded estimate (draw/render offset)
     int diff;                 // pathwise estimator: write each render's clamp derivatives
     int hd;                   // high-dimensional parameters: draws made by k_perturb_hd, skip a1 here
     const float* tex_all;     // texture scenes: [R][tex_D] per-render textures, or null
@@ -188,6 +189,7 @@ struct InstLaunch {
 // per (render, parameter) perturbation, weight and perturbed parameter.
 struct HdDraws {
     int D, R, sampler, antithetic;
+    int draw_begin;           // global index of draw 0 (sharded estimates)
     unsigned long long seed;
     unsigned step;
     const int* step_dev;      // resident job: device step counter added to `step`, else null

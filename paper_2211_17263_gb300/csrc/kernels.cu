@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         if (tid < D) s_theta[tid] = J.theta[r * D + tid];
     } else {
         const bool anti = J.antithetic && (r & 1);
-        const unsigned index = J.antithetic ? unsigned(r >> 1) : unsigned(r);
+        const unsigned index = (J.antithetic ? unsigned(r >> 1) : unsigned(r)) +
+                               unsigned(J.antithetic ? J.pair_begin : 2 * J.pair_begin);
         const int nu = sampler_uniforms(J.sampler, D);
         const int nblk = (nu + 3) / 4;
         if (tid < nblk) {
@@ -337,7 +338,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         S.n_sph = B.n_sph;
         S.n_quad = B.n_quad;
         S.n_box = B.n_box;
-        const unsigned field = J.render_mode ? (J.crn ? 0u : unsigned(r)) : (J.crn ? 0u : unsigned(r + 1));
+        const unsigned field =
+            J.render_mode ? (J.crn ? 0u : unsigned(r)) : (J.crn ? 0u : unsigned(r + 1 + 2 * J.pair_begin));
         S.seed_lo = unsigned(J.seed);
         S.seed_hi = unsigned(J.seed >> 32);
         S.step = step;
@@ -1733,7 +1735,7 @@ __device__ __forceinline__ unsigned hd_step(const HdDraws& H) {
 __global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
     pdl_enter();
     __shared__ double s_z[kBlock / 32], s_r[kBlock / 32];
-    const unsigned index = blockIdx.x, step = hd_step(H);
+    const unsigned index = blockIdx.x + unsigned(H.draw_begin), step = hd_step(H);
     const int D = H.D, n_exp = (D + 1) / 2, nz = D + (D % 2 == 0 ? 1 : 0);
     double zs = 0.0, rs = 0.0;
     for (int j = threadIdx.x; j < nz; j += kBlock) {
@@ -1754,7 +1756,7 @@ __global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
             z += s_z[w];
             r += s_r[w];
         }
-        H.norms[index] = make_float2(float(sqrt(z)), float(sqrt(r)));
+        H.norms[blockIdx.x] = make_float2(float(sqrt(z)), float(sqrt(r)));
     }
 }
 
@@ -1766,11 +1768,12 @@ __global__ void __launch_bounds__(kBlock) k_hd_perturb(const HdDraws H) {
     if (i >= size_t(H.R) * size_t(H.D)) return;
     const int r = int(i / size_t(H.D)), d = int(i - size_t(r) * size_t(H.D));
     const bool anti = H.antithetic && (r & 1);
-    const unsigned index = H.antithetic ? unsigned(r >> 1) : unsigned(r), step = hd_step(H);
+    const unsigned local = H.antithetic ? unsigned(r >> 1) : unsigned(r), step = hd_step(H);
+    const unsigned index = local + unsigned(H.draw_begin);
     float tt, wt;
     if (H.sampler == kRadial) {
         const float z = hd_normal(H, index, step, (H.D + 1) / 2, d);
-        const float2 nr = H.norms[index];
+        const float2 nr = H.norms[local];
         const float dir = z / nr.x;
         tt = nr.y * dir;
         wt = H.c_radial * dir;

@@ -231,6 +231,7 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     I.sampler = o->sampler;
     I.antithetic = o->antithetic ? 1 : 0;
     I.crn = o->crn ? 1 : 0;
+    I.pair_begin = o->pair_begin;
     I.c_radial = float(std::sqrt(2.0) * std::exp(std::lgamma(0.5 * (D + 1)) - std::lgamma(0.5 * D)));
     IL.total_blocks = R;
     IL.queue_reset = ctl + 0;
