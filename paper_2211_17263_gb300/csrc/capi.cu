@@ -478,9 +478,11 @@ static size_t seg_slots(size_t n) {
     return paths * kSeg;
 }
 
+// recorded-path list of n paths: codes, segment words, shared radiance, the segment pool
+// (2 float4 per slot) and the path states (4 float4 per group of kSeg slots)
 static size_t afflist_bytes(size_t n) {
     return 2 * ((sizeof(unsigned) * n + 255) & ~size_t(255)) + ((sizeof(float) * 3 * n + 255) & ~size_t(255)) +
-           sizeof(float4) * 2 * seg_slots(n);
+           sizeof(float4) * 2 * seg_slots(n) + sizeof(float4) * 4 * (seg_slots(n) / kSeg);
 }
 
 static void afflist_carve(TraceJob& J, void* base, size_t n) {
@@ -492,6 +494,8 @@ static void afflist_carve(TraceJob& J, void* base, size_t n) {
     J.aff_lsh = reinterpret_cast<float*>(b);
     b += (sizeof(float) * 3 * n + 255) & ~size_t(255);
     J.seg_pool = reinterpret_cast<float4*>(b);
+    b += sizeof(float4) * 2 * seg_slots(n);
+    J.seg_state = reinterpret_cast<float4*>(b);
     J.seg_cap = unsigned(seg_slots(n));
 }
 

@@ -145,6 +145,7 @@ struct TraceJob {
     unsigned* aff_segw;       // segment word: where its touching segments are kept, or "every render"
     float* aff_lsh;           // [3] radiance of the path in the shared pass
     float4* seg_pool;         // [seg_cap][2] touching segments (o, tmax), (d, 0), kSeg slots per path
+    float4* seg_state;        // [seg_cap / kSeg][4] path state where a path's renders part (see note_touch)
     unsigned seg_cap;
     const float4* var_box;    // [R][kMaxVariant][2] per-render bounds of the perturbed primitives
     unsigned* aff_cursor;     // [R] next list entry of each render in the per-render pass

@@ -518,9 +518,20 @@ __device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d,
 // Union over the job's R renders of the perturbed primitives' bounds (shared mode; each
 // render's bounds are inflated so that a slab test is conservative against the exact
 // intersection tests), and the pool that keeps the segments touching them.
+// One live path sample (Eq. 1's integrand along one path; Eq. 3 averages them).
+struct Path {
+    float3 o, d, beta, L;
+    unsigned pixel;  // y * W + x
+    int s, b;        // sample index, vertex index
+    int slot;        // pixel slot inside the warp's block (per-render pass: the path's record)
+    bool specular;   // emission counts: camera rays and rays after specular bounces
+    unsigned seg;    // shared pass: touching-segment word (see note_touch)
+};
+
 struct VarBoxes {
     float4 lo[kMaxVariant], hi[kMaxVariant];  // union over renders
     float4* seg_pool;                         // touching segments, kSeg slots per path
+    float4* seg_state;                        // 4 per path group: where the path's renders part
     unsigned* seg_ctr;                        // slots claimed
     unsigned seg_cap;                         // slots available
     int n;
@@ -537,41 +548,75 @@ __device__ __forceinline__ bool slab_touch(float3 lo, float3 hi, float3 o, float
     return tn <= tf;
 }
 
-// Touching segments of a shared-pass path: the path's segment word is 0 (no segment
-// touched a union box), kSegFull (every render traces the path again: a bound material
-// was hit, or the path touched more than kSeg times, or the pool ran out) or
-// ((first slot / kSeg + 1) << 3 | count) for count <= kSeg segments kept in the pool as
-// (o, tmax), (d, 0). The per-render pass tests them against each render's own bounds.
-constexpr unsigned kSegFull = 0xffffffffu;
+// Touching segments of a shared-pass path. A path that touches a union box of the
+// perturbed primitives claims a group g of kSeg segment slots and keeps, besides the
+// segments, its state at the start of the vertex of the first touch: up to there none of
+// its rays can meet a render's own primitive, so every render's path agrees with the
+// shared one and the per-render pass resumes from that state instead of the camera.
+// A path's segment word p.seg is
+//   0                          no ray touched a union box;
+//   (g + 1) << 3 | count       count <= kSeg touching segments (o, tmax), (d, 0) in slots
+//                              kSeg g ..; a render traces the path again only if one of them
+//                              touches that render's own bounds;
+//   kSegAll | (g + 1) << 3     every render traces the path again from state g (a bound
+//                              material was hit, or more than kSeg segments touched);
+//   kSegFull                   every render traces the path again from the camera (the pool
+//                              ran out before the first touch).
+// State g: (o, d.x), (d.y, d.z, beta.x, beta.y), (beta.z, L), (vertex b, emission flag).
+// A first touch by a shadow ray is kept as the vertex's state after its emission was
+// added (o and d from the stash below), with the emission flag cleared so that the
+// resumed vertex does not add it again.
+constexpr unsigned kSegAll = 0x80000000u, kSegFull = 0xffffffffu;
 
-template <bool kCount>
-__device__ __forceinline__ void note_touch(const VarBoxes& V, float3 o, float3 d, float tmax, unsigned& seg,
+// Ray (o, d) of each shared-pass thread's current vertex, kept while its path has not
+// touched (a shadow ray's first touch records the vertex's state).
+__shared__ float s_stash[6][kBlock];
+
+template <bool kNee>
+__device__ __forceinline__ unsigned open_group(const VarBoxes& V, const Path& p) {
+    const unsigned base = atomicAdd(V.seg_ctr, unsigned(kSeg));
+    if (base + unsigned(kSeg) > V.seg_cap) return kSegFull;
+    const unsigned g = base / unsigned(kSeg);
+    float3 o = p.o, d = p.d;
+    if (kNee) {
+        const int t = threadIdx.x;
+        o = f3(s_stash[0][t], s_stash[1][t], s_stash[2][t]);
+        d = f3(s_stash[3][t], s_stash[4][t], s_stash[5][t]);
+    }
+    float4* st = V.seg_state + 4 * size_t(g);
+    st[0] = make_float4(o.x, o.y, o.z, d.x);
+    st[1] = make_float4(d.y, d.z, p.beta.x, p.beta.y);
+    st[2] = make_float4(p.beta.z, p.L.x, p.L.y, p.L.z);
+    st[3] = make_float4(__int_as_float(p.b), __int_as_float((!kNee && p.specular) ? 1 : 0), 0.0f, 0.0f);
+    return (g + 1u) << 3;
+}
+
+// Test the segment o + t d, 0 <= t <= tmax, of path p against the union boxes and keep it
+// if it touches (kNee: a shadow ray). The caller returns kAffected once kSegAll is set.
+template <bool kCount, bool kNee>
+__device__ __forceinline__ void note_touch(const VarBoxes& V, float3 o, float3 d, float tmax, Path& p,
                                            Counters& cnt) {
     const float3 inv = rcp3(d);
     const float tm = tmax * 1.0001f + 1e-3f;
     bool hit = false;
     for (int k = 0; k < V.n; ++k) hit = hit || slab_touch(xyz(V.lo[k]), xyz(V.hi[k]), o, inv, tm);
     if (kCount) cnt.box += V.n;
-    if (!hit || seg == kSegFull) return;
-    unsigned base, n;
+    if (!hit) return;
+    unsigned seg = p.seg;
     if (seg == 0u) {
-        base = atomicAdd(V.seg_ctr, unsigned(kSeg));
-        n = 0u;
-        if (base + unsigned(kSeg) > V.seg_cap) {
-            seg = kSegFull;
+        seg = open_group<kNee>(V, p);
+        if (seg == kSegFull) {
+            p.seg = kSegFull;
             return;
         }
-    } else {
-        base = ((seg >> 3) - 1u) * unsigned(kSeg);
-        n = seg & 7u;
-        if (n == unsigned(kSeg)) {
-            seg = kSegFull;
-            return;
-        }
+    } else if ((seg & 7u) == unsigned(kSeg)) {
+        p.seg = seg | kSegAll;
+        return;
     }
-    V.seg_pool[2 * size_t(base + n) + 0] = make_float4(o.x, o.y, o.z, tmax);
-    V.seg_pool[2 * size_t(base + n) + 1] = make_float4(d.x, d.y, d.z, 0.0f);
-    seg = ((base / unsigned(kSeg) + 1u) << 3) | (n + 1u);
+    const size_t slot = size_t((seg >> 3) - 1u) * kSeg + (seg & 7u);
+    V.seg_pool[2 * slot + 0] = make_float4(o.x, o.y, o.z, tmax);
+    V.seg_pool[2 * slot + 1] = make_float4(d.x, d.y, d.z, 0.0f);
+    p.seg = seg + 1u;
 }
 
 __device__ __forceinline__ uint4 path_words(const InstScene& S, unsigned pixel, int s, int b, int slot) {
@@ -602,16 +647,6 @@ __device__ __forceinline__ float3 tex_albedo(const InstScene& S, int slot, float
     return f3(fminf(fmaxf(__ldg(q), 0.0f), 1.0f), fminf(fmaxf(__ldg(q + 1), 0.0f), 1.0f),
               fminf(fmaxf(__ldg(q + 2), 0.0f), 1.0f));
 }
-
-// One live path sample (Eq. 1's integrand along one path; Eq. 3 averages them).
-struct Path {
-    float3 o, d, beta, L;
-    unsigned pixel;  // y * W + x
-    int s, b;        // sample index, vertex index
-    int slot;        // pixel slot inside the warp's block (per-render pass: the path's record)
-    bool specular;   // emission counts: camera rays and rays after specular bounces
-    unsigned seg;    // shared pass: touching-segment word (see note_touch)
-};
 
 // Camera ray of sample s through pixel (x, y): pinhole, box-filtered jitter (slot 2).
 __device__ __forceinline__ void start_path(const InstScene& S, int W, int H, int x, int y, int s, int slot,
@@ -716,10 +751,19 @@ template <bool kCount, bool kShared, int kND = 0>
 __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt,
                                        const VarBoxes* V = nullptr, Tangents<kND>* tn = nullptr,
                                        const TraceJob* Jd = nullptr) {
+    if (kShared && p.seg == 0u) {
+        const int t = threadIdx.x;
+        s_stash[0][t] = p.o.x;
+        s_stash[1][t] = p.o.y;
+        s_stash[2][t] = p.o.z;
+        s_stash[3][t] = p.d.x;
+        s_stash[4][t] = p.d.y;
+        s_stash[5][t] = p.d.z;
+    }
     const Hit h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
     if (kShared) {
-        note_touch<kCount>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, p.seg, cnt);
-        if (p.seg == kSegFull) return kAffected;
+        note_touch<kCount, false>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, p, cnt);
+        if (p.seg & kSegAll) return kAffected;
     }
     if (h.slot < 0) {
         if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, xyz(S.bg), -1);
@@ -741,8 +785,8 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
         ng = box_normal(S, h.slot, p.o, p.d, rcp3(p.d));
         mat = as_int(S.prim[h.slot][0].w);
     }
-    if (kShared && ((V->mats >> mat) & 1u)) {
-        p.seg = kSegFull;
+    if (kShared && ((V->mats >> mat) & 1u)) {  // every render from here (state: this vertex)
+        p.seg = (p.seg == 0u ? open_group<false>(*V, p) : p.seg) | kSegAll;
         return kAffected;
     }
     const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
@@ -790,8 +834,8 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
                 const float dist = dist2 * inv_dist;
                 if (!occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u)) {
                     if (kShared) {
-                        note_touch<kCount>(*V, po, wi, dist, p.seg, cnt);
-                        if (p.seg == kSegFull) return kAffected;
+                        note_touch<kCount, true>(*V, po, wi, dist, p, cnt);
+                        if (p.seg & kSegAll) return kAffected;
                     }
                     const float g = cx * cl * (inv_dist * inv_dist) * S.light_area[li] * float(S.n_lights) *
                                     0.3183098861837907f;
@@ -992,6 +1036,7 @@ __device__ void build_var_boxes(WarpSmem& W, const TraceJob& J, int lane) {
     }
     if (lane == 0) {
         W.vb.seg_pool = J.seg_pool;
+        W.vb.seg_state = J.seg_state;
         W.vb.seg_ctr = J.share_ctl + 2;
         W.vb.seg_cap = J.seg_cap;
         W.vb.n = J.n_var;
@@ -1360,7 +1405,7 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
                 bool need = false;
                 if (e < n_codes) {  // does a kept segment of the path touch render r's bounds?
                     const unsigned sw = __ldcg(J.aff_segw + e);
-                    need = sw == kSegFull;
+                    need = (sw & kSegAll) != 0u;
                     const unsigned s0 = ((sw >> 3) - 1u) * unsigned(kSeg), ns = need ? 0u : (sw & 7u);
                     for (unsigned q = 0; q < ns && !need; ++q) {
                         const float4 A = __ldcg(J.seg_pool + 2 * size_t(s0 + q));
@@ -1382,10 +1427,24 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
             const unsigned avail = tail - head, rank = unsigned(__popc(fr & lt_mask));
             if (!alive && rank < avail) {
                 const unsigned e = ring[(head + rank) % kAffRing];
-                const unsigned code = __ldcg(J.aff_codes + e);
+                const unsigned code = __ldcg(J.aff_codes + e), sw = __ldcg(J.aff_segw + e);
                 const int pixel = int(code >> 6), smp = int(code & 63u);
-                const int y = div_magic(pixel, J.W, magic_W);
-                start_path(S, J.W, J.H, pixel - y * J.W, y, smp, int(e), p);
+                if (sw == kSegFull) {
+                    const int y = div_magic(pixel, J.W, magic_W);
+                    start_path(S, J.W, J.H, pixel - y * J.W, y, smp, int(e), p);
+                } else {  // resume where the path's renders part
+                    const float4* st = J.seg_state + 4 * size_t(((sw & ~kSegAll) >> 3) - 1u);
+                    const float4 a = __ldcg(st), b = __ldcg(st + 1), c = __ldcg(st + 2), q = __ldcg(st + 3);
+                    p.o = f3(a.x, a.y, a.z);
+                    p.d = f3(a.w, b.x, b.y);
+                    p.beta = f3(b.z, b.w, c.x);
+                    p.L = f3(c.y, c.z, c.w);
+                    p.b = __float_as_int(q.x);
+                    p.specular = __float_as_int(q.y) != 0;
+                    p.pixel = unsigned(pixel);
+                    p.s = smp;
+                    p.slot = int(e);
+                }
                 if (kCount) ++cnt.paths;
                 alive = true;
             }

@@ -162,6 +162,28 @@ def test_deterministic_across_launch_shapes(ctx):
     assert np.allclose(L4, L1, rtol=1e-12)  # block shape changes only the FP64 summation grouping
 
 
+def _occlusion_with_albedo():
+    """The box's position and a sphere's red albedo: a path that meets the sphere is traced
+    again by every render from that vertex on, one that touched the box's bounds before
+    from its first touch."""
+    wl = workloads.scaled(workloads.config_occlusion(), width=48, height=40, spp=4, pairs=4)
+    sph = int(wl.scene.prim_mat[1])
+    wl.bindings = np.vstack([wl.bindings, [[workloads.BIND_MAT_ALBEDO, sph, 0]]]).astype(np.int32)
+    wl.theta_ref = np.append(wl.theta_ref, 0.6).astype(np.float32)
+    wl.theta0 = np.append(wl.theta0, 0.85).astype(np.float32)
+    wl.sigma = np.append(wl.sigma, 0.05).astype(np.float32)
+    return wl
+
+
+def _small_pool_overflow():
+    """sigma = 1.5: the union of the sphere's bounds covers the view, every path touches it
+    and the segment pool (4096 paths here) runs out; the later paths are traced again from
+    the camera."""
+    wl = workloads.scaled(workloads.config_small(), pairs=4)
+    wl.sigma = np.full_like(wl.sigma, 1.5)
+    return wl
+
+
 @pytest.mark.parametrize("make", [workloads.config_small, workloads.config_occlusion,
                                   lambda: workloads.scaled(workloads.config_occlusion(), width=45, height=37, spp=7),
                                   # 64 renders: the render mask uses all 64 bits
@@ -169,7 +191,11 @@ def test_deterministic_across_launch_shapes(ctx):
                                                            pairs=32),
                                   # 80 renders: a touched path is traced again by every render
                                   lambda: workloads.scaled(workloads.config_occlusion(), width=40, height=40, spp=4,
-                                                           pairs=40)])
+                                                           pairs=40),
+                                  # depth 6 with Russian roulette: renders resume mid-path
+                                  lambda: workloads.scaled(workloads.config_occlusion(), width=48, height=40, spp=4,
+                                                           pairs=4, depth=6, rr_start=2),
+                                  _occlusion_with_albedo, _small_pool_overflow])
 def test_path_sharing_is_bit_identical(ctx, make):
     """With common random numbers, a path is traced once in the scene without the
     perturbed primitives; only the renders whose own primitives one of its rays may meet
