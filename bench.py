@@ -453,6 +453,10 @@ def main():
                                             line["mpaths_per_s"] / 1000.0)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, target_host)
+            # the same oracle on one thread (one bounded sample), beside the all-core figure
+            one = cpu_baseline(wl, target_host, nthreads=1, budget_s=3.0, max_steps=1)
+            line["cpu_baseline"]["single_thread"] = {"value": one["value"], "unit": one["unit"],
+                                                     "sample": one["sample"]}
         print(json.dumps(line), flush=True)
     job.release()
     ctx.close()
