@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     __shared__ float s_theta[kMaxD];
     __shared__ float s_scalar[2];
     __shared__ int s_job;
+    __shared__ __align__(16) BaseScene s_base;  // the job's base scene, staged once (int4 stores)
+    __shared__ InstScene s_inst;  // render r's scene, built here and written out in one copy
 
     const int tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) {
@@ -181,13 +183,35 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     if (tid == 0 && J.aff_cursor) J.aff_cursor[r] = 0u;
     const int D = J.D;
     const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
+    const float theta_d = (tid < D && J.theta) ? J.theta[(J.render_mode ? r * D : 0) + tid] : 0.0f;
+    {  // stage the base scene: all loads in flight at once, then the shared-memory stores
+        constexpr int n16 = int(sizeof(BaseScene) / 16), n4 = int(sizeof(BaseScene) / 4);
+        constexpr int kPer = (n16 + kInstBlock - 1) / kInstBlock;
+        if (J.base && (reinterpret_cast<size_t>(J.base) & 15) == 0) {
+            const int4* src = reinterpret_cast<const int4*>(J.base);
+            int4* dst = reinterpret_cast<int4*>(&s_base);
+            int4 v[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)
+                if (tid + q * kInstBlock < n16) v[q] = __ldg(src + tid + q * kInstBlock);
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)
+                if (tid + q * kInstBlock < n16) dst[tid + q * kInstBlock] = v[q];
+            for (int i = 4 * n16 + tid; i < n4; i += kInstBlock)
+                reinterpret_cast<int*>(&s_base)[i] = __ldg(reinterpret_cast<const int*>(J.base) + i);
+        } else if (J.base) {
+            for (int i = tid; i < n4; i += kInstBlock)
+                reinterpret_cast<int*>(&s_base)[i] = __ldg(reinterpret_cast<const int*>(J.base) + i);
+        }
+    }
+    __syncthreads();
 
     // ---- a1: perturbation and weight of render r --------------------------------
     // (texture scenes: the draws are made by the high-dimensional kernels, k_hd_*)
-    const bool texscene = J.base && J.base->tex_mat >= 0;
+    const bool texscene = J.base && s_base.tex_mat >= 0;
     if (texscene) {
     } else if (J.render_mode) {
-        if (tid < D) s_theta[tid] = J.theta[r * D + tid];
+        if (tid < D) s_theta[tid] = theta_d;
     } else {
         const bool anti = J.antithetic && (r & 1);
         const unsigned index = (J.antithetic ? unsigned(r >> 1) : unsigned(r)) +
@@ -261,7 +285,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
                 tau = -tau;
                 w = -w;
             }
-            s_theta[tid] = J.theta[tid] + tau;  // FP32 sum: the parameters this render gets
+            s_theta[tid] = theta_d + tau;  // FP32 sum: the parameters this render gets
             if (J.tau_out) J.tau_out[r * D + tid] = tau;
             if (J.w_out) J.w_out[r * D + tid] = w;
         }
@@ -270,8 +294,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     if (!J.scenes) return;  // draws only
 
     // ---- a2: bind theta_r into the scene -----------------------------------------
-    const BaseScene& B = *J.base;
-    InstScene& S = J.scenes[r];
+    const BaseScene& B = s_base;
+    InstScene& S = s_inst;
     if (tid < kMaxDiff) {  // pathwise estimator: derivative of each parameter's clamp
         float dc = 0.0f;
         if (J.diff && !texscene && tid < D) {
@@ -369,6 +393,18 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
             ++nl;
         }
         S.n_lights = nl;
+    }
+    __syncthreads();
+    {  // write out what the render kernels stage: header, used materials, used primitives
+        const float4* src = reinterpret_cast<const float4*>(&s_inst);
+        float4* dst = reinterpret_cast<float4*>(J.scenes + r);
+        constexpr int kHead = int(offsetof(InstScene, mat) / 16);
+        constexpr int kPrim = int(offsetof(InstScene, prim) / 16);
+        const int nm = 2 * B.n_mats, np = 4 * B.n_prims;
+        for (int i = tid; i < kHead + nm + np; i += kInstBlock) {
+            const int o = (i < kHead + nm) ? i : kPrim + (i - kHead - nm);
+            dst[o] = src[o];
+        }
     }
 }
 
