@@ -151,7 +151,7 @@ struct TraceJob {
     unsigned* aff_cursor;     // [R] next list entry of each render in the per-render pass
     int* aff_tiles;           // [tiles] blocks with affected paths (appended by the shared pass)
     unsigned* share_ctl;      // [0] listed blocks, [1] recorded paths, [2] segment slots claimed,
-                              // [3] epilogue queue; zeroed by the instantiation launch
+                              // [3] spare; zeroed by the instantiation launch
     // Pathwise estimator (Eq. 9): diff_n parameters, all albedo (kind 2) or emission (kind 3)
     // of material diff_mat, channel diff_comp; each block writes its partial sums of
     // (I - T) dI/dtheta_k to gpartials [R][tiles][diff_n]; k_finalize reduces them per render

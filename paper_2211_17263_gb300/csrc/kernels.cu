@@ -1536,11 +1536,8 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
     if (!job_shares) continue;
     const unsigned n_items = __ldcg(J.share_ctl + 0);
     const float inv = mean_scale(J.spp);
-    for (;;) {
-        unsigned item = 0;
-        if (lane == 0) item = atomicAdd(J.share_ctl + 3, 1u);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= n_items) break;
+    const unsigned gw = blockIdx.x * kWarps + unsigned(warp), nw = gridDim.x * kWarps;
+    for (unsigned item = gw; item < n_items; item += nw) {  // listed blocks cost alike: a static split
         const int t = __ldcg(J.aff_tiles + item);
         if (t < 0 || t >= J.tiles) {
             if (lane == 0) atomicOr(L.status, kStatusBadItem);
@@ -1636,6 +1633,13 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
 #pragma unroll
         for (int q = 0; q < 8; ++q) a[q] = 0.0;
         int i = tid;
+        for (; i + 31 * kBlock < n; i += 32 * kBlock) {  // 32 loads in flight, then the same adds
+            double v[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = __ldcg(src + size_t(i + q * kBlock) * stride);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) a[q & 7] += v[q];
+        }
         for (; i + 7 * kBlock < n; i += 8 * kBlock) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) a[q] += __ldcg(src + size_t(i + q * kBlock) * stride);
