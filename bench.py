@@ -359,31 +359,32 @@ def main():
 
     # end to end through the C ABI with host buffers: H2D inputs, gradient, Adam, D2H results
     e2e = None
-    theta_h = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32)).pin_memory()
-    sigma_h = torch.from_numpy(np.ascontiguousarray(wl.sigma, np.float32)).pin_memory()
-    target_h = torch.from_numpy(target_host).pin_memory()
-    theta_d, sigma_d = torch.empty_like(theta_h, device=f"cuda:{local}"), torch.empty_like(sigma_h, device=f"cuda:{local}")
-    target_d = torch.empty_like(target_h, device=f"cuda:{local}")
-    m_d = torch.zeros_like(theta_d)
-    v_d = torch.zeros_like(theta_d)
-    g_d = torch.empty_like(theta_d)
-    L_d = torch.empty(wl.renders, dtype=torch.float32, device=f"cuda:{local}")
-    out_h = torch.empty(2 * wl.D + wl.renders, dtype=torch.float32).pin_memory()
-    h2d = 4 * (2 * wl.D + 4 * wl.width * wl.height)
-    d2h = 4 * (2 * wl.D + wl.renders)
+    # one pinned host buffer and one device buffer, laid out [target (4HW) | sigma | theta | grad | losses]:
+    # each step uploads [target | sigma | theta] and downloads [theta | grad | losses], one copy each way
+    D, R, npx4 = wl.D, wl.renders, 4 * wl.width * wl.height
+    host = torch.empty(npx4 + 3 * D + R, dtype=torch.float32).pin_memory()
+    host[:npx4] = torch.from_numpy(np.ascontiguousarray(target_host, np.float32).reshape(-1))
+    host[npx4: npx4 + D] = torch.from_numpy(np.ascontiguousarray(wl.sigma, np.float32))
+    host[npx4 + D: npx4 + 2 * D] = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32))
+    buf = torch.empty_like(host, device=f"cuda:{local}")
+    target_d = buf[:npx4].view(wl.height, wl.width, 4)
+    sigma_d, theta_d = buf[npx4: npx4 + D], buf[npx4 + D: npx4 + 2 * D]
+    g_d, L_d = buf[npx4 + 2 * D: npx4 + 3 * D], buf[npx4 + 3 * D:]
+    m_d = torch.zeros(D, dtype=torch.float32, device=f"cuda:{local}")
+    v_d = torch.zeros_like(m_d)
+    out_h = torch.empty(2 * D + R, dtype=torch.float32).pin_memory()
+    h2d = 4 * (npx4 + 2 * D)
+    d2h = 4 * (2 * D + R)
+    opts = scene.grad_opts(wl, step=0)
 
     def e2e_step(k):
-        theta_d.copy_(theta_h, non_blocking=True)
-        sigma_d.copy_(sigma_h, non_blocking=True)
-        target_d.copy_(target_h, non_blocking=True)
-        opts = scene.grad_opts(wl, step=k)
+        buf[: npx4 + 2 * D].copy_(host[: npx4 + 2 * D], non_blocking=True)
+        opts.step = k
         scene.smoothed_grad(theta_d, sigma_d, target_d, opts, grad=g_d, losses=L_d)
         ctx.adam_step(theta_d, m_d, v_d, g_d, k + 1, wl.lr)
-        out_h[: wl.D].copy_(theta_d, non_blocking=True)
-        out_h[wl.D: 2 * wl.D].copy_(g_d, non_blocking=True)
-        out_h[2 * wl.D:].copy_(L_d, non_blocking=True)
+        out_h.copy_(buf[npx4 + D:], non_blocking=True)
         torch.cuda.current_stream().synchronize()
-        theta_h.copy_(out_h[: wl.D])
+        host[npx4 + D: npx4 + 2 * D] = out_h[:D]  # the next step starts from the updated theta
 
     for k in range(args.warmup):
         e2e_step(k)
