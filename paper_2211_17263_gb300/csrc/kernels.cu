@@ -34,9 +34,10 @@ namespace prdpt {
 constexpr unsigned kFull = 0xffffffffu;  // all lanes of a warp
 
 // Programmatic dependent launch: the kernels of a step are launched so that the next one
-// may be scheduled while the previous one drains. Each kernel first waits until every
-// kernel before it in the stream has completed and its writes are visible (a no-op for a
-// launch without the attribute), then lets the next kernel be scheduled.
+// may be scheduled while the previous one drains. Each kernel reads only host-written data
+// (job descriptors, the base scene) before pdl_enter, which waits until every kernel
+// before it in the stream has completed and its writes are visible (a no-op for a launch
+// without the attribute), then lets the next kernel be scheduled.
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -149,7 +150,6 @@ __device__ __forceinline__ void prim_bounds(const float4* P, int type, float3& l
 // k_instantiate: one CTA (kInstBlock threads) per render
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) {
-    pdl_enter();
     __shared__ float s_u[4 * 32];
     __shared__ float s_red[kInstBlock];
     __shared__ float s_theta[kMaxD];
@@ -159,10 +159,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     __shared__ InstScene s_inst;  // render r's scene, built here and written out in one copy
 
     const int tid = threadIdx.x;
-    if (blockIdx.x == 0 && tid == 0) {
-        if (L.queue_reset) *L.queue_reset = 0u;
-        if (L.queue_reset2) *L.queue_reset2 = 0u;
-    }
+    // Before waiting on the previous kernel: only data the host wrote (job descriptors, the
+    // base scene). Parameters, step counters and work counters come after the wait.
     if (tid == 0) {
         int j = 0;
         if (L.jobs) {
@@ -178,12 +176,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     __syncthreads();
     const InstJob& J = L.jobs ? L.jobs[s_job] : L.job0;
     const int r = blockIdx.x - J.block_begin;
-    if (r == 0 && tid == 0 && J.share_reset)
-        for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
-    if (tid == 0 && J.aff_cursor) J.aff_cursor[r] = 0u;
     const int D = J.D;
-    const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
-    const float theta_d = (tid < D && J.theta) ? J.theta[(J.render_mode ? r * D : 0) + tid] : 0.0f;
     {  // stage the base scene: all loads in flight at once, then the shared-memory stores
         constexpr int n16 = int(sizeof(BaseScene) / 16), n4 = int(sizeof(BaseScene) / 4);
         constexpr int kPer = (n16 + kInstBlock - 1) / kInstBlock;
@@ -204,6 +197,16 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
                 reinterpret_cast<int*>(&s_base)[i] = __ldg(reinterpret_cast<const int*>(J.base) + i);
         }
     }
+    pdl_enter();
+    if (blockIdx.x == 0 && tid == 0) {
+        if (L.queue_reset) *L.queue_reset = 0u;
+        if (L.queue_reset2) *L.queue_reset2 = 0u;
+    }
+    if (r == 0 && tid == 0 && J.share_reset)
+        for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
+    if (tid == 0 && J.aff_cursor) J.aff_cursor[r] = 0u;
+    const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
+    const float theta_d = (tid < D && J.theta) ? J.theta[(J.render_mode ? r * D : 0) + tid] : 0.0f;
     __syncthreads();
 
     // ---- a1: perturbation and weight of render r --------------------------------
@@ -1258,7 +1261,6 @@ __device__ __forceinline__ void diff_epilogue(const TraceJob& J, int r, int t, c
 template <bool kRender, bool kCount, bool kShare, int kND>
 __global__ void __launch_bounds__(kND > 0 ? kDiffBlock : kBlock, kND > 0 ? kDiffMinBlocks : kTraceMinBlocks)
     k_trace(const __grid_constant__ TraceLaunch L) {
-    pdl_enter();
     constexpr int kW = (kND > 0 ? kDiffBlock : kBlock) / 32;
     __shared__ WarpSmem s_warp[kW];
     __shared__ unsigned long long s_dacc[kND > 0 ? kW : 1][kND > 0 ? kND : 1][32];
@@ -1268,6 +1270,17 @@ __global__ void __launch_bounds__(kND > 0 ? kDiffBlock : kBlock, kND > 0 ? kDiff
     const TraceJob& J = W.job;
     int cur_job = -1, cur_r = -1;
     Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (!L.jobs) {  // a single job's descriptor is host data: copied before the wait
+        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        unsigned* dst = reinterpret_cast<unsigned*>(&W.job);
+        for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
+        __syncwarp();
+    }
+    pdl_enter();
+    if (!L.jobs) {
+        if (kShare) build_var_boxes(W, J, lane);  // the renders' bounds: written by k_instantiate
+        cur_job = 0;
+    }
 
     for (;;) {
         // ---- pop one work item for this warp --------------------------------------
@@ -1382,7 +1395,6 @@ constexpr int kAffRing = 64;  // ring entries per warp (the ring never holds mor
 
 template <bool kCount>
 __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(const __grid_constant__ TraceLaunch L) {
-    pdl_enter();
     __shared__ InstScene s_scene[kWarps];
     __shared__ TraceJob s_job[kWarps];
     __shared__ unsigned s_ring[kWarps][kAffRing];
@@ -1395,11 +1407,12 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
     Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     const int njobs = L.jobs ? L.njobs : 1;
     for (int jb = 0; jb < njobs; ++jb) {  // the jobs of a packed launch one after another
-    {
+    {  // job descriptors are host data: the first is copied before the wait on the previous kernel
         const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + jb : &L.job0);
         unsigned* dst = reinterpret_cast<unsigned*>(&J);
         for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
         __syncwarp();
+        if (jb == 0) pdl_enter();
     }
     const bool job_shares = J.share != 0;
     __syncwarp();  // every lane has read the descriptor before the next copy may overwrite it
@@ -1519,17 +1532,17 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
 // bit-identical to the per-render path. Clears the affected radiance it read, so the
 // buffers are zero for the next step.
 __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constant__ TraceLaunch L) {
-    pdl_enter();
     __shared__ TraceJob s_job[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TraceJob& J = s_job[warp];
     const int njobs = L.jobs ? L.njobs : 1;
     for (int jb = 0; jb < njobs; ++jb) {  // the jobs of a packed launch one after another
-    {
+    {  // job descriptors are host data: the first is copied before the wait on the previous kernel
         const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + jb : &L.job0);
         unsigned* dst = reinterpret_cast<unsigned*>(&J);
         for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
         __syncwarp();
+        if (jb == 0) pdl_enter();
     }
     const bool job_shares = J.share != 0;
     __syncwarp();  // every lane has read the descriptor before the next copy may overwrite it
@@ -1607,7 +1620,6 @@ __device__ __forceinline__ void adam_update(float& th, float& m, float& v, float
 // warp shuffle tree, then the eight warp sums in order). The CTA that completes a job's
 // last render forms the gradient in FP64 (one warp per parameter) and applies Adam.
 __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ TraceLaunch L) {
-    pdl_enter();
     __shared__ double s_red[kBlock / 32];
     __shared__ int s_job, s_last;
     const int tid = threadIdx.x;
@@ -1624,6 +1636,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const __grid_constant__ Tra
         s_job = j;
     }
     __syncthreads();
+    pdl_enter();  // the job lookup above reads host data only
     const TraceJob& J = L.jobs ? L.jobs[s_job] : L.job0;
     const int r = int(blockIdx.x) - J.fin_begin;
     // fixed-order sum of src[i * stride], i < n: strided per thread into eight
