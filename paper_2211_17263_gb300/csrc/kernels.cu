@@ -1085,6 +1085,16 @@ __device__ void build_var_boxes(WarpSmem& W, const TraceJob& J, int lane) {
     __syncwarp();
 }
 
+// a += v modulo 2^64 on a shared-memory word, as two native 32-bit atomics: the low
+// word's carry (seen from the value it held before the add) goes into the high word.
+// Concurrent adds give the exact sum whatever their order; the word is read only after
+// every add has completed.
+__device__ __forceinline__ void smem_add_u64(unsigned long long* a, unsigned long long v) {
+    unsigned* w = reinterpret_cast<unsigned*>(a);  // little-endian: w[0] low, w[1] high
+    const unsigned lo = unsigned(v), old = atomicAdd(w, lo);
+    atomicAdd(w + 1, unsigned(v >> 32) + (old + lo < old ? 1u : 0u));
+}
+
 // k-th (0-based) set bit of m.
 __device__ __forceinline__ int nth_set_bit(unsigned long long m, int k) {
     int pos = 0;
@@ -1140,12 +1150,12 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
         // every ended path counts in the shared radiance; the per-render pass later adds,
         // for each render in a recorded path's mask, its own radiance minus this value
         if (ended) {
-            atomicAdd(&acc[0][p.slot], to_fixed(p.L.x));
-            atomicAdd(&acc[1][p.slot], to_fixed(p.L.y));
-            atomicAdd(&acc[2][p.slot], to_fixed(p.L.z));
+            smem_add_u64(&acc[0][p.slot], to_fixed(p.L.x));
+            smem_add_u64(&acc[1][p.slot], to_fixed(p.L.y));
+            smem_add_u64(&acc[2][p.slot], to_fixed(p.L.z));
 #pragma unroll
             for (int k = 0; k < kND; ++k)  // tangents: signed fixed point, exact and order-free
-                if (k < J.diff_n) atomicAdd(&dacc[k][p.slot], to_fixed_signed(tn.dL[k]));
+                if (k < J.diff_n) smem_add_u64(&dacc[k][p.slot], to_fixed_signed(tn.dL[k]));
         }
         if (kShared) {  // record the paths some render must trace itself
             const bool rec = ended && p.seg != 0u;
