@@ -1430,11 +1430,17 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
     const unsigned n_codes = __ldcg(J.share_ctl + 1);
     const unsigned magic_W = 0xffffffffu / unsigned(J.W) + 1u;
     for (int k = 0; k < J.R; ++k) {
+        {  // the next render, in the order gwarp + k, ..., with entries left: 32 cursors at a time
+            const bool left = k + lane < J.R && __ldcg(J.aff_cursor + (gwarp + k + lane) % J.R) < n_codes;
+            const unsigned m = __ballot_sync(kFull, left);
+            if (!m) {
+                k += 31;
+                continue;
+            }
+            k += __ffs(m) - 1;
+        }
         const int r = (gwarp + k) % J.R;
         unsigned* cursor = J.aff_cursor + r;
-        unsigned seen = 0;
-        if (lane == 0) seen = __ldcg(cursor);
-        if (__shfl_sync(kFull, seen, 0) >= n_codes) continue;  // nothing left for this render
         {  // stage render r's scene
             const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
             float4* dst = reinterpret_cast<float4*>(&S);
