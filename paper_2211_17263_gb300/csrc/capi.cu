@@ -919,7 +919,7 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     j->step = reinterpret_cast<int*>(j->rdone + kMaxRenders);
     j->done = reinterpret_cast<unsigned*>(j->step + 1);
     j->queue = j->done + 1;
-    unsigned* share_ctl = j->queue + 1;  // path-sharing counters: listed blocks, paths, two queues
+    unsigned* share_ctl = j->queue + 1;  // path-sharing counters: listed blocks, paths, segment slots, spare
     j->w = reinterpret_cast<float*>(b + off_w);
     j->partials = reinterpret_cast<double*>(b + off_p);
     j->scenes = reinterpret_cast<InstScene*>(b + off_s);

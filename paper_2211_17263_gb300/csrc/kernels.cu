@@ -2,7 +2,8 @@
 //
 //   k_instantiate   one CTA per render: Philox draws -> perturbation tau and weight
 //                   w (Sec. 3.2, Eq. 11, Algorithm 1), theta +- tau bound into the
-//                   scene (Eq. 10's P(theta - tau_i)), derived constants precomputed.
+//                   scene (Eq. 10's P(theta - tau_i)), derived constants precomputed;
+//                   the scene is built in shared memory and written out in one copy.
 //   k_trace         persistent render kernel. Each warp pulls (render, pixel block)
 //                   work items from a queue, stages the render's scene in its own
 //                   shared-memory slot, and traces the block's pixels x samples as a
@@ -10,20 +11,28 @@
 //                   at once (ballot + popc), so live paths stay packed in the warp.
 //                   Radiance is accumulated per pixel in 2^-32 fixed point (integer
 //                   adds are order-independent, so results do not depend on which
-//                   lane traced which path). The pixel means, the squared error
-//                   against the target and the block's partial sum are formed in
-//                   FP64 in registers -- the perturbed image never reaches HBM.
-//                   Each block's partial is a plain store; no CTA-wide barriers, no
-//                   fences or atomics per item, no spin waits.
+//                   lane traced which path). Each pixel's error against the target is
+//                   formed exactly in integers, squared in FP32, and summed per block
+//                   in FP64 -- the perturbed image never reaches HBM. Variants: path
+//                   sharing (a block of all renders traced once in the scene without
+//                   the perturbed primitives, recording the paths that may differ) and
+//                   the pathwise estimator (Eq. 9, forward-mode tangents).
+//   k_trace_affected  path sharing, per-render pass: each render traces again the
+//                   recorded paths that may meet its own primitives, resuming where
+//                   the renders part, and adds its radiance minus the shared one.
+//   k_shared_epilogue path sharing: the blocks with recorded paths, all renders.
 //   k_finalize      one CTA per render: L_r from the block partials (fixed order); the
 //                   CTA completing a job's last render forms the gradient of Eq. 10
-//                   and applies Adam.
+//                   (or the mean of Eq. 9's pathwise gradients) and applies Adam.
+//   k_hd_norms, k_hd_perturb, k_hd_grad  high-dimensional parameters (texture scenes):
+//                   D-dimensional draws and the gradient W^T dL with Adam.
 //   k_adam          standalone Adam update.
 //   k_philox        raw Philox words (for bit-exact checks of the random streams).
+//   k_ffma_probe    FMA-chain throughput probe (the FP32 peak of the roofline).
 //
-// FP32 throughout the path tracer; every reduction is in a fixed order, so results
-// are deterministic and independent of the launch shape and of other jobs sharing
-// the launch.
+// FP32 throughout the path tracer; every floating-point reduction is in a fixed order
+// and every per-pixel sum is an integer sum, so results are deterministic and
+// independent of the launch shape and of other jobs sharing the launch.
 #include <cstddef>
 #include <cstdint>
 
