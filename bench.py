@@ -114,10 +114,23 @@ def _measured_peaks():
         return {}
 
 
-def _kernel_source_sha():
+def _code_only(text):
+    """Source text without // comments and blank lines (comment edits do not change a kernel)."""
+    lines = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip() if "//" in line and '"' not in line.split("//", 1)[0] else line.rstrip()
+        if code.strip():
+            lines.append(code)
+    return "\n".join(lines)
+
+
+def _kernel_source_sha(read=None):
+    """Hash of the kernel sources' code; a profile summary is used only while it matches."""
     h = hashlib.sha256()
     for f in ("kernels.cu", "internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2211_17263_gb300", "csrc", f), "rb").read())
+        path = os.path.join("paper_2211_17263_gb300", "csrc", f)
+        text = read(path) if read else open(os.path.join(ROOT, path)).read()
+        h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
 
