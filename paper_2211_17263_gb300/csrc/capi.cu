@@ -1146,8 +1146,10 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             c->d_trace = static_cast<TraceJob*>(p);
             c->batch_cap = n;
         }
-        PRDPT_CUDA(cudaMemcpy(c->d_inst, inst.data(), sizeof(InstJob) * n, cudaMemcpyHostToDevice));
-        PRDPT_CUDA(cudaMemcpy(c->d_trace, trace.data(), sizeof(TraceJob) * n, cudaMemcpyHostToDevice));
+        // in stream order: a previous packed step on this stream may still be reading them
+        // (pageable source: the call returns once the host data is staged)
+        PRDPT_CUDA(cudaMemcpyAsync(c->d_inst, inst.data(), sizeof(InstJob) * n, cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(c->d_trace, trace.data(), sizeof(TraceJob) * n, cudaMemcpyHostToDevice, st_));
         c->batch_ids = ids;
         c->batch_blocks = blocks;
         c->batch_nshare = nshare;

@@ -119,3 +119,36 @@ def test_job_release_and_reuse_of_batch(ctx):
     api.step_batch(ctx, [b])
     assert b.read()["steps"] == 2
     b.release()
+
+
+def test_alternating_batches_on_a_side_stream(ctx):
+    """Packed steps of two different job sets, alternating on a non-blocking stream with no
+    host synchronisation in between: each change of set uploads new job descriptors, in
+    stream order, so the steps still in flight keep theirs. Every job ends where it ends
+    when it steps alone."""
+    from paper_2211_17263_gb300 import api
+    wls = [workloads.scaled(workloads.config_small(seed=21), width=48, height=40, spp=4, pairs=3),
+           workloads.scaled(workloads.config_occlusion(seed=22), width=64, height=48, spp=4, pairs=4),
+           workloads.scaled(workloads.config_gi_box(seed=23), width=40, height=32, spp=2, pairs=2)]
+    targets = [oracle.render_target(w) for w in wls]
+    steps = [4, 8, 4]  # job 1 is in both sets
+    alone = []
+    for w, t, n in zip(wls, targets, steps):
+        j = _job(ctx, w, t)
+        for _ in range(n):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    jobs = [_job(ctx, w, t) for w, t in zip(wls, targets)]
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(4):
+        api.step_batch(ctx, [jobs[0], jobs[1]], stream=side)
+        api.step_batch(ctx, [jobs[1], jobs[2]], stream=side)
+    side.synchronize()
+    for j, a, n in zip(jobs, alone, steps):
+        b = j.read()
+        assert b["steps"] == n
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(a[key], b[key]), key
+        j.release()
