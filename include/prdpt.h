@@ -20,6 +20,12 @@
  *  - Calls taking `stream` (a cudaStream_t, NULL = legacy default stream) only
  *    enqueue work and return; their device-side results are ready when the stream
  *    reaches that point. Calls without a stream are synchronous.
+ *  - Order on the GPU: prdpt_render_batch, prdpt_sample_perturbations,
+ *    prdpt_smoothed_grad and prdpt_step_batch use the context's shared scratch
+ *    buffers and work counters, so such calls on one context must execute in order
+ *    (one stream, or streams ordered by events). A resident job has buffers of its
+ *    own: different jobs may step (prdpt_step) concurrently on different streams,
+ *    while the steps of one job must be ordered.
  *  - Images are row-major [H][W] of float4 (R, G, B, pad); pixel (0,0) is the top
  *    left; the pad channel is written as 0 and ignored on input.
  *  - Random numbers: Philox4x32-10 with key = 64-bit seed; counter words
