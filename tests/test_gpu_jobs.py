@@ -152,3 +152,33 @@ def test_alternating_batches_on_a_side_stream(ctx):
         for key in ("theta", "grad", "losses"):
             assert np.array_equal(a[key], b[key]), key
         j.release()
+
+
+def test_jobs_step_concurrently_on_their_own_streams(ctx):
+    """Resident jobs own their buffers: two jobs (one sharing paths, one not) stepping
+    on two streams at once end exactly where they end stepping alone."""
+    from paper_2211_17263_gb300 import api
+    wls = [workloads.scaled(workloads.config_occlusion(seed=31), width=64, height=48, spp=4, pairs=4),
+           workloads.scaled(workloads.config_gi_box(seed=32), width=48, height=40, spp=2, pairs=2)]
+    targets = [oracle.render_target(w) for w in wls]
+    alone = []
+    for w, t in zip(wls, targets):
+        j = _job(ctx, w, t)
+        for _ in range(5):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    jobs = [_job(ctx, w, t) for w, t in zip(wls, targets)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for _ in range(5):
+        for j, s in zip(jobs, streams):
+            j.step(s)
+    for s in streams:
+        s.synchronize()
+    for j, a in zip(jobs, alone):
+        b = j.read()
+        assert b["steps"] == 5
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(a[key], b[key]), key
+        j.release()
