@@ -1140,22 +1140,29 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
     const unsigned lt_mask = (1u << lane) - 1u;
     Path p;
     Tangents<kND> tn;
-    int task = lane;
-    bool alive = task < ntasks;
-    int slot, smp;
-    decode(alive ? task : 0, slot, smp);
-    if (alive) {
-        const int row = div_magic(slot, vw, magic_w);
-        start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
-        if (kShared) p.seg = 0u;
-        if (kND > 0) tan_reset(tn);
-        if (kCount) ++cnt.paths;
-    }
-    int next = 32;
-    while (__any_sync(kFull, alive)) {
+    bool alive = false, ended = true;  // every lane takes its first task at the first refill
+    int next = 0, slot, smp;
+    for (;;) {
+        // lanes whose path ended take the next tasks, in lane order (one code site for the
+        // first tasks and the later ones)
+        const unsigned need = __ballot_sync(kFull, ended);
+        const int mine = next + __popc(need & lt_mask);
+        decode((ended && mine < ntasks) ? mine : 0, slot, smp);
+        if (ended) {
+            alive = mine < ntasks;
+            if (alive) {
+                const int row = div_magic(slot, vw, magic_w);
+                start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
+                if (kShared) p.seg = 0u;
+                if (kND > 0) tan_reset(tn);
+                if (kCount) ++cnt.paths;
+            }
+        }
+        next += __popc(need);
+        if (!__any_sync(kFull, alive)) break;
         int st = kLive;
         if (alive) st = advance<kCount, kShared, kND>(S, J.depth, J.rr_start, p, cnt, V, &tn, &J);
-        const bool ended = alive && st != kLive;
+        ended = alive && st != kLive;
         // every ended path counts in the shared radiance; the per-render pass later adds,
         // for each render in a recorded path's mask, its own radiance minus this value
         if (ended) {
@@ -1184,21 +1191,6 @@ __device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, 
                 if (lane == 0) *recorded = 1u;
             }
         }
-        const unsigned need = __ballot_sync(kFull, ended);
-        const int mine = next + __popc(need & lt_mask);
-        decode((ended && mine < ntasks) ? mine : 0, slot, smp);
-        if (ended) {
-            task = mine;
-            alive = task < ntasks;
-            if (alive) {
-                const int row = div_magic(slot, vw, magic_w);
-                start_path(S, J.W, J.H, x0 + slot - row * vw, y0 + row, smp, slot, p);
-                if (kShared) p.seg = 0u;
-                if (kND > 0) tan_reset(tn);
-                if (kCount) ++cnt.paths;
-            }
-        }
-        next += __popc(need);
     }
     __syncwarp();
 }
