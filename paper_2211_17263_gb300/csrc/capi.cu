@@ -49,7 +49,7 @@ struct Job {
     float* w = nullptr;
     bool tex = false;              // texture scene: D > kMaxD parameters
     float* tex_all = nullptr;      // [R][D] per-render textures
-    float2* norms = nullptr;       // [R] radial-sampler norms
+    HdNorm* norms = nullptr;       // [R] radial-sampler norms
     unsigned long long* share = nullptr;
     unsigned long long* accaff = nullptr;
     void* afflist = nullptr;
@@ -104,7 +104,7 @@ struct prdpt_ctx {
     size_t s_cursor_n = 0;
     float* s_tex = nullptr;       // texture scenes: [R][D] per-render textures
     size_t s_tex_n = 0;
-    float2* s_norms = nullptr;    // texture scenes: [draws] radial-sampler norms
+    HdNorm* s_norms = nullptr;    // texture scenes: [draws] radial-sampler norms (counters kept zero)
     size_t s_norms_n = 0;
     double* s_gpart = nullptr;    // pathwise estimator: [R][tiles][D] gradient partials
     size_t s_gpart_n = 0;
@@ -605,9 +605,16 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     return PRDPT_OK;
 }
 
+// CTAs per draw of the radial sampler's norms in D dimensions: about 2048 terms each.
+static int hd_norm_split(int D) {
+    const long long terms = (long long)D + 1 + (D + 1) / 2;
+    const long long n = (terms + 2047) / 2048;
+    return int(n < 1 ? 1 : (n > kNormSplitMax ? kNormSplitMax : n));
+}
+
 // Draws of a texture scene (D > kMaxD parameters) by the high-dimensional kernels.
 static HdDraws hd_draws(const Scene* s, const prdpt_grad_opts* o, const float* theta, const float* sigma,
-                        float2* norms, float* theta_out, float* w_out) {
+                        HdNorm* norms, float* theta_out, float* w_out) {
     HdDraws H{};
     H.D = s->D;
     H.R = 2 * o->pairs;
@@ -620,6 +627,7 @@ static HdDraws hd_draws(const Scene* s, const prdpt_grad_opts* o, const float* t
     H.sigma = sigma;
     H.c_radial = float(radial_constant(s->D));
     H.norms = norms;
+    H.norm_split = hd_norm_split(s->D);
     H.theta_out = theta_out;
     H.w_out = w_out;
     return H;
@@ -681,7 +689,7 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* si
     std::lock_guard<std::mutex> lk(c->mu);
     PRDPT_CUDA(cudaSetDevice(c->device));
     if (D > kMaxD) {  // the high-dimensional kernels
-        if (prdpt_status st = grow(c, &c->s_norms, &c->s_norms_n, (size_t)2 * o->pairs)) return st;
+        if (prdpt_status st = grow_zeroed(c, &c->s_norms, &c->s_norms_n, (size_t)2 * o->pairs)) return st;
         HdDraws H{};
         H.D = D;
         H.R = 2 * o->pairs;
@@ -693,6 +701,7 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* si
         H.sigma = sigma_dev;
         H.c_radial = float(radial_constant(D));
         H.norms = c->s_norms;
+        H.norm_split = hd_norm_split(D);
         H.tau_out = tau_dev;
         H.w_out = w_dev;
         PRDPT_CUDA(launch_hd_draws(H, static_cast<cudaStream_t>(stream)));
@@ -761,7 +770,7 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
     if (tex) {  // a1 over the texture's D parameters: per-render textures and weights
         if (prdpt_status st = grow(c, &c->s_tex, &c->s_tex_n, (size_t)R * D)) return st;
-        if (prdpt_status st = grow(c, &c->s_norms, &c->s_norms_n, (size_t)R)) return st;
+        if (prdpt_status st = grow_zeroed(c, &c->s_norms, &c->s_norms_n, (size_t)R)) return st;
         PRDPT_CUDA(launch_hd_draws(hd_draws(s, o, theta_dev, sigma_dev, c->s_norms, c->s_tex, c->s_w), st_));
     }
     InstLaunch IL{};
@@ -899,7 +908,7 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const size_t off_hs = (off_rg + (probe.diff ? sizeof(double) * (size_t)R * kMaxDiff : 0) + 255) & ~size_t(255);
     const size_t off_tx = (off_hs + (tex ? sizeof(float) * 5 * (size_t)D : 0) + 255) & ~size_t(255);
     const size_t off_nr = (off_tx + (tex ? sizeof(float) * (size_t)R * D : 0) + 255) & ~size_t(255);
-    const size_t total = off_nr + (tex ? sizeof(float2) * (size_t)R : 0);
+    const size_t total = off_nr + (tex ? sizeof(HdNorm) * (size_t)R : 0);
     void* base = nullptr;
     if (prdpt_status st = dev_alloc(c, &base, total)) {
         delete j;
@@ -941,8 +950,9 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         j->sigma0 = j->v + D;
         j->grad = j->sigma0 + D;
         j->tex_all = reinterpret_cast<float*>(b + off_tx);
-        j->norms = reinterpret_cast<float2*>(b + off_nr);
+        j->norms = reinterpret_cast<HdNorm*>(b + off_nr);
         if (e == cudaSuccess) e = cudaMemset(j->theta, 0, sizeof(float) * 5 * (size_t)D);
+        if (e == cudaSuccess) e = cudaMemset(j->norms, 0, sizeof(HdNorm) * (size_t)R);  // part counters
     }
     if (e == cudaSuccess) e = cudaMemcpy(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
@@ -1043,6 +1053,7 @@ static HdDraws job_hd_draws(const Job* j) {
     H.sigma_min = I.sigma_min;
     H.c_radial = I.c_radial;
     H.norms = j->norms;
+    H.norm_split = hd_norm_split(j->D);
     H.theta_out = j->tex_all;
     H.w_out = j->w;
     return H;

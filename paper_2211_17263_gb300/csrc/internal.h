@@ -188,6 +188,17 @@ struct InstLaunch {
 
 // High-dimensional parameter draws (texture scenes, D > kMaxD): norms per draw, then
 // per (render, parameter) perturbation, weight and perturbed parameter.
+constexpr int kNormSplitMax = 64;  // radial sampler: CTAs per draw for the norms of D > kMaxD normals
+
+// One draw of the radial sampler in D > kMaxD dimensions: v = (|z|, radius) and the
+// partial sums (|z|^2, radius^2) of its CTAs; ctr counts the parts done and is reset to 0
+// by the CTA that combines them (so it is zero between launches).
+struct HdNorm {
+    float2 v;
+    unsigned ctr, pad;
+    double2 part[kNormSplitMax];
+};
+
 struct HdDraws {
     int D, R, sampler, antithetic;
     int draw_begin;           // global index of draw 0 (sharded estimates)
@@ -198,7 +209,8 @@ struct HdDraws {
     const float* sigma;       // [D] bandwidth (sigma0 when annealing)
     int anneal, total_steps;
     float sigma_min, c_radial;
-    float2* norms;            // [draws] (|z|, radius) of the radial sampler
+    HdNorm* norms;            // [draws] the radial sampler's norms (counters zero on entry)
+    int norm_split;           // CTAs per draw in k_hd_norms (1..kNormSplitMax)
     float* theta_out;         // [R][D] theta + tau (per-render texture), or null
     float* tau_out;           // [R][D] or null
     float* w_out;             // [R][D] or null

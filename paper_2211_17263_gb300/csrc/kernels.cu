@@ -1858,20 +1858,28 @@ __device__ __forceinline__ unsigned hd_step(const HdDraws& H) {
     return H.step + (H.step_dev ? unsigned(*H.step_dev) : 0u);
 }
 
-// Radial sampler (Sec. 3.2, reading R1) in D dimensions, one CTA per draw: the norm of
-// the D Box-Muller normals and the chi_{D+1} radius (sum of (D+1)/2 exponentials, plus
-// one more squared normal when D is even), each summed in FP64 in a fixed order.
+// Radial sampler (Sec. 3.2, reading R1) in D dimensions: the norm of the D Box-Muller
+// normals and the chi_{D+1} radius (sum of (D+1)/2 exponentials, plus one more squared
+// normal when D is even). Each draw's terms are split into norm_split contiguous parts,
+// one CTA each, summed in FP64 in a fixed order; the CTA that finishes a draw's last part
+// adds the parts in order.
 __global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
-    pdl_enter();
     __shared__ double s_z[kBlock / 32], s_r[kBlock / 32];
-    const unsigned index = blockIdx.x + unsigned(H.draw_begin), step = hd_step(H);
+    __shared__ int s_last;
+    const int split = H.norm_split, part = int(blockIdx.x) % split;
+    const unsigned local = blockIdx.x / unsigned(split);
+    pdl_enter();
+    const unsigned index = local + unsigned(H.draw_begin), step = hd_step(H);
     const int D = H.D, n_exp = (D + 1) / 2, nz = D + (D % 2 == 0 ? 1 : 0);
+    const int z0 = int((long long)nz * part / split), z1 = int((long long)nz * (part + 1) / split);
+    const int e0 = int((long long)n_exp * part / split), e1 = int((long long)n_exp * (part + 1) / split);
     double zs = 0.0, rs = 0.0;
-    for (int j = threadIdx.x; j < nz; j += kBlock) {
+    for (int j = z0 + int(threadIdx.x); j < z1; j += kBlock) {
         const float z = hd_normal(H, index, step, n_exp, j);
         if (j < D) zs += double(z * z); else rs += double(z * z);
     }
-    for (int j = threadIdx.x; j < n_exp; j += kBlock) rs += double(-2.0f * logf(perturb_uniform(H, index, step, j)));
+    for (int j = e0 + int(threadIdx.x); j < e1; j += kBlock)
+        rs += double(-2.0f * logf(perturb_uniform(H, index, step, j)));
     zs = warp_sum_d(zs);
     rs = warp_sum_d(rs);
     if ((threadIdx.x & 31) == 0) {
@@ -1879,13 +1887,28 @@ __global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
         s_r[threadIdx.x >> 5] = rs;
     }
     __syncthreads();
+    HdNorm& N = H.norms[local];
     if (threadIdx.x == 0) {
         double z = 0.0, r = 0.0;
         for (int w = 0; w < kBlock / 32; ++w) {
             z += s_z[w];
             r += s_r[w];
         }
-        H.norms[blockIdx.x] = make_float2(float(sqrt(z)), float(sqrt(r)));
+        N.part[part] = make_double2(z, r);
+        __threadfence();
+        s_last = atomicAdd(&N.ctr, 1u) == unsigned(split - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double z = 0.0, r = 0.0;
+        for (int q = 0; q < split; ++q) {
+            const double2 v = __ldcg(&N.part[q]);
+            z += v.x;
+            r += v.y;
+        }
+        N.v = make_float2(float(sqrt(z)), float(sqrt(r)));
+        N.ctr = 0u;  // ready for the next launch
     }
 }
 
@@ -1902,7 +1925,7 @@ __global__ void __launch_bounds__(kBlock) k_hd_perturb(const HdDraws H) {
     float tt, wt;
     if (H.sampler == kRadial) {
         const float z = hd_normal(H, index, step, (H.D + 1) / 2, d);
-        const float2 nr = H.norms[local];
+        const float2 nr = H.norms[local].v;
         const float dir = z / nr.x;
         tt = nr.y * dir;
         wt = H.c_radial * dir;
@@ -1955,7 +1978,8 @@ __global__ void __launch_bounds__(kBlock) k_hd_grad(const HdGrad G) {
 cudaError_t launch_hd_draws(const HdDraws& H, cudaStream_t stream) {
     if (H.D <= 0 || H.R <= 0) return cudaSuccess;
     if (H.sampler == kRadial) {
-        const cudaError_t e = launch_pdl(k_hd_norms, H.antithetic ? H.R / 2 : H.R, kBlock, stream, H);
+        if (H.norm_split < 1 || H.norm_split > kNormSplitMax) return cudaErrorInvalidValue;
+        const cudaError_t e = launch_pdl(k_hd_norms, (H.antithetic ? H.R / 2 : H.R) * H.norm_split, kBlock, stream, H);
         if (e != cudaSuccess) return e;
     }
     const size_t n = size_t(H.R) * size_t(H.D);
