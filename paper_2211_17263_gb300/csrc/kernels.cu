@@ -1844,14 +1844,30 @@ __device__ __forceinline__ float perturb_uniform(const HdDraws& H, unsigned inde
     return u01(x);
 }
 
-// Box-Muller normal j of a draw whose pairs start at uniform `base` (as bm_normal).
-__device__ __forceinline__ float hd_normal(const HdDraws& H, unsigned index, unsigned step, int base, int j) {
-    const float a = perturb_uniform(H, index, step, base + 2 * (j / 2));
-    const float b = perturb_uniform(H, index, step, base + 2 * (j / 2) + 1);
-    const float rad = sqrtf(-2.0f * logf(a));
+// Uniforms k and k + 1 of a draw (one Philox block unless k is a block's last word).
+__device__ __forceinline__ float2 perturb_uniform_pair(const HdDraws& H, unsigned index, unsigned step, int k) {
+    const uint4 w = philox(make_uint4(index, unsigned(k >> 2), step, kTagPerturb << 28), unsigned(H.seed),
+                           unsigned(H.seed >> 32));
+    const int q = k & 3;
+    const unsigned xa = q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+    unsigned xb;
+    if (q < 3) {
+        xb = q == 0 ? w.y : (q == 1 ? w.z : w.w);
+    } else {
+        xb = philox(make_uint4(index, unsigned(k >> 2) + 1u, step, kTagPerturb << 28), unsigned(H.seed),
+                    unsigned(H.seed >> 32)).x;
+    }
+    return make_float2(u01(xa), u01(xb));
+}
+
+// Box-Muller normals 2m and 2m + 1 of a draw whose pairs start at uniform `base` (as
+// bm_normal): (cos, sin) parts.
+__device__ __forceinline__ float2 hd_normal_pair(const HdDraws& H, unsigned index, unsigned step, int base, int m) {
+    const float2 ab = perturb_uniform_pair(H, index, step, base + 2 * m);
+    const float rad = sqrtf(-2.0f * logf(ab.x));
     float sn, cs;
-    sincospif(2.0f * b, &sn, &cs);
-    return rad * ((j & 1) ? sn : cs);
+    sincospif(2.0f * ab.y, &sn, &cs);
+    return make_float2(rad * cs, rad * sn);
 }
 
 __device__ __forceinline__ unsigned hd_step(const HdDraws& H) {
@@ -1870,13 +1886,15 @@ __global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
     const unsigned local = blockIdx.x / unsigned(split);
     pdl_enter();
     const unsigned index = local + unsigned(H.draw_begin), step = hd_step(H);
-    const int D = H.D, n_exp = (D + 1) / 2, nz = D + (D % 2 == 0 ? 1 : 0);
-    const int z0 = int((long long)nz * part / split), z1 = int((long long)nz * (part + 1) / split);
+    const int D = H.D, n_exp = (D + 1) / 2, nz = D + (D % 2 == 0 ? 1 : 0), npair = (nz + 1) / 2;
+    const int m0 = int((long long)npair * part / split), m1 = int((long long)npair * (part + 1) / split);
     const int e0 = int((long long)n_exp * part / split), e1 = int((long long)n_exp * (part + 1) / split);
     double zs = 0.0, rs = 0.0;
-    for (int j = z0 + int(threadIdx.x); j < z1; j += kBlock) {
-        const float z = hd_normal(H, index, step, n_exp, j);
-        if (j < D) zs += double(z * z); else rs += double(z * z);
+    for (int m = m0 + int(threadIdx.x); m < m1; m += kBlock) {  // normals 2m and 2m + 1
+        const float2 z = hd_normal_pair(H, index, step, n_exp, m);
+        const float q0 = z.x * z.x, q1 = z.y * z.y;
+        if (2 * m < D) zs += double(q0); else rs += double(q0);
+        if (2 * m + 1 < D) zs += double(q1); else if (2 * m + 1 < nz) rs += double(q1);
     }
     for (int j = e0 + int(threadIdx.x); j < e1; j += kBlock)
         rs += double(-2.0f * logf(perturb_uniform(H, index, step, j)));
@@ -1912,46 +1930,61 @@ __global__ void __launch_bounds__(kBlock) k_hd_norms(const HdDraws H) {
     }
 }
 
-// One thread per (render, parameter): tau, w and theta + tau of every sampler (as the
-// small-D sampler, per dimension), antithetic renders negated.
+// One thread per (render, pair of parameters 2m, 2m + 1): tau, w and theta + tau of every
+// sampler (as the small-D sampler, per dimension), antithetic renders negated. A pair of
+// Box-Muller normals comes from one pair of uniforms, so a thread forms both.
 __global__ void __launch_bounds__(kBlock) k_hd_perturb(const HdDraws H) {
     pdl_enter();
+    const size_t half = (size_t(H.D) + 1) / 2;
     const size_t i = size_t(blockIdx.x) * kBlock + threadIdx.x;
-    if (i >= size_t(H.R) * size_t(H.D)) return;
-    const int r = int(i / size_t(H.D)), d = int(i - size_t(r) * size_t(H.D));
+    if (i >= size_t(H.R) * half) return;
+    const int r = int(i / half), m = int(i - size_t(r) * half);
     const bool anti = H.antithetic && (r & 1);
     const unsigned local = H.antithetic ? unsigned(r >> 1) : unsigned(r), step = hd_step(H);
     const unsigned index = local + unsigned(H.draw_begin);
-    float tt, wt;
+    float tt[2], wt[2];
     if (H.sampler == kRadial) {
-        const float z = hd_normal(H, index, step, (H.D + 1) / 2, d);
+        const float2 z = hd_normal_pair(H, index, step, (H.D + 1) / 2, m);
         const float2 nr = H.norms[local].v;
-        const float dir = z / nr.x;
-        tt = nr.y * dir;
-        wt = H.c_radial * dir;
+        const float dir0 = z.x / nr.x, dir1 = z.y / nr.x;
+        tt[0] = nr.y * dir0;
+        wt[0] = H.c_radial * dir0;
+        tt[1] = nr.y * dir1;
+        wt[1] = H.c_radial * dir1;
     } else if (H.sampler == kPerDim) {
-        const float xi = perturb_uniform(H, index, step, d);
+        const float2 xi2 = perturb_uniform_pair(H, index, step, 2 * m);
         const float c1 = 0.7978845608028654f;  // sqrt(2/pi)
-        if (xi < 0.5f) {
-            tt = -sqrtf(-2.0f * logf(2.0f * xi));
-            wt = -c1;
-        } else {
-            tt = sqrtf(-2.0f * logf(2.0f * (1.0f - xi)));
-            wt = c1;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float xi = k == 0 ? xi2.x : xi2.y;
+            if (xi < 0.5f) {
+                tt[k] = -sqrtf(-2.0f * logf(2.0f * xi));
+                wt[k] = -c1;
+            } else {
+                tt[k] = sqrtf(-2.0f * logf(2.0f * (1.0f - xi)));
+                wt[k] = c1;
+            }
         }
     } else {
-        tt = hd_normal(H, index, step, 0, d);
-        wt = tt;
+        const float2 z = hd_normal_pair(H, index, step, 0, m);
+        tt[0] = wt[0] = z.x;
+        tt[1] = wt[1] = z.y;
     }
-    const float sg = sigma_sched(H.sigma, H.anneal, H.total_steps, H.sigma_min, d, int(step));
-    float tau = sg * tt, w = wt / sg;
-    if (anti) {
-        tau = -tau;
-        w = -w;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int d = 2 * m + k;
+        if (d >= H.D) break;
+        const float sg = sigma_sched(H.sigma, H.anneal, H.total_steps, H.sigma_min, d, int(step));
+        float tau = sg * tt[k], w = wt[k] / sg;
+        if (anti) {
+            tau = -tau;
+            w = -w;
+        }
+        const size_t o = size_t(r) * size_t(H.D) + size_t(d);
+        if (H.theta_out) H.theta_out[o] = H.theta[d] + tau;  // FP32 sum: the parameters this render gets
+        if (H.tau_out) H.tau_out[o] = tau;
+        if (H.w_out) H.w_out[o] = w;
     }
-    if (H.theta_out) H.theta_out[i] = H.theta[d] + tau;  // FP32 sum: the parameters this render gets
-    if (H.tau_out) H.tau_out[i] = tau;
-    if (H.w_out) H.w_out[i] = w;
 }
 
 // a6 + a7 over D parameters: g_d = (1/2P) sum_p w_{2p,d} (L_2p - L_2p+1) (a skinny GEMV,
@@ -1982,7 +2015,7 @@ cudaError_t launch_hd_draws(const HdDraws& H, cudaStream_t stream) {
         const cudaError_t e = launch_pdl(k_hd_norms, (H.antithetic ? H.R / 2 : H.R) * H.norm_split, kBlock, stream, H);
         if (e != cudaSuccess) return e;
     }
-    const size_t n = size_t(H.R) * size_t(H.D);
+    const size_t n = size_t(H.R) * ((size_t(H.D) + 1) / 2);  // one thread per (render, parameter pair)
     return launch_pdl(k_hd_perturb, int((n + kBlock - 1) / kBlock), kBlock, stream, H);
 }
 
