@@ -665,7 +665,8 @@ static prdpt_status fill_diff(TraceJob& J, const BaseScene& B, const prdpt_grad_
     return PRDPT_OK;
 }
 
-static int diff_slots(const TraceJob& J) { return J.diff ? (J.diff_n <= 4 ? 4 : 8) : 0; }
+// tangent slots of the pathwise render kernel: the smallest of 4, 6, 8 that holds every parameter
+static int diff_slots(const TraceJob& J) { return J.diff ? (J.diff_n <= 4 ? 4 : (J.diff_n <= 6 ? 6 : 8)) : 0; }
 
 static void fill_inst_grad(InstJob& J, const Scene* s, const prdpt_grad_opts* o) {
     fill_inst_common(J, s, 2 * o->pairs, s->D, o->width, o->height);

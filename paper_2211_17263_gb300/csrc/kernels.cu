@@ -1800,6 +1800,9 @@ cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaS
     if (L.diff_nd == 4)
         return launch_pdl(count ? k_trace<false, true, false, 4> : k_trace<false, false, false, 4>, grid, kDiffBlock,
                           stream, L);
+    if (L.diff_nd == 6)
+        return launch_pdl(count ? k_trace<false, true, false, 6> : k_trace<false, false, false, 6>, grid, kDiffBlock,
+                          stream, L);
     if (L.diff_nd == 8)
         return launch_pdl(count ? k_trace<false, true, false, 8> : k_trace<false, false, false, 8>, grid, kDiffBlock,
                           stream, L);

@@ -1,7 +1,7 @@
 """GPU parity of the pathwise estimator (Eq. 9, kappa-dP) against the FP64 oracle on the
 same draws and path samples: per-render losses and the mean of the renders' pathwise
 loss gradients, for albedo and emission parameters (depth 1 and multi-bounce with
-Russian roulette, ragged image blocks, 4- and 8-slot tangent kernels), a resident job's
+Russian roulette, ragged image blocks, 4-, 6- and 8-slot tangent kernels), a resident job's
 trajectory, and the argument checks."""
 import numpy as np
 import pytest
@@ -37,7 +37,21 @@ def _cases():
         "small-d3-rr": lambda: workloads.scaled(small(), width=33, height=20, spp=4, pairs=2, depth=3, rr_start=1),
         "small-4-params": lambda: _subset(workloads.scaled(small(), width=24, height=24, spp=2, pairs=2), 4),
         "gi-walls": lambda: workloads.scaled(gi(), width=48, height=37, spp=4, pairs=2),
+        "gi-8-params": lambda: _with_back_wall_rg(workloads.scaled(gi(), width=40, height=32, spp=4, pairs=2)),
     }
+
+
+def _with_back_wall_rg(wl):
+    """Eight parameters (the 8-slot tangent kernel): the two side walls' RGB and material 0's
+    red and green albedo."""
+    m = 0
+    extra = np.array([[workloads.BIND_MAT_ALBEDO, m, 0], [workloads.BIND_MAT_ALBEDO, m, 1]], np.int32)
+    base = wl.scene.mat_param[m, :2].astype(np.float32)
+    wl.bindings = np.vstack([wl.bindings, extra]).astype(np.int32)
+    wl.theta_ref = np.append(wl.theta_ref, base).astype(np.float32)
+    wl.theta0 = np.append(wl.theta0, base + np.float32(0.1)).astype(np.float32)
+    wl.sigma = np.append(wl.sigma, np.full(2, 0.125, np.float32)).astype(np.float32)
+    return wl
 
 
 def _subset(wl, n):
