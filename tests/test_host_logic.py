@@ -29,3 +29,20 @@ def test_block_shapes_cover_images_exactly():
                     assert x < W and y < H
                     seen[y, x] += 1
             assert np.all(seen == 1)
+
+
+def test_profile_hash_ignores_comments_only():
+    """bench.py reports the committed ncu counters only while the kernel sources hash as
+    when they were taken; comment and blank-line edits keep the hash, code edits change it."""
+    import bench
+    src = 'int f(int x) {  // doubles\n    // a comment line\n\n    return 2 * x;\n}\n'
+    commented = 'int f(int x) {  // twice x\n\n    // another comment\n    return 2 * x;  // result\n}\n'
+    changed = 'int f(int x) {  // doubles\n    return 3 * x;\n}\n'
+    assert bench._code_only(src) == bench._code_only(commented)
+    assert bench._code_only(src) != bench._code_only(changed)
+    files = {"paper_2211_17263_gb300/csrc/kernels.cu": src, "paper_2211_17263_gb300/csrc/internal.h": "int g;\n"}
+    h1 = bench._kernel_source_sha(lambda p: files[p])
+    files["paper_2211_17263_gb300/csrc/kernels.cu"] = commented
+    assert bench._kernel_source_sha(lambda p: files[p]) == h1
+    files["paper_2211_17263_gb300/csrc/kernels.cu"] = changed
+    assert bench._kernel_source_sha(lambda p: files[p]) != h1
