@@ -1144,8 +1144,8 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
                 items_share = items;
             }
         }
-        PRDPT_CUDA(cudaStreamSynchronize(st_));  // the old descriptors may still be in use
         if ((size_t)n > c->batch_cap) {
+            PRDPT_CUDA(cudaStreamSynchronize(st_));  // the old arrays may still be in use
             dev_free(c, c->d_inst);
             dev_free(c, c->d_trace);
             c->d_inst = nullptr;
