@@ -372,32 +372,29 @@ def main():
 
     # end to end through the C ABI with host buffers: H2D inputs, gradient, Adam, D2H results
     e2e = None
-    # one pinned host buffer and one device buffer, laid out [target (4HW) | sigma | theta | grad | losses]:
-    # each step uploads [target | sigma | theta] and downloads [theta | grad | losses], one copy each way
+    # through the C ABI with host buffers (prdpt_smoothed_grad_host): each step uploads theta,
+    # sigma and the target from page-locked memory, computes the gradient, downloads the
+    # gradient and the losses, and Adam updates theta on the host
     D, R, npx4 = wl.D, wl.renders, 4 * wl.width * wl.height
-    host = torch.empty(npx4 + 3 * D + R, dtype=torch.float32).pin_memory()
-    host[:npx4] = torch.from_numpy(np.ascontiguousarray(target_host, np.float32).reshape(-1))
-    host[npx4: npx4 + D] = torch.from_numpy(np.ascontiguousarray(wl.sigma, np.float32))
-    host[npx4 + D: npx4 + 2 * D] = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32))
-    buf = torch.empty_like(host, device=f"cuda:{local}")
-    target_d = buf[:npx4].view(wl.height, wl.width, 4)
-    sigma_d, theta_d = buf[npx4: npx4 + D], buf[npx4 + D: npx4 + 2 * D]
-    g_d, L_d = buf[npx4 + 2 * D: npx4 + 3 * D], buf[npx4 + 3 * D:]
-    m_d = torch.zeros(D, dtype=torch.float32, device=f"cuda:{local}")
-    v_d = torch.zeros_like(m_d)
-    out_h = torch.empty(2 * D + R, dtype=torch.float32).pin_memory()
+    theta_h = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32)).pin_memory()
+    sigma_h = torch.from_numpy(np.ascontiguousarray(wl.sigma, np.float32)).pin_memory()
+    target_h = torch.from_numpy(np.ascontiguousarray(target_host, np.float32)).pin_memory()
+    g_h = torch.empty(D, dtype=torch.float32).pin_memory()
+    L_h = torch.empty(R, dtype=torch.float32).pin_memory()
+    th, gv = theta_h.numpy(), g_h.numpy()
+    m_h, v_h = np.zeros(D, np.float32), np.zeros(D, np.float32)
+    b1, b2, eps = np.float32(0.9), np.float32(0.999), np.float32(1e-8)
     h2d = 4 * (npx4 + 2 * D)
-    d2h = 4 * (2 * D + R)
+    d2h = 4 * (D + R)
     opts = scene.grad_opts(wl, step=0)
 
     def e2e_step(k):
-        buf[: npx4 + 2 * D].copy_(host[: npx4 + 2 * D], non_blocking=True)
         opts.step = k
-        scene.smoothed_grad(theta_d, sigma_d, target_d, opts, grad=g_d, losses=L_d)
-        ctx.adam_step(theta_d, m_d, v_d, g_d, k + 1, wl.lr)
-        out_h.copy_(buf[npx4 + D:], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        host[npx4 + D: npx4 + 2 * D] = out_h[:D]  # the next step starts from the updated theta
+        scene.smoothed_grad_host(theta_h, sigma_h, target_h, opts, grad=g_h, losses=L_h)
+        m_h[:] = b1 * m_h + (1 - b1) * gv  # Adam (the kernel's FP32 update, on the host)
+        v_h[:] = b2 * v_h + (1 - b2) * gv * gv
+        bc1, bc2 = -np.expm1((k + 1) * np.log1p(b1 - 1)), -np.expm1((k + 1) * np.log1p(b2 - 1))
+        th[:] = th - np.float32(wl.lr) * (m_h / np.float32(bc1)) / (np.sqrt(v_h / np.float32(bc2)) + eps)
 
     for k in range(args.warmup):
         e2e_step(k)

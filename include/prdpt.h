@@ -21,7 +21,7 @@
  *    enqueue work and return; their device-side results are ready when the stream
  *    reaches that point. Calls without a stream are synchronous.
  *  - Order on the GPU: prdpt_render_batch, prdpt_sample_perturbations,
- *    prdpt_smoothed_grad and prdpt_step_batch use the context's shared scratch
+ *    prdpt_smoothed_grad(_host) and prdpt_step_batch use the context's shared scratch
  *    buffers and work counters, so such calls on one context must execute in order
  *    (one stream, or streams ordered by events). A resident job has buffers of its
  *    own: different jobs may step (prdpt_step) concurrently on different streams,
@@ -191,6 +191,17 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* ctx, int32_t D, const float* 
 prdpt_status prdpt_smoothed_grad(prdpt_ctx* ctx, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
                                  const prdpt_grad_opts* opts, const float* target_dev, float* grad_dev,
                                  float* losses_dev, void* stream);
+
+/* The same gradient with host buffers, for callers whose inputs and results live in host
+ * memory: copies theta_host [D], sigma_host [D] and target_host [H][W][4] into the
+ * context's scratch on `stream`, computes the gradient as prdpt_smoothed_grad, copies
+ * grad_host [D] and losses_host [2P] (NULL allowed) back, and returns when the stream has
+ * reached that point (synchronous). Page-locked host buffers make the copies direct DMA;
+ * pageable ones are staged by the CUDA runtime. Shares the context's scratch (see the
+ * ordering rules above). */
+prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* ctx, int32_t scene_id, const float* theta_host,
+                                      const float* sigma_host, const prdpt_grad_opts* opts, const float* target_host,
+                                      float* grad_host, float* losses_host, void* stream);
 
 /* One Adam update (Sec. 3.4; PyTorch's formula, FP32 arithmetic as its FP32 Adam; t is
  * the 1-based step) of D parameters in place: theta_dev, m_dev, v_dev [D], grad_dev [D]. */

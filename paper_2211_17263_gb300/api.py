@@ -25,6 +25,17 @@ def _dev_ptr(t: torch.Tensor):
     return C.c_void_p(t.data_ptr())
 
 
+def _host_ptr(a):
+    """Address of a contiguous float32 host buffer (numpy array or CPU torch tensor)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("host buffers must be contiguous float32 CPU tensors")
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host buffers must be contiguous float32 arrays")
+    return C.c_void_p(a.ctypes.data)
+
+
 def _np_ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -134,6 +145,18 @@ class Scene:
             seed=wl.seed, step=step, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm,
             no_path_sharing=no_path_sharing,
             estimator=getattr(wl, "estimator", 0) if estimator is None else estimator, pair_begin=pair_begin)
+
+    def smoothed_grad_host(self, theta, sigma, target, opts, grad=None, losses=None, stream=None):
+        """The gradient with host buffers (prdpt_smoothed_grad_host): theta, sigma [D] and target
+        [H, W, 4] float32 in host memory (numpy or CPU tensors; page-locked ones copy fastest);
+        returns (grad [D], losses [2P]) in host memory when the call returns."""
+        if grad is None:
+            grad = np.empty(self.D, np.float32)
+        if losses is None:
+            losses = np.empty(2 * opts.pairs, np.float32)
+        capi.prdpt_smoothed_grad_host(self.ctx.handle, self.id, _host_ptr(theta), _host_ptr(sigma), opts,
+                                      _host_ptr(target), _host_ptr(grad), _host_ptr(losses), _stream_ptr(stream))
+        return grad, losses
 
     def smoothed_grad(self, theta: torch.Tensor, sigma: torch.Tensor, target: torch.Tensor, opts,
                       grad: torch.Tensor | None = None, losses: torch.Tensor | None = None, stream=None):

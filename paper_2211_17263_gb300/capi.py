@@ -33,7 +33,7 @@ EXPORTS = [
     "prdpt_job_create", "prdpt_step", "prdpt_step_batch", "prdpt_job_read", "prdpt_job_release",
     "prdpt_philox_words", "prdpt_counters_enable", "prdpt_counters_read", "prdpt_kernel_timing_enable",
     "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static", "prdpt_memory_used",
-    "prdpt_fp32_peak_probe",
+    "prdpt_fp32_peak_probe", "prdpt_smoothed_grad_host",
 ]
 
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         "prdpt_render_batch": ([vp, i32, vp, i32, P(prdpt_render_opts), vp, vp], i32),
         "prdpt_sample_perturbations": ([vp, i32, vp, P(prdpt_grad_opts), vp, vp, vp], i32),
         "prdpt_smoothed_grad": ([vp, i32, vp, vp, P(prdpt_grad_opts), vp, vp, vp, vp], i32),
+        "prdpt_smoothed_grad_host": ([vp, i32, vp, vp, P(prdpt_grad_opts), vp, vp, vp, vp], i32),
         "prdpt_adam_step": ([vp, i32, vp, vp, vp, vp, i32, f32, f32, f32, f32, vp], i32),
         "prdpt_job_create": ([vp, i32, P(prdpt_job_desc), P(i32)], i32),
         "prdpt_step": ([vp, i32, vp], i32),
@@ -178,6 +179,12 @@ def prdpt_sample_perturbations(ctx, D, sigma_dev, opts, tau_dev, w_dev, stream):
 def prdpt_smoothed_grad(ctx, scene_id, theta_dev, sigma_dev, opts, target_dev, grad_dev, losses_dev, stream):
     return check(load().prdpt_smoothed_grad(ctx, scene_id, theta_dev, sigma_dev, C.byref(opts), target_dev, grad_dev,
                                             losses_dev, stream), "prdpt_smoothed_grad", ctx)
+
+
+def prdpt_smoothed_grad_host(ctx, scene_id, theta_host, sigma_host, opts, target_host, grad_host, losses_host,
+                             stream):
+    return check(load().prdpt_smoothed_grad_host(ctx, scene_id, theta_host, sigma_host, C.byref(opts), target_host,
+                                                 grad_host, losses_host, stream), "prdpt_smoothed_grad_host", ctx)
 
 
 def prdpt_adam_step(ctx, D, theta_dev, m_dev, v_dev, grad_dev, t, lr, beta1, beta2, eps, stream):

@@ -85,6 +85,8 @@ struct prdpt_ctx {
     size_t s_scenes_n = 0;
     float* s_w = nullptr;
     size_t s_w_n = 0;
+    float* s_host_io = nullptr;   // prdpt_smoothed_grad_host: theta, sigma, target, grad, losses
+    size_t s_host_io_n = 0;
     double* s_partials = nullptr;
     size_t s_partials_n = 0;
     double* s_losses = nullptr;
@@ -849,6 +851,43 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
         G.grad_out = grad_dev;
         PRDPT_CUDA(launch_hd_grad(G, st_));
     }
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* c, int32_t scene_id, const float* theta_host,
+                                      const float* sigma_host, const prdpt_grad_opts* o, const float* target_host,
+                                      float* grad_host, float* losses_host, void* stream) {
+    if (!c || !o || !theta_host || !sigma_host || !target_host || !grad_host)
+        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    float *theta_d, *sigma_d, *target_d, *grad_d, *losses_d;
+    size_t D, R;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        Scene* s = get_scene(c, scene_id);
+        if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
+        if (prdpt_status st = check_grad_opts(o)) return st;
+        PRDPT_CUDA(cudaSetDevice(c->device));
+        D = size_t(s->D);
+        R = 2 * size_t(o->pairs);
+        const size_t pix4 = 4 * size_t(o->width) * size_t(o->height);
+        // [target (16-byte aligned for float4 loads) | theta | sigma | grad | losses]
+        if (prdpt_status st = grow(c, &c->s_host_io, &c->s_host_io_n, pix4 + 3 * D + R)) return st;
+        target_d = c->s_host_io;
+        theta_d = target_d + pix4;
+        sigma_d = theta_d + D;
+        grad_d = sigma_d + D;
+        losses_d = grad_d + D;
+        PRDPT_CUDA(cudaMemcpyAsync(target_d, target_host, sizeof(float) * pix4, cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(theta_d, theta_host, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(sigma_d, sigma_host, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+    }
+    if (prdpt_status st = prdpt_smoothed_grad(c, scene_id, theta_d, sigma_d, o, target_d, grad_d, losses_d, stream))
+        return st;
+    PRDPT_CUDA(cudaMemcpyAsync(grad_host, grad_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
+    if (losses_host)
+        PRDPT_CUDA(cudaMemcpyAsync(losses_host, losses_d, sizeof(float) * R, cudaMemcpyDeviceToHost, st_));
+    PRDPT_CUDA(cudaStreamSynchronize(st_));
     return PRDPT_OK;
 }
 
