@@ -197,6 +197,14 @@ int choose_block(prdpt_ctx* c, int requested, int R, int W, int H, bool render) 
     return 8;
 }
 
+// The render kernels number their work items (render x pixel block) with 32-bit integers.
+prdpt_status check_items(long long items) {
+    if (items > 0x7fffffffLL)
+        return fail(PRDPT_E_INVALID_ARG, "more than 2^31 - 1 work items (renders x pixel blocks): use larger "
+                                         "blocks, fewer renders or a smaller image");
+    return PRDPT_OK;
+}
+
 void tiles_for(int pixels, int W, int H, int* bw, int* bh, int* tiles_x, int* tiles) {
     block_shape(pixels, bw, bh);
     *tiles_x = (W + *bw - 1) / *bw;
@@ -599,6 +607,7 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     J.n_prims = s->host.n_prims;
     J.n_mats = s->host.n_mats;
     tiles_for(px, o->width, o->height, &J.bw, &J.bh, &J.tiles_x, &J.tiles);
+    if (prdpt_status st = check_items((long long)n * J.tiles)) return st;
     TL.total_items = n * J.tiles;
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
@@ -751,6 +760,7 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, o->width, o->height, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, o->width, o->height, &bw, &bh, &tiles_x, &tiles);
+    if (prdpt_status st = check_items(probe.share ? (long long)tiles : (long long)R * tiles)) return st;
     if (probe.share) {
         const size_t pix = (size_t)o->width * o->height;
         if (prdpt_status st = grow(c, &c->s_share, &c->s_share_n, (size_t)tiles * 96)) return st;
@@ -922,6 +932,10 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, W, H, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, W, H, &bw, &bh, &tiles_x, &tiles);
+    if (prdpt_status st = check_items(probe.share ? (long long)tiles : (long long)R * tiles)) {
+        delete j;
+        return st;
+    }
     j->tiles = tiles;
     j->ctas_per_sm = o->ctas_per_sm;
     // one device block per job: small state first (zeroed), then w, partials, scenes, target
@@ -1177,6 +1191,8 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             trace[i] = j->trace;
             trace[i].item_begin = items;
             trace[i].fin_begin = blocks - j->R;  // same prefix as the sampler CTAs
+            if (prdpt_status st = check_items((long long)items + (j->trace.share ? j->tiles : j->R * j->tiles)))
+                return st;
             items += j->trace.share ? j->tiles : j->R * j->tiles;
             if (j->trace.share) {
                 nshare++;

@@ -182,3 +182,22 @@ def test_jobs_step_concurrently_on_their_own_streams(ctx):
         for key in ("theta", "grad", "losses"):
             assert np.array_equal(a[key], b[key]), key
         j.release()
+
+
+def test_too_many_work_items_is_an_argument_error(ctx):
+    """The render kernels number (render, pixel block) work items with 32-bit integers: a
+    job of 512 renders of 8192^2 pixels in 8-pixel blocks (4.3 G items) is refused with an
+    argument error before anything is allocated or read."""
+    from paper_2211_17263_gb300 import api, capi
+    wl = workloads.config_occlusion()
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    small = np.zeros(16, np.float32)  # never read: the call fails before the uploads
+    opts = scene.grad_opts(wl, pairs=256, block_pixels=8, no_path_sharing=1)
+    opts.width = opts.height = 8192
+    desc = capi.prdpt_job_desc(grad=opts, theta0_host=small.ctypes.data, sigma0_host=small.ctypes.data,
+                               target_host=small.ctypes.data, lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8,
+                               sigma_min=0.01, anneal=0, total_steps=1)
+    before = ctx.memory_used()
+    with pytest.raises(capi.PrdptError, match="work items"):
+        capi.prdpt_job_create(ctx.handle, scene.id, desc)
+    assert ctx.memory_used() == before
