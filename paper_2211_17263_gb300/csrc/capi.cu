@@ -477,14 +477,15 @@ prdpt_status prdpt_scene_release(prdpt_ctx* c, int32_t scene_id) {
 }
 
 // Path sharing across renders is exact when all renders share their path samples (crn)
-// and only geometry is perturbed: emitters and their materials must stay fixed, at most
-// kMaxVariant primitives move, and a pixel's samples fit one 64-bit mask.
+// and emitters stay fixed: at most kMaxVariant primitives move (bound materials other
+// than emitters' are allowed: a path that meets one is traced again by every render), and
+// a recorded path's sample index fits the 6 bits of its code (spp <= kMaxShareSpp).
 // Recorded-path list of a path-sharing job with room for n paths: codes and segment
 // words (u32) and shared-pass radiance (3 floats), then the touching-segment pool
-// (2 float4 per slot, kSeg slots per path for one path in 16; a path that finds the
-// pool full is traced again by every render).
+// (2 float4 per slot, kSeg slots and one path state for one path in 8, at least 4096
+// paths; a path that finds the pool full is traced again by every render from the camera).
 static size_t seg_slots(size_t n) {
-    const size_t paths = n / 16 > 4096 ? n / 16 : 4096;
+    const size_t paths = n / 8 > 4096 ? n / 8 : 4096;
     return paths * kSeg;
 }
 
