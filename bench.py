@@ -382,29 +382,20 @@ def main():
 
     # end to end through the C ABI with host buffers: H2D inputs, gradient, Adam, D2H results
     e2e = None
-    # through the C ABI with host buffers (prdpt_smoothed_grad_host): each step uploads theta,
-    # sigma and the target from page-locked memory, computes the gradient, downloads the
-    # gradient and the losses, and Adam updates theta on the host
+    # through the C ABI with host buffers (prdpt_step_host): each step uploads theta, Adam's
+    # m and v, sigma and the target from page-locked memory, computes the gradient, applies
+    # Adam on the device and downloads theta, m, v, the gradient and the losses
     D, R, npx4 = wl.D, wl.renders, 4 * wl.width * wl.height
-    theta_h = torch.from_numpy(np.ascontiguousarray(wl.theta0, np.float32)).pin_memory()
-    sigma_h = torch.from_numpy(np.ascontiguousarray(wl.sigma, np.float32)).pin_memory()
-    target_h = torch.from_numpy(np.ascontiguousarray(target_host, np.float32)).pin_memory()
-    g_h = torch.empty(D, dtype=torch.float32).pin_memory()
-    L_h = torch.empty(R, dtype=torch.float32).pin_memory()
-    th, gv = theta_h.numpy(), g_h.numpy()
-    m_h, v_h = np.zeros(D, np.float32), np.zeros(D, np.float32)
-    b1, b2, eps = np.float32(0.9), np.float32(0.999), np.float32(1e-8)
-    h2d = 4 * (npx4 + 2 * D)
-    d2h = 4 * (D + R)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()  # noqa: E731
+    theta_h, sigma_h, target_h = pin(wl.theta0), pin(wl.sigma), pin(target_host)
+    m_h, v_h, g_h, L_h = pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(R))
+    h2d = 4 * (npx4 + 4 * D)
+    d2h = 4 * (4 * D + R)
     opts = scene.grad_opts(wl, step=0)
 
     def e2e_step(k):
         opts.step = k
-        scene.smoothed_grad_host(theta_h, sigma_h, target_h, opts, grad=g_h, losses=L_h)
-        m_h[:] = b1 * m_h + (1 - b1) * gv  # Adam (the kernel's FP32 update, on the host)
-        v_h[:] = b2 * v_h + (1 - b2) * gv * gv
-        bc1, bc2 = -np.expm1((k + 1) * np.log1p(b1 - 1)), -np.expm1((k + 1) * np.log1p(b2 - 1))
-        th[:] = th - np.float32(wl.lr) * (m_h / np.float32(bc1)) / (np.sqrt(v_h / np.float32(bc2)) + eps)
+        scene.step_host(theta_h, m_h, v_h, k + 1, wl.lr, sigma_h, target_h, opts, grad=g_h, losses=L_h)
 
     for k in range(args.warmup):
         e2e_step(k)

@@ -21,7 +21,7 @@
  *    enqueue work and return; their device-side results are ready when the stream
  *    reaches that point. Calls without a stream are synchronous.
  *  - Order on the GPU: prdpt_render_batch, prdpt_sample_perturbations,
- *    prdpt_smoothed_grad(_host) and prdpt_step_batch use the context's shared scratch
+ *    prdpt_smoothed_grad(_host), prdpt_step_host and prdpt_step_batch use the context's shared scratch
  *    buffers and work counters, so such calls on one context must execute in order
  *    (one stream, or streams ordered by events). A resident job has buffers of its
  *    own: different jobs may step (prdpt_step) concurrently on different streams,
@@ -202,6 +202,16 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* ctx, int32_t scene_id, const float* 
 prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* ctx, int32_t scene_id, const float* theta_host,
                                       const float* sigma_host, const prdpt_grad_opts* opts, const float* target_host,
                                       float* grad_host, float* losses_host, void* stream);
+
+/* A whole optimisation step with host buffers: the gradient as prdpt_smoothed_grad_host
+ * at theta_host, then one Adam update (as prdpt_adam_step, step t >= 1, lr, beta1, beta2,
+ * eps) of theta_host, m_host and v_host [D], which are read and written back in place.
+ * grad_host [D] and losses_host [2P] receive the step's gradient and losses (either may be
+ * NULL). Synchronous; shares the context's scratch like prdpt_smoothed_grad_host. */
+prdpt_status prdpt_step_host(prdpt_ctx* ctx, int32_t scene_id, float* theta_host, float* m_host, float* v_host,
+                             int32_t t, float lr, float beta1, float beta2, float eps, const float* sigma_host,
+                             const prdpt_grad_opts* opts, const float* target_host, float* grad_host,
+                             float* losses_host, void* stream);
 
 /* One Adam update (Sec. 3.4; PyTorch's formula, FP32 arithmetic as its FP32 Adam; t is
  * the 1-based step) of D parameters in place: theta_dev, m_dev, v_dev [D], grad_dev [D]. */

@@ -158,6 +158,16 @@ class Scene:
                                       _host_ptr(target), _host_ptr(grad), _host_ptr(losses), _stream_ptr(stream))
         return grad, losses
 
+    def step_host(self, theta, m, v, t, lr, sigma, target, opts, grad=None, losses=None, beta1=0.9, beta2=0.999,
+                  eps=1e-8, stream=None):
+        """One optimisation step with host buffers (prdpt_step_host): the gradient at theta,
+        then Adam step t (1-based) updating theta, m, v [D] (float32 host arrays) in place.
+        grad [D] and losses [2P], if given, receive the step's gradient and losses."""
+        capi.prdpt_step_host(self.ctx.handle, self.id, _host_ptr(theta), _host_ptr(m), _host_ptr(v), int(t), lr,
+                             beta1, beta2, eps, _host_ptr(sigma), opts, _host_ptr(target),
+                             None if grad is None else _host_ptr(grad), None if losses is None else _host_ptr(losses),
+                             _stream_ptr(stream))
+
     def smoothed_grad(self, theta: torch.Tensor, sigma: torch.Tensor, target: torch.Tensor, opts,
                       grad: torch.Tensor | None = None, losses: torch.Tensor | None = None, stream=None):
         if grad is None:

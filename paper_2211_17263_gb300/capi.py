@@ -33,7 +33,7 @@ EXPORTS = [
     "prdpt_job_create", "prdpt_step", "prdpt_step_batch", "prdpt_job_read", "prdpt_job_release",
     "prdpt_philox_words", "prdpt_counters_enable", "prdpt_counters_read", "prdpt_kernel_timing_enable",
     "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static", "prdpt_memory_used",
-    "prdpt_fp32_peak_probe", "prdpt_smoothed_grad_host",
+    "prdpt_fp32_peak_probe", "prdpt_smoothed_grad_host", "prdpt_step_host",
 ]
 
 
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
         "prdpt_sample_perturbations": ([vp, i32, vp, P(prdpt_grad_opts), vp, vp, vp], i32),
         "prdpt_smoothed_grad": ([vp, i32, vp, vp, P(prdpt_grad_opts), vp, vp, vp, vp], i32),
         "prdpt_smoothed_grad_host": ([vp, i32, vp, vp, P(prdpt_grad_opts), vp, vp, vp, vp], i32),
+        "prdpt_step_host": ([vp, i32, vp, vp, vp, i32, f32, f32, f32, f32, vp, P(prdpt_grad_opts), vp, vp, vp, vp],
+                            i32),
         "prdpt_adam_step": ([vp, i32, vp, vp, vp, vp, i32, f32, f32, f32, f32, vp], i32),
         "prdpt_job_create": ([vp, i32, P(prdpt_job_desc), P(i32)], i32),
         "prdpt_step": ([vp, i32, vp], i32),
@@ -185,6 +187,13 @@ def prdpt_smoothed_grad_host(ctx, scene_id, theta_host, sigma_host, opts, target
                              stream):
     return check(load().prdpt_smoothed_grad_host(ctx, scene_id, theta_host, sigma_host, C.byref(opts), target_host,
                                                  grad_host, losses_host, stream), "prdpt_smoothed_grad_host", ctx)
+
+
+def prdpt_step_host(ctx, scene_id, theta_host, m_host, v_host, t, lr, beta1, beta2, eps, sigma_host, opts,
+                    target_host, grad_host, losses_host, stream):
+    return check(load().prdpt_step_host(ctx, scene_id, theta_host, m_host, v_host, t, lr, beta1, beta2, eps,
+                                        sigma_host, C.byref(opts), target_host, grad_host, losses_host, stream),
+                 "prdpt_step_host", ctx)
 
 
 def prdpt_adam_step(ctx, D, theta_dev, m_dev, v_dev, grad_dev, t, lr, beta1, beta2, eps, stream):

@@ -865,13 +865,22 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     return PRDPT_OK;
 }
 
-prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* c, int32_t scene_id, const float* theta_host,
-                                      const float* sigma_host, const prdpt_grad_opts* o, const float* target_host,
-                                      float* grad_host, float* losses_host, void* stream) {
-    if (!c || !o || !theta_host || !sigma_host || !target_host || !grad_host)
-        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+struct HostAdam {  // prdpt_step_host: Adam state in host memory, updated in place
+    float *theta, *m, *v;
+    int t;
+    float lr, b1, b2, eps;
+};
+
+// The gradient with host buffers, and with `adam` one Adam update of theta, m, v.
+prdpt_status host_buffer_call(prdpt_ctx* c, int32_t scene_id, const float* theta_host, const float* sigma_host,
+                              const prdpt_grad_opts* o, const float* target_host, float* grad_host,
+                              float* losses_host, void* stream, const HostAdam* adam) {
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
-    float *theta_d, *sigma_d, *target_d, *grad_d, *losses_d;
+    float *theta_d, *sigma_d, *target_d, *grad_d, *losses_d, *m_d, *v_d;
     size_t D, R;
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -882,24 +891,63 @@ prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* c, int32_t scene_id, const floa
         D = size_t(s->D);
         R = 2 * size_t(o->pairs);
         const size_t pix4 = 4 * size_t(o->width) * size_t(o->height);
-        // [target (16-byte aligned for float4 loads) | theta | sigma | grad | losses]
-        if (prdpt_status st = grow(c, &c->s_host_io, &c->s_host_io_n, pix4 + 3 * D + R)) return st;
+        // [target (16-byte aligned for float4 loads) | theta | sigma | grad | losses | m | v]
+        if (prdpt_status st = grow(c, &c->s_host_io, &c->s_host_io_n, pix4 + 5 * D + R)) return st;
         target_d = c->s_host_io;
         theta_d = target_d + pix4;
         sigma_d = theta_d + D;
         grad_d = sigma_d + D;
         losses_d = grad_d + D;
+        m_d = losses_d + R;
+        v_d = m_d + D;
         PRDPT_CUDA(cudaMemcpyAsync(target_d, target_host, sizeof(float) * pix4, cudaMemcpyHostToDevice, st_));
         PRDPT_CUDA(cudaMemcpyAsync(theta_d, theta_host, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
         PRDPT_CUDA(cudaMemcpyAsync(sigma_d, sigma_host, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+        if (adam) {
+            PRDPT_CUDA(cudaMemcpyAsync(m_d, adam->m, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+            PRDPT_CUDA(cudaMemcpyAsync(v_d, adam->v, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+        }
     }
     if (prdpt_status st = prdpt_smoothed_grad(c, scene_id, theta_d, sigma_d, o, target_d, grad_d, losses_d, stream))
         return st;
-    PRDPT_CUDA(cudaMemcpyAsync(grad_host, grad_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
+    if (adam) {
+        if (prdpt_status st = prdpt_adam_step(c, int32_t(D), theta_d, m_d, v_d, grad_d, adam->t, adam->lr, adam->b1,
+                                              adam->b2, adam->eps, stream))
+            return st;
+        PRDPT_CUDA(cudaMemcpyAsync(adam->theta, theta_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(adam->m, m_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(adam->v, v_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
+    }
+    if (grad_host) PRDPT_CUDA(cudaMemcpyAsync(grad_host, grad_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
     if (losses_host)
         PRDPT_CUDA(cudaMemcpyAsync(losses_host, losses_d, sizeof(float) * R, cudaMemcpyDeviceToHost, st_));
     PRDPT_CUDA(cudaStreamSynchronize(st_));
     return PRDPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* c, int32_t scene_id, const float* theta_host,
+                                      const float* sigma_host, const prdpt_grad_opts* o, const float* target_host,
+                                      float* grad_host, float* losses_host, void* stream) {
+    if (!c || !o || !theta_host || !sigma_host || !target_host || !grad_host)
+        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    return host_buffer_call(c, scene_id, theta_host, sigma_host, o, target_host, grad_host, losses_host, stream,
+                            nullptr);
+}
+
+prdpt_status prdpt_step_host(prdpt_ctx* c, int32_t scene_id, float* theta_host, float* m_host, float* v_host,
+                             int32_t t, float lr, float beta1, float beta2, float eps, const float* sigma_host,
+                             const prdpt_grad_opts* o, const float* target_host, float* grad_host,
+                             float* losses_host, void* stream) {
+    if (!c || !o || !theta_host || !m_host || !v_host || !sigma_host || !target_host)
+        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    if (t < 1) return fail(PRDPT_E_INVALID_ARG, "t must be >= 1");
+    const HostAdam adam{theta_host, m_host, v_host, t, lr, beta1, beta2, eps};
+    return host_buffer_call(c, scene_id, theta_host, sigma_host, o, target_host, grad_host, losses_host, stream,
+                            &adam);
 }
 
 prdpt_status prdpt_adam_step(prdpt_ctx* c, int32_t D, float* theta_dev, float* m_dev, float* v_dev,

@@ -228,3 +228,26 @@ def test_host_buffer_gradient_equals_device_call(ctx):
             th, sg, tg = (torch.from_numpy(a).pin_memory() for a in (th, sg, tg))
         g, L = scene.smoothed_grad_host(th, sg, tg, opts)
         assert np.array_equal(g, g_dev.cpu().numpy()) and np.array_equal(L, L_dev.cpu().numpy())
+
+
+def test_host_buffer_step_follows_the_device_calls(ctx):
+    """prdpt_step_host (gradient and Adam with theta, m, v in host memory) follows, bit for
+    bit over three steps, the trajectory of prdpt_smoothed_grad plus prdpt_adam_step on
+    device buffers."""
+    wl = workloads.scaled(workloads.config_occlusion(), width=40, height=32, spp=4, pairs=3)
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = oracle.render_target(wl).astype(np.float32)
+    th_d, m_d, v_d = _t(wl.theta0), torch.zeros(wl.D, device="cuda"), torch.zeros(wl.D, device="cuda")
+    th_h = np.ascontiguousarray(wl.theta0, np.float32)
+    m_h, v_h = np.zeros(wl.D, np.float32), np.zeros(wl.D, np.float32)
+    g_h, L_h = np.empty(wl.D, np.float32), np.empty(wl.renders, np.float32)
+    sg, tg = np.ascontiguousarray(wl.sigma, np.float32), np.ascontiguousarray(target)
+    for t in range(3):
+        opts = scene.grad_opts(wl, step=t)
+        g_d, L_d = scene.smoothed_grad(th_d, _t(wl.sigma), _t(target), opts)
+        ctx.adam_step(th_d, m_d, v_d, g_d, t + 1, wl.lr)
+        scene.step_host(th_h, m_h, v_h, t + 1, wl.lr, sg, tg, opts, grad=g_h, losses=L_h)
+        torch.cuda.synchronize()
+        assert np.array_equal(g_h, g_d.cpu().numpy()) and np.array_equal(L_h, L_d.cpu().numpy())
+        for host, dev in ((th_h, th_d), (m_h, m_d), (v_h, v_d)):
+            assert np.array_equal(host, dev.cpu().numpy())
