@@ -196,9 +196,11 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* ctx, int32_t scene_id, const float* 
  * memory: copies theta_host [D], sigma_host [D] and target_host [H][W][4] into the
  * context's scratch on `stream`, computes the gradient as prdpt_smoothed_grad, copies
  * grad_host [D] and losses_host [2P] (NULL allowed) back, and returns when the stream has
- * reached that point (synchronous). Page-locked host buffers make the copies direct DMA;
- * pageable ones are staged by the CUDA runtime. Shares the context's scratch (see the
- * ordering rules above). */
+ * reached that point (synchronous). theta and sigma travel through a page-locked staging
+ * buffer of the context; a page-locked target is copied by direct DMA, a pageable one is
+ * staged by the CUDA runtime. Holds the context for the whole call (concurrent calls on
+ * one context from several host threads run one after another) and shares its scratch
+ * (see the ordering rules above). */
 prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* ctx, int32_t scene_id, const float* theta_host,
                                       const float* sigma_host, const prdpt_grad_opts* opts, const float* target_host,
                                       float* grad_host, float* losses_host, void* stream);

@@ -85,8 +85,10 @@ struct prdpt_ctx {
     size_t s_scenes_n = 0;
     float* s_w = nullptr;
     size_t s_w_n = 0;
-    float* s_host_io = nullptr;   // prdpt_smoothed_grad_host: theta, sigma, target, grad, losses
+    float* s_host_io = nullptr;   // host-buffer calls: target, theta, sigma, m, v, grad, losses
     size_t s_host_io_n = 0;
+    float* h_stage = nullptr;     // host-buffer calls: page-locked staging of the small vectors
+    size_t h_stage_n = 0;
     double* s_partials = nullptr;
     size_t s_partials_n = 0;
     double* s_losses = nullptr;
@@ -335,6 +337,7 @@ prdpt_status prdpt_destroy(prdpt_ctx* c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto& kv : c->allocs) cudaFree(kv.first);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
     for (auto& ev : c->ev_used) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -744,12 +747,14 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* si
     return PRDPT_OK;
 }
 
-prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
-                                 const prdpt_grad_opts* o, const float* target_dev, float* grad_dev,
-                                 float* losses_dev, void* stream) {
-    if (!c || !o || !theta_dev || !sigma_dev || !target_dev || !grad_dev)
-        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
-    std::lock_guard<std::mutex> lk(c->mu);
+}  // extern "C"
+
+namespace {
+
+// prdpt_smoothed_grad with the context's mutex held by the caller.
+prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
+                                  const prdpt_grad_opts* o, const float* target_dev, float* grad_dev,
+                                  float* losses_dev, void* stream) {
     Scene* s = get_scene(c, scene_id);
     if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
     if (prdpt_status st = check_grad_opts(o)) return st;
@@ -865,6 +870,19 @@ prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* th
     return PRDPT_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+prdpt_status prdpt_smoothed_grad(prdpt_ctx* c, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
+                                 const prdpt_grad_opts* o, const float* target_dev, float* grad_dev,
+                                 float* losses_dev, void* stream) {
+    if (!c || !o || !theta_dev || !sigma_dev || !target_dev || !grad_dev)
+        return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    return smoothed_grad_locked(c, scene_id, theta_dev, sigma_dev, o, target_dev, grad_dev, losses_dev, stream);
+}
+
 }  // extern "C"
 
 namespace {
@@ -875,53 +893,68 @@ struct HostAdam {  // prdpt_step_host: Adam state in host memory, updated in pla
     float lr, b1, b2, eps;
 };
 
-// The gradient with host buffers, and with `adam` one Adam update of theta, m, v.
+// The gradient with host buffers, and with `adam` one Adam update of theta, m, v. The
+// small vectors go through a page-locked staging buffer (one upload, one download); the
+// target is copied straight from the caller's buffer.
 prdpt_status host_buffer_call(prdpt_ctx* c, int32_t scene_id, const float* theta_host, const float* sigma_host,
                               const prdpt_grad_opts* o, const float* target_host, float* grad_host,
                               float* losses_host, void* stream, const HostAdam* adam) {
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
-    float *theta_d, *sigma_d, *target_d, *grad_d, *losses_d, *m_d, *v_d;
+    float *theta_d, *sigma_d, *target_d, *grad_d, *losses_d, *m_d, *v_d, *stage;
     size_t D, R;
+    std::lock_guard<std::mutex> lk(c->mu);  // the whole call: the scratch and staging are per context
     {
-        std::lock_guard<std::mutex> lk(c->mu);
         Scene* s = get_scene(c, scene_id);
         if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
         if (prdpt_status st = check_grad_opts(o)) return st;
         PRDPT_CUDA(cudaSetDevice(c->device));
         D = size_t(s->D);
         R = 2 * size_t(o->pairs);
-        const size_t pix4 = 4 * size_t(o->width) * size_t(o->height);
-        // [target (16-byte aligned for float4 loads) | theta | sigma | grad | losses | m | v]
-        if (prdpt_status st = grow(c, &c->s_host_io, &c->s_host_io_n, pix4 + 5 * D + R)) return st;
+        const size_t pix4 = 4 * size_t(o->width) * size_t(o->height), small = 5 * D + R;
+        // device: [target (16-byte aligned for float4 loads) | theta | sigma | m | v | grad | losses]
+        if (prdpt_status st = grow(c, &c->s_host_io, &c->s_host_io_n, pix4 + small)) return st;
+        if (c->h_stage_n < small) {  // the previous call has synchronised: the old buffer is idle
+            if (c->h_stage) cudaFreeHost(c->h_stage);
+            c->h_stage = nullptr;
+            c->h_stage_n = 0;
+            void* p = nullptr;
+            PRDPT_CUDA(cudaHostAlloc(&p, sizeof(float) * small, cudaHostAllocDefault));
+            c->h_stage = static_cast<float*>(p);
+            c->h_stage_n = small;
+        }
+        stage = c->h_stage;
         target_d = c->s_host_io;
         theta_d = target_d + pix4;
         sigma_d = theta_d + D;
-        grad_d = sigma_d + D;
-        losses_d = grad_d + D;
-        m_d = losses_d + R;
+        m_d = sigma_d + D;
         v_d = m_d + D;
-        PRDPT_CUDA(cudaMemcpyAsync(target_d, target_host, sizeof(float) * pix4, cudaMemcpyHostToDevice, st_));
-        PRDPT_CUDA(cudaMemcpyAsync(theta_d, theta_host, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
-        PRDPT_CUDA(cudaMemcpyAsync(sigma_d, sigma_host, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+        grad_d = v_d + D;
+        losses_d = grad_d + D;
+        std::memcpy(stage, theta_host, sizeof(float) * D);
+        std::memcpy(stage + D, sigma_host, sizeof(float) * D);
         if (adam) {
-            PRDPT_CUDA(cudaMemcpyAsync(m_d, adam->m, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
-            PRDPT_CUDA(cudaMemcpyAsync(v_d, adam->v, sizeof(float) * D, cudaMemcpyHostToDevice, st_));
+            std::memcpy(stage + 2 * D, adam->m, sizeof(float) * D);
+            std::memcpy(stage + 3 * D, adam->v, sizeof(float) * D);
         }
+        PRDPT_CUDA(cudaMemcpyAsync(theta_d, stage, sizeof(float) * (adam ? 4 : 2) * D, cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(target_d, target_host, sizeof(float) * pix4, cudaMemcpyHostToDevice, st_));
     }
-    if (prdpt_status st = prdpt_smoothed_grad(c, scene_id, theta_d, sigma_d, o, target_d, grad_d, losses_d, stream))
+    if (prdpt_status st = smoothed_grad_locked(c, scene_id, theta_d, sigma_d, o, target_d, grad_d, losses_d, stream))
         return st;
-    if (adam) {
+    if (adam)
         if (prdpt_status st = prdpt_adam_step(c, int32_t(D), theta_d, m_d, v_d, grad_d, adam->t, adam->lr, adam->b1,
                                               adam->b2, adam->eps, stream))
             return st;
-        PRDPT_CUDA(cudaMemcpyAsync(adam->theta, theta_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
-        PRDPT_CUDA(cudaMemcpyAsync(adam->m, m_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
-        PRDPT_CUDA(cudaMemcpyAsync(adam->v, v_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
-    }
-    if (grad_host) PRDPT_CUDA(cudaMemcpyAsync(grad_host, grad_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st_));
-    if (losses_host)
-        PRDPT_CUDA(cudaMemcpyAsync(losses_host, losses_d, sizeof(float) * R, cudaMemcpyDeviceToHost, st_));
+    // one download of [theta | sigma | m | v | grad | losses] into the staging buffer
+    PRDPT_CUDA(cudaMemcpyAsync(stage, theta_d, sizeof(float) * (5 * D + R), cudaMemcpyDeviceToHost, st_));
     PRDPT_CUDA(cudaStreamSynchronize(st_));
+    if (adam) {
+        std::memcpy(adam->theta, stage, sizeof(float) * D);
+        std::memcpy(adam->m, stage + 2 * D, sizeof(float) * D);
+        std::memcpy(adam->v, stage + 3 * D, sizeof(float) * D);
+    }
+    if (grad_host) std::memcpy(grad_host, stage + 4 * D, sizeof(float) * D);
+    if (losses_host) std::memcpy(losses_host, stage + 5 * D, sizeof(float) * R);
     return PRDPT_OK;
 }
 
