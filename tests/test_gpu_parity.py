@@ -175,6 +175,30 @@ def _occlusion_with_albedo():
     return wl
 
 
+def _moving_primitive(wl, prim, offset):
+    """wl with theta = the position of primitive `prim` (sigma 0.05), started at `offset`."""
+    c0 = wl.scene.prim_geom[prim, :3].astype(np.float32)
+    wl.bindings = np.array([[workloads.BIND_PRIM_POS, prim, c] for c in range(3)], np.int32)
+    wl.theta_ref = c0.copy()
+    wl.theta0 = (c0 + np.asarray(offset, np.float32)).astype(np.float32)
+    wl.sigma = np.full(3, 0.05, np.float32)
+    return wl
+
+
+def _gi_box_moving_box():
+    """The GI box with a moving box beside the mirror sphere (mirror bounces, Russian
+    roulette): renders resume after specular vertices with their emission flag."""
+    wl = workloads.scaled(workloads.config_gi_box(), width=40, height=32, spp=4, pairs=3)
+    return _moving_primitive(wl, 5, (0.05, -0.03, 0.0))
+
+
+def _caustic_moving_glass():
+    """The caustic scene with the glass sphere moving: paths refract through the moving
+    primitive and reach the light after dielectric bounces."""
+    wl = workloads.scaled(workloads.config_caustic(), width=40, height=40, spp=4, pairs=3)
+    return _moving_primitive(wl, 1, (0.04, 0.02, -0.03))
+
+
 def _small_pool_overflow():
     """sigma = 1.5: the union of the sphere's bounds covers the view, every path touches it
     and the segment pool (4096 paths here) runs out; the later paths are traced again from
@@ -195,7 +219,8 @@ def _small_pool_overflow():
                                   # depth 6 with Russian roulette: renders resume mid-path
                                   lambda: workloads.scaled(workloads.config_occlusion(), width=48, height=40, spp=4,
                                                            pairs=4, depth=6, rr_start=2),
-                                  _occlusion_with_albedo, _small_pool_overflow])
+                                  _occlusion_with_albedo, _small_pool_overflow, _gi_box_moving_box,
+                                  _caustic_moving_glass])
 def test_path_sharing_is_bit_identical(ctx, make):
     """With common random numbers, a path is traced once in the scene without the
     perturbed primitives; only the renders whose own primitives one of its rays may meet
@@ -211,6 +236,12 @@ def test_path_sharing_is_bit_identical(ctx, make):
         torch.cuda.synchronize()
         res.append((g.cpu().numpy(), L.cpu().numpy()))
     assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][0], res[1][0])
+    # and sharing was in use: fewer paths traced than every render tracing every path
+    ctx.counters_enable(True)
+    scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, scene.grad_opts(wl, step=5))
+    paths = ctx.counters_read()[3]
+    ctx.counters_enable(False)
+    assert 0 < paths < wl.renders * wl.width * wl.height * wl.spp
 
 
 def test_host_buffer_gradient_equals_device_call(ctx):
