@@ -389,8 +389,8 @@ def main():
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()  # noqa: E731
     theta_h, sigma_h, target_h = pin(wl.theta0), pin(wl.sigma), pin(target_host)
     m_h, v_h, g_h, L_h = pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(R))
-    h2d = 4 * (npx4 + 4 * D)
-    d2h = 4 * (4 * D + R)
+    h2d = 4 * (npx4 + 4 * D + 1)  # target; sigma, Adam's step, theta, m, v in one staged copy
+    d2h = 4 * (4 * D + R)  # theta, m, v, gradient, losses in one copy
     opts = scene.grad_opts(wl, step=0)
 
     def e2e_step(k):

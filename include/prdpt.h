@@ -208,8 +208,10 @@ prdpt_status prdpt_smoothed_grad_host(prdpt_ctx* ctx, int32_t scene_id, const fl
 /* A whole optimisation step with host buffers: the gradient as prdpt_smoothed_grad_host
  * at theta_host, then one Adam update (as prdpt_adam_step, step t >= 1, lr, beta1, beta2,
  * eps) of theta_host, m_host and v_host [D], which are read and written back in place.
- * grad_host [D] and losses_host [2P] receive the step's gradient and losses (either may be
- * NULL). Synchronous; shares the context's scratch like prdpt_smoothed_grad_host. */
+ * The update runs in the gradient's last kernel on the device, with the same arithmetic
+ * as prdpt_adam_step. grad_host [D] and losses_host [2P] receive the step's gradient and
+ * losses (either may be NULL). Synchronous; shares the context's scratch like
+ * prdpt_smoothed_grad_host. */
 prdpt_status prdpt_step_host(prdpt_ctx* ctx, int32_t scene_id, float* theta_host, float* m_host, float* v_host,
                              int32_t t, float lr, float beta1, float beta2, float eps, const float* sigma_host,
                              const prdpt_grad_opts* opts, const float* target_host, float* grad_host,

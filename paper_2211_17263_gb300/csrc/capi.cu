@@ -752,9 +752,18 @@ prdpt_status prdpt_sample_perturbations(prdpt_ctx* c, int32_t D, const float* si
 namespace {
 
 // prdpt_smoothed_grad with the context's mutex held by the caller.
+// Adam state on the device for a call that also takes the optimiser step: the last CTA of
+// k_finalize (k_hd_grad for texture scenes) updates theta, m, v; *step holds t - 1 and is
+// advanced to t on the device.
+struct AdamDev {
+    float *theta, *m, *v;
+    int* step;
+    float lr, b1, b2, eps;
+};
+
 prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* theta_dev, const float* sigma_dev,
                                   const prdpt_grad_opts* o, const float* target_dev, float* grad_dev,
-                                  float* losses_dev, void* stream) {
+                                  float* losses_dev, void* stream, const AdamDev* adam = nullptr) {
     Scene* s = get_scene(c, scene_id);
     if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
     if (prdpt_status st = check_grad_opts(o)) return st;
@@ -850,6 +859,16 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         J.rgrads = c->s_rgrads;
     }
     J.hd = tex ? 1 : 0;
+    if (adam) {
+        J.theta = adam->theta;
+        J.m = adam->m;
+        J.v = adam->v;
+        J.step_dev = adam->step;
+        J.lr = adam->lr;
+        J.b1 = adam->b1;
+        J.b2 = adam->b2;
+        J.eps = adam->eps;
+    }
     TL.diff_nd = diff_slots(J);
     TL.total_items = J.share ? tiles : R * tiles;
     TL.share = J.share;
@@ -865,6 +884,16 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         G.w = c->s_w;
         G.losses = c->s_losses;
         G.grad_out = grad_dev;
+        if (adam) {
+            G.theta = adam->theta;
+            G.m = adam->m;
+            G.v = adam->v;
+            G.step_dev = adam->step;
+            G.lr = adam->lr;
+            G.b1 = adam->b1;
+            G.b2 = adam->b2;
+            G.eps = adam->eps;
+        }
         PRDPT_CUDA(launch_hd_grad(G, st_));
     }
     return PRDPT_OK;
@@ -893,15 +922,16 @@ struct HostAdam {  // prdpt_step_host: Adam state in host memory, updated in pla
     float lr, b1, b2, eps;
 };
 
-// The gradient with host buffers, and with `adam` one Adam update of theta, m, v. The
-// small vectors go through a page-locked staging buffer (one upload, one download); the
-// target is copied straight from the caller's buffer.
+// The gradient with host buffers, and with `adam` one Adam update of theta, m, v, taken by
+// the gradient's last kernel. The small vectors go through a page-locked staging buffer (one
+// upload, one download of what the caller gets back); the target is copied straight from
+// the caller's buffer.
 prdpt_status host_buffer_call(prdpt_ctx* c, int32_t scene_id, const float* theta_host, const float* sigma_host,
                               const prdpt_grad_opts* o, const float* target_host, float* grad_host,
                               float* losses_host, void* stream, const HostAdam* adam) {
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
-    float *theta_d, *sigma_d, *target_d, *grad_d, *losses_d, *m_d, *v_d, *stage;
-    size_t D, R;
+    float *target_d, *io_d, *stage;
+    size_t D, R, small;
     std::lock_guard<std::mutex> lk(c->mu);  // the whole call: the scratch and staging are per context
     {
         Scene* s = get_scene(c, scene_id);
@@ -910,8 +940,10 @@ prdpt_status host_buffer_call(prdpt_ctx* c, int32_t scene_id, const float* theta
         PRDPT_CUDA(cudaSetDevice(c->device));
         D = size_t(s->D);
         R = 2 * size_t(o->pairs);
-        const size_t pix4 = 4 * size_t(o->width) * size_t(o->height), small = 5 * D + R;
-        // device: [target (16-byte aligned for float4 loads) | theta | sigma | m | v | grad | losses]
+        const size_t pix4 = 4 * size_t(o->width) * size_t(o->height);
+        small = 5 * D + 1 + R;
+        // device: [target (16-byte aligned for float4 loads) | sigma | step | theta | m | v | grad | losses],
+        // the staging buffer mirrors everything after the target
         if (prdpt_status st = grow(c, &c->s_host_io, &c->s_host_io_n, pix4 + small)) return st;
         if (c->h_stage_n < small) {  // the previous call has synchronised: the old buffer is idle
             if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -924,37 +956,38 @@ prdpt_status host_buffer_call(prdpt_ctx* c, int32_t scene_id, const float* theta
         }
         stage = c->h_stage;
         target_d = c->s_host_io;
-        theta_d = target_d + pix4;
-        sigma_d = theta_d + D;
-        m_d = sigma_d + D;
-        v_d = m_d + D;
-        grad_d = v_d + D;
-        losses_d = grad_d + D;
-        std::memcpy(stage, theta_host, sizeof(float) * D);
-        std::memcpy(stage + D, sigma_host, sizeof(float) * D);
+        io_d = target_d + pix4;
+        const int32_t step0 = adam ? adam->t - 1 : 0;
+        std::memcpy(stage, sigma_host, sizeof(float) * D);
+        std::memcpy(stage + D, &step0, sizeof(step0));
+        std::memcpy(stage + D + 1, theta_host, sizeof(float) * D);
         if (adam) {
-            std::memcpy(stage + 2 * D, adam->m, sizeof(float) * D);
-            std::memcpy(stage + 3 * D, adam->v, sizeof(float) * D);
+            std::memcpy(stage + 2 * D + 1, adam->m, sizeof(float) * D);
+            std::memcpy(stage + 3 * D + 1, adam->v, sizeof(float) * D);
         }
-        PRDPT_CUDA(cudaMemcpyAsync(theta_d, stage, sizeof(float) * (adam ? 4 : 2) * D, cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(io_d, stage, sizeof(float) * ((adam ? 4 : 2) * D + 1), cudaMemcpyHostToDevice, st_));
         PRDPT_CUDA(cudaMemcpyAsync(target_d, target_host, sizeof(float) * pix4, cudaMemcpyHostToDevice, st_));
     }
-    if (prdpt_status st = smoothed_grad_locked(c, scene_id, theta_d, sigma_d, o, target_d, grad_d, losses_d, stream))
-        return st;
+    float *sigma_d = io_d, *theta_d = io_d + D + 1, *grad_d = io_d + 4 * D + 1;
+    AdamDev ad{};
     if (adam)
-        if (prdpt_status st = prdpt_adam_step(c, int32_t(D), theta_d, m_d, v_d, grad_d, adam->t, adam->lr, adam->b1,
-                                              adam->b2, adam->eps, stream))
-            return st;
-    // one download of [theta | sigma | m | v | grad | losses] into the staging buffer
-    PRDPT_CUDA(cudaMemcpyAsync(stage, theta_d, sizeof(float) * (5 * D + R), cudaMemcpyDeviceToHost, st_));
+        ad = AdamDev{theta_d, io_d + 2 * D + 1, io_d + 3 * D + 1, reinterpret_cast<int*>(io_d + D),
+                     adam->lr, adam->b1, adam->b2, adam->eps};
+    if (prdpt_status st = smoothed_grad_locked(c, scene_id, theta_d, sigma_d, o, target_d, grad_d, grad_d + D, stream,
+                                               adam ? &ad : nullptr))
+        return st;
+    // one download: [theta | m | v | grad | losses] after an optimiser step, else [grad | losses]
+    const size_t first = adam ? D + 1 : 4 * D + 1;
+    PRDPT_CUDA(cudaMemcpyAsync(stage + first, io_d + first, sizeof(float) * (small - first), cudaMemcpyDeviceToHost,
+                               st_));
     PRDPT_CUDA(cudaStreamSynchronize(st_));
     if (adam) {
-        std::memcpy(adam->theta, stage, sizeof(float) * D);
-        std::memcpy(adam->m, stage + 2 * D, sizeof(float) * D);
-        std::memcpy(adam->v, stage + 3 * D, sizeof(float) * D);
+        std::memcpy(adam->theta, stage + D + 1, sizeof(float) * D);
+        std::memcpy(adam->m, stage + 2 * D + 1, sizeof(float) * D);
+        std::memcpy(adam->v, stage + 3 * D + 1, sizeof(float) * D);
     }
-    if (grad_host) std::memcpy(grad_host, stage + 4 * D, sizeof(float) * D);
-    if (losses_host) std::memcpy(losses_host, stage + 5 * D, sizeof(float) * R);
+    if (grad_host) std::memcpy(grad_host, stage + 4 * D + 1, sizeof(float) * D);
+    if (losses_host) std::memcpy(losses_host, stage + 5 * D + 1, sizeof(float) * R);
     return PRDPT_OK;
 }
 

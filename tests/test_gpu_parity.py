@@ -261,11 +261,23 @@ def test_host_buffer_gradient_equals_device_call(ctx):
         assert np.array_equal(g, g_dev.cpu().numpy()) and np.array_equal(L, L_dev.cpu().numpy())
 
 
-def test_host_buffer_step_follows_the_device_calls(ctx):
-    """prdpt_step_host (gradient and Adam with theta, m, v in host memory) follows, bit for
-    bit over three steps, the trajectory of prdpt_smoothed_grad plus prdpt_adam_step on
-    device buffers."""
-    wl = workloads.scaled(workloads.config_occlusion(), width=40, height=32, spp=4, pairs=3)
+def _host_step_case(name):
+    if name == "occlusion":  # Eq. 10 with path sharing: Adam in k_finalize
+        return workloads.scaled(workloads.config_occlusion(), width=40, height=32, spp=4, pairs=3)
+    if name == "albedo":  # Eq. 9: Adam after the mean of the pathwise render gradients
+        return workloads.scaled(workloads.config_small_albedo(), width=24, height=16, spp=4, pairs=2)
+    wl = workloads.config_texture(res=8, px_per_texel=2)  # D = 192: Adam in k_hd_grad
+    wl.pairs, wl.spp = 3, 2
+    return wl
+
+
+@pytest.mark.parametrize("name", ["occlusion", "albedo", "texture"])
+def test_host_buffer_step_follows_the_device_calls(ctx, name):
+    """prdpt_step_host (gradient and Adam with theta, m, v in host memory; the update taken
+    by the gradient's last kernel) follows, bit for bit over three steps, the trajectory of
+    prdpt_smoothed_grad plus prdpt_adam_step on device buffers, and a gradient-only host
+    call between its steps leaves it unchanged."""
+    wl = _host_step_case(name)
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     target = oracle.render_target(wl).astype(np.float32)
     th_d, m_d, v_d = _t(wl.theta0), torch.zeros(wl.D, device="cuda"), torch.zeros(wl.D, device="cuda")
@@ -282,3 +294,6 @@ def test_host_buffer_step_follows_the_device_calls(ctx):
         assert np.array_equal(g_h, g_d.cpu().numpy()) and np.array_equal(L_h, L_d.cpu().numpy())
         for host, dev in ((th_h, th_d), (m_h, m_d), (v_h, v_d)):
             assert np.array_equal(host, dev.cpu().numpy())
+        g2, L2 = scene.smoothed_grad_host(th_h, sg, tg, opts)
+        g2_d, L2_d = scene.smoothed_grad(th_d, _t(wl.sigma), _t(target), opts)
+        assert np.array_equal(g2, g2_d.cpu().numpy()) and np.array_equal(L2, L2_d.cpu().numpy())
