@@ -246,19 +246,25 @@ def test_path_sharing_is_bit_identical(ctx, make):
 
 def test_host_buffer_gradient_equals_device_call(ctx):
     """prdpt_smoothed_grad_host (inputs and results in host memory, pageable or
-    page-locked) returns the device call's gradient and losses bit for bit."""
+    page-locked, on the default or another stream) returns the device call's gradient and
+    losses bit for bit, call after call with changing targets."""
     wl = workloads.scaled(workloads.config_occlusion(), width=48, height=40, spp=4, pairs=4)
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     target = oracle.render_target(wl).astype(np.float32)
     opts = scene.grad_opts(wl, step=3)
-    g_dev, L_dev = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
-    torch.cuda.synchronize()
-    for pinned in (False, True):
-        th, sg, tg = (np.ascontiguousarray(a, np.float32) for a in (wl.theta0, wl.sigma, target))
-        if pinned:
-            th, sg, tg = (torch.from_numpy(a).pin_memory() for a in (th, sg, tg))
-        g, L = scene.smoothed_grad_host(th, sg, tg, opts)
-        assert np.array_equal(g, g_dev.cpu().numpy()) and np.array_equal(L, L_dev.cpu().numpy())
+    side = torch.cuda.Stream()
+    # the target travels on a stream of its own: alternate two targets so that a result
+    # computed before its target arrived would show
+    for target_k in (target, 0.5 * target, target):
+        g_dev, L_dev = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target_k), opts)
+        torch.cuda.synchronize()
+        for pinned in (False, True):
+            th, sg, tg = (np.ascontiguousarray(a, np.float32) for a in (wl.theta0, wl.sigma, target_k))
+            if pinned:
+                th, sg, tg = (torch.from_numpy(a).pin_memory() for a in (th, sg, tg))
+            for stream in (None, side):
+                g, L = scene.smoothed_grad_host(th, sg, tg, opts, stream=stream)
+                assert np.array_equal(g, g_dev.cpu().numpy()) and np.array_equal(L, L_dev.cpu().numpy())
 
 
 def _host_step_case(name):
