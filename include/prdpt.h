@@ -17,6 +17,10 @@
  *    torch tensor storage); *_host pointers are host memory owned by the caller.
  *    The library never frees caller memory and never keeps caller pointers after
  *    a call returns, except where a call says so.
+ *  - Host threads: calls on one context may come from several threads. Each call
+ *    holds the context while it checks its arguments and enqueues its work (and, for a
+ *    synchronous call, until it returns), so calls from different threads run one
+ *    after another on the host; their GPU work overlaps as the stream rules below allow.
  *  - Calls taking `stream` (a cudaStream_t, NULL = legacy default stream) only
  *    enqueue work and return; their device-side results are ready when the stream
  *    reaches that point. Calls without a stream are synchronous.

@@ -1250,6 +1250,7 @@ static HdGrad job_hd_grad(const Job* j) {
 
 prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);  // the job table, counters and timing events (enqueue only)
     Job* j = get_job(c, job_id);
     if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
@@ -1385,6 +1386,7 @@ static prdpt_status check_status(prdpt_ctx* c) {
 prdpt_status prdpt_job_read(prdpt_ctx* c, int32_t job_id, float* theta_host, float* grad_host, float* losses_host,
                             int32_t* steps_host) {
     if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);  // the job may not be released while it is read
     Job* j = get_job(c, job_id);
     if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
     PRDPT_CUDA(cudaSetDevice(c->device));
@@ -1426,6 +1428,7 @@ prdpt_status prdpt_philox_words(prdpt_ctx* c, uint64_t seed, uint32_t c0_base, u
 
 prdpt_status prdpt_counters_enable(prdpt_ctx* c, int32_t enable) {
     if (!c) return fail(PRDPT_E_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
     PRDPT_CUDA(cudaSetDevice(c->device));
     if (enable) PRDPT_CUDA(cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long)));
     c->counting = enable != 0;
@@ -1434,6 +1437,7 @@ prdpt_status prdpt_counters_enable(prdpt_ctx* c, int32_t enable) {
 
 prdpt_status prdpt_counters_read(prdpt_ctx* c, uint64_t* counts_host) {
     if (!c || !counts_host) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
     PRDPT_CUDA(cudaSetDevice(c->device));
     PRDPT_CUDA(cudaDeviceSynchronize());
     PRDPT_CUDA(cudaMemcpy(counts_host, c->counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));

@@ -184,6 +184,57 @@ def test_jobs_step_concurrently_on_their_own_streams(ctx):
         j.release()
 
 
+def test_jobs_step_from_several_host_threads(ctx):
+    """Two host threads step two jobs on their own streams while a third creates, reads
+    and releases jobs on the same context: the stepped jobs end exactly where they end
+    stepping alone."""
+    import threading
+    wls = [workloads.scaled(workloads.config_occlusion(seed=41), width=48, height=40, spp=4, pairs=4),
+           workloads.scaled(workloads.config_small(seed=42), width=40, height=32, spp=4, pairs=4)]
+    targets = [oracle.render_target(w) for w in wls]
+    alone = []
+    for w, t in zip(wls, targets):
+        j = _job(ctx, w, t)
+        for _ in range(20):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    jobs = [_job(ctx, w, t) for w, t in zip(wls, targets)]
+    torch.cuda.synchronize()
+    errors = []
+
+    def stepper(j):
+        try:
+            s = torch.cuda.Stream()
+            for _ in range(20):
+                j.step(s)
+            s.synchronize()
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(e)
+
+    def churn():
+        try:
+            for _ in range(5):
+                j = _job(ctx, wls[1], targets[1])
+                j.read()
+                j.release()
+        except Exception as e:  # noqa: BLE001
+            errors.append(e)
+
+    threads = [threading.Thread(target=stepper, args=(j,)) for j in jobs] + [threading.Thread(target=churn)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for j, a in zip(jobs, alone):
+        b = j.read()
+        assert b["steps"] == 20
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(a[key], b[key]), key
+        j.release()
+
+
 def test_too_many_work_items_is_an_argument_error(ctx):
     """The render kernels number (render, pixel block) work items with 32-bit integers: a
     job of 512 renders of 8192^2 pixels in 8-pixel blocks (4.3 G items) is refused with an
