@@ -21,10 +21,14 @@ Path Tracing"):
 Parity pins (tests/test_oracle_*.py): Philox against curand's host generator and
 published known answers; the sampler against its closed-form distribution; the
 estimator against closed-form smoothed gradients and quadrature; the tracer
-against the white furnace and analytic irradiance; Adam against torch.optim.Adam.
+against the white furnace and analytic irradiance; the dielectric event (`dielectric`)
+against the textbook Fresnel equations and Snell's law; Russian roulette against the
+furnace mean; Adam against torch.optim.Adam. `library` runs the functions from a copy
+of the oracle built with a planted mistake, to show that a pin catches it.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 
@@ -49,45 +53,63 @@ class _SceneArrays(C.Structure):
 _LOSS_CB = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_float), C.c_int, C.c_int, C.c_void_p)
 
 
+def _bind(L):
+    """Argument and result types of the oracle's exported functions."""
+    vp, i32, u32, u64, dbl = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double
+    L.orc_philox_fill.argtypes = [u64, u32, u32, u32, u32, i32, vp]
+    L.orc_u01.argtypes = [u32]
+    L.orc_u01.restype = dbl
+    L.orc_sampler_uniforms.argtypes = [i32, i32]
+    L.orc_sampler_uniforms.restype = i32
+    L.orc_radial_constant.argtypes = [i32]
+    L.orc_radial_constant.restype = dbl
+    L.orc_sample_unit.argtypes = [i32, i32, vp, vp, vp]
+    L.orc_sample.argtypes = [i32, i32, vp, u64, u32, u32, vp, vp, vp]
+    L.orc_intersect.argtypes = [vp, i32, vp, vp, vp]
+    L.orc_intersect.restype = dbl
+    L.orc_dielectric.argtypes = [vp, vp, dbl, dbl, vp, vp, vp, vp]
+    L.orc_dielectric.restype = i32
+    L.orc_render.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, i32, vp, i32]
+    L.orc_render.restype = i32
+    L.orc_render_pixels.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, vp, i32, vp]
+    L.orc_render_pixels.restype = i32
+    L.orc_mse.argtypes = [vp, vp, i32, i32]
+    L.orc_mse.restype = dbl
+    L.orc_smoothed_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64,
+                                    u32, vp, vp, vp, vp, vp, i32]
+    L.orc_smoothed_grad.restype = i32
+    L.orc_estimate.argtypes = [i32, i32, i32, vp, vp, i32, i32, u64, u32, _LOSS_CB, vp, vp, vp, vp, vp]
+    L.orc_estimate.restype = i32
+    L.orc_sample_unit_batch.argtypes = [i32, i32, i32, vp, vp, vp]
+    L.orc_render_tangent.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, vp, vp, i32]
+    L.orc_render_tangent.restype = i32
+    L.orc_kdp_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64, u32,
+                               vp, vp, vp, vp, vp, i32]
+    L.orc_kdp_grad.restype = i32
+    L.orc_adam.argtypes = [i32, vp, vp, vp, vp, i32, dbl, dbl, dbl, dbl]
+    L.orc_sigma_schedule.argtypes = [dbl, dbl, i32, i32]
+    L.orc_sigma_schedule.restype = dbl
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        vp, i32, u32, u64, dbl = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double
-        L.orc_philox_fill.argtypes = [u64, u32, u32, u32, u32, i32, vp]
-        L.orc_u01.argtypes = [u32]
-        L.orc_u01.restype = dbl
-        L.orc_sampler_uniforms.argtypes = [i32, i32]
-        L.orc_sampler_uniforms.restype = i32
-        L.orc_radial_constant.argtypes = [i32]
-        L.orc_radial_constant.restype = dbl
-        L.orc_sample_unit.argtypes = [i32, i32, vp, vp, vp]
-        L.orc_sample.argtypes = [i32, i32, vp, u64, u32, u32, vp, vp, vp]
-        L.orc_intersect.argtypes = [vp, i32, vp, vp, vp]
-        L.orc_intersect.restype = dbl
-        L.orc_render.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, i32, vp, i32]
-        L.orc_render.restype = i32
-        L.orc_render_pixels.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, vp, i32, vp]
-        L.orc_render_pixels.restype = i32
-        L.orc_mse.argtypes = [vp, vp, i32, i32]
-        L.orc_mse.restype = dbl
-        L.orc_smoothed_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64,
-                                        u32, vp, vp, vp, vp, vp, i32]
-        L.orc_smoothed_grad.restype = i32
-        L.orc_estimate.argtypes = [i32, i32, i32, vp, vp, i32, i32, u64, u32, _LOSS_CB, vp, vp, vp, vp, vp]
-        L.orc_estimate.restype = i32
-        L.orc_sample_unit_batch.argtypes = [i32, i32, i32, vp, vp, vp]
-        L.orc_render_tangent.argtypes = [vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32, vp, vp, i32]
-        L.orc_render_tangent.restype = i32
-        L.orc_kdp_grad.argtypes = [vp, vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, i32, u64, u32,
-                                   vp, vp, vp, vp, vp, i32]
-        L.orc_kdp_grad.restype = i32
-        L.orc_adam.argtypes = [i32, vp, vp, vp, vp, i32, dbl, dbl, dbl, dbl]
-        L.orc_sigma_schedule.argtypes = [dbl, dbl, i32, i32]
-        L.orc_sigma_schedule.restype = dbl
-        _lib = L
+        _lib = _bind(C.CDLL(_build.build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Run the oracle's functions from another build of its source (the tests use this to
+    plant a mistake in a copy of the oracle and check that a pin catches it)."""
+    global _lib
+    saved = lib()
+    _lib = _bind(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _param_dim(binds: np.ndarray) -> int:
@@ -202,6 +224,18 @@ def intersect(scene, prim: int, o, d):
     n = np.zeros(3, np.float64)
     t = lib().orc_intersect(h.ref, prim, _ptr(o), _ptr(d), _ptr(n))
     return t, n
+
+
+def dielectric(direction, normal, ior: float, u: float, point=(0.0, 0.0, 0.0)):
+    """The tracer's smooth-dielectric event for one ray: direction (unit) meets a surface of
+    index `ior` (outside index 1) with outward unit normal at `point`; u is the uniform of
+    the reflect-or-refract choice. Returns dict(reflected, dir, org, F, rs, rp)."""
+    d = np.ascontiguousarray(direction, np.float64)
+    n = np.ascontiguousarray(normal, np.float64)
+    p = np.ascontiguousarray(point, np.float64)
+    nd, no, fr = np.zeros(3), np.zeros(3), np.zeros(3)
+    refl = lib().orc_dielectric(_ptr(d), _ptr(n), float(ior), float(u), _ptr(p), _ptr(nd), _ptr(no), _ptr(fr))
+    return {"reflected": bool(refl), "dir": nd, "org": no, "F": float(fr[0]), "rs": float(fr[1]), "rp": float(fr[2])}
 
 
 def render(scene, bindings, thetas, width, height, spp, depth, rr_start=-1, seed=0, step=0, tag=TAG_PATH,

@@ -26,7 +26,9 @@
  * Parity pins: Philox against curand's host generator and published known
  * answers; sampler against its closed-form distribution; estimator against
  * closed-form smoothed gradients; tracer against the white furnace and analytic
- * irradiance; Adam against torch.optim.Adam. All pins live in tests/.
+ * irradiance; the smooth dielectric against the textbook Fresnel equations and
+ * Snell's law; Russian roulette against the furnace mean and the unrouletted image;
+ * Adam against torch.optim.Adam. All pins live in tests/.
  */
 #include <math.h>
 #include <pthread.h>
@@ -492,6 +494,68 @@ static void path_uniforms(const orc_trace_opts* o, uint32_t pixel, int s, int b,
     uniforms4(o->seed, pixel, c1, o->step, c3, u);
 }
 
+/* Fresnel reflectance of an unpolarised wave at a smooth dielectric interface (the
+ * textbook Fresnel equations in their cosine form): ci = cos(incidence) > 0, eta =
+ * n_incident / n_transmitted. Returns F = (r_s^2 + r_p^2) / 2 with the amplitude
+ * ratios r_s, r_p and the cosine of the refraction angle ct; F = 1 (and r_s, r_p, ct
+ * = 1, 1, 0) under total internal reflection, when Snell's law has no solution. */
+static double fresnel_dielectric(double ci, double eta, double* rs_out, double* rp_out, double* ct_out) {
+    double s2t = eta * eta * (1.0 - ci * ci); /* sin^2 of the refraction angle (Snell) */
+    if (s2t >= 1.0) {
+        *rs_out = 1.0;
+        *rp_out = 1.0;
+        *ct_out = 0.0;
+        return 1.0;
+    }
+    double ct = sqrt(1.0 - s2t);
+    double rs = (eta * ci - ct) / (eta * ci + ct);
+    double rp = (ci - eta * ct) / (ci + eta * ct);
+    *rs_out = rs;
+    *rp_out = rp;
+    *ct_out = ct;
+    return 0.5 * (rs * rs + rp * rp);
+}
+
+/* Scattering at a smooth dielectric of index `ior` (outside index 1): the ray
+ * direction dir meets a surface with outward geometric normal ng at point p. With
+ * probability F (uniform u < F) the ray is reflected, otherwise refracted by Snell's
+ * law; the new origin is offset by ORC_EPS to the side the new ray leaves into.
+ * fr receives F and the amplitude ratios r_s, r_p. Returns 1 for a reflection, 0 for
+ * a refraction. */
+static int dielectric_event(v3 dir, v3 ng, double ior, double u, v3 p, v3* dir_out, v3* org_out, double fr[3]) {
+    double ci = -dot(dir, ng);
+    double eta;
+    v3 n; /* normal on the incident side */
+    if (ci > 0.0) { eta = 1.0 / ior; n = ng; }
+    else { eta = ior; n = mul(ng, -1.0); ci = -ci; }
+    double rs, rp, ct;
+    double F = fresnel_dielectric(ci, eta, &rs, &rp, &ct);
+    fr[0] = F;
+    fr[1] = rs;
+    fr[2] = rp;
+    if (u < F) {
+        *dir_out = normalize(add(dir, mul(n, 2.0 * ci)));
+        *org_out = add(p, mul(n, ORC_EPS));
+        return 1;
+    }
+    *dir_out = normalize(add(mul(dir, eta), mul(n, eta * ci - ct)));
+    *org_out = sub(p, mul(n, ORC_EPS));
+    return 0;
+}
+
+/* Test hook: the dielectric event of the tracer for one ray (dir unit, ng the outward
+ * unit normal, p the hit point). Writes the new direction and origin, and F, r_s, r_p
+ * of the incidence; returns 1 for a reflection. */
+int orc_dielectric(const double* dir, const double* ng, double ior, double u, const double* p, double* dir_out,
+                   double* org_out, double* fresnel_out) {
+    v3 nd, no;
+    int refl = dielectric_event(V(dir[0], dir[1], dir[2]), V(ng[0], ng[1], ng[2]), ior, u, V(p[0], p[1], p[2]), &nd,
+                                &no, fresnel_out);
+    dir_out[0] = nd.x; dir_out[1] = nd.y; dir_out[2] = nd.z;
+    org_out[0] = no.x; org_out[1] = no.y; org_out[2] = no.z;
+    return refl;
+}
+
 /* Forward-mode tangents of a path sample for Eq. 9's pathwise derivative dP/dtheta with
  * respect to n bound material parameters: kind 2 (albedo) or 3 (emission) of material
  * mat, colour channel c; dclamp is the derivative of the clamp applied at instantiation
@@ -642,28 +706,11 @@ static v3 trace_path_t(const orc_scene* sc, const orc_trace_opts* o, int x, int 
             specular = 1;
         } else { /* smooth dielectric: exact unpolarised Fresnel, reflect or refract */
             if (last) break;
-            double ci = -dot(dir, ng);
-            double eta;
-            v3 n;
-            if (ci > 0.0) { eta = 1.0 / m->ior; n = ng; }
-            else { eta = m->ior; n = mul(ng, -1.0); ci = -ci; }
-            double s2t = eta * eta * (1.0 - ci * ci);
-            double F, ct = 0.0;
-            if (s2t >= 1.0) {
-                F = 1.0; /* total internal reflection */
-            } else {
-                ct = sqrt(1.0 - s2t);
-                double rs = (eta * ci - ct) / (eta * ci + ct);
-                double rp = (ci - eta * ct) / (ci + eta * ct);
-                F = 0.5 * (rs * rs + rp * rp);
-            }
-            if (u1[2] < F) {
-                dir = normalize(add(dir, mul(n, 2.0 * ci)));
-                org = add(p, mul(n, ORC_EPS));
-            } else {
-                dir = normalize(add(mul(dir, eta), mul(n, eta * ci - ct)));
-                org = sub(p, mul(n, ORC_EPS));
-            }
+            double fr[3];
+            v3 nd, no;
+            dielectric_event(dir, ng, m->ior, u1[2], p, &nd, &no, fr);
+            dir = nd;
+            org = no;
             scatter_tangents(ts, dB, beta, albedo, pr->mat);
             beta = hmul(beta, albedo);
             specular = 1;
