@@ -35,8 +35,11 @@
  *  - Random numbers: Philox4x32-10 with key = 64-bit seed; counter words
  *    (c0, c1, c2, c3). Perturbation draws use (pair or draw index, block, step,
  *    1 << 28); path samples use (pixel y*W+x, sample | vertex << 16 | slot << 24,
- *    step, tag << 28 | render field), slot 0 = BSDF / Russian roulette, slot 1 =
- *    light sample, slot 2 = pixel jitter. Uniforms are ((word >> 9) * 2 + 1) / 2^24.
+ *    step, tag << 28 | render field). The four uniforms of slot 0 are the light point
+ *    (u, v) of next-event estimation and the BSDF sample (u1, u2); slot 1 holds the
+ *    light choice, the Russian-roulette uniform and the dielectric's reflect-or-refract
+ *    uniform (its fourth word is unused); slot 2 (vertex 0 only) is the pixel jitter
+ *    (x, y). Uniforms are ((word >> 9) * 2 + 1) / 2^24.
  *  - Limits: at most PRDPT_MAX_PRIMS primitives, PRDPT_MAX_MATS materials,
  *    PRDPT_MAX_LIGHTS emitters, PRDPT_MAX_D parameters and PRDPT_MAX_PAIRS
  *    antithetic pairs per call. Width and height at most 8192, spp at most 65535,
@@ -292,21 +295,28 @@ prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);
  * another allocator (a framework's caching allocator, a fixed arena of a serving
  * runtime), or code that may not grow its footprint or create a context after
  * start-up. It takes no context and allocates nothing: the scene comes from host
- * memory (`scene`, `binds`, D as for prdpt_scene_upload), theta_dev, sigma_dev,
- * target_dev, grad_dev and losses_dev (NULL allowed) are the caller's device buffers
- * exactly as for prdpt_smoothed_grad, and every intermediate buffer lives in one
- * fixed 6 MiB __device__ array that each GPU loading the library holds until the
- * process exits.
- * Limits: at most 32 antithetic pairs and 2P x (image blocks) x 8 bytes of loss
- * partials within the 6 MiB (512 x 512 with 32-pixel blocks fits 32 pairs); larger
- * requests return PRDPT_E_OUT_OF_BUDGET with a message. All calls share that array
- * and each call overwrites what the last one left: calls that overlap on the GPU
- * (different streams, no ordering) race and must not be issued. The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) and the
- * device's SM count; make that first call before any stream capture. Errors are
- * written to err (err_len bytes, may be NULL); there is no context to query.
- * Only the Eq. 10 estimator (opts->estimator = 0). The paper has no counterpart to this
- * entry point. */
+ * memory (`scene`, `binds`, D as for prdpt_scene_upload, checked by the same rules;
+ * no texture bindings), theta_dev, sigma_dev, target_dev, grad_dev and losses_dev (NULL
+ * allowed) are the caller's device buffers exactly as for prdpt_smoothed_grad, and
+ * every intermediate buffer lives in one fixed 6 MiB __device__ array that each GPU
+ * loading the library holds until the process exits. The call enqueues three kernels
+ * and one memset on `stream` and returns; the scene is passed as a kernel parameter,
+ * so no host buffer needs to outlive the call. With the same block_pixels it gives the
+ * same losses and gradient as prdpt_smoothed_grad, bit for bit; block_pixels = 0 means
+ * 32-pixel blocks here.
+ * Limits: 1..32 antithetic pairs, pair_begin 0..2^26, and 2P x (image blocks) x 8 bytes
+ * of loss partials within the 6 MiB (512 x 512 with 32-pixel blocks fits 32 pairs);
+ * larger requests return PRDPT_E_OUT_OF_BUDGET with a message, before any launch. All
+ * calls share that array and each call overwrites what the last one left: calls that
+ * overlap on the GPU (different streams, no ordering) race and must not be issued.
+ * Calls from several host threads enqueue one after another (a lock per device), so
+ * calls on one stream are ordered. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and the device's SM count; make that first call
+ * before any stream capture. Errors are written to err (err_len bytes, may be NULL);
+ * there is no context to query, and the kernels' device status word is not reported
+ * (the host checks above leave the kernels nothing to refuse). Only
+ * opts->estimator = PRDPT_ESTIMATOR_KERNEL_GRADIENT. The paper has no counterpart to
+ * this entry point. */
 prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene, const prdpt_param_binding* binds, int32_t D,
                                         const float* theta_dev, const float* sigma_dev, const prdpt_grad_opts* opts,
                                         const float* target_dev, float* grad_dev, float* losses_dev, void* stream,

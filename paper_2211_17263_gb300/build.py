@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libprdpt.so")
 SOURCES = ["kernels.cu", "capi.cu", "noalloc.cu"]
-HEADERS = ["internal.h", os.path.join("..", "..", "include", "prdpt.h")]
+HEADERS = ["internal.h", "scene_host.h", os.path.join("..", "..", "include", "prdpt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -14,6 +14,7 @@
 
 #include "../../include/prdpt.h"
 #include "internal.h"
+#include "scene_host.h"
 
 using namespace prdpt;
 
@@ -356,94 +357,8 @@ prdpt_status prdpt_scene_upload(prdpt_ctx* c, const prdpt_scene_desc* sd, const 
                                 int32_t D, int32_t* scene_id_out) {
     if (!c || !sd || !binds || !scene_id_out) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
-    if (sd->n_prims < 1 || sd->n_prims > kMaxPrims) return fail(PRDPT_E_INVALID_ARG, "n_prims must be in 1..32");
-    if (sd->n_mats < 1 || sd->n_mats > kMaxMats) return fail(PRDPT_E_INVALID_ARG, "n_mats must be in 1..32");
-    const bool texture = D >= 1 && binds[0].kind == kBindTexture;
-    if (texture) {  // one row (4, material, T) standing for the T x T x 3 texel albedos
-        const int m = binds[0].index, T = binds[0].component;
-        if (m < 0 || m >= sd->n_mats) return fail(PRDPT_E_INVALID_ARG, "texture binding: material index out of range");
-        if (T < 1 || T > kMaxTexRes) return fail(PRDPT_E_INVALID_ARG, "texture binding: resolution must be in 1..1024");
-        if (D != 3 * T * T) return fail(PRDPT_E_INVALID_ARG, "texture binding: D must be 3 * resolution^2");
-    } else if (D < 1 || D > kMaxD) {
-        return fail(PRDPT_E_INVALID_ARG, "D must be in 1..64 (or 3 T^2 for one texture binding)");
-    }
-    if (!sd->prim_type || !sd->prim_mat || !sd->prim_geom || !sd->mat_type || !sd->mat_param || !sd->camera ||
-        !sd->background)
-        return fail(PRDPT_E_INVALID_ARG, "scene array is NULL");
     BaseScene B;
-    std::memset(&B, 0, sizeof(B));
-    B.n_prims = sd->n_prims;
-    B.n_mats = sd->n_mats;
-    B.D = D;
-    B.tex_mat = texture ? binds[0].index : -1;
-    B.tex_res = texture ? binds[0].component : 0;
-    for (int i = 0; i < sd->n_mats; ++i) {
-        if (sd->mat_type[i] < 0 || sd->mat_type[i] > 2) return fail(PRDPT_E_INVALID_ARG, "bad material type");
-        B.mat_type[i] = sd->mat_type[i];
-        for (int q = 0; q < 8; ++q) B.mat_param[i][q] = sd->mat_param[8 * i + q];
-    }
-    std::vector<bool> emission_bound(sd->n_mats, false);
-    for (int d = 0; d < (texture ? 0 : D); ++d) {
-        const int k = binds[d].kind, idx = binds[d].index, comp = binds[d].component;
-        if (k == kBindPos || k == kBindRadius) {
-            if (idx < 0 || idx >= sd->n_prims) return fail(PRDPT_E_INVALID_ARG, "binding: primitive index out of range");
-            if (k == kBindRadius && sd->prim_type[idx] != kSphere)
-                return fail(PRDPT_E_INVALID_ARG, "binding: radius of a non-sphere");
-        } else if (k == kBindAlbedo || k == kBindEmission) {
-            if (idx < 0 || idx >= sd->n_mats) return fail(PRDPT_E_INVALID_ARG, "binding: material index out of range");
-            if (k == kBindEmission) emission_bound[idx] = true;
-        } else {
-            return fail(PRDPT_E_INVALID_ARG, "binding: unknown kind");
-        }
-        if (k != kBindRadius && (comp < 0 || comp > 2)) return fail(PRDPT_E_INVALID_ARG, "binding: component must be 0..2");
-        B.bind_kind[d] = k;
-        B.bind_index[d] = idx;
-        B.bind_comp[d] = (k == kBindRadius) ? 0 : comp;
-    }
-    int n_light_candidates = 0;
-    for (int i = 0; i < sd->n_prims; ++i) {
-        const int t = sd->prim_type[i], m = sd->prim_mat[i];
-        if (t < 0 || t > 2) return fail(PRDPT_E_INVALID_ARG, "bad primitive type");
-        if (m < 0 || m >= sd->n_mats) return fail(PRDPT_E_INVALID_ARG, "primitive material out of range");
-        const bool can_emit = is_emissive(&sd->mat_param[8 * m]) || emission_bound[m];
-        if (t == kBox && can_emit) return fail(PRDPT_E_INVALID_ARG, "emissive boxes are not supported");
-        if (can_emit) ++n_light_candidates;
-        B.prim_type[i] = t;
-        B.prim_mat[i] = m;
-        for (int q = 0; q < 9; ++q) B.prim_geom[i][q] = sd->prim_geom[9 * i + q];
-        if (t == kSphere) ++B.n_sph;
-        if (t == kQuad) ++B.n_quad;
-        if (t == kBox) ++B.n_box;
-    }
-    if (n_light_candidates > kMaxLights) return fail(PRDPT_E_INVALID_ARG, "more than 8 emitters");
-    int next[3] = {0, B.n_sph, B.n_sph + B.n_quad};  // record slots grouped by type, stable
-    for (int i = 0; i < sd->n_prims; ++i) B.prim_slot[i] = next[B.prim_type[i]]++;
-    // camera basis (double, then rounded)
-    double eye[3], look[3], up[3];
-    for (int q = 0; q < 3; ++q) {
-        eye[q] = sd->camera[q];
-        look[q] = sd->camera[3 + q];
-        up[q] = sd->camera[6 + q];
-    }
-    double f[3] = {look[0] - eye[0], look[1] - eye[1], look[2] - eye[2]};
-    double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-    if (!(fn > 0)) return fail(PRDPT_E_INVALID_ARG, "camera eye equals look-at");
-    for (double& x : f) x /= fn;
-    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
-    double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    if (!(rn > 0)) return fail(PRDPT_E_INVALID_ARG, "camera up is parallel to the view direction");
-    for (double& x : r) x /= rn;
-    double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
-    for (int q = 0; q < 3; ++q) {
-        B.eye[q] = float(eye[q]);
-        B.fwd[q] = float(f[q]);
-        B.right[q] = float(r[q]);
-        B.up[q] = float(u[q]);
-        B.bg[q] = sd->background[q];
-    }
-    const double vfov = sd->camera[9];
-    if (!(vfov > 0 && vfov < 180)) return fail(PRDPT_E_INVALID_ARG, "field of view must be in (0, 180) degrees");
-    B.tan_half = float(std::tan(0.5 * vfov * M_PI / 180.0));
+    if (const char* why = build_base_scene(sd, binds, D, true, &B)) return fail(PRDPT_E_INVALID_ARG, why);
 
     Scene* s = new Scene();
     s->host = B;

@@ -12,7 +12,9 @@
 //
 // Host code never dereferences that array: its name in host code is only a stand-in.
 // The device address is obtained once per device with cudaGetSymbolAddress (with that
-// device current) and passed to the kernels like any other pointer.
+// device current) and passed to the kernels like any other pointer. The call enqueues
+// kernels and one memset only: the scene travels as a kernel parameter and is written
+// into the array by the first kernel, so no host buffer has to outlive the call.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,14 +22,16 @@
 
 #include "../../include/prdpt.h"
 #include "internal.h"
+#include "scene_host.h"
 
 using namespace prdpt;
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(6) << 20;  // 6 MiB per device
-constexpr int kStaticMaxRenders = 64;                    // at most 32 antithetic pairs
+constexpr int kStaticMaxPairs = 32;                      // 64 renders
 constexpr int kMaxDevices = 64;
+constexpr int kCtlWords = 16;                            // [0] queue, [1] done counter, [2] status, rest spare
 
 // The shared scratch of every call on a device.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -38,100 +42,28 @@ struct DeviceSetup {
     int sms = 0, occ = 0;
 };
 
-std::mutex g_setup_mu;
+// One lock per device: held from the set-up through the last launch of a call, so calls
+// from several host threads enqueue one after another (their scratch use then follows
+// the streams' order; calls on different, unordered streams still race on the GPU).
+std::mutex g_mu[kMaxDevices];
 DeviceSetup g_setup[kMaxDevices];
 
 prdpt_status report(char* err, size_t err_len, prdpt_status code, const char* msg) {
-    if (err && err_len > 0) {
-        std::snprintf(err, err_len, "%s", msg);
-    }
+    if (err && err_len > 0) std::snprintf(err, err_len, "%s", msg);
     return code;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Scene validation and host-side precomputation, as for an uploaded scene.
-bool build_base_scene(const prdpt_scene_desc* sd, const prdpt_param_binding* binds, int D, BaseScene* B,
-                      const char** why) {
-    *why = nullptr;
-    if (sd->n_prims < 1 || sd->n_prims > kMaxPrims) return *why = "n_prims must be in 1..32", false;
-    if (sd->n_mats < 1 || sd->n_mats > kMaxMats) return *why = "n_mats must be in 1..32", false;
-    if (D < 1 || D > kMaxD) return *why = "D must be in 1..64", false;
-    if (!sd->prim_type || !sd->prim_mat || !sd->prim_geom || !sd->mat_type || !sd->mat_param || !sd->camera ||
-        !sd->background)
-        return *why = "scene array is NULL", false;
-    std::memset(B, 0, sizeof(*B));
-    B->tex_mat = -1;  // no texture parameters in this entry point
-    B->n_prims = sd->n_prims;
-    B->n_mats = sd->n_mats;
-    B->D = D;
-    bool emission_bound[kMaxMats] = {};
-    for (int i = 0; i < sd->n_mats; ++i) {
-        if (sd->mat_type[i] < 0 || sd->mat_type[i] > 2) return *why = "bad material type", false;
-        B->mat_type[i] = sd->mat_type[i];
-        for (int q = 0; q < 8; ++q) B->mat_param[i][q] = sd->mat_param[8 * i + q];
-    }
-    for (int d = 0; d < D; ++d) {
-        const int k = binds[d].kind, idx = binds[d].index, comp = binds[d].component;
-        if (k == kBindPos || k == kBindRadius) {
-            if (idx < 0 || idx >= sd->n_prims) return *why = "binding: primitive index out of range", false;
-            if (k == kBindRadius && sd->prim_type[idx] != kSphere) return *why = "binding: radius of a non-sphere", false;
-        } else if (k == kBindAlbedo || k == kBindEmission) {
-            if (idx < 0 || idx >= sd->n_mats) return *why = "binding: material index out of range", false;
-            if (k == kBindEmission) emission_bound[idx] = true;
-        } else {
-            return *why = "binding: unknown kind", false;
-        }
-        if (k != kBindRadius && (comp < 0 || comp > 2)) return *why = "binding: component must be 0..2", false;
-        B->bind_kind[d] = k;
-        B->bind_index[d] = idx;
-        B->bind_comp[d] = (k == kBindRadius) ? 0 : comp;
-    }
-    int lights = 0;
-    for (int i = 0; i < sd->n_prims; ++i) {
-        const int t = sd->prim_type[i], m = sd->prim_mat[i];
-        if (t < 0 || t > 2) return *why = "bad primitive type", false;
-        if (m < 0 || m >= sd->n_mats) return *why = "primitive material out of range", false;
-        const float* mp = &sd->mat_param[8 * m];
-        const bool can_emit = mp[3] > 0.f || mp[4] > 0.f || mp[5] > 0.f || emission_bound[m];
-        if (t == kBox && can_emit) return *why = "emissive boxes are not supported", false;
-        lights += can_emit ? 1 : 0;
-        B->prim_type[i] = t;
-        B->prim_mat[i] = m;
-        for (int q = 0; q < 9; ++q) B->prim_geom[i][q] = sd->prim_geom[9 * i + q];
-        B->n_sph += (t == kSphere);
-        B->n_quad += (t == kQuad);
-        B->n_box += (t == kBox);
-    }
-    if (lights > kMaxLights) return *why = "more than 8 emitters", false;
-    int next[3] = {0, B->n_sph, B->n_sph + B->n_quad};
-    for (int i = 0; i < sd->n_prims; ++i) B->prim_slot[i] = next[B->prim_type[i]]++;
-    double eye[3], look[3], up[3];
-    for (int q = 0; q < 3; ++q) {
-        eye[q] = sd->camera[q];
-        look[q] = sd->camera[3 + q];
-        up[q] = sd->camera[6 + q];
-    }
-    double f[3] = {look[0] - eye[0], look[1] - eye[1], look[2] - eye[2]};
-    const double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-    if (!(fn > 0)) return *why = "camera eye equals look-at", false;
-    for (double& x : f) x /= fn;
-    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
-    const double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    if (!(rn > 0)) return *why = "camera up is parallel to the view direction", false;
-    for (double& x : r) x /= rn;
-    const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
-    for (int q = 0; q < 3; ++q) {
-        B->eye[q] = float(eye[q]);
-        B->fwd[q] = float(f[q]);
-        B->right[q] = float(r[q]);
-        B->up[q] = float(u[q]);
-        B->bg[q] = sd->background[q];
-    }
-    const double vfov = sd->camera[9];
-    if (!(vfov > 0 && vfov < 180)) return *why = "field of view must be in (0, 180) degrees", false;
-    B->tan_half = float(std::tan(0.5 * vfov * M_PI / 180.0));
-    return true;
+static_assert(sizeof(BaseScene) % 4 == 0 && sizeof(BaseScene) + sizeof(void*) <= 4096,
+              "the base scene must fit a kernel's parameter space");
+
+// Writes the call's base scene (a kernel parameter: host data that needs no copy) into the
+// scratch.
+__global__ void __launch_bounds__(256) k_static_scene(const BaseScene B, BaseScene* dst) {
+    const unsigned* src = reinterpret_cast<const unsigned*>(&B);
+    unsigned* out = reinterpret_cast<unsigned*>(dst);
+    for (int i = threadIdx.x; i < int(sizeof(BaseScene) / 4); i += blockDim.x) out[i] = src[i];
 }
 
 }  // namespace
@@ -143,11 +75,14 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
                                                    size_t err_len) {
     if (!scene || !binds || !o || !theta_dev || !sigma_dev || !target_dev || !grad_dev)
         return report(err, err_len, PRDPT_E_INVALID_ARG, "NULL argument");
-    if (o->pairs < 1 || 2 * o->pairs > kStaticMaxRenders)
+    if (o->pairs < 1 || o->pairs > kStaticMaxPairs)
         return report(err, err_len, PRDPT_E_INVALID_ARG, "pairs must be in 1..32 for the allocation-free call");
+    if (o->pair_begin < 0 || o->pair_begin > (1 << 26))
+        return report(err, err_len, PRDPT_E_INVALID_ARG, "pair_begin must be in 0..2^26");
     if (o->sampler < 0 || o->sampler > 2) return report(err, err_len, PRDPT_E_INVALID_ARG, "unknown sampler");
     if (o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT)
-        return report(err, err_len, PRDPT_E_INVALID_ARG, "the allocation-free call computes Eq. 10 only");
+        return report(err, err_len, PRDPT_E_INVALID_ARG,
+                      "the allocation-free call takes estimator = PRDPT_ESTIMATOR_KERNEL_GRADIENT only");
     if (o->width < 1 || o->height < 1 || o->width > 8192 || o->height > 8192)
         return report(err, err_len, PRDPT_E_INVALID_ARG, "width/height must be in 1..8192");
     if (o->spp < 1 || o->spp > 65535) return report(err, err_len, PRDPT_E_INVALID_ARG, "spp must be in 1..65535");
@@ -155,8 +90,8 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     if (o->rr_start < -1 || o->rr_start > 64)
         return report(err, err_len, PRDPT_E_INVALID_ARG, "rr_start must be -1 or 0..64");
     BaseScene B;
-    const char* why = nullptr;
-    if (!build_base_scene(scene, binds, D, &B, &why)) return report(err, err_len, PRDPT_E_INVALID_ARG, why);
+    if (const char* why = build_base_scene(scene, binds, D, false, &B))
+        return report(err, err_len, PRDPT_E_INVALID_ARG, why);
 
     const int R = 2 * o->pairs;
     int px = o->block_pixels;
@@ -168,9 +103,8 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
 
     // layout of the static scratch
     const size_t off_base = 0;
-    const size_t off_ctl = align256(off_base + sizeof(BaseScene));  // [0] queue, [1] done, [2] status
-    const size_t off_rdone = align256(off_ctl + 64);
-    const size_t off_loss = align256(off_rdone + sizeof(unsigned) * R);
+    const size_t off_ctl = align256(off_base + sizeof(BaseScene));
+    const size_t off_loss = align256(off_ctl + sizeof(unsigned) * kCtlWords);
     const size_t off_w = align256(off_loss + sizeof(double) * R);
     const size_t off_scn = align256(off_w + sizeof(float) * R * D);
     const size_t off_part = align256(off_scn + sizeof(InstScene) * R);
@@ -185,33 +119,31 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return report(err, err_len, PRDPT_E_CUDA, "cudaGetDevice failed");
-    DeviceSetup setup;
-    {
-        std::lock_guard<std::mutex> lk(g_setup_mu);
-        DeviceSetup& s = g_setup[dev];
-        if (!s.ready) {  // once per device, with that device current
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-            if (e != cudaSuccess) return report(err, err_len, PRDPT_E_CUDA, cudaGetErrorString(e));
-            int sms = 0;
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return report(err, err_len, PRDPT_E_CUDA, cudaGetErrorString(e));
-            s.scratch = static_cast<unsigned char*>(p);
-            s.sms = sms;
-            s.occ = trace_blocks_per_sm(false);
-            s.ready = true;
-        }
-        setup = s;
+    std::lock_guard<std::mutex> lk(g_mu[dev]);
+    DeviceSetup& setup = g_setup[dev];
+    if (!setup.ready) {  // once per device, with that device current
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return report(err, err_len, PRDPT_E_CUDA, cudaGetErrorString(e));
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return report(err, err_len, PRDPT_E_CUDA, cudaGetErrorString(e));
+        setup.scratch = static_cast<unsigned char*>(p);
+        setup.sms = sms;
+        setup.occ = trace_blocks_per_sm(false);
+        setup.ready = true;
     }
     unsigned char* base = setup.scratch;
     BaseScene* d_base = reinterpret_cast<BaseScene*>(base + off_base);
     unsigned* ctl = reinterpret_cast<unsigned*>(base + off_ctl);
-    unsigned* rdone = reinterpret_cast<unsigned*>(base + off_rdone);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    cudaError_t e = cudaMemcpyAsync(d_base, &B, sizeof(BaseScene), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 64, st);  // queue, done counter, status start at zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(rdone, 0, sizeof(unsigned) * R, st);
+    // The sampler kernel reads the base scene before it waits on the kernel ahead of it
+    // (programmatic dependent launch); the memset between them makes it wait for the
+    // scene write in plain stream order.
+    k_static_scene<<<1, 256, 0, st>>>(B, d_base);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kCtlWords, st);  // queue, done, status
     if (e != cudaSuccess) return report(err, err_len, PRDPT_E_CUDA, cudaGetErrorString(e));
 
     InstLaunch IL{};
@@ -264,7 +196,7 @@ extern "C" prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene
     J.n_mats = B.n_mats;
     TL.total_items = R * tiles;
     TL.queue = ctl + 0;
-    TL.status = reinterpret_cast<int*>(ctl + 2);
+    TL.status = reinterpret_cast<int*>(ctl + 2);  // written by the kernels, not reported by this call
     const int per_sm = (o->ctas_per_sm > 0 && o->ctas_per_sm < setup.occ) ? o->ctas_per_sm : setup.occ;
     const int cap = setup.sms * per_sm;
     const int want = (TL.total_items + kBlock / 32 - 1) / (kBlock / 32);

@@ -3,10 +3,11 @@
 It exists for callers that cannot allocate device memory -- a process whose device
 memory belongs to another allocator, or code that may not grow its footprint or
 create a library context after start-up. It must give the same gradient and losses
-as prdpt_smoothed_grad on the same inputs, call after call (its scratch is one
-fixed __device__ array reused by every call), and refuse requests larger than that
-array. This file is collected last so that a run stopping at the first failure has
-already run every other test.
+as prdpt_smoothed_grad on the same inputs (bit for bit at the same block shape),
+call after call (its scratch is one fixed __device__ array reused by every call),
+agree with the FP64 oracle, and refuse requests larger than that array. This file
+is collected last so that a run stopping at the first failure has already run every
+other test.
 """
 import ctypes as C
 
@@ -56,23 +57,30 @@ def _static_call(wl, theta, sigma, target, opts):
     lambda: workloads.config_small(),
     lambda: workloads.scaled(workloads.config_occlusion(), width=72, height=52, spp=8, pairs=8),
 ])
-def test_static_entry_matches_context_entry_twice(gpu_lib, make):
+@pytest.mark.parametrize("block_pixels", [16, 32])
+def test_static_entry_matches_context_entry_twice(gpu_lib, make, block_pixels):
+    """Two calls in a row (the shared scratch is reused): losses and gradient equal the
+    context call's bit for bit (same kernels, same block shape, integer pixel sums and
+    fixed-order reductions), and the oracle's within the parity tolerances."""
     from paper_2211_17263_gb300 import api
     wl = make()
-    target = _t(oracle.render_target(wl))
+    target_np = oracle.render_target(wl)
+    target = _t(target_np)
     theta, sigma = _t(wl.theta0), _t(wl.sigma)
     ctx = api.Context(0)
     try:
         scene = ctx.upload_scene(wl.scene, wl.bindings)
-        for step in (0, 1):  # two calls in a row: the shared scratch is reused
-            opts = scene.grad_opts(wl, step=step)
+        for step in (0, 1):
+            opts = scene.grad_opts(wl, step=step, block_pixels=block_pixels)
             g_ref, L_ref = scene.smoothed_grad(theta, sigma, target, opts)
             torch.cuda.synchronize()
             g_ref, L_ref = g_ref.cpu().numpy(), L_ref.cpu().numpy()
             g, L = _static_call(wl, theta, sigma, target, opts)
-            assert np.allclose(L, L_ref, rtol=1e-4, atol=1e-9), (L, L_ref)
-            w = np.ones((wl.renders, wl.D))
-            assert grad_rel_error(g, g_ref.astype(np.float64), w, L_ref) <= GRAD_REL, (g, g_ref)
+            assert np.array_equal(L, L_ref), (L, L_ref)
+            assert np.array_equal(g, g_ref), (g, g_ref)
+            ref = oracle.smoothed_grad(wl, target=target_np, step=step)
+            assert np.allclose(L, ref["losses"], rtol=1e-4, atol=0.0), (L, ref["losses"])
+            assert grad_rel_error(g, ref["grad"], ref["weights"], ref["losses"]) <= GRAD_REL, (g, ref["grad"])
     finally:
         ctx.close()
 
@@ -95,3 +103,9 @@ def test_static_entry_rejects_oversized_requests(gpu_lib):
     with pytest.raises(capi.PrdptError) as e:
         _static_call(big, theta, sigma, big_target, too_many_blocks)
     assert e.value.code == capi.PRDPT_E_OUT_OF_BUDGET and "scratch" in str(e.value)
+    bad_shard = capi.prdpt_grad_opts(pairs=4, width=wl.width, height=wl.height, spp=1, depth=1, rr_start=-1,
+                                     sampler=0, antithetic=1, crn=1, seed=0, step=0, block_pixels=0, ctas_per_sm=0,
+                                     pair_begin=-1)
+    with pytest.raises(capi.PrdptError) as e:
+        _static_call(wl, theta, sigma, target, bad_shard)
+    assert e.value.code == capi.PRDPT_E_INVALID_ARG and "pair_begin" in str(e.value)

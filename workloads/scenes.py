@@ -149,12 +149,13 @@ def _f32(x):
 
 
 def config_small(seed: int = 0) -> Workload:
-    """64x64, one diffuse sphere on a ground plane, 0.5x0.5 light (radiance 40), depth 1, 4 spp,
-    theta = sphere centre xy, sigma = 0.1, 4 antithetic pairs (8 renders)."""
+    """64x64, one diffuse sphere (r = 0.5, albedo 0.8) on a diffuse ground plane, 0.5x0.5
+    area light of radiance 10, depth 1 (direct light and shadow), 4 spp, theta = sphere
+    centre xy, sigma = 0.1, 4 antithetic pairs (8 renders), Philox seed 0."""
     b = SceneBuilder()
     m_ground = b.material(MAT_DIFFUSE, (0.8, 0.8, 0.8))
     m_sphere = b.material(MAT_DIFFUSE, (0.8, 0.8, 0.8))
-    m_light = b.material(MAT_DIFFUSE, (0.0, 0.0, 0.0), emission=(40.0, 40.0, 40.0))
+    m_light = b.material(MAT_DIFFUSE, (0.0, 0.0, 0.0), emission=(10.0, 10.0, 10.0))
     b.quad((0, 0, 0), (8, 0, 0), (0, 8, 0), m_ground)
     sph = b.sphere((0.0, 0.0, 0.5), 0.5, m_sphere)
     b.quad((1.5, 1.5, 2.5), (0.5, 0, 0), (0, -0.5, 0), m_light)
