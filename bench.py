@@ -5,9 +5,13 @@ perturbations (Sec. 3.2), bind theta +- tau into the scene, path-trace the R
 perturbed renders with the per-pixel loss reduced inside the render kernel, form
 the gradient of Eq. 10 and apply Adam -- all on the device.
 
-Workload: the occlusion scene (256x256, three diffuse spheres and a 0.4^3 box on a
-plane under a 1x1 area light, depth 4, 16 spp, theta = box centre, sigma = 0.05,
-N = 16 renders = 8 antithetic pairs), synthetic and seeded.
+Workload (default): the caustic task, the largest single-GPU configuration -- a
+512x512 image of a glass sphere (IOR 1.5) above a diffuse floor lit by a small
+0.2x0.2 area light, path depth 12 with Russian roulette from the 4th vertex,
+theta = light position (3-D), sigma = 0.125, N = 64 renders (32 antithetic pairs) x
+64 spp = 1.07 G paths per step; synthetic and seeded. `--workload` measures the
+other workloads (occlusion 256^2, GI box 512^2, small 64^2, texture, Eq. 9 ones).
+The serving mix (continuous batching of concurrent jobs) is measured beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -134,14 +138,16 @@ def _kernel_source_sha(read=None):
     return h.hexdigest()[:16]
 
 
+def _profile_path(workload_name):
+    return os.path.join(ROOT, "profiles", f"render_pipeline_{workload_name}_ncu.md")
+
+
 def _profiled(workload_name, key):
-    """A per-step figure of the occlusion workload's render kernels from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    if not workload_name.startswith("occlusion"):
-        return None
-    path = os.path.join(ROOT, "profiles", "render_pipeline_occlusion-256x256_ncu.md")
+    """A per-step figure of the workload's render kernels from the committed ncu summary
+    profiles/render_pipeline_<workload>_ncu.md, if it was taken on the current kernel
+    source (hash of the code without comments); else None."""
     try:
-        text = open(path).read()
+        text = open(_profile_path(workload_name)).read()
     except OSError:
         return None
     vals = {}
@@ -161,13 +167,18 @@ CPU_SAMPLE_MAX_PATHS = 40_000_000  # larger steps are sampled (one pair, 4 spp) 
 
 
 def _issue_rate(workload_name, sms, sm_mhz, pipeline_ms, per_render_ms):
+    """Warp instructions issued per second against 4 schedulers x SMs x clock: counts per
+    step from the committed ncu summary (None unless its kernel source hash matches),
+    times from this run."""
     peak = 4.0 * sms * sm_mhz * 1e6 / 1e9  # G warp instructions / s
     out = {"unit": "G warp instr/s", "peak": peak}
     for key, ms, name in (("warp_instructions_per_step", pipeline_ms, "pipeline"),
                           ("warp_instructions_per_step_no_sharing", per_render_ms, "per_render_kernel")):
         n = _profiled(workload_name, key)
         if n is None or not ms:
-            return None
+            if name == "pipeline":
+                return None
+            continue
         out[name] = n / (ms * 1e-3) / 1e9
         out[name + "_frac"] = out[name] / peak
     return out
@@ -197,36 +208,47 @@ def cpu_baseline(wl, target, nthreads=0, budget_s=10.0, max_steps=20):
                       f"{dt:.2f} s per full step", "cpu_model": _cpu_model()}
 
 
-def serving_bench(device, n_jobs, steps_per_job, gpaths_per_s, seed=0):
+def serving_bench(device, n_jobs, steps_per_job, modes, seed=0):
     """Serving mix (jobs drawn from the small, occlusion and GI-box workloads with random
-    resolution 128-512, N in {8,16,32,64} renders, spp in {8,...,64}): Poisson arrivals at
-    1.5x the plain path's estimated capacity, served one job per launch ("plain") and with
-    continuous batching ("batched"), on the same arrival sequence."""
+    resolution 128-512, N in {8,16,32,64} renders, spp in {8,...,64}; 100 steps per job, 300
+    for GI-box jobs, unless steps_per_job is given): Poisson arrivals at 1.5x the plain
+    path's capacity, measured first from one timed step of each job alone, served one job
+    per launch ("plain"), packed ("batched") and packed with CUDA-graph replay ("graphed"),
+    on the same arrival sequence."""
     import workloads
     from paper_2211_17263_gb300 import api
-    from paper_2211_17263_gb300.serve import Server
+    from paper_2211_17263_gb300.serve import Server, plain_capacity
 
     base = workloads.serving_mix(n_jobs=n_jobs, seed=seed)
-    mean_paths = float(np.mean([wl.paths_per_step for _, wl in base])) * steps_per_job
-    capacity_jobs_per_s = gpaths_per_s * 1e9 / mean_paths
-    rate = 1.5 * capacity_jobs_per_s
+    steps_of = (lambda wl: steps_per_job) if steps_per_job else (lambda wl: wl.steps)
+    ctx = api.Context(device, hbm_budget_bytes=150 * 10 ** 9)
+    try:
+        cap = plain_capacity(ctx, [wl for _, wl in base], steps_of)
+    finally:
+        ctx.close()
+    rate = 1.5 * cap["jobs_per_s"]
     rng = np.random.default_rng(seed + 7)
     t, arrivals = 0.0, []
     for _, wl in base:
         t += float(rng.exponential(1.0 / rate))
         arrivals.append((t, wl))
-    out = {"jobs": n_jobs, "steps_per_job": steps_per_job, "arrival_rate_jobs_per_s": rate,
-           "hbm_budget_bytes": 150 * 10 ** 9}
-    for mode in ("plain", "batched", "graphed"):
+    out = {"jobs": n_jobs, "job_steps": int(sum(steps_of(wl) for _, wl in base)),
+           "steps_per_job": steps_per_job or "100 (GI box: 300)",
+           "subset": "the first n jobs of the 256-job mix" if n_jobs < 256 else "the full mix",
+           "plain_capacity": cap, "arrival_rate_jobs_per_s": rate, "hbm_budget_bytes": 150 * 10 ** 9}
+    for mode in modes:
         ctx = api.Context(device, hbm_budget_bytes=150 * 10 ** 9)
         try:
-            rep, _ = Server(ctx, mode=mode, max_active=256).run(arrivals, steps_per_job=lambda wl: steps_per_job)
+            rep, _ = Server(ctx, mode=mode, max_active=256).run(arrivals, steps_per_job=steps_of)
         finally:
             ctx.close()
         out[mode] = {k: rep[k] for k in ("steps_per_s", "mpaths_per_s", "p50_ms", "p99_ms", "peak_active", "wall_s",
-                                         "graph_replays")}
-    out["batched_over_plain"] = out["batched"]["steps_per_s"] / out["plain"]["steps_per_s"]
-    out["graphed_over_plain"] = out["graphed"]["steps_per_s"] / out["plain"]["steps_per_s"]
+                                         "graph_replays", "graph_captures", "admission_ms_mean", "ticks")
+                     if k in rep}
+    if "plain" in out:
+        for mode in modes:
+            if mode != "plain":
+                out[f"{mode}_over_plain"] = out[mode]["steps_per_s"] / out["plain"]["steps_per_s"]
     return out
 
 
@@ -236,15 +258,18 @@ def run_reference(args, rank, world):
         return
     import oracle
     import workloads
-    wl = workloads.config_occlusion()
-    target = oracle.render_target(wl)
+    wl = getattr(workloads, WORKLOADS[args.workload])()
     cores = os.cpu_count() or 1
-    # whole steps while K of them fit in about 100 s; else each step is a bounded sample
-    # (one pair at 4 spp) whose time is scaled by the ratio of path counts
-    t0 = time.perf_counter()
-    oracle.smoothed_grad(wl, target=target, nthreads=cores, step=0)
-    full = time.perf_counter() - t0
+    target = oracle.render_target(wl, nthreads=cores)
+    # whole steps while K of them fit in about 100 s; else (and always above
+    # CPU_SAMPLE_MAX_PATHS paths per step) each step is a bounded sample -- one pair at
+    # 4 spp -- whose time is scaled by the ratio of path counts
     run, scale, what = wl, 1.0, "whole steps"
+    full = float("inf")
+    if wl.paths_per_step <= CPU_SAMPLE_MAX_PATHS:
+        t0 = time.perf_counter()
+        oracle.smoothed_grad(wl, target=target, nthreads=cores, step=0)
+        full = time.perf_counter() - t0
     if full * args.steps > 100.0:
         run = workloads.scaled(wl, spp=4, pairs=1)
         scale = wl.paths_per_step / run.paths_per_step
@@ -273,15 +298,19 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--block-pixels", type=int, default=0, help="pixels per warp work item (8, 16, 32; 0 = auto)")
-    ap.add_argument("--serving-jobs", type=int, default=64, help="jobs in the serving mix (0 = skip serving)")
-    ap.add_argument("--serving-steps", type=int, default=4, help="steps per served job")
-    ap.add_argument("--workload", default="occlusion", choices=sorted(WORKLOADS),
-                    help="occlusion is the headline workload; the others are measured on request")
+    ap.add_argument("--block-pixels", type=int, default=0,
+                    help="pixels per warp work item (8, 16, 32; 0 = the autotuned or default shape)")
+    ap.add_argument("--serving-jobs", type=int, default=12,
+                    help="jobs of the serving mix served in each mode (0 = skip serving); 256 is the full mix")
+    ap.add_argument("--serving-steps", type=int, default=0,
+                    help="steps per served job (0 = the mix's own: 100, and 300 for GI-box jobs)")
+    ap.add_argument("--serving-modes", default="plain,batched,graphed")
+    ap.add_argument("--workload", default="caustic", choices=sorted(WORKLOADS),
+                    help="caustic (512^2, 64 renders x 64 spp, depth 12) is the headline; the others on request")
     ap.add_argument("--estimator", default="auto", choices=["auto", "kernel", "pathwise"],
                     help="auto: the workload's own; kernel: Eq. 10 with the radial sampler; pathwise: Eq. 9 "
                          "(Gaussian draws; material bindings only)")
@@ -298,7 +327,7 @@ def main():
     import torch.distributed as dist
 
     import workloads
-    from paper_2211_17263_gb300 import api
+    from paper_2211_17263_gb300 import api, autotune
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
@@ -321,7 +350,16 @@ def main():
     target = scene.render_batch(dev(wl.theta_ref[None]), wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
                                 seed=wl.seed, step=0, tag=3, crn=1)[0]
     target_host = target.cpu().numpy()
-    job = api.Job(scene, wl, target_host, block_pixels=args.block_pixels)
+    # launch shape: given, else the autotuner's choice for this workload shape (tuned now if
+    # the cache has no entry; the tuning steps run before and outside the timed region)
+    tuned = None
+    if args.block_pixels:
+        shape = {"block_pixels": args.block_pixels, "ctas_per_sm": 0, "source": "--block-pixels"}
+    else:
+        tuned = autotune.autotune(scene, wl, target_host)
+        shape = {"block_pixels": tuned["block_pixels"], "ctas_per_sm": tuned["ctas_per_sm"],
+                 "source": "autotuner (cached)" if tuned["cached"] else "autotuner"}
+    job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"])
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         job.step(stream)
@@ -334,6 +372,7 @@ def main():
     ctx.counters_enable(False)
     flops_step = (counts[0] * FLOPS["sphere_test"] + counts[1] * FLOPS["quad_test"] + counts[2] * FLOPS["box_test"]
                   + counts[3] * FLOPS["path"] + counts[4] * FLOPS["vertex"])
+    sharing = counts[3] < wl.paths_per_step  # path sharing traces fewer paths than R x H x W x S
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > L2
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -360,38 +399,41 @@ def main():
                                    device=f"cuda:{local}")
     state = job.read()
 
-    # the per-render kernel on the same workload (path sharing off): its own roofline
-    plain_job = api.Job(scene, wl, target_host, block_pixels=args.block_pixels, no_path_sharing=1)
-    for _ in range(3):
+    # with path sharing: the per-render kernel on the same workload (sharing off), its own
+    # roofline; without, the timed step already is the per-render kernel
+    per_render = None
+    if sharing:
+        plain_job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"],
+                            ctas_per_sm=shape["ctas_per_sm"], no_path_sharing=1)
+        for _ in range(3):
+            plain_job.step(stream)
+        ctx.counters_enable(True)
         plain_job.step(stream)
-    ctx.counters_enable(True)
-    plain_job.step(stream)
-    pcounts = ctx.counters_read()
-    ctx.counters_enable(False)
-    torch.cuda.synchronize()
-    ctx.kernel_timing(True)
-    n_plain = min(args.steps, 100)
-    for _ in range(n_plain):
-        flush.zero_()
-        plain_job.step(stream)
-    p_ms, p_launches = ctx.kernel_timing_read()
-    ctx.kernel_timing(False)
-    plain_job.release()
-    pflops = (pcounts[0] * FLOPS["sphere_test"] + pcounts[1] * FLOPS["quad_test"] + pcounts[2] * FLOPS["box_test"]
-              + pcounts[3] * FLOPS["path"] + pcounts[4] * FLOPS["vertex"])
+        pcounts = ctx.counters_read()
+        ctx.counters_enable(False)
+        torch.cuda.synchronize()
+        ctx.kernel_timing(True)
+        n_plain = min(args.steps, 100)
+        for _ in range(n_plain):
+            flush.zero_()
+            plain_job.step(stream)
+        p_ms, p_launches = ctx.kernel_timing_read()
+        ctx.kernel_timing(False)
+        plain_job.release()
+        pflops = (pcounts[0] * FLOPS["sphere_test"] + pcounts[1] * FLOPS["quad_test"]
+                  + pcounts[2] * FLOPS["box_test"] + pcounts[3] * FLOPS["path"] + pcounts[4] * FLOPS["vertex"])
+        per_render = {"counts": pcounts, "ms": p_ms / max(p_launches, 1), "flops": pflops}
 
-    # end to end through the C ABI with host buffers: H2D inputs, gradient, Adam, D2H results
-    e2e = None
-    # through the C ABI with host buffers (prdpt_step_host): each step uploads theta, Adam's
-    # m and v, sigma and the target from page-locked memory, computes the gradient, applies
-    # Adam on the device and downloads theta, m, v, the gradient and the losses
+    # end to end through the C ABI with host buffers (prdpt_step_host): each step uploads
+    # theta, Adam's m and v, sigma and the target from page-locked memory, computes the
+    # gradient, applies Adam on the device and downloads theta, m, v, the gradient and the losses
     D, R, npx4 = wl.D, wl.renders, 4 * wl.width * wl.height
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()  # noqa: E731
     theta_h, sigma_h, target_h = pin(wl.theta0), pin(wl.sigma), pin(target_host)
     m_h, v_h, g_h, L_h = pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(R))
     h2d = 4 * (npx4 + 4 * D + 1)  # target; sigma, Adam's step, theta, m, v in one staged copy
     d2h = 4 * (4 * D + R)  # theta, m, v, gradient, losses in one copy
-    opts = scene.grad_opts(wl, step=0)
+    opts = scene.grad_opts(wl, step=0, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"])
 
     def e2e_step(k):
         opts.step = k
@@ -407,7 +449,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_s = pdist.max_over_ranks((time.perf_counter() - t0) / args.steps, world, device=f"cuda:{local}")
-    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "call": "prdpt_step_host"}
 
     if rank == 0:
         peaks = _measured_peaks()
@@ -416,53 +459,69 @@ def main():
         fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
         trace_avg_ms = trace_ms / max(launches, 1)
         achieved = flops_step / (trace_avg_ms * 1e-3) / 1e12
-        p_avg_ms = p_ms / max(p_launches, 1)
-        p_achieved = pflops / (p_avg_ms * 1e-3) / 1e12
         value = world * 1000.0 / step_ms
+        traffic = _profiled(wl.name, "dram_bytes_per_step")
+        kernels = ("render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue, k_finalize)"
+                   if sharing else "render kernel k_trace + k_finalize")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "renders": wl.renders, "pairs": wl.pairs, "width": wl.width,
-                       "height": wl.height, "spp": wl.spp, "depth": wl.depth, "D": wl.D,
+                       "height": wl.height, "spp": wl.spp, "depth": wl.depth, "rr_start": wl.rr_start, "D": wl.D,
                        "estimator": "Eq. 9 (pathwise)" if getattr(wl, "estimator", 0) == 1 else "Eq. 10",
+                       "launch_shape": shape, "path_sharing": bool(sharing),
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            # paths of the method per second: R x H x W x S per step; with path sharing
+            # ("effective") fewer are traced -- mpaths_traced_per_s counts those
             "mpaths_per_s": world * wl.paths_per_step / (step_ms * 1e-3) / 1e6,
-            # ray segments (closest-hit rays + shadow rays) traced per second: as executed
-            # (shared pass + re-traced paths) and as the method defines them (every render)
+            "mpaths_per_s_kind": "effective (R x H x W x S per step; path sharing traces fewer)" if sharing
+                                 else "traced (R x H x W x S per step, every path traced)",
+            "mpaths_traced_per_s": world * counts[3] / (step_ms * 1e-3) / 1e6,
+            # ray segments (closest-hit rays + shadow rays) traced per second
             "msegments_per_s": world * (counts[5] + counts[6]) / (step_ms * 1e-3) / 1e6,
-            "msegments_per_s_method": world * (pcounts[5] + pcounts[6]) / (step_ms * 1e-3) / 1e6,
             "wall_s": wall,
             "render_kernel_ms": trace_avg_ms,
             "work_per_step": {"sphere_tests": counts[0], "quad_tests": counts[1], "box_tests": counts[2],
                               "paths": counts[3], "vertices": counts[4], "shadow_rays": counts[5],
                               "closest_hit_rays": counts[6]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": _profiled(wl.name, "dram_bytes_per_step"),
-                         "kernel": ("render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue,"
-                                    " k_finalize)" if counts[3] < wl.paths_per_step else "k_trace + k_finalize"),
+                         "frac": achieved / fp32_peak, "traffic": traffic,
+                         "traffic_source": (f"ncu, profiles/{os.path.basename(_profile_path(wl.name))} (kernel "
+                                            "source hash matches)") if traffic is not None else None,
+                         "kernel": kernels,
+                         "achieved_basis": "model FP32 flop per step from the kernels' work counters / mean "
+                                           "CUDA-event time of the step's kernels",
                          "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
                                        f" x 2 flop x {sm_max:.0f} MHz"},
-            "roofline_per_render_kernel": {
-                "bound": "alu", "achieved": p_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": p_achieved / fp32_peak, "kernel": "k_trace (path sharing off) + k_finalize",
-                "ms_per_step": p_avg_ms, "paths_per_step": pcounts[3]},
-            # diagnostic beside the algorithmic roofline: warp instructions issued per second
-            # (ncu count per step from the committed summary) against 4 schedulers x SMs x clock
-            "issue_rate": _issue_rate(wl.name, props.multi_processor_count, sm_max, trace_avg_ms, p_avg_ms),
             "fp32_probe": {"achieved_tflops": probe_tflops, "ms": probe_ms,
                            "frac_of_peak": probe_tflops / fp32_peak},
             "e2e": e2e,
             # sampler, render kernel(s), finalisation; path sharing adds the per-render and
             # epilogue passes; texture scenes add the D-dimensional draws and gradient kernels
-            "gpu_launches": ((5 if counts[3] < wl.paths_per_step else 3)
+            "gpu_launches": ((5 if sharing else 3)
                              + ((3 if wl.sampler == workloads.SAMPLER_RADIAL else 2) if wl.D > 64 else 0)) * args.steps,
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
         }
-        if world == 1 and args.serving_jobs > 0 and args.workload == "occlusion":
+        if per_render is not None:
+            p_achieved = per_render["flops"] / (per_render["ms"] * 1e-3) / 1e12
+            line["roofline_per_render_kernel"] = {
+                "bound": "alu", "achieved": p_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": p_achieved / fp32_peak, "kernel": "k_trace (path sharing off) + k_finalize",
+                "ms_per_step": per_render["ms"], "paths_per_step": per_render["counts"][3]}
+        issue = _issue_rate(wl.name, props.multi_processor_count, sm_max, trace_avg_ms,
+                            per_render["ms"] if per_render else None)
+        if issue is not None:
+            issue["source"] = "warp instructions per step from the committed ncu summary; times from this run"
+        line["issue_rate"] = issue
+        if tuned is not None:
+            line["autotune"] = {"choice": {"block_pixels": tuned["block_pixels"], "ctas_per_sm": tuned["ctas_per_sm"]},
+                                "cached": tuned["cached"], "ms": tuned.get("ms"),
+                                "tried": tuned.get("tried")}
+        if world == 1 and args.serving_jobs > 0:
             line["serving"] = serving_bench(local, args.serving_jobs, args.serving_steps,
-                                            line["mpaths_per_s"] / 1000.0)
+                                            [m for m in args.serving_modes.split(",") if m])
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, target_host)
             # the same oracle on one thread (one bounded sample), beside the all-core figure

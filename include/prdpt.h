@@ -176,7 +176,9 @@ const char* prdpt_last_error(prdpt_ctx* ctx);
 prdpt_status prdpt_scene_upload(prdpt_ctx* ctx, const prdpt_scene_desc* scene, const prdpt_param_binding* binds,
                                 int32_t D, int32_t* scene_id_out);
 
-/* Free a scene. Jobs using it must have been released. Synchronous. */
+/* Free a scene. Jobs using it must have been released (each job keeps its own copy of
+ * the scene). Does not wait for the device: the scene's block is reused once the last
+ * stateless call that read it has completed. */
 prdpt_status prdpt_scene_release(prdpt_ctx* ctx, int32_t scene_id);
 
 /* Render n scenes at parameter vectors thetas_dev [n][D] (Eq. 3 per pixel):
@@ -230,8 +232,12 @@ prdpt_status prdpt_adam_step(prdpt_ctx* ctx, int32_t D, float* theta_dev, float*
                              const float* grad_dev, int32_t t, float lr, float beta1, float beta2, float eps,
                              void* stream);
 
-/* Create a resident job on a scene: copies theta0, sigma0 and the target into
- * library-owned device memory (charged to the HBM budget). Synchronous. */
+/* Create a resident job on a scene: copies theta0, sigma0, the target (target_host may be
+ * NULL: then the target starts at zero and is rendered on the device by
+ * prdpt_job_render_target) and the scene into library-owned device memory, charged to the
+ * HBM budget. The block may be one a released job or scene left behind (see
+ * prdpt_job_release). Synchronous, but the uploads run on a stream of the context's own
+ * that waits for no other work on the device. */
 prdpt_status prdpt_job_create(prdpt_ctx* ctx, int32_t scene_id, const prdpt_job_desc* desc, int32_t* job_out);
 
 /* One optimisation step of a resident job, all on the device: draw perturbations,
@@ -246,13 +252,27 @@ prdpt_status prdpt_step(prdpt_ctx* ctx, int32_t job_id, void* stream);
 prdpt_status prdpt_step_batch(prdpt_ctx* ctx, const int32_t* job_ids, int32_t n, void* stream);
 
 /* Copy a job's current parameters [D], last gradient [D], last per-render losses
- * [2P] and completed-step count to the host (any pointer may be NULL).
- * Synchronises the job's last stream and checks the device status word. */
+ * [2P] and completed-step count to the host (any pointer may be NULL). Waits for the
+ * job's last enqueued work only (after a step enqueued inside a CUDA-graph capture: for
+ * the whole device) and checks the device status word. */
 prdpt_status prdpt_job_read(prdpt_ctx* ctx, int32_t job_id, float* theta_host, float* grad_host,
                             float* losses_host, int32_t* steps_host);
 
-/* Free a job's device memory. Synchronous. */
+/* Release a job. Does not wait for the device: the job's block is kept by the context
+ * and reused (by a later prdpt_job_create or prdpt_scene_upload of a fitting size) only
+ * once the job's last enqueued work has completed; blocks are returned to the device
+ * when an allocation would otherwise exceed the budget or the device. A job stepped
+ * inside a CUDA-graph capture waits for the device here (replays are not tracked); such a
+ * graph must not be replayed after the release. */
 prdpt_status prdpt_job_release(prdpt_ctx* ctx, int32_t job_id);
+
+/* Render the target image of a job (Sec. 4.1: the target is a render at the reference
+ * parameters) straight into its device buffer: one render at theta_ref_dev [D] (device
+ * memory; for a texture scene the texture itself) on random stream TARGET (tag 3), step
+ * 0, common path field 0, with the job's image size, spp, depth, Russian roulette and
+ * seed -- the same image as prdpt_render_batch with those options. Enqueued on `stream`;
+ * the job's steps must come after it in stream order. No host round trip. */
+prdpt_status prdpt_job_render_target(prdpt_ctx* ctx, int32_t job_id, const float* theta_ref_dev, void* stream);
 
 /* Philox4x32-10 words for counters (c0_base + i, c1, c2, c3), key = seed:
  * words_dev [n][4]. Exposed so that the random streams can be checked bit for bit. */
@@ -275,7 +295,8 @@ prdpt_status prdpt_counters_read(prdpt_ctx* ctx, uint64_t* counts_host);
 prdpt_status prdpt_kernel_timing_enable(prdpt_ctx* ctx, int32_t enable);
 prdpt_status prdpt_kernel_timing_read(prdpt_ctx* ctx, double* total_ms, int64_t* launches);
 
-/* Device memory the context currently holds (scenes, jobs, scratch), in bytes. */
+/* Device memory the context currently holds (scenes, jobs, scratch, and released job and
+ * scene blocks kept for reuse), in bytes. */
 prdpt_status prdpt_memory_used(prdpt_ctx* ctx, uint64_t* bytes_out);
 
 /* FP32 issue-rate probe (a measurement utility; the paper has no counterpart): one

@@ -180,25 +180,49 @@ class Scene:
 
 
 class Job:
-    """A resident optimisation job: parameters, Adam state and target live on the device."""
+    """A resident optimisation job: parameters, Adam state and target live on the device.
 
-    def __init__(self, scene: Scene, wl, target_host: np.ndarray, step0=0, block_pixels=0, ctas_per_sm=0,
-                 anneal=None, lr=None, sampler=None, no_path_sharing=0):
+    target_host: the [H, W, 4] target image, or None to render it on the device later
+    (render_target). With block_pixels = ctas_per_sm = 0 the launch shape is the one the
+    autotuner cached for this workload's shape, if any (see autotune.py), else the
+    library's default."""
+
+    def __init__(self, scene: Scene, wl, target_host: np.ndarray | None, step0=0, block_pixels=0, ctas_per_sm=0,
+                 anneal=None, lr=None, sampler=None, no_path_sharing=0, use_tuned=True):
         self.scene = scene
         self.D = scene.D
         self.R = 2 * wl.pairs
         self._theta0 = np.ascontiguousarray(wl.theta0, np.float32)
         self._sigma0 = np.ascontiguousarray(wl.sigma, np.float32)
-        self._target = np.ascontiguousarray(target_host, np.float32)
-        if self._target.shape != (wl.height, wl.width, 4):
-            raise ValueError("target must be [H, W, 4] float32")
+        self._target = None
+        if target_host is not None:
+            self._target = np.ascontiguousarray(target_host, np.float32)
+            if self._target.shape != (wl.height, wl.width, 4):
+                raise ValueError("target must be [H, W, 4] float32")
+        self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm, "source": "given"}
+        if use_tuned and block_pixels == 0 and ctas_per_sm == 0:
+            from . import autotune
+            hit = autotune.cached_shape(wl)
+            if hit is not None:
+                block_pixels, ctas_per_sm = hit["block_pixels"], hit["ctas_per_sm"]
+                self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm,
+                                     "source": "autotuner cache"}
+            else:
+                self.launch_shape["source"] = "library default"
         desc = capi.prdpt_job_desc(
             grad=scene.grad_opts(wl, step=step0, sampler=sampler, block_pixels=block_pixels,
                                  ctas_per_sm=ctas_per_sm, no_path_sharing=no_path_sharing),
-            theta0_host=_np_ptr(self._theta0), sigma0_host=_np_ptr(self._sigma0), target_host=_np_ptr(self._target),
+            theta0_host=_np_ptr(self._theta0), sigma0_host=_np_ptr(self._sigma0),
+            target_host=None if self._target is None else _np_ptr(self._target),
             lr=wl.lr if lr is None else lr, beta1=0.9, beta2=0.999, eps=1e-8, sigma_min=wl.sigma_min,
             anneal=wl.anneal if anneal is None else anneal, total_steps=wl.steps)
         self.id = capi.prdpt_job_create(scene.ctx.handle, scene.id, desc)
+
+    def render_target(self, theta_ref: torch.Tensor, stream=None):
+        """Render the job's target at theta_ref [D] (device tensor) into its device buffer
+        (prdpt_job_render_target), enqueued on `stream`; no host round trip."""
+        capi.prdpt_job_render_target(self.scene.ctx.handle, self.id, _dev_ptr(theta_ref.reshape(-1)),
+                                     _stream_ptr(stream))
 
     def step(self, stream=None):
         capi.prdpt_step(self.scene.ctx.handle, self.id, _stream_ptr(stream))

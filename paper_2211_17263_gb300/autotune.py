@@ -17,6 +17,11 @@ import numpy as np
 from . import api
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "prdpt_gb300", "autotune.json")
+
+
+def default_cache() -> str:
+    """The cache file: $PRDPT_AUTOTUNE_CACHE if set, else DEFAULT_CACHE."""
+    return os.environ.get("PRDPT_AUTOTUNE_CACHE") or DEFAULT_CACHE
 CANDIDATES = [(px, cps) for px in (32, 16, 8) for cps in (3, 2, 1)]
 _lock = threading.Lock()
 
@@ -45,6 +50,18 @@ def _store(path, table):
     os.replace(tmp, path)
 
 
+def cached_shape(wl, cache_path: str | None = ""):
+    """The cached best launch shape for this workload's shape, or None (never tunes).
+    cache_path "" means default_cache(); None disables the lookup."""
+    if cache_path == "":
+        cache_path = default_cache()
+    if not cache_path:
+        return None
+    with _lock:
+        hit = _load(cache_path).get(shape_key(wl))
+    return hit
+
+
 def time_candidate(scene: api.Scene, wl, target_host: np.ndarray, block_pixels: int, ctas_per_sm: int,
                    steps: int = 3) -> float:
     """Mean render-kernel time (ms) of `steps` resident steps with this launch shape."""
@@ -63,9 +80,12 @@ def time_candidate(scene: api.Scene, wl, target_host: np.ndarray, block_pixels: 
         job.release()
 
 
-def autotune(scene: api.Scene, wl, target_host: np.ndarray, cache_path: str | None = DEFAULT_CACHE,
+def autotune(scene: api.Scene, wl, target_host: np.ndarray, cache_path: str | None = "",
              candidates=None, steps: int = 3, force: bool = False) -> dict:
-    """Best (block_pixels, ctas_per_sm) for this workload shape; cached by shape_key."""
+    """Best (block_pixels, ctas_per_sm) for this workload shape; cached by shape_key
+    (cache_path "" means default_cache(); None: no cache)."""
+    if cache_path == "":
+        cache_path = default_cache()
     key = shape_key(wl)
     if cache_path and not force:
         with _lock:

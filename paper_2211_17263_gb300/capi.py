@@ -33,7 +33,7 @@ EXPORTS = [
     "prdpt_job_create", "prdpt_step", "prdpt_step_batch", "prdpt_job_read", "prdpt_job_release",
     "prdpt_philox_words", "prdpt_counters_enable", "prdpt_counters_read", "prdpt_kernel_timing_enable",
     "prdpt_kernel_timing_read", "prdpt_sync", "prdpt_smoothed_grad_static", "prdpt_memory_used",
-    "prdpt_fp32_peak_probe", "prdpt_smoothed_grad_host", "prdpt_step_host",
+    "prdpt_fp32_peak_probe", "prdpt_smoothed_grad_host", "prdpt_step_host", "prdpt_job_render_target",
 ]
 
 
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         "prdpt_step_batch": ([vp, P(i32), i32, vp], i32),
         "prdpt_job_read": ([vp, i32, vp, vp, vp, P(i32)], i32),
         "prdpt_job_release": ([vp, i32], i32),
+        "prdpt_job_render_target": ([vp, i32, vp, vp], i32),
         "prdpt_philox_words": ([vp, u64, u32, u32, u32, u32, i32, vp, vp], i32),
         "prdpt_counters_enable": ([vp, i32], i32),
         "prdpt_counters_read": ([vp, P(u64)], i32),
@@ -225,6 +226,10 @@ def prdpt_job_read(ctx, job_id, theta_host, grad_host, losses_host):
 
 def prdpt_job_release(ctx, job_id):
     return check(load().prdpt_job_release(ctx, job_id), "prdpt_job_release", ctx)
+
+
+def prdpt_job_render_target(ctx, job_id, theta_ref_dev, stream):
+    return check(load().prdpt_job_render_target(ctx, job_id, theta_ref_dev, stream), "prdpt_job_render_target", ctx)
 
 
 def prdpt_philox_words(ctx, seed, c0_base, c1, c2, c3, n, words_dev, stream):

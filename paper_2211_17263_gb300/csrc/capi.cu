@@ -4,6 +4,7 @@
 // the stateless calls, descriptor arrays for packed launches) and turns each call
 // into at most two kernel launches: k_instantiate (sampler + scene binding) and
 // k_trace (persistent render with the fused loss / gradient / Adam epilogue).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,10 +39,17 @@ struct Scene {
     BaseScene* dev = nullptr;
     int D = 0;
     int jobs = 0;
+    cudaEvent_t use = nullptr;  // recorded after each stateless call that reads `dev`
+    bool used = false;
+    bool captured = false;      // read by work captured into a CUDA graph (no event to wait on)
 };
 
 struct Job {
     void* base = nullptr;  // the job's one device allocation
+    BaseScene* scene_copy = nullptr;  // the job's own copy of its scene (in `base`)
+    cudaEvent_t last = nullptr;       // recorded after each enqueue of the job's work
+    bool used = false;
+    bool captured = false;            // stepped inside a CUDA-graph capture: replays are not tracked
     int scene = -1;
     int D = 0, R = 0, tiles = 0, ctas_per_sm = 0;
     size_t bytes = 0;
@@ -125,6 +133,23 @@ struct prdpt_ctx {
     // optional CUDA-event timing of the render kernel, recorded on its launch stream
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+    // page-locked staging of the packed-step descriptors, two slots used in turn; each
+    // slot's event marks the end of its last upload
+    unsigned char* h_desc[2] = {nullptr, nullptr};
+    size_t h_desc_n = 0;
+    cudaEvent_t h_desc_ev[2] = {nullptr, nullptr};
+    int desc_slot = 0;
+    // released job and scene blocks kept for reuse (cudaFree would synchronise the device):
+    // a block is reused once the event recorded after its last use has completed
+    struct Cached {
+        void* p;
+        size_t bytes;
+        cudaEvent_t ready;  // null: idle already
+    };
+    std::vector<Cached> cache;
+    size_t cached_bytes = 0;
+    std::vector<cudaEvent_t> ev_pool;  // unrecorded events for jobs and scenes
+    cudaStream_t io = nullptr;  // non-blocking stream of the synchronous uploads and reads
     std::mutex mu;
 };
 
@@ -162,6 +187,103 @@ prdpt_status grow(prdpt_ctx* c, T** p, size_t* cap, size_t n) {
     if (st) return st;
     *cap = n;
     return PRDPT_OK;
+}
+
+// Is `st` capturing a CUDA graph? An event recorded there marks nothing at replay time,
+// so work enqueued during a capture is not tracked by events (conservatively true when
+// the query itself fails).
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Mark the end of a job's (or scene's) enqueued work on `st`.
+cudaError_t mark_use(cudaEvent_t ev, bool* used, bool* captured, cudaStream_t st) {
+    if (capturing(st)) {
+        *captured = true;
+        return cudaSuccess;
+    }
+    *used = true;
+    return cudaEventRecord(ev, st);
+}
+
+cudaEvent_t take_event(prdpt_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Has the work before `e` completed? (A not-ready query leaves no error behind.)
+bool event_done(cudaEvent_t e) {
+    if (!e) return true;
+    const cudaError_t q = cudaEventQuery(e);
+    if (q == cudaErrorNotReady) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// Free every cached block whose last use has completed (cudaFree synchronises the device;
+// this runs only when an allocation would not fit otherwise).
+void trim_cache(prdpt_ctx* c) {
+    std::vector<prdpt_ctx::Cached> keep;
+    for (auto& b : c->cache) {
+        if (event_done(b.ready)) {
+            if (b.ready) c->ev_pool.push_back(b.ready);
+            c->cached_bytes -= b.bytes;
+            dev_free(c, b.p);
+        } else {
+            keep.push_back(b);
+        }
+    }
+    c->cache.swap(keep);
+}
+
+// A job or scene block: a cached block of 1..2x the size whose last use has completed,
+// else a new allocation (after trimming the cache if the budget or the device is full).
+prdpt_status block_alloc(prdpt_ctx* c, void** p, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    int best = -1;
+    for (int i = 0; i < (int)c->cache.size(); ++i) {
+        const auto& b = c->cache[i];
+        if (b.bytes < bytes || b.bytes > 2 * bytes) continue;
+        if (best >= 0 && b.bytes >= c->cache[best].bytes) continue;
+        if (!event_done(b.ready)) continue;
+        best = i;
+    }
+    if (best >= 0) {
+        prdpt_ctx::Cached b = c->cache[best];
+        c->cache.erase(c->cache.begin() + best);
+        c->cached_bytes -= b.bytes;
+        if (b.ready) c->ev_pool.push_back(b.ready);
+        *p = b.p;
+        return PRDPT_OK;
+    }
+    prdpt_status st = dev_alloc(c, p, bytes);
+    if (st != PRDPT_OK && !c->cache.empty()) {
+        trim_cache(c);
+        st = dev_alloc(c, p, bytes);
+    }
+    return st;
+}
+
+// Keep a released block for reuse; `ready` (owned by the cache from now on, may be null)
+// completes when the block's last use has.
+void block_release(prdpt_ctx* c, void* p, cudaEvent_t ready) {
+    auto it = c->allocs.find(p);
+    if (it == c->allocs.end()) return;
+    c->cache.push_back({p, it->second, ready});
+    c->cached_bytes += it->second;
 }
 
 bool is_emissive(const float* mp) { return mp[3] > 0.f || mp[4] > 0.f || mp[5] > 0.f; }
@@ -311,9 +433,15 @@ prdpt_status prdpt_create(prdpt_ctx** out, int32_t device, uint64_t hbm_budget_b
     c->occ_grad = trace_blocks_per_sm(false);
     c->occ_render = trace_blocks_per_sm(true);
     c->occ_diff = trace_diff_blocks_per_sm();
+    e = cudaStreamCreateWithFlags(&c->io, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(PRDPT_E_CUDA, std::string("cudaStreamCreateWithFlags: ") + cudaGetErrorString(e));
+    }
     void* p = nullptr;
     prdpt_status st = dev_alloc(c, &p, 128);  // status word, then 8 counters
     if (st) {
+        cudaStreamDestroy(c->io);
         delete c;
         return st;
     }
@@ -339,6 +467,10 @@ prdpt_status prdpt_destroy(prdpt_ctx* c) {
     cudaDeviceSynchronize();
     for (auto& kv : c->allocs) cudaFree(kv.first);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (int k = 0; k < 2; ++k) {
+        if (c->h_desc[k]) cudaFreeHost(c->h_desc[k]);
+        if (c->h_desc_ev[k]) cudaEventDestroy(c->h_desc_ev[k]);
+    }
     for (auto& ev : c->ev_used) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -347,8 +479,20 @@ prdpt_status prdpt_destroy(prdpt_ctx* c) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
     }
-    for (Scene* s : c->scenes) delete s;
-    for (Job* j : c->jobs) delete j;
+    for (auto& b : c->cache)
+        if (b.ready) cudaEventDestroy(b.ready);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (Scene* s : c->scenes)
+        if (s) {
+            if (s->use) cudaEventDestroy(s->use);
+            delete s;
+        }
+    for (Job* j : c->jobs)
+        if (j) {
+            if (j->last) cudaEventDestroy(j->last);
+            delete j;
+        }
+    if (c->io) cudaStreamDestroy(c->io);
     delete c;
     return PRDPT_OK;
 }
@@ -364,17 +508,22 @@ prdpt_status prdpt_scene_upload(prdpt_ctx* c, const prdpt_scene_desc* sd, const 
     s->host = B;
     s->D = D;
     void* p = nullptr;
-    prdpt_status st = dev_alloc(c, &p, sizeof(BaseScene));
+    prdpt_status st = block_alloc(c, &p, sizeof(BaseScene));
     if (st) {
         delete s;
         return st;
     }
     s->dev = static_cast<BaseScene*>(p);
-    cudaError_t e = cudaMemcpy(s->dev, &s->host, sizeof(BaseScene), cudaMemcpyHostToDevice);
+    s->use = take_event(c);
+    // on the context's own stream: the copy waits for no other work on the device
+    cudaError_t e = s->use ? cudaMemcpyAsync(s->dev, &s->host, sizeof(BaseScene), cudaMemcpyHostToDevice, c->io)
+                           : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
     if (e != cudaSuccess) {
-        dev_free(c, s->dev);
+        block_release(c, s->dev, nullptr);
+        if (s->use) c->ev_pool.push_back(s->use);
         delete s;
-        return fail(PRDPT_E_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+        return fail(PRDPT_E_CUDA, std::string("scene upload: ") + cudaGetErrorString(e));
     }
     c->scenes.push_back(s);
     *scene_id_out = (int)c->scenes.size() - 1;
@@ -387,8 +536,12 @@ prdpt_status prdpt_scene_release(prdpt_ctx* c, int32_t scene_id) {
     Scene* s = get_scene(c, scene_id);
     if (!s) return fail(PRDPT_E_NOT_FOUND, "unknown scene");
     if (s->jobs) return fail(PRDPT_E_INVALID_ARG, "scene still has jobs");
-    cudaDeviceSynchronize();
-    dev_free(c, s->dev);
+    // jobs read their own copy of the scene; only the stateless calls read this block, and
+    // it is reused only after the last of them has completed
+    if (s->captured) PRDPT_CUDA(cudaDeviceSynchronize());
+    const bool track = s->used && !s->captured;
+    block_release(c, s->dev, track ? s->use : nullptr);
+    if (!track) c->ev_pool.push_back(s->use);
     delete s;
     c->scenes[scene_id] = nullptr;
     return PRDPT_OK;
@@ -532,6 +685,7 @@ prdpt_status prdpt_render_batch(prdpt_ctx* c, int32_t scene_id, const float* the
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
     PRDPT_CUDA(timed_trace(c, &TL, 1, nullptr, true, st_, o->ctas_per_sm));
+    PRDPT_CUDA(mark_use(s->use, &s->used, &s->captured, st_));  // the scene block is in use until here
     return PRDPT_OK;
 }
 
@@ -811,6 +965,7 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         }
         PRDPT_CUDA(launch_hd_grad(G, st_));
     }
+    PRDPT_CUDA(mark_use(s->use, &s->used, &s->captured, st_));  // the scene block is in use until here
     return PRDPT_OK;
 }
 
@@ -943,7 +1098,7 @@ prdpt_status prdpt_adam_step(prdpt_ctx* c, int32_t D, float* theta_dev, float* m
 }
 
 prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_desc* d, int32_t* job_out) {
-    if (!c || !d || !job_out || !d->theta0_host || !d->sigma0_host || !d->target_host)
+    if (!c || !d || !job_out || !d->theta0_host || !d->sigma0_host)
         return fail(PRDPT_E_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
     Scene* s = get_scene(c, scene_id);
@@ -992,11 +1147,18 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     const size_t off_hs = (off_rg + (probe.diff ? sizeof(double) * (size_t)R * kMaxDiff : 0) + 255) & ~size_t(255);
     const size_t off_tx = (off_hs + (tex ? sizeof(float) * 5 * (size_t)D : 0) + 255) & ~size_t(255);
     const size_t off_nr = (off_tx + (tex ? sizeof(float) * (size_t)R * D : 0) + 255) & ~size_t(255);
-    const size_t total = off_nr + (tex ? sizeof(HdNorm) * (size_t)R : 0);
+    const size_t off_bs = (off_nr + (tex ? sizeof(HdNorm) * (size_t)R : 0) + 255) & ~size_t(255);
+    const size_t total = off_bs + sizeof(BaseScene);  // the job's own copy of its scene
     void* base = nullptr;
-    if (prdpt_status st = dev_alloc(c, &base, total)) {
+    if (prdpt_status st = block_alloc(c, &base, total)) {
         delete j;
         return st;
+    }
+    j->last = take_event(c);
+    if (!j->last) {
+        block_release(c, base, nullptr);
+        delete j;
+        return fail(PRDPT_E_CUDA, "cudaEventCreate failed");
     }
     j->bytes = total;
     j->base = base;
@@ -1026,7 +1188,11 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         j->aff = reinterpret_cast<int*>(b + off_af);
     }
     j->tex = tex;
-    cudaError_t e = cudaMemset(base, 0, off_w);
+    j->scene_copy = reinterpret_cast<BaseScene*>(b + off_bs);
+    // uploads on the context's own stream (they wait for no other work on the device); the
+    // block may be a reused one, so everything that must start at zero is cleared here
+    cudaStream_t io = c->io;
+    cudaError_t e = cudaMemsetAsync(base, 0, off_w, io);
     if (tex) {
         j->theta = reinterpret_cast<float*>(b + off_hs);
         j->m = j->theta + D;
@@ -1035,20 +1201,33 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         j->grad = j->sigma0 + D;
         j->tex_all = reinterpret_cast<float*>(b + off_tx);
         j->norms = reinterpret_cast<HdNorm*>(b + off_nr);
-        if (e == cudaSuccess) e = cudaMemset(j->theta, 0, sizeof(float) * 5 * (size_t)D);
-        if (e == cudaSuccess) e = cudaMemset(j->norms, 0, sizeof(HdNorm) * (size_t)R);  // part counters
+        if (e == cudaSuccess) e = cudaMemsetAsync(j->theta, 0, sizeof(float) * 5 * (size_t)D, io);
+        if (e == cudaSuccess) e = cudaMemsetAsync(j->norms, 0, sizeof(HdNorm) * (size_t)R, io);  // part counters
     }
-    if (e == cudaSuccess) e = cudaMemcpy(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(j->target, d->target_host, sizeof(float4) * (size_t)W * H, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && probe.share) e = cudaMemset(j->accaff, 0, sizeof(unsigned long long) * 3 * (size_t)R * pix);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->scene_copy, &s->host, sizeof(BaseScene), cudaMemcpyHostToDevice, io);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->theta, d->theta0_host, sizeof(float) * D, cudaMemcpyHostToDevice, io);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->sigma0, d->sigma0_host, sizeof(float) * D, cudaMemcpyHostToDevice, io);
+    if (e == cudaSuccess) {
+        if (d->target_host)
+            e = cudaMemcpyAsync(j->target, d->target_host, sizeof(float4) * (size_t)W * H, cudaMemcpyHostToDevice, io);
+        else  // rendered later on the device (prdpt_job_render_target)
+            e = cudaMemsetAsync(j->target, 0, sizeof(float4) * (size_t)W * H, io);
+    }
+    if (e == cudaSuccess && probe.share)
+        e = cudaMemsetAsync(j->accaff, 0, sizeof(unsigned long long) * 3 * (size_t)R * pix, io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(io);
     if (e != cudaSuccess) {
-        dev_free(c, base);
+        c->ev_pool.push_back(j->last);
+        block_release(c, base, nullptr);
         delete j;
         return fail(PRDPT_E_CUDA, std::string("job upload: ") + cudaGetErrorString(e));
     }
     InstJob& I = j->inst;
     fill_inst_grad(I, s, o);
+    I.base = j->scene_copy;
     I.scenes = j->scenes;
     I.theta = j->theta;
     I.sigma = j->sigma0;
@@ -1185,6 +1364,7 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     TL.status = c->status;
     PRDPT_CUDA(timed_trace(c, &TL, 1, &TL, false, st_, j->ctas_per_sm));
     if (j->tex) PRDPT_CUDA(launch_hd_grad(job_hd_grad(j), st_));  // a6 + a7 over the texture
+    PRDPT_CUDA(mark_use(j->last, &j->used, &j->captured, st_));  // the job's buffers are in use until here
     return PRDPT_OK;
 }
 
@@ -1193,6 +1373,9 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     std::lock_guard<std::mutex> lk(c->mu);
     std::vector<int> ids(job_ids, job_ids + n);
     cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    if (ids != c->batch_ids && capturing(st_))
+        return fail(PRDPT_E_INVALID_ARG, "a packed step captured into a CUDA graph must step the same jobs as the "
+                                         "previous packed step: run it once outside the capture first");
     if (ids != c->batch_ids) {
         // path-sharing jobs first (one render-kernel launch with items = pixel blocks), then
         // the rest (items = (render, block)); the order of the jobs does not change results
@@ -1230,7 +1413,8 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
                 items_share = items;
             }
         }
-        if ((size_t)n > c->batch_cap) {
+        if ((size_t)n > c->batch_cap) {  // room for at least 64 jobs, doubling (rarely grows)
+            const size_t cap = std::max<size_t>(std::max<size_t>(64, 2 * c->batch_cap), (size_t)n);
             PRDPT_CUDA(cudaStreamSynchronize(st_));  // the old arrays may still be in use
             dev_free(c, c->d_inst);
             dev_free(c, c->d_trace);
@@ -1238,16 +1422,41 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             c->d_trace = nullptr;
             c->batch_cap = 0;
             void* p = nullptr;
-            if (prdpt_status st = dev_alloc(c, &p, sizeof(InstJob) * n)) return st;
+            if (prdpt_status st = dev_alloc(c, &p, sizeof(InstJob) * cap)) return st;
             c->d_inst = static_cast<InstJob*>(p);
-            if (prdpt_status st = dev_alloc(c, &p, sizeof(TraceJob) * n)) return st;
+            if (prdpt_status st = dev_alloc(c, &p, sizeof(TraceJob) * cap)) return st;
             c->d_trace = static_cast<TraceJob*>(p);
-            c->batch_cap = n;
+            c->batch_cap = cap;
         }
-        // in stream order: a previous packed step on this stream may still be reading them
-        // (pageable source: the call returns once the host data is staged)
-        PRDPT_CUDA(cudaMemcpyAsync(c->d_inst, inst.data(), sizeof(InstJob) * n, cudaMemcpyHostToDevice, st_));
-        PRDPT_CUDA(cudaMemcpyAsync(c->d_trace, trace.data(), sizeof(TraceJob) * n, cudaMemcpyHostToDevice, st_));
+        // Uploaded in stream order (a previous packed step on this stream may still be
+        // reading the arrays) from one of two page-locked staging slots, so the call does not
+        // wait for the stream: the slot is rewritten only once its previous upload has run.
+        const size_t bytes = sizeof(InstJob) * n + sizeof(TraceJob) * n;
+        const int k = c->desc_slot;
+        c->desc_slot ^= 1;
+        if (c->h_desc_ev[k]) PRDPT_CUDA(cudaEventSynchronize(c->h_desc_ev[k]));
+        else PRDPT_CUDA(cudaEventCreateWithFlags(&c->h_desc_ev[k], cudaEventDisableTiming));
+        if (bytes > c->h_desc_n) {
+            const size_t want = std::max<size_t>(bytes, 2 * c->h_desc_n);
+            for (int q = 0; q < 2; ++q) {
+                if (c->h_desc_ev[q]) PRDPT_CUDA(cudaEventSynchronize(c->h_desc_ev[q]));
+                if (c->h_desc[q]) cudaFreeHost(c->h_desc[q]);
+                c->h_desc[q] = nullptr;
+            }
+            c->h_desc_n = 0;
+            for (int q = 0; q < 2; ++q) {
+                void* h = nullptr;
+                PRDPT_CUDA(cudaHostAlloc(&h, want, cudaHostAllocDefault));
+                c->h_desc[q] = static_cast<unsigned char*>(h);
+            }
+            c->h_desc_n = want;
+        }
+        std::memcpy(c->h_desc[k], inst.data(), sizeof(InstJob) * n);
+        std::memcpy(c->h_desc[k] + sizeof(InstJob) * n, trace.data(), sizeof(TraceJob) * n);
+        PRDPT_CUDA(cudaMemcpyAsync(c->d_inst, c->h_desc[k], sizeof(InstJob) * n, cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaMemcpyAsync(c->d_trace, c->h_desc[k] + sizeof(InstJob) * n, sizeof(TraceJob) * n,
+                                   cudaMemcpyHostToDevice, st_));
+        PRDPT_CUDA(cudaEventRecord(c->h_desc_ev[k], st_));
         c->batch_ids = ids;
         c->batch_blocks = blocks;
         c->batch_nshare = nshare;
@@ -1288,12 +1497,18 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     FL.fin_total = c->batch_blocks;
     FL.status = c->status;
     PRDPT_CUDA(timed_trace(c, TL, nL, &FL, false, st_, 0));
+    for (int i = 0; i < n; ++i) {  // every job's buffers are in use until here
+        Job* j = get_job(c, ids[i]);
+        PRDPT_CUDA(mark_use(j->last, &j->used, &j->captured, st_));
+    }
     return PRDPT_OK;
 }
 
+// The context's device status word, read on the context's own stream.
 static prdpt_status check_status(prdpt_ctx* c) {
     int st = 0;
-    PRDPT_CUDA(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    PRDPT_CUDA(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->io));
+    PRDPT_CUDA(cudaStreamSynchronize(c->io));
     if (st) return fail(PRDPT_E_DEVICE, "device status word " + std::to_string(st));
     return PRDPT_OK;
 }
@@ -1305,12 +1520,16 @@ prdpt_status prdpt_job_read(prdpt_ctx* c, int32_t job_id, float* theta_host, flo
     Job* j = get_job(c, job_id);
     if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
     PRDPT_CUDA(cudaSetDevice(c->device));
-    PRDPT_CUDA(cudaDeviceSynchronize());
+    if (j->captured) PRDPT_CUDA(cudaDeviceSynchronize());  // graph replays are not tracked
+    else if (j->used) PRDPT_CUDA(cudaEventSynchronize(j->last));  // the job's last enqueued work only
     if (prdpt_status st = check_status(c)) return st;
-    if (theta_host) PRDPT_CUDA(cudaMemcpy(theta_host, j->theta, sizeof(float) * j->D, cudaMemcpyDeviceToHost));
-    if (grad_host) PRDPT_CUDA(cudaMemcpy(grad_host, j->grad, sizeof(float) * j->D, cudaMemcpyDeviceToHost));
-    if (losses_host) PRDPT_CUDA(cudaMemcpy(losses_host, j->losses, sizeof(float) * j->R, cudaMemcpyDeviceToHost));
-    if (steps_host) PRDPT_CUDA(cudaMemcpy(steps_host, j->step, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaStream_t io = c->io;
+    if (theta_host) PRDPT_CUDA(cudaMemcpyAsync(theta_host, j->theta, sizeof(float) * j->D, cudaMemcpyDeviceToHost, io));
+    if (grad_host) PRDPT_CUDA(cudaMemcpyAsync(grad_host, j->grad, sizeof(float) * j->D, cudaMemcpyDeviceToHost, io));
+    if (losses_host)
+        PRDPT_CUDA(cudaMemcpyAsync(losses_host, j->losses, sizeof(float) * j->R, cudaMemcpyDeviceToHost, io));
+    if (steps_host) PRDPT_CUDA(cudaMemcpyAsync(steps_host, j->step, sizeof(int), cudaMemcpyDeviceToHost, io));
+    PRDPT_CUDA(cudaStreamSynchronize(io));
     return PRDPT_OK;
 }
 
@@ -1319,8 +1538,12 @@ prdpt_status prdpt_job_release(prdpt_ctx* c, int32_t job_id) {
     std::lock_guard<std::mutex> lk(c->mu);
     Job* j = get_job(c, job_id);
     if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
-    PRDPT_CUDA(cudaDeviceSynchronize());
-    dev_free(c, j->base);
+    // no synchronisation: the block is kept and reused once the job's last work has
+    // completed (after a graph capture that work is not tracked: wait for the device)
+    if (j->captured) PRDPT_CUDA(cudaDeviceSynchronize());
+    const bool track = j->used && !j->captured;
+    block_release(c, j->base, track ? j->last : nullptr);
+    if (!track) c->ev_pool.push_back(j->last);
     Scene* s = get_scene(c, j->scene);
     if (s) s->jobs--;
     for (int q : c->batch_ids)
@@ -1330,6 +1553,62 @@ prdpt_status prdpt_job_release(prdpt_ctx* c, int32_t job_id) {
         }
     delete j;
     c->jobs[job_id] = nullptr;
+    return PRDPT_OK;
+}
+
+prdpt_status prdpt_job_render_target(prdpt_ctx* c, int32_t job_id, const float* theta_ref_dev, void* stream) {
+    if (!c || !theta_ref_dev) return fail(PRDPT_E_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    Job* j = get_job(c, job_id);
+    if (!j) return fail(PRDPT_E_NOT_FOUND, "unknown job");
+    PRDPT_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st_ = static_cast<cudaStream_t>(stream);
+    const TraceJob& T = j->trace;
+    // one render at theta_ref on stream TARGET, step 0, common path field 0, with the job's
+    // image size, spp, depth and Russian roulette, built in the job's own scene slot 0
+    InstLaunch IL{};
+    std::memset(&IL.job0, 0, sizeof(InstJob));
+    IL.job0.base = j->scene_copy;
+    IL.job0.scenes = j->scenes;
+    IL.job0.theta = theta_ref_dev;
+    IL.job0.seed = j->inst.seed;
+    IL.job0.step = 0;
+    IL.job0.tag = kTagTarget;
+    IL.job0.crn = 1;
+    IL.job0.render_mode = 1;
+    IL.job0.R = 1;
+    IL.job0.D = j->D;
+    IL.job0.W = T.W;
+    IL.job0.H = T.H;
+    IL.job0.c_radial = j->inst.c_radial;
+    if (j->tex) {  // texture scenes: theta_ref [D] is the texture itself
+        IL.job0.hd = 1;
+        IL.job0.tex_all = theta_ref_dev;
+        IL.job0.tex_D = j->D;
+    }
+    IL.total_blocks = 1;
+    IL.queue_reset = j->queue;
+    PRDPT_CUDA(launch_instantiate(IL, st_));
+    TraceLaunch TL{};
+    TraceJob& J = TL.job0;
+    J.scenes = j->scenes;
+    J.images = j->target;
+    J.W = T.W;
+    J.H = T.H;
+    J.spp = T.spp;
+    J.depth = T.depth;
+    J.rr_start = T.rr_start;
+    J.R = 1;
+    J.D = j->D;
+    J.n_prims = T.n_prims;
+    J.n_mats = T.n_mats;
+    const int px = choose_block(c, 0, 1, T.W, T.H, true);
+    tiles_for(px, T.W, T.H, &J.bw, &J.bh, &J.tiles_x, &J.tiles);
+    TL.total_items = J.tiles;
+    TL.queue = j->queue;
+    TL.status = c->status;
+    PRDPT_CUDA(launch_trace(TL, true, grid_for(c, TL.total_items, true, 0), st_));
+    PRDPT_CUDA(mark_use(j->last, &j->used, &j->captured, st_));
     return PRDPT_OK;
 }
 

@@ -9,6 +9,10 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # the autotuner's shape cache: a fresh file per test session, so jobs created without
+    # a launch shape take the library's default unless a test fills the cache itself
+    import tempfile
+    os.environ["PRDPT_AUTOTUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="prdpt_tune_"), "autotune.json")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
 

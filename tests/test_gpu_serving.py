@@ -6,8 +6,11 @@
   one-job-per-launch mode).
 * HBM-budget admission: with a budget that fits only a few jobs, the rest wait and are
   admitted as finished jobs free their memory; all complete.
-* The autotuner returns one of its candidates, caches it, and the tuned launch gives the
-  same losses as the default launch (block shape only regroups FP64 partial sums).
+* Admission renders the target on the device (the same image as a host-supplied one), and
+  released job blocks are reused without new device memory.
+* The autotuner returns one of its candidates and caches it; a job created without a
+  launch shape then takes the cached one and runs exactly as a job given that shape
+  (the CTA count never changes results; the block shape only regroups FP64 partial sums).
 """
 import numpy as np
 import pytest
@@ -68,21 +71,20 @@ def test_served_results_equal_alone(gpu_lib, mode):
 
 
 def test_budget_limits_admission(gpu_lib):
-    from paper_2211_17263_gb300 import api
-    from paper_2211_17263_gb300.serve import Server
+    from paper_2211_17263_gb300 import api, capi
+    from paper_2211_17263_gb300.serve import Server, admit_job
     arrivals = [(0.0, a[1]) for a in _mix()]
     probe = api.Context(0)  # measure what each job holds, then allow roughly two at a time
     try:
-        sizes, before = [], probe.memory_used()
+        sizes = []
+        side = torch.cuda.Stream()
         for _, wl in arrivals:
-            _alone(probe, wl, 1)
-        srv = Server(probe, mode="batched")
-        for _, wl in arrivals:
-            from paper_2211_17263_gb300.serve import ServedJob
-            sj = ServedJob(wl=wl, arrival=0.0, steps=1)
-            srv._admit(sj)
+            before = probe.memory_used()
+            scene, job, ready = admit_job(probe, wl, side)
+            ready.synchronize()
             sizes.append(probe.memory_used() - before)
-            srv._retire(sj, 0.0)
+            job.release()
+            capi.prdpt_scene_release(probe.handle, scene.id)
     finally:
         probe.close()
     budget = 2 * max(sizes) + 64 * 1024  # plus the context's own scratch (control words, descriptors)
@@ -95,27 +97,123 @@ def test_budget_limits_admission(gpu_lib):
         ctx.close()
 
 
-def test_autotune_picks_and_caches(gpu_lib, tmp_path):
+def test_device_rendered_target_equals_host_target(gpu_lib):
+    """prdpt_job_render_target renders the same target as prdpt_render_batch: the job's
+    trajectory is bit-identical to a job given that image from the host."""
+    from paper_2211_17263_gb300 import api
+    for wl in (workloads.scaled(workloads.config_occlusion(seed=2), width=40, height=36, spp=4, pairs=3),
+               workloads.scaled(workloads.config_gi_box(seed=3), width=24, height=20, spp=2, pairs=2)):
+        ctx = api.Context(0)
+        try:
+            scene = ctx.upload_scene(wl.scene, wl.bindings)
+            th = torch.as_tensor(np.ascontiguousarray(wl.theta_ref, np.float32), device="cuda")
+            target = scene.render_batch(th[None], wl.width, wl.height, wl.spp, wl.depth, wl.rr_start,
+                                        seed=wl.seed, step=0, tag=3, crn=1)[0].cpu().numpy()
+            a = api.Job(scene, wl, target)
+            b = api.Job(scene, wl, None)
+            b.render_target(th)
+            for _ in range(4):
+                a.step()
+                b.step()
+            ra, rb = a.read(), b.read()
+            for key in ("theta", "grad", "losses"):
+                assert np.array_equal(ra[key], rb[key]), (wl.name, key)
+            a.release()
+            b.release()
+        finally:
+            ctx.close()
+
+
+def test_released_blocks_are_reused(gpu_lib):
+    """A released job's block is kept and handed to the next job of a fitting size once its
+    work has completed (no new device memory); the new job's results are unaffected."""
+    from paper_2211_17263_gb300 import api
+    wl = workloads.scaled(workloads.config_occlusion(seed=5), width=48, height=40, spp=2, pairs=2)
+    ref = api.Context(0)
+    try:
+        alone = _alone(ref, wl, 3)
+    finally:
+        ref.close()
+    ctx = api.Context(0)
+    try:
+        scene = ctx.upload_scene(wl.scene, wl.bindings)
+        th = torch.as_tensor(np.ascontiguousarray(wl.theta_ref, np.float32), device="cuda")
+        first = api.Job(scene, wl, None)
+        first.render_target(th)
+        for _ in range(5):
+            first.step()
+        first.release()  # returns at once; the block is in use until the five steps finish
+        torch.cuda.synchronize()
+        held = ctx.memory_used()
+        again = api.Job(scene, wl, None)
+        assert ctx.memory_used() == held  # the cached block, not a new allocation
+        again.render_target(th)
+        for _ in range(3):
+            again.step()
+        res = again.read()
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(res[key], alone[key]), key
+        again.release()
+    finally:
+        ctx.close()
+
+
+def test_autotune_picks_and_caches(gpu_lib, tmp_path, monkeypatch):
     from paper_2211_17263_gb300 import api
     from paper_2211_17263_gb300.autotune import CANDIDATES, autotune
     import oracle
     wl = workloads.scaled(workloads.config_occlusion(), width=96, height=64, spp=4, pairs=4)
     target = oracle.render_target(wl)
+    cache = str(tmp_path / "tune.json")
+    monkeypatch.setenv("PRDPT_AUTOTUNE_CACHE", cache)
     ctx = api.Context(0)
     try:
         scene = ctx.upload_scene(wl.scene, wl.bindings)
-        cache = str(tmp_path / "tune.json")
-        best = autotune(scene, wl, target, cache_path=cache, steps=2)
+        default = api.Job(scene, wl, target)  # empty cache: the library's default shape
+        assert default.launch_shape["source"] == "library default"
+        best = autotune(scene, wl, target, steps=2)
         assert (best["block_pixels"], best["ctas_per_sm"]) in CANDIDATES and not best["cached"]
-        again = autotune(scene, wl, target, cache_path=cache)
+        again = autotune(scene, wl, target)
         assert again["cached"] and again["block_pixels"] == best["block_pixels"]
-        tuned = api.Job(scene, wl, target, block_pixels=best["block_pixels"], ctas_per_sm=best["ctas_per_sm"])
-        default = api.Job(scene, wl, target)
-        tuned.step()
-        default.step()
-        a, b = tuned.read(), default.read()
-        assert np.allclose(a["losses"], b["losses"], rtol=1e-6)
-        tuned.release()
-        default.release()
+        # a job created without a launch shape now takes the tuned one, and runs exactly as
+        # a job given that shape explicitly
+        tuned = api.Job(scene, wl, target)
+        assert tuned.launch_shape["source"] == "autotuner cache"
+        assert tuned.launch_shape["block_pixels"] == best["block_pixels"]
+        explicit = api.Job(scene, wl, target, block_pixels=best["block_pixels"], ctas_per_sm=best["ctas_per_sm"],
+                           use_tuned=False)
+        for j in (tuned, explicit, default):
+            for _ in range(2):
+                j.step()
+        a, b, c = tuned.read(), explicit.read(), default.read()
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(a[key], b[key]), key
+        # the CTA count never changes results; the block shape only regroups the FP64 sums
+        # of per-block partials, so losses agree to rounding
+        assert np.allclose(a["losses"], c["losses"], rtol=1e-6)
+        for j in (tuned, explicit, default):
+            j.release()
+    finally:
+        ctx.close()
+
+
+def test_ctas_per_sm_does_not_change_results(gpu_lib):
+    from paper_2211_17263_gb300 import api
+    import oracle
+    wl = workloads.scaled(workloads.config_caustic(), width=64, height=48, spp=4, pairs=2)
+    target = oracle.render_target(wl)
+    ctx = api.Context(0)
+    try:
+        scene = ctx.upload_scene(wl.scene, wl.bindings)
+        res = []
+        for cps in (1, 2, 0):
+            j = api.Job(scene, wl, target, block_pixels=16, ctas_per_sm=cps, use_tuned=False)
+            for _ in range(2):
+                j.step()
+            res.append(j.read())
+            j.release()
+        for r in res[1:]:
+            for key in ("theta", "grad", "losses"):
+                assert np.array_equal(r[key], res[0][key]), key
     finally:
         ctx.close()
