@@ -304,6 +304,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-pixels", type=int, default=0,
                     help="pixels per warp work item (8, 16, 32; 0 = the autotuned or default shape)")
+    ap.add_argument("--render-groups", type=int, default=0,
+                    help="with --block-pixels: renders traced side by side per warp (0 = automatic, -1 = off)")
     ap.add_argument("--serving-jobs", type=int, default=12,
                     help="jobs of the serving mix served in each mode (0 = skip serving); 256 is the full mix")
     ap.add_argument("--serving-steps", type=int, default=0,
@@ -354,12 +356,15 @@ def main():
     # the cache has no entry; the tuning steps run before and outside the timed region)
     tuned = None
     if args.block_pixels:
-        shape = {"block_pixels": args.block_pixels, "ctas_per_sm": 0, "source": "--block-pixels"}
+        shape = {"block_pixels": args.block_pixels, "ctas_per_sm": 0, "render_groups": args.render_groups,
+                 "source": "--block-pixels"}
     else:
         tuned = autotune.autotune(scene, wl, target_host)
         shape = {"block_pixels": tuned["block_pixels"], "ctas_per_sm": tuned["ctas_per_sm"],
+                 "render_groups": tuned.get("render_groups", 0),
                  "source": "autotuner (cached)" if tuned["cached"] else "autotuner"}
-    job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"])
+    job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"],
+                  render_groups=shape["render_groups"], use_tuned=False)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         job.step(stream)
@@ -404,7 +409,7 @@ def main():
     per_render = None
     if sharing:
         plain_job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"],
-                            ctas_per_sm=shape["ctas_per_sm"], no_path_sharing=1)
+                            ctas_per_sm=shape["ctas_per_sm"], no_path_sharing=1, render_groups=-1, use_tuned=False)
         for _ in range(3):
             plain_job.step(stream)
         ctx.counters_enable(True)
@@ -433,7 +438,8 @@ def main():
     m_h, v_h, g_h, L_h = pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(D)), pin(np.zeros(R))
     h2d = 4 * (npx4 + 4 * D + 1)  # target; sigma, Adam's step, theta, m, v in one staged copy
     d2h = 4 * (4 * D + R)  # theta, m, v, gradient, losses in one copy
-    opts = scene.grad_opts(wl, step=0, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"])
+    opts = scene.grad_opts(wl, step=0, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"],
+                           render_groups=shape["render_groups"])
 
     def e2e_step(k):
         opts.step = k
@@ -462,7 +468,8 @@ def main():
         value = world * 1000.0 / step_ms
         traffic = _profiled(wl.name, "dram_bytes_per_step")
         kernels = ("render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue, k_finalize)"
-                   if sharing else "render kernel k_trace + k_finalize")
+                   if sharing else ("render-group kernel k_trace_group + k_finalize" if shape["render_groups"] >= 0
+                                    else "render kernel k_trace + k_finalize"))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

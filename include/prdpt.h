@@ -143,6 +143,12 @@ typedef struct {
                                   computes pairs [pair_begin, pair_begin + pairs) with their global
                                   draw indices (and, with crn = 0, global path-stream fields), and
                                   returns their mean; shards combine as g = sum_s (P_s / P) g_s */
+    int32_t render_groups;     /* renders traced side by side in one warp when paths are not shared
+                                  (each lane one render of the same path sample; same result, bit for
+                                  bit): 0 = automatic (the largest of 32, 16, 8, 4, 2 that divides 2P
+                                  and whose per-render records fit), -1 = off (one render per work
+                                  item), or 2, 4, 8, 16, 32. Used with crn = 1, the Eq. 10 estimator
+                                  and no texture or emission bindings; ignored otherwise */
 } prdpt_grad_opts;
 #define PRDPT_ESTIMATOR_KERNEL_GRADIENT 0 /* Eq. 10: sum_r w_r L_r */
 #define PRDPT_ESTIMATOR_PATHWISE 1        /* Eq. 9: mean_r dL/dtheta (theta + tau_r) */

@@ -137,14 +137,15 @@ class Scene:
         return out
 
     def grad_opts(self, wl, step=0, pairs=None, sampler=None, antithetic=None, crn=None, block_pixels=0,
-                  ctas_per_sm=0, no_path_sharing=0, estimator=None, pair_begin=0):
+                  ctas_per_sm=0, no_path_sharing=0, estimator=None, pair_begin=0, render_groups=0):
         return capi.prdpt_grad_opts(
             pairs=wl.pairs if pairs is None else pairs, width=wl.width, height=wl.height, spp=wl.spp,
             depth=wl.depth, rr_start=wl.rr_start, sampler=wl.sampler if sampler is None else sampler,
             antithetic=wl.antithetic if antithetic is None else antithetic, crn=wl.crn if crn is None else crn,
             seed=wl.seed, step=step, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm,
             no_path_sharing=no_path_sharing,
-            estimator=getattr(wl, "estimator", 0) if estimator is None else estimator, pair_begin=pair_begin)
+            estimator=getattr(wl, "estimator", 0) if estimator is None else estimator, pair_begin=pair_begin,
+            render_groups=render_groups)
 
     def smoothed_grad_host(self, theta, sigma, target, opts, grad=None, losses=None, stream=None):
         """The gradient with host buffers (prdpt_smoothed_grad_host): theta, sigma [D] and target
@@ -188,7 +189,7 @@ class Job:
     library's default."""
 
     def __init__(self, scene: Scene, wl, target_host: np.ndarray | None, step0=0, block_pixels=0, ctas_per_sm=0,
-                 anneal=None, lr=None, sampler=None, no_path_sharing=0, use_tuned=True):
+                 anneal=None, lr=None, sampler=None, no_path_sharing=0, use_tuned=True, render_groups=0):
         self.scene = scene
         self.D = scene.D
         self.R = 2 * wl.pairs
@@ -199,19 +200,22 @@ class Job:
             self._target = np.ascontiguousarray(target_host, np.float32)
             if self._target.shape != (wl.height, wl.width, 4):
                 raise ValueError("target must be [H, W, 4] float32")
-        self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm, "source": "given"}
-        if use_tuned and block_pixels == 0 and ctas_per_sm == 0:
+        self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm,
+                             "render_groups": render_groups, "source": "given"}
+        if use_tuned and block_pixels == 0 and ctas_per_sm == 0 and render_groups == 0:
             from . import autotune
             hit = autotune.cached_shape(wl)
             if hit is not None:
                 block_pixels, ctas_per_sm = hit["block_pixels"], hit["ctas_per_sm"]
+                render_groups = hit.get("render_groups", 0)
                 self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm,
-                                     "source": "autotuner cache"}
+                                     "render_groups": render_groups, "source": "autotuner cache"}
             else:
                 self.launch_shape["source"] = "library default"
         desc = capi.prdpt_job_desc(
             grad=scene.grad_opts(wl, step=step0, sampler=sampler, block_pixels=block_pixels,
-                                 ctas_per_sm=ctas_per_sm, no_path_sharing=no_path_sharing),
+                                 ctas_per_sm=ctas_per_sm, no_path_sharing=no_path_sharing,
+                                 render_groups=render_groups),
             theta0_host=_np_ptr(self._theta0), sigma0_host=_np_ptr(self._sigma0),
             target_host=None if self._target is None else _np_ptr(self._target),
             lr=wl.lr if lr is None else lr, beta1=0.9, beta2=0.999, eps=1e-8, sigma_min=wl.sigma_min,

@@ -1,10 +1,14 @@
 """Autotuner for the render kernel's launch shape.
 
-Candidates are (pixels per warp work item, resident CTAs per SM): the block of pixels a
-warp traces as one task pool, and how many 256-thread CTAs the persistent grid keeps per
-SM (the number of live warps). Each candidate is timed with CUDA events on the render
-launches of a throwaway resident job of the same shape; the fastest is cached in a JSON
-file keyed by the shape, so later jobs of that shape start from the tuned launch.
+Candidates are (pixels per warp work item, resident CTAs per SM, render groups): the
+block of pixels a warp traces as one work item, how many 256-thread CTAs the persistent
+grid keeps per SM (the number of live warps), and whether renders are traced side by side
+in one warp (render_groups = 0: automatic group size; -1: one render per work item). Each
+candidate is timed with CUDA events on the render launches of a throwaway resident job of
+the same shape; the fastest is cached in a JSON file keyed by the shape, so later jobs of
+that shape start from the tuned launch (api.Job looks it up when given no shape). The CTA
+count and the render grouping never change results; the block shape regroups the FP64
+sums of per-block partials (results agree to rounding).
 """
 from __future__ import annotations
 
@@ -22,7 +26,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "prdpt_gb300", "
 def default_cache() -> str:
     """The cache file: $PRDPT_AUTOTUNE_CACHE if set, else DEFAULT_CACHE."""
     return os.environ.get("PRDPT_AUTOTUNE_CACHE") or DEFAULT_CACHE
-CANDIDATES = [(px, cps) for px in (32, 16, 8) for cps in (3, 2, 1)]
+CANDIDATES = [(px, cps, rg) for px in (32, 16, 8) for cps in (3, 2) for rg in (0, -1)]
 _lock = threading.Lock()
 
 
@@ -63,10 +67,11 @@ def cached_shape(wl, cache_path: str | None = ""):
 
 
 def time_candidate(scene: api.Scene, wl, target_host: np.ndarray, block_pixels: int, ctas_per_sm: int,
-                   steps: int = 3) -> float:
+                   steps: int = 3, render_groups: int = 0) -> float:
     """Mean render-kernel time (ms) of `steps` resident steps with this launch shape."""
     ctx = scene.ctx
-    job = api.Job(scene, wl, target_host, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm)
+    job = api.Job(scene, wl, target_host, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm,
+                  render_groups=render_groups, use_tuned=False)
     try:
         job.step()  # warm-up
         ctx.sync()
@@ -93,12 +98,12 @@ def autotune(scene: api.Scene, wl, target_host: np.ndarray, cache_path: str | No
         if hit:
             return dict(hit, cached=True)
     results = []
-    for px, cps in (candidates or CANDIDATES):
-        ms = time_candidate(scene, wl, target_host, px, cps, steps)
-        results.append({"block_pixels": px, "ctas_per_sm": cps, "ms": ms})
+    for px, cps, rg in (candidates or CANDIDATES):
+        ms = time_candidate(scene, wl, target_host, px, cps, steps, rg)
+        results.append({"block_pixels": px, "ctas_per_sm": cps, "render_groups": rg, "ms": ms})
     best = min(results, key=lambda r: r["ms"])
-    entry = {"block_pixels": best["block_pixels"], "ctas_per_sm": best["ctas_per_sm"], "ms": best["ms"],
-             "tried": results}
+    entry = {"block_pixels": best["block_pixels"], "ctas_per_sm": best["ctas_per_sm"],
+             "render_groups": best["render_groups"], "ms": best["ms"], "tried": results}
     if cache_path:
         with _lock:
             table = _load(cache_path)

@@ -63,7 +63,7 @@ class prdpt_grad_opts(C.Structure):
         ("depth", C.c_int32), ("rr_start", C.c_int32), ("sampler", C.c_int32), ("antithetic", C.c_int32),
         ("crn", C.c_int32), ("seed", C.c_uint64), ("step", C.c_uint32), ("block_pixels", C.c_int32),
         ("ctas_per_sm", C.c_int32), ("no_path_sharing", C.c_int32), ("estimator", C.c_int32),
-        ("pair_begin", C.c_int32),
+        ("pair_begin", C.c_int32), ("render_groups", C.c_int32),
     ]
 
 

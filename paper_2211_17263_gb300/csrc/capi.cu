@@ -80,7 +80,7 @@ struct Job {
 struct prdpt_ctx {
     int device = 0;
     int sms = 0;
-    int occ_grad = 1, occ_render = 1, occ_diff = 1;
+    int occ_grad = 1, occ_render = 1, occ_diff = 1, occ_group = 1;
     uint64_t budget = 0, used = 0;
     std::map<void*, size_t> allocs;
     std::vector<Scene*> scenes;
@@ -102,7 +102,8 @@ struct prdpt_ctx {
     size_t s_partials_n = 0;
     double* s_losses = nullptr;
     size_t s_losses_n = 0;
-    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2..3] batch queues, [4..7] sharing counters
+    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2..3] batch queues, [4..7] sharing
+                                  // counters, [8] third batch queue (16 words)
     unsigned long long* s_share = nullptr;  // path sharing: [tiles][96] shared radiance
     size_t s_share_n = 0;
     int* s_aff = nullptr;         // path sharing: list of blocks with affected paths
@@ -128,8 +129,10 @@ struct prdpt_ctx {
     InstJob* d_inst = nullptr;
     TraceJob* d_trace = nullptr;
     size_t batch_cap = 0;
-    int batch_items = 0, batch_blocks = 0;
-    int batch_nshare = 0, batch_items_share = 0;  // path-sharing jobs come first in the packed arrays
+    int batch_blocks = 0;
+    // the packed arrays hold the path-sharing jobs, then the render-group jobs, then the
+    // per-render ones: jobs and work items of each kind (one render launch per kind)
+    int batch_jobs[3] = {0, 0, 0}, batch_items[3] = {0, 0, 0};
     // optional CUDA-event timing of the render kernel, recorded on its launch stream
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -361,6 +364,23 @@ int grid_for_diff(prdpt_ctx* c, int items, int ctas_per_sm) {
     return need < cap ? need : cap;
 }
 
+// Persistent grid of the render-group kernel (CTAs of kGroupBlock threads; ctas_per_sm counts
+// 256-thread CTAs, so it allows twice as many of these).
+int grid_for_group(prdpt_ctx* c, int items, int ctas_per_sm) {
+    const int per_sm = (ctas_per_sm > 0 && 2 * ctas_per_sm < c->occ_group) ? 2 * ctas_per_sm : c->occ_group;
+    const int cap = c->sms * per_sm;
+    const int need = (items + kGroupBlock / 32 - 1) / (kGroupBlock / 32);
+    return need < cap ? need : cap;
+}
+
+// Work items of a gradient job's render launch: pixel blocks (path sharing), (block, group
+// of gsize renders) (render-group mode) or (render, block).
+long long job_items(const TraceJob& J) {
+    if (J.share) return J.tiles;
+    if (J.gsize > 0) return (long long)J.tiles * (J.R / J.gsize);
+    return (long long)J.R * J.tiles;
+}
+
 // Launch the render kernel(s), bracketed by events on their stream when timing is on.
 // Ls[0..nL): render-kernel launches (a packed step has one for its path-sharing jobs and
 // one for the rest); a launch with share = 1 is followed by the affected-path and block
@@ -384,7 +404,8 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch* Ls, int nL, const Trace
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < nL; ++i) {
         const int grid = Ls[i].diff_nd ? grid_for_diff(c, Ls[i].total_items, ctas_per_sm)
-                                       : grid_for(c, Ls[i].total_items, render, ctas_per_sm);
+                         : (Ls[i].group && !render) ? grid_for_group(c, Ls[i].total_items, ctas_per_sm)
+                                                    : grid_for(c, Ls[i].total_items, render, ctas_per_sm);
         e = launch_trace(Ls[i], render, grid, stream);
         if (e != cudaSuccess) return e;
     }
@@ -433,6 +454,7 @@ prdpt_status prdpt_create(prdpt_ctx** out, int32_t device, uint64_t hbm_budget_b
     c->occ_grad = trace_blocks_per_sm(false);
     c->occ_render = trace_blocks_per_sm(true);
     c->occ_diff = trace_diff_blocks_per_sm();
+    c->occ_group = trace_group_blocks_per_sm();
     e = cudaStreamCreateWithFlags(&c->io, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
@@ -623,6 +645,48 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
         I->n_var = J.n_var;
         for (int k = 0; k < J.n_var; ++k) I->var_prim[k] = prims[k];
     }
+}
+
+// Render-group mode for a gradient job that does not share paths (see render_groups in
+// prdpt.h): the perturbed primitives (position and radius bindings, emitters included) and
+// the bound materials (albedo bindings) become per-render records of each lane; gsize
+// renders of one path sample are traced side by side. Needs common random numbers (the
+// renders' paths then agree until a perturbed primitive intervenes), the Eq. 10 estimator,
+// no texture and no emission bindings (those change which primitives emit).
+static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o) {
+    J.gsize = 0;
+    J.gstride = 0;
+    if (J.share || o->render_groups < 0 || !o->crn || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT ||
+        B.tex_mat >= 0)
+        return;
+    unsigned prims = 0u, mats = 0u;
+    for (int d = 0; d < B.D; ++d) {
+        const int k = B.bind_kind[d], idx = B.bind_index[d];
+        if (k == kBindEmission) return;
+        if (k == kBindAlbedo) mats |= 1u << idx;
+        if (k == kBindPos || k == kBindRadius) prims |= 1u << B.prim_slot[idx];
+    }
+    const int n = __builtin_popcount(prims), nm = __builtin_popcount(mats);
+    if (n > kMaxVariant) return;
+    const int stride = 4 * n + 2 * nm + 2;  // primitive records, material records, 8 emitter areas
+    const int R = J.R;
+    int G = 0;
+    if (o->render_groups > 0) {
+        const int g = o->render_groups;
+        if ((g & (g - 1)) == 0 && g >= 2 && g <= 32 && R % g == 0 && g * stride <= kGroupTabRows) G = g;
+    } else {
+        for (int g = 32; g >= 2; g >>= 1)
+            if (R % g == 0 && g * stride <= kGroupTabRows) {
+                G = g;
+                break;
+            }
+    }
+    if (!G) return;
+    J.gsize = G;
+    J.gstride = stride;
+    J.n_var = n;
+    J.var_prims = prims;
+    J.var_mats = mats;
 }
 
 static void fill_inst_common(InstJob& J, const Scene* s, int R, int D, int W, int H) {
@@ -913,6 +977,7 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
     J.n_prims = s->host.n_prims;
     J.n_mats = s->host.n_mats;
     fill_share(J, s->host, o);
+    fill_group(J, s->host, o);
     if (J.share) {
         J.share_acc = c->s_share;
         J.acc_aff = c->s_accaff;
@@ -939,8 +1004,9 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         J.eps = adam->eps;
     }
     TL.diff_nd = diff_slots(J);
-    TL.total_items = J.share ? tiles : R * tiles;
+    TL.total_items = int(job_items(J));
     TL.share = J.share;
+    TL.group = J.gsize > 0 ? 1 : 0;
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
@@ -1278,6 +1344,7 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         T.rgrads = reinterpret_cast<double*>(b + off_rg);
     }
     fill_share(T, s->host, o, &I);
+    fill_group(T, s->host, o);
     if (T.share) {
         T.share_acc = j->share;
         T.acc_aff = j->accaff;
@@ -1356,8 +1423,9 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
     TL.job0 = j->trace;
-    TL.total_items = j->trace.share ? j->tiles : j->R * j->tiles;
+    TL.total_items = int(job_items(j->trace));
     TL.share = j->trace.share;
+    TL.group = j->trace.gsize > 0 ? 1 : 0;
     TL.diff_nd = diff_slots(j->trace);
     TL.queue = j->queue;
     TL.counters = c->counting ? c->counters : nullptr;
@@ -1388,30 +1456,28 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             if (j->trace.diff) return fail(PRDPT_E_INVALID_ARG, "pathwise-estimator jobs step alone (prdpt_step)");
             if (j->tex) return fail(PRDPT_E_INVALID_ARG, "texture jobs step alone (prdpt_step)");
         }
-        for (int pass = 0; pass < 2; ++pass)
+        auto kind = [](const Job* j) { return j->trace.share ? 0 : (j->trace.gsize > 0 ? 1 : 2); };
+        for (int pass = 0; pass < 3; ++pass)
             for (int i = 0; i < n; ++i) {
                 Job* j = get_job(c, ids[i]);
-                if ((j->trace.share != 0) == (pass == 0)) order.push_back(j);
+                if (kind(j) == pass) order.push_back(j);
             }
         std::vector<InstJob> inst(n);
         std::vector<TraceJob> trace(n);
-        int blocks = 0, items = 0, nshare = 0, items_share = 0;
+        int blocks = 0, jobs_of[3] = {0, 0, 0}, items_of[3] = {0, 0, 0};
         for (int i = 0; i < n; ++i) {
             Job* j = order[i];
-            if (i > 0 && !j->trace.share && order[i - 1]->trace.share) items = 0;  // second launch
+            const int kd = kind(j);
             inst[i] = j->inst;
             inst[i].block_begin = blocks;
             blocks += j->R;
             trace[i] = j->trace;
-            trace[i].item_begin = items;
+            trace[i].item_begin = items_of[kd];  // items are numbered per launch
             trace[i].fin_begin = blocks - j->R;  // same prefix as the sampler CTAs
-            if (prdpt_status st = check_items((long long)items + (j->trace.share ? j->tiles : j->R * j->tiles)))
-                return st;
-            items += j->trace.share ? j->tiles : j->R * j->tiles;
-            if (j->trace.share) {
-                nshare++;
-                items_share = items;
-            }
+            const long long it = job_items(j->trace);
+            if (prdpt_status st = check_items((long long)items_of[kd] + it)) return st;
+            items_of[kd] += int(it);
+            jobs_of[kd]++;
         }
         if ((size_t)n > c->batch_cap) {  // room for at least 64 jobs, doubling (rarely grows)
             const size_t cap = std::max<size_t>(std::max<size_t>(64, 2 * c->batch_cap), (size_t)n);
@@ -1459,9 +1525,10 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
         PRDPT_CUDA(cudaEventRecord(c->h_desc_ev[k], st_));
         c->batch_ids = ids;
         c->batch_blocks = blocks;
-        c->batch_nshare = nshare;
-        c->batch_items_share = items_share;
-        c->batch_items = nshare < n ? items : 0;
+        for (int q = 0; q < 3; ++q) {
+            c->batch_jobs[q] = jobs_of[q];
+            c->batch_items[q] = items_of[q];
+        }
     }
     InstLaunch IL{};
     IL.jobs = c->d_inst;
@@ -1469,23 +1536,22 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     IL.total_blocks = c->batch_blocks;
     IL.queue_reset = c->s_ctl + 2;
     IL.queue_reset2 = c->s_ctl + 3;
+    IL.queue_reset3 = c->s_ctl + 8;
     PRDPT_CUDA(launch_instantiate(IL, st_));
-    TraceLaunch TL[2] = {};
-    int nL = 0;
-    if (c->batch_nshare > 0) {  // path-sharing jobs
-        TraceLaunch& T = TL[nL++];
-        T.jobs = c->d_trace;
-        T.njobs = c->batch_nshare;
-        T.total_items = c->batch_items_share;
-        T.share = 1;
-        T.queue = c->s_ctl + 2;
-    }
-    if (c->batch_nshare < n) {  // every render of the other jobs
-        TraceLaunch& T = TL[nL++];
-        T.jobs = c->d_trace + c->batch_nshare;
-        T.njobs = n - c->batch_nshare;
-        T.total_items = c->batch_items;
-        T.queue = c->s_ctl + 3;
+    TraceLaunch TL[3] = {};
+    int nL = 0, first = 0;
+    unsigned* queues[3] = {c->s_ctl + 2, c->s_ctl + 3, c->s_ctl + 8};
+    for (int kd = 0; kd < 3; ++kd) {  // path-sharing jobs, render-group jobs, per-render jobs
+        if (c->batch_jobs[kd] > 0) {
+            TraceLaunch& T = TL[nL++];
+            T.jobs = c->d_trace + first;
+            T.njobs = c->batch_jobs[kd];
+            T.total_items = c->batch_items[kd];
+            T.share = kd == 0 ? 1 : 0;
+            T.group = kd == 1 ? 1 : 0;
+            T.queue = queues[kd];
+        }
+        first += c->batch_jobs[kd];
     }
     for (int i = 0; i < nL; ++i) {
         TL[i].counters = c->counting ? c->counters : nullptr;

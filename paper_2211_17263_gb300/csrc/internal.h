@@ -165,6 +165,10 @@ struct TraceJob {
     int var_slot[kMaxVariant];  // their record slots
     unsigned var_prims;       // record-slot bitmask of perturbed primitives
     unsigned var_mats;        // bitmask of materials whose parameters are bound
+    // Render-group mode (k_trace_group): gsize renders per work item (0: per-render items);
+    // each render's row of the per-warp table holds gstride float4 (its records of the
+    // n_var perturbed primitives, of the bound materials, and its emitter areas)
+    int gsize, gstride;
 };
 struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)
@@ -172,6 +176,7 @@ struct TraceLaunch {
     int njobs, total_items;
     int share;                // 1: every job of the launch shares paths (selects the kernel variant)
     int diff_nd;              // pathwise estimator: tangent slots of the kernel variant (0, 4 or 8)
+    int group;                // 1: every job of the launch runs in render-group mode (k_trace_group)
     int fin_total;            // packed launch: finalisation CTAs (sum of R over jobs)
     unsigned* queue;          // work-queue head, zeroed by the instantiation launch
     unsigned long long* counters;  // [8] or null (null: the uncounted kernel variant runs)
@@ -184,6 +189,7 @@ struct InstLaunch {
     int njobs, total_blocks;
     unsigned* queue_reset;    // zeroed by CTA 0
     unsigned* queue_reset2;   // zeroed by CTA 0 (second queue of a packed launch), or null
+    unsigned* queue_reset3;   // zeroed by CTA 0 (third queue of a packed launch), or null
 };
 
 // High-dimensional parameter draws (texture scenes, D > kMaxD): norms per draw, then
@@ -248,6 +254,9 @@ cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, uns
 // Resident CTAs per SM of the render kernel; the pathwise-estimator variant runs CTAs of
 // kDiffBlock threads.
 int trace_blocks_per_sm(bool render_mode);
+int trace_group_blocks_per_sm();
+constexpr int kGroupBlock = 128;    // render-group CTAs: 4 warps (their per-warp tables fit 48 KB)
+constexpr int kGroupTabRows = 192;  // float4 of a warp's per-render record table (render-group mode)
 constexpr int kDiffBlock = 128;
 int trace_diff_blocks_per_sm();
 

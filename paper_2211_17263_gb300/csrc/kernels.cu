@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     if (blockIdx.x == 0 && tid == 0) {
         if (L.queue_reset) *L.queue_reset = 0u;
         if (L.queue_reset2) *L.queue_reset2 = 0u;
+        if (L.queue_reset3) *L.queue_reset3 = 0u;
     }
     if (r == 0 && tid == 0 && J.share_reset)
         for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
@@ -430,9 +431,9 @@ struct Counters {
     unsigned sph, quad, box, paths, vertices, shadow, rays, pad;
 };
 
-__device__ __forceinline__ float sphere_t(const InstScene& S, int i, float3 o, float3 d) {
-    const float4 a = S.prim[i][0];
-    const float r2 = S.prim[i][1].x;
+__device__ __forceinline__ float sphere_t(const float4* P, float3 o, float3 d) {
+    const float4 a = P[0];
+    const float r2 = P[1].x;
     const float3 oc = o - xyz(a);
     const float b = dot3(oc, d);
     const float3 l = oc - d * b;  // centre offset from the ray line: better conditioned than b^2 - c
@@ -444,8 +445,8 @@ __device__ __forceinline__ float sphere_t(const InstScene& S, int i, float3 o, f
     return (t > kEps) ? t : INFINITY;
 }
 
-__device__ __forceinline__ float quad_t(const InstScene& S, int i, float3 o, float3 d) {
-    const float4 a = S.prim[i][0], nb = S.prim[i][1], uu = S.prim[i][2], vv = S.prim[i][3];
+__device__ __forceinline__ float quad_t(const float4* P, float3 o, float3 d) {
+    const float4 a = P[0], nb = P[1], uu = P[2], vv = P[3];
     const float3 n = xyz(nb);
     const float den = dot3(n, d);
     if (fabsf(den) < 1e-12f) return INFINITY;
@@ -458,8 +459,8 @@ __device__ __forceinline__ float quad_t(const InstScene& S, int i, float3 o, flo
 }
 
 // Slab test; returns the nearest t > eps (entering, or leaving from inside).
-__device__ __forceinline__ float box_t(const InstScene& S, int i, float3 o, float3 inv) {
-    const float3 lo = xyz(S.prim[i][0]), hi = xyz(S.prim[i][1]);
+__device__ __forceinline__ float box_t(const float4* P, float3 o, float3 inv) {
+    const float3 lo = xyz(P[0]), hi = xyz(P[1]);
     const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
     const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
     const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
@@ -470,9 +471,9 @@ __device__ __forceinline__ float box_t(const InstScene& S, int i, float3 o, floa
     return (tf > kEps) ? tf : INFINITY;
 }
 
-// Outward normal of box i at the hit found by box_t.
-__device__ __forceinline__ float3 box_normal(const InstScene& S, int i, float3 o, float3 d, float3 inv) {
-    const float3 lo = xyz(S.prim[i][0]), hi = xyz(S.prim[i][1]);
+// Outward normal of box record P at the hit found by box_t.
+__device__ __forceinline__ float3 box_normal(const float4* P, float3 o, float3 d, float3 inv) {
+    const float3 lo = xyz(P[0]), hi = xyz(P[1]);
     float tn[3], tf[3];
     const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z}, ii[3] = {inv.x, inv.y, inv.z};
     const float l3[3] = {lo.x, lo.y, lo.z}, h3[3] = {hi.x, hi.y, hi.z};
@@ -516,19 +517,19 @@ __device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 
     }
     for (int i = 0; i < ns; ++i) {
         if (kSkip && ((skip >> i) & 1u)) continue;
-        const float t = sphere_t(S, i, o, d);
+        const float t = sphere_t(S.prim[i], o, d);
         if (t < h.t) { h.t = t; h.slot = i; h.type = kSphere; }
     }
     for (int i = ns; i < ns + nq; ++i) {
         if (kSkip && ((skip >> i) & 1u)) continue;
-        const float t = quad_t(S, i, o, d);
+        const float t = quad_t(S.prim[i], o, d);
         if (t < h.t) { h.t = t; h.slot = i; h.type = kQuad; }
     }
     if (nb) {
         const float3 inv = rcp3(d);
         for (int i = ns + nq; i < ns + nq + nb; ++i) {
             if (kSkip && ((skip >> i) & 1u)) continue;
-            const float t = box_t(S, i, o, inv);
+            const float t = box_t(S.prim[i], o, inv);
             if (t < h.t) { h.t = t; h.slot = i; h.type = kBox; }
         }
     }
@@ -545,20 +546,116 @@ __device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d,
     for (int i = 0; i < ns; ++i) {
         if (i == light || (kSkip && ((skip >> i) & 1u))) continue;
         if (kCount) ++cnt.sph;
-        if (sphere_t(S, i, o, d) < dist) return true;
+        if (sphere_t(S.prim[i], o, d) < dist) return true;
     }
     for (int i = ns; i < ns + nq; ++i) {
         if (i == light || (kSkip && ((skip >> i) & 1u))) continue;
         if (kCount) ++cnt.quad;
-        if (quad_t(S, i, o, d) < dist) return true;
+        if (quad_t(S.prim[i], o, d) < dist) return true;
     }
     if (nb) {
         const float3 inv = rcp3(d);
         for (int i = ns + nq; i < ns + nq + nb; ++i) {
             if (i == light || (kSkip && ((skip >> i) & 1u))) continue;
             if (kCount) ++cnt.box;
-            if (box_t(S, i, o, inv) < dist) return true;
+            if (box_t(S.prim[i], o, inv) < dist) return true;
         }
+    }
+    return false;
+}
+
+// Render-group mode: the lanes of a warp trace the same path samples for up to 32
+// renders of a job at once (with common random numbers the renders' paths agree until a
+// perturbed primitive intervenes, so the lanes stay coherent). The invariant part of the
+// scene is the warp's staged InstScene; each lane reads its own render's records of the
+// perturbed primitives and bound materials, and the emitter areas, from its row of a
+// per-warp table:
+//   [4 k .. 4 k + 3]     record of the k-th perturbed primitive (in record-slot order)
+//   [4 n + 2 j .. + 1]   record of the j-th bound material (in material order)
+//   [4 n + 2 m .. + 1]   the render's emitter areas (8 floats), m = bound materials
+struct GroupLane {
+    const float4* rec;  // this lane's row
+    unsigned prims;     // record-slot mask of the perturbed primitives
+    unsigned mats;      // mask of the bound materials
+    int n_var;          // perturbed primitives
+};
+
+// Record of primitive slot `slot`: the lane's own for a perturbed primitive, else the
+// staged scene's.
+template <bool kGroup>
+__device__ __forceinline__ const float4* prim_rec(const InstScene& S, int slot, const GroupLane* g) {
+    if constexpr (kGroup) {
+        if ((g->prims >> slot) & 1u) return g->rec + 4 * __popc(g->prims & ((1u << slot) - 1u));
+    }
+    return S.prim[slot];
+}
+
+template <bool kGroup>
+__device__ __forceinline__ const float4* mat_rec(const InstScene& S, int m, const GroupLane* g) {
+    if constexpr (kGroup) {
+        if ((g->mats >> m) & 1u) return g->rec + 4 * g->n_var + 2 * __popc(g->mats & ((1u << m) - 1u));
+    }
+    return S.mat[m];
+}
+
+template <bool kGroup>
+__device__ __forceinline__ float light_area(const InstScene& S, int li, const GroupLane* g) {
+    if constexpr (kGroup)
+        return reinterpret_cast<const float*>(g->rec + 4 * g->n_var + 2 * __popc(g->mats))[li];
+    return S.light_area[li];
+}
+
+// The lane's perturbed primitives against a ray: closer hits replace h (the staged scene's
+// closest hit over the other primitives).
+template <bool kCount>
+__device__ __forceinline__ void group_hit(const InstScene& S, const GroupLane& g, float3 o, float3 d, Hit& h,
+                                          Counters& cnt) {
+    unsigned m = g.prims;
+    for (int k = 0; m; ++k) {
+        const int slot = __ffs(m) - 1;
+        m &= m - 1u;
+        const float4* P = g.rec + 4 * k;
+        float t;
+        int type;
+        if (slot < S.n_sph) {
+            t = sphere_t(P, o, d);
+            type = kSphere;
+            if (kCount) ++cnt.sph;
+        } else if (slot < S.n_sph + S.n_quad) {
+            t = quad_t(P, o, d);
+            type = kQuad;
+            if (kCount) ++cnt.quad;
+        } else {
+            t = box_t(P, o, rcp3(d));
+            type = kBox;
+            if (kCount) ++cnt.box;
+        }
+        if (t < h.t) { h.t = t; h.slot = slot; h.type = type; }
+    }
+}
+
+// Is one of the lane's perturbed primitives other than slot `light` hit closer than dist?
+template <bool kCount>
+__device__ __forceinline__ bool group_occluded(const InstScene& S, const GroupLane& g, float3 o, float3 d, float dist,
+                                               int light, Counters& cnt) {
+    unsigned m = g.prims;
+    for (int k = 0; m; ++k) {
+        const int slot = __ffs(m) - 1;
+        m &= m - 1u;
+        if (slot == light) continue;
+        const float4* P = g.rec + 4 * k;
+        float t;
+        if (slot < S.n_sph) {
+            t = sphere_t(P, o, d);
+            if (kCount) ++cnt.sph;
+        } else if (slot < S.n_sph + S.n_quad) {
+            t = quad_t(P, o, d);
+            if (kCount) ++cnt.quad;
+        } else {
+            t = box_t(P, o, rcp3(d));
+            if (kCount) ++cnt.box;
+        }
+        if (t < dist) return true;
     }
     return false;
 }
@@ -684,8 +781,8 @@ __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
 // Albedo of a textured quad at hit point pt: texel (floor(s T), floor(t T)) with
 // s = (pt - c).u / |u|^2 + 1/2, t = (pt - c).v / |v|^2 + 1/2 (each clamped to [0, T-1]) of
 // the render's texture [T][T][3]; channels clamped to [0, 1].
-__device__ __forceinline__ float3 tex_albedo(const InstScene& S, int slot, float3 pt) {
-    const float4 c = S.prim[slot][0], u = S.prim[slot][2], v = S.prim[slot][3];
+__device__ __forceinline__ float3 tex_albedo(const InstScene& S, const float4* P, float3 pt) {
+    const float4 c = P[0], u = P[2], v = P[3];
     const float3 l = pt - xyz(c);
     const float s = fmaf(dot3(l, xyz(u)), u.w, 0.5f), t = fmaf(dot3(l, xyz(v)), v.w, 0.5f);
     const int T = S.tex_res;
@@ -795,10 +892,10 @@ __device__ __forceinline__ void tan_rr(Tangents<kND>& t, float inv_q) {
     for (int k = 0; k < kND; ++k) t.dB[k] *= inv_q;
 }
 
-template <bool kCount, bool kShared, int kND = 0>
+template <bool kCount, bool kShared, int kND = 0, bool kGroup = false>
 __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt,
                                        const VarBoxes* V = nullptr, Tangents<kND>* tn = nullptr,
-                                       const TraceJob* Jd = nullptr) {
+                                       const TraceJob* Jd = nullptr, const GroupLane* gl = nullptr) {
     if (kShared && p.seg == 0u) {
         const int t = threadIdx.x;
         s_stash[0][t] = p.o.x;
@@ -808,7 +905,13 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
         s_stash[4][t] = p.d.y;
         s_stash[5][t] = p.d.z;
     }
-    const Hit h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
+    Hit h;
+    if constexpr (kGroup) {  // the staged scene without the perturbed primitives, then the lane's own
+        h = closest_hit<kCount, true>(S, p.o, p.d, cnt, gl->prims);
+        group_hit<kCount>(S, *gl, p.o, p.d, h, cnt);
+    } else {
+        h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
+    }
     if (kShared) {
         note_touch<kCount, false>(*V, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, p, cnt);
         if (p.seg & kSegAll) return kAffected;
@@ -820,28 +923,30 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
     }
     if (kCount) ++cnt.vertices;
     const float3 pt = p.o + p.d * h.t;
+    const float4* P = prim_rec<kGroup>(S, h.slot, gl);
     float3 ng;
     int mat;
     if (h.type == kSphere) {
-        const float4 a = S.prim[h.slot][0];
-        ng = (pt - xyz(a)) * S.prim[h.slot][1].y;
-        mat = as_int(S.prim[h.slot][1].z);
+        const float4 a = P[0];
+        ng = (pt - xyz(a)) * P[1].y;
+        mat = as_int(P[1].z);
     } else if (h.type == kQuad) {
-        ng = xyz(S.prim[h.slot][1]);
-        mat = as_int(S.prim[h.slot][0].w);
+        ng = xyz(P[1]);
+        mat = as_int(P[0].w);
     } else {
-        ng = box_normal(S, h.slot, p.o, p.d, rcp3(p.d));
-        mat = as_int(S.prim[h.slot][0].w);
+        ng = box_normal(P, p.o, p.d, rcp3(p.d));
+        mat = as_int(P[0].w);
     }
     if (kShared && ((V->mats >> mat) & 1u)) {  // every render from here (state: this vertex)
         p.seg = (p.seg == 0u ? open_group<false>(*V, p) : p.seg) | kSegAll;
         return kAffected;
     }
-    const float4 m0 = S.mat[mat][0], m1 = S.mat[mat][1];
+    const float4* M = mat_rec<kGroup>(S, mat, gl);
+    const float4 m0 = M[0], m1 = M[1];
     const int mtype = as_int(m0.w);
     const float3 emission = xyz(m1);
     float3 albedo = xyz(m0);
-    if (mat == S.tex_mat && h.type == kQuad) albedo = tex_albedo(S, h.slot, pt);
+    if (mat == S.tex_mat && h.type == kQuad) albedo = tex_albedo(S, P, pt);
     if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f) {
         if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, emission, mat);
         p.L = p.L + p.beta * emission;
@@ -858,12 +963,13 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
             int li = int((((w1.x >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
             li = min(li, S.n_lights - 1);
             const int4 lt = S.light[li];
+            const float4* LP = prim_rec<kGroup>(S, lt.y, gl);
             const float lu = u01(w0.x), lv = u01(w0.y);
             float3 yl, ny;
             if (lt.x == kQuad) {
-                const float3 uu = xyz(S.prim[lt.y][2]), vv = xyz(S.prim[lt.y][3]);
-                yl = xyz(S.prim[lt.y][0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
-                ny = xyz(S.prim[lt.y][1]);
+                const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
+                yl = xyz(LP[0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
+                ny = xyz(LP[1]);
             } else {
                 const float z = 1.0f - 2.0f * lu;
                 const float rr2 = fmaxf(0.0f, 1.0f - z * z);
@@ -871,7 +977,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
                 float sp, cp;
                 sincospif(2.0f * lv, &sp, &cp);
                 ny = f3(rr_ * cp, rr_ * sp, z);
-                yl = xyz(S.prim[lt.y][0]) + ny * S.prim[lt.y][0].w;
+                yl = xyz(LP[0]) + ny * LP[0].w;
             }
             const float3 dv = yl - po;
             const float dist2 = dot3(dv, dv);
@@ -880,15 +986,22 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
             const float cx = dot3(ns, wi), cl = -dot3(ny, wi);
             if (cx > 0.0f && cl > 0.0f) {
                 const float dist = dist2 * inv_dist;
-                if (!occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u)) {
+                bool blocked;
+                if constexpr (kGroup)
+                    blocked = occluded<kCount, true>(S, po, wi, dist, lt.y, cnt, gl->prims) ||
+                              group_occluded<kCount>(S, *gl, po, wi, dist, lt.y, cnt);
+                else
+                    blocked = occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u);
+                if (!blocked) {
                     if (kShared) {
                         note_touch<kCount, true>(*V, po, wi, dist, p, cnt);
                         if (p.seg & kSegAll) return kAffected;
                     }
-                    const float g = cx * cl * (inv_dist * inv_dist) * S.light_area[li] * float(S.n_lights) *
-                                    0.3183098861837907f;
-                    if (kND > 0) tan_nee(*tn, *Jd, S, p.beta, albedo, mat, xyz(S.mat[lt.w][1]), lt.w, g);
-                    p.L = p.L + p.beta * albedo * xyz(S.mat[lt.w][1]) * g;
+                    const float g = cx * cl * (inv_dist * inv_dist) * light_area<kGroup>(S, li, gl) *
+                                    float(S.n_lights) * 0.3183098861837907f;
+                    const float3 Le = xyz(mat_rec<kGroup>(S, lt.w, gl)[1]);
+                    if (kND > 0) tan_nee(*tn, *Jd, S, p.beta, albedo, mat, Le, lt.w, g);
+                    p.L = p.L + p.beta * albedo * Le * g;
                 }
             }
         }
@@ -1044,10 +1157,10 @@ struct WarpSmem {
 
 };
 
-// Copy render r's scene (header, used materials, used primitives) into the warp's slot.
-__device__ __forceinline__ void stage_scene(WarpSmem& W, const TraceJob& J, int r, int lane) {
+// Copy render r's scene (header, used materials, used primitives) into a warp's slot.
+__device__ __forceinline__ void stage_scene(InstScene& S, const TraceJob& J, int r, int lane) {
     const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
-    float4* dst = reinterpret_cast<float4*>(&W.scene);
+    float4* dst = reinterpret_cast<float4*>(&S);
     constexpr int kHead = int(offsetof(InstScene, mat) / 16);
     constexpr int kPrim = int(offsetof(InstScene, prim) / 16);
     const int nm = 2 * J.n_mats, np = 4 * J.n_prims;
@@ -1328,7 +1441,7 @@ __global__ void __launch_bounds__(kND > 0 ? kDiffBlock : kBlock, kND > 0 ? kDiff
             break;
         }
         if (r != cur_r) {  // a2 -> shared memory
-            stage_scene(W, J, r, lane);
+            stage_scene(W.scene, J, r, lane);
             cur_r = r;
         }
 
@@ -1381,6 +1494,162 @@ __global__ void __launch_bounds__(kND > 0 ? kDiffBlock : kBlock, kND > 0 ? kDiff
         dst[32 + lane] = W.acc[1][lane];
         dst[64 + lane] = W.acc[2][lane];
         if (lane == 0) J.aff_tiles[atomicAdd(J.share_ctl + 0, 1u)] = t;
+        __syncwarp();
+    }
+    if (kCount) {
+        const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
+                                          warp_sum_u(cnt.paths), warp_sum_u(cnt.vertices), warp_sum_u(cnt.shadow),
+                                          warp_sum_u(cnt.rays), 0u};
+        if (lane == 0)
+            for (int i = 0; i < kNumCounters; ++i) atomicAdd(L.counters + i, (unsigned long long)v[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_trace_group: render-group variant of the per-render kernel (a3-a5)
+// ---------------------------------------------------------------------------
+// A work item is (pixel block t, render group g): G = J.gsize consecutive renders of a
+// job (G divides R; 32 / G lanes per render). Lane l traces render g G + (l mod G), and
+// the 32 / G lanes of one render take the samples s = l / G, l / G + 32 / G, ... of the
+// current pixel: all lanes follow one pixel, so with common random numbers the renders'
+// paths agree until a perturbed primitive intervenes and the warp stays coherent. The
+// block's pixels are taken in bit-reversed slot order and their squared errors summed
+// pairwise in that order, which is the shuffle tree of the per-render kernel's epilogue:
+// with the same block shape, the same integer pixel sums and the same FP32 path
+// arithmetic, every partial is bit-identical to the per-render kernel's.
+constexpr int kGroupTab = kGroupTabRows;  // float4 per warp for the group's per-render records
+static_assert(offsetof(InstScene, light_area) % 16 == 0, "emitter areas are copied as two float4");
+
+struct GroupSmem {
+    InstScene scene;  // the invariant part (render g G's records of the other primitives)
+    TraceJob job;
+    float4 tab[kGroupTab];
+    double pair[5][32];  // each lane's pairwise-sum stack (touched once per pixel)
+    unsigned long long acc[3][32];  // each lane's radiance sums of the current pixel, 2^-32 fixed point
+};
+
+constexpr int kGroupMinBlocks = 6;  // 128-thread CTAs, <= 85 registers: 24 resident warps per SM
+
+__device__ __forceinline__ int brev5(int q) { return int(__brev(unsigned(q)) >> 27); }
+
+// Pairwise sum over 32 values pushed in order: level l of the stack (s[l][lane]) holds a
+// completed subtree of 2^l values; value q merges with levels 0, 1, ... while bit l of q is
+// set. After the 32nd push the result is the total, summed as ((v0 + v1) + (v2 + v3)) + ...
+__device__ __forceinline__ double pairwise_push(int q, double v, double (*s)[32], int lane) {
+    int l = 0;
+    for (; (q >> l) & 1; ++l) v = s[l][lane] + v;
+    if (l < 5) s[l][lane] = v;
+    return v;
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(const __grid_constant__ TraceLaunch L) {
+    __shared__ GroupSmem s_grp[kGroupBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    GroupSmem& W = s_grp[warp];
+    const TraceJob& J = W.job;
+    int cur_job = -1, cur_item_g = -1;
+    Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (!L.jobs) {  // a single job's descriptor is host data: copied before the wait
+        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        unsigned* dst = reinterpret_cast<unsigned*>(&W.job);
+        for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
+        __syncwarp();
+        cur_job = 0;
+    }
+    pdl_enter();
+    for (;;) {
+        unsigned item = 0;
+        int j = 0;
+        if (lane == 0) {
+            item = atomicAdd(L.queue, 1u);
+            if (item < unsigned(L.total_items) && L.jobs) {
+                int lo = 0, hi = L.njobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) / 2;
+                    if (L.jobs[mid].item_begin <= int(item)) lo = mid; else hi = mid - 1;
+                }
+                j = lo;
+            }
+        }
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= unsigned(L.total_items)) break;
+        j = __shfl_sync(kFull, j, 0);
+        if (j != cur_job) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs ? L.jobs + j : &L.job0);
+            unsigned* dst = reinterpret_cast<unsigned*>(&W.job);
+            for (int i = lane; i < int(sizeof(TraceJob) / 4); i += 32) dst[i] = src[i];
+            __syncwarp();
+            cur_job = j;
+            cur_item_g = -1;
+        }
+        const int G = J.gsize, ngr = J.R / G, stride = J.gstride;
+        const int li = int(item) - J.item_begin;
+        const int g = li % ngr, t = li / ngr;  // group-interleaved: neighbouring items share pixels
+        if (G < 1 || G > 32 || (32 % G) != 0 || t >= J.tiles || G * stride > kGroupTab) {
+            if (lane == 0) atomicOr(L.status, kStatusBadItem);
+            break;
+        }
+        if (g != cur_item_g) {  // stage render g G's scene and the group's per-render records
+            stage_scene(W.scene, J, g * G, lane);
+            const int n = J.n_var, nm = __popc(J.var_mats);
+            for (int i = lane; i < G * stride; i += 32) {
+                const int gi = i / stride, q = i - gi * stride;
+                const InstScene& R = J.scenes[g * G + gi];
+                float4 v;
+                if (q < 4 * n) {  // record of the (q / 4)-th perturbed primitive
+                    const int slot = nth_set_bit(J.var_prims, q >> 2);
+                    v = __ldg(&R.prim[slot][q & 3]);
+                } else if (q < 4 * n + 2 * nm) {  // record of a bound material
+                    const int m = nth_set_bit(J.var_mats, (q - 4 * n) >> 1);
+                    v = __ldg(&R.mat[m][(q - 4 * n) & 1]);
+                } else {  // emitter areas
+                    v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n - 2 * nm));
+                }
+                W.tab[i] = v;
+            }
+            __syncwarp();
+            cur_item_g = g;
+        }
+        const int gi = lane % G, ks = lane / G, nsg = 32 / G;  // render in group, sample group, groups
+        const GroupLane gl{W.tab + gi * stride, J.var_prims, J.var_mats, J.n_var};
+        const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
+        const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
+        const int npx = vw * vh;
+        const unsigned magic_w = 0xffffffffu / unsigned(vw) + 1u;
+        const float inv = mean_scale(J.spp);
+        double part = 0.0;
+        for (int q = 0; q < 32; ++q) {
+            const int slot = brev5(q);  // pixels in bit-reversed slot order (see above)
+            double e = 0.0;
+            if (slot < npx) {
+                const int row = div_magic(slot, vw, magic_w);
+                const int px = x0 + slot - row * vw, py = y0 + row;
+                W.acc[0][lane] = 0ull;
+                W.acc[1][lane] = 0ull;
+                W.acc[2][lane] = 0ull;
+                for (int smp = ks; smp < J.spp; smp += nsg) {
+                    Path p;
+                    start_path(W.scene, J.W, J.H, px, py, smp, slot, p);
+                    if (kCount) ++cnt.paths;
+                    while (advance<kCount, false, 0, true>(W.scene, J.depth, J.rr_start, p, cnt, nullptr, nullptr,
+                                                          nullptr, &gl) == kLive) {
+                    }
+                    W.acc[0][lane] += to_fixed(p.L.x);
+                    W.acc[1][lane] += to_fixed(p.L.y);
+                    W.acc[2][lane] += to_fixed(p.L.z);
+                }
+                unsigned long long a0 = W.acc[0][lane], a1 = W.acc[1][lane], a2 = W.acc[2][lane];
+                for (int o = G; o < 32; o <<= 1) {  // the render's other sample groups
+                    a0 += __shfl_xor_sync(kFull, a0, o);
+                    a1 += __shfl_xor_sync(kFull, a1, o);
+                    a2 += __shfl_xor_sync(kFull, a2, o);
+                }
+                e = pixel_sq_error(a0, a1, a2, __ldg(J.target + size_t(py) * J.W + px), unsigned(J.spp), inv);
+            }
+            part = pairwise_push(q, e, W.pair, lane);
+        }
+        if (ks == 0) J.partials[size_t(g * G + gi) * J.tiles + t] = part;  // a5: one partial per block
         __syncwarp();
     }
     if (kCount) {
@@ -1789,9 +2058,17 @@ int trace_blocks_per_sm(bool render_mode) {
     return n > 0 ? n : 1;
 }
 
+int trace_group_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_group<false>, kGroupBlock, 0);
+    return n > 0 ? n : 1;
+}
+
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream) {
     if (L.total_items <= 0) return cudaSuccess;
     const bool count = L.counters != nullptr;
+    if (L.group && !render_mode)
+        return launch_pdl(count ? k_trace_group<true> : k_trace_group<false>, grid, kGroupBlock, stream, L);
     const bool share = !render_mode && L.share;
     if (render_mode) return launch_pdl(count ? k_trace<true, true, false, 0> : k_trace<true, false, false, 0>, grid, kBlock,
                                        stream, L);

@@ -32,7 +32,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(capi.prdpt_param_binding) == 12
     assert ctypes.sizeof(capi.prdpt_scene_desc) == 8 + 7 * 8
     assert ctypes.sizeof(capi.prdpt_render_opts) == 5 * 4 + 4 + 8 + 4 * 4 + 8
-    assert ctypes.sizeof(capi.prdpt_grad_opts) == 9 * 4 + 4 + 8 + 6 * 4
+    assert ctypes.sizeof(capi.prdpt_grad_opts) == 9 * 4 + 4 + 8 + 7 * 4 + 4  # trailing pad to 8-byte alignment
     assert ctypes.sizeof(capi.prdpt_job_desc) == ctypes.sizeof(capi.prdpt_grad_opts) + 3 * 8 + 7 * 4 + 4
 
 

@@ -109,6 +109,40 @@ def test_packed_mixed_sharing_equal_alone(ctx):
             jobs[i].release()
 
 
+def test_packed_three_kinds_equal_alone(ctx):
+    """A batch with path-sharing jobs, render-group jobs and one-render-per-item jobs: the
+    packed step runs one render launch per kind; every job matches its single-job step."""
+    from paper_2211_17263_gb300 import api
+    cfgs = [(workloads.config_caustic(seed=51), 40, 32, 2, 8, 0),     # render groups of 16
+            (workloads.config_occlusion(seed=52), 48, 40, 4, 3, 0),   # path sharing
+            (workloads.config_gi_box(seed=53), 40, 32, 2, 4, -1),     # one render per item
+            (workloads.config_gi_box(seed=54), 32, 24, 2, 2, 0)]      # render groups of 4
+    wls = [workloads.scaled(wl, width=w, height=h, spp=spp, pairs=p) for wl, w, h, spp, p, _ in cfgs]
+    groups = [c[5] for c in cfgs]
+    targets = [oracle.render_target(w) for w in wls]
+
+    def make(i):
+        scene = ctx.upload_scene(wls[i].scene, wls[i].bindings)
+        return api.Job(scene, wls[i], targets[i], render_groups=groups[i], use_tuned=False)
+
+    alone = []
+    for i in range(len(wls)):
+        j = make(i)
+        for _ in range(2):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    order = [3, 0, 2, 1]
+    jobs = {i: make(i) for i in order}
+    for _ in range(2):
+        api.step_batch(ctx, [jobs[i] for i in order])
+    for i in order:
+        b = jobs[i].read()
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(alone[i][key], b[key]), (i, key)
+        jobs[i].release()
+
+
 def test_job_release_and_reuse_of_batch(ctx):
     from paper_2211_17263_gb300 import api
     wl = workloads.scaled(workloads.config_small(), width=16, height=16, spp=1, pairs=1)

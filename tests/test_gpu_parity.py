@@ -244,6 +244,55 @@ def test_path_sharing_is_bit_identical(ctx, make):
     assert 0 < paths < wl.renders * wl.width * wl.height * wl.spp
 
 
+@pytest.mark.parametrize("make,groups", [
+    # the caustic task: 64 renders, the light moves (a perturbed emitter in every lane's records)
+    (lambda: workloads.scaled(workloads.config_caustic(), width=72, height=52, spp=4, pairs=32), (0, 32, 8, 2)),
+    # the GI box: the light moves and two walls' albedos are bound (per-render materials)
+    (lambda: workloads.scaled(workloads.config_gi_box(), width=48, height=40, spp=4, pairs=16), (0, 16, 4)),
+    # ragged blocks, renders not a multiple of 4
+    (lambda: workloads.scaled(workloads.config_caustic(), width=37, height=29, spp=3, pairs=3), (0, 2)),
+    # a moving box with path sharing off, and Russian roulette
+    (lambda: workloads.scaled(workloads.config_occlusion(), width=48, height=40, spp=4, pairs=4, depth=6,
+                              rr_start=2), (0, 8, 2)),
+])
+@pytest.mark.parametrize("block_pixels", [8, 32])
+def test_render_groups_are_bit_identical(ctx, make, groups, block_pixels):
+    """Render-group mode traces each path sample for several renders side by side (one lane
+    per render) with the invariant scene shared and each lane's perturbed primitives and
+    materials its own: every loss and the gradient equal tracing one render per work item,
+    bit for bit, for every group size, and the same paths are traced."""
+    wl = make()
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = _t(oracle.render_target(wl))
+    res, paths = {}, {}
+    for rg in (-1,) + tuple(groups):
+        opts = scene.grad_opts(wl, step=3, block_pixels=block_pixels, no_path_sharing=1, render_groups=rg)
+        ctx.counters_enable(True)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
+        torch.cuda.synchronize()
+        paths[rg] = ctx.counters_read()[3]
+        ctx.counters_enable(False)
+        res[rg] = (g.cpu().numpy(), L.cpu().numpy())
+    for rg in groups:
+        assert np.array_equal(res[rg][1], res[-1][1]), (rg, res[rg][1], res[-1][1])
+        assert np.array_equal(res[rg][0], res[-1][0]), (rg, res[rg][0], res[-1][0])
+        assert paths[rg] == paths[-1] == wl.renders * wl.width * wl.height * wl.spp
+
+
+def test_render_groups_match_oracle(ctx):
+    """The caustic and GI-box gradients in render-group mode against the FP64 oracle."""
+    for wl in (workloads.scaled(workloads.config_caustic(), width=64, height=48, spp=4, pairs=8),
+               workloads.scaled(workloads.config_gi_box(), width=48, height=40, spp=4, pairs=8)):
+        scene = ctx.upload_scene(wl.scene, wl.bindings)
+        target = oracle.render_target(wl)
+        opts = scene.grad_opts(wl, step=1, render_groups=16)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
+        torch.cuda.synchronize()
+        ref = oracle.smoothed_grad(wl, target=target, step=1)
+        err = grad_rel_error(g.cpu().numpy(), ref["grad"], ref["weights"], ref["losses"])
+        assert err <= GRAD_REL, (wl.name, err)
+
+
 def test_host_buffer_gradient_equals_device_call(ctx):
     """prdpt_smoothed_grad_host (inputs and results in host memory, pageable or
     page-locked, on the default or another stream) returns the device call's gradient and

@@ -172,7 +172,8 @@ def test_autotune_picks_and_caches(gpu_lib, tmp_path, monkeypatch):
         default = api.Job(scene, wl, target)  # empty cache: the library's default shape
         assert default.launch_shape["source"] == "library default"
         best = autotune(scene, wl, target, steps=2)
-        assert (best["block_pixels"], best["ctas_per_sm"]) in CANDIDATES and not best["cached"]
+        assert (best["block_pixels"], best["ctas_per_sm"], best["render_groups"]) in CANDIDATES
+        assert not best["cached"]
         again = autotune(scene, wl, target)
         assert again["cached"] and again["block_pixels"] == best["block_pixels"]
         # a job created without a launch shape now takes the tuned one, and runs exactly as
@@ -181,7 +182,7 @@ def test_autotune_picks_and_caches(gpu_lib, tmp_path, monkeypatch):
         assert tuned.launch_shape["source"] == "autotuner cache"
         assert tuned.launch_shape["block_pixels"] == best["block_pixels"]
         explicit = api.Job(scene, wl, target, block_pixels=best["block_pixels"], ctas_per_sm=best["ctas_per_sm"],
-                           use_tuned=False)
+                           render_groups=best["render_groups"], use_tuned=False)
         for j in (tuned, explicit, default):
             for _ in range(2):
                 j.step()
