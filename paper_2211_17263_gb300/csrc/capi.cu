@@ -660,15 +660,20 @@ static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
         B.tex_mat >= 0)
         return;
     unsigned prims = 0u, mats = 0u;
+    bool radius = false;
     for (int d = 0; d < B.D; ++d) {
         const int k = B.bind_kind[d], idx = B.bind_index[d];
         if (k == kBindEmission) return;
         if (k == kBindAlbedo) mats |= 1u << idx;
         if (k == kBindPos || k == kBindRadius) prims |= 1u << B.prim_slot[idx];
+        radius = radius || k == kBindRadius;
     }
     const int n = __builtin_popcount(prims), nm = __builtin_popcount(mats);
     if (n > kMaxVariant) return;
-    const int stride = 4 * n + 2 * nm + 2;  // primitive records, material records, 8 emitter areas
+    // per render: the perturbed primitives' records (4 float4 each), the bound materials'
+    // albedo rows, and the 8 emitter areas when a radius binding can change one
+    const int stride = 4 * n + nm + (radius ? 2 : 0);
+    if (stride == 0) return;
     const int R = J.R;
     int G = 0;
     if (o->render_groups > 0) {

@@ -167,7 +167,8 @@ struct TraceJob {
     unsigned var_mats;        // bitmask of materials whose parameters are bound
     // Render-group mode (k_trace_group): gsize renders per work item (0: per-render items);
     // each render's row of the per-warp table holds gstride float4 (its records of the
-    // n_var perturbed primitives, of the bound materials, and its emitter areas)
+    // n_var perturbed primitives, the albedo rows of the bound materials, and its emitter
+    // areas when a radius binding can change them)
     int gsize, gstride;
 };
 struct TraceLaunch {

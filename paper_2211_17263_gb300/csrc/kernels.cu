@@ -567,17 +567,19 @@ __device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d,
 // Render-group mode: the lanes of a warp trace the same path samples for up to 32
 // renders of a job at once (with common random numbers the renders' paths agree until a
 // perturbed primitive intervenes, so the lanes stay coherent). The invariant part of the
-// scene is the warp's staged InstScene; each lane reads its own render's records of the
-// perturbed primitives and bound materials, and the emitter areas, from its row of a
-// per-warp table:
-//   [4 k .. 4 k + 3]     record of the k-th perturbed primitive (in record-slot order)
-//   [4 n + 2 j .. + 1]   record of the j-th bound material (in material order)
-//   [4 n + 2 m .. + 1]   the render's emitter areas (8 floats), m = bound materials
+// scene is the warp's staged InstScene; each lane reads what differs between renders from
+// its row of a per-warp table:
+//   [4 k .. 4 k + 3]   record of the k-th perturbed primitive (in record-slot order)
+//   [4 n + j]          albedo row (albedo, type) of the j-th bound material (only albedos
+//                      are bound in this mode; the emission row is the staged scene's)
+//   [4 n + m .. + 1]   the render's emitter areas (8 floats), only when a radius binding
+//                      can change an emitter's area (m = bound materials)
 struct GroupLane {
     const float4* rec;  // this lane's row
     unsigned prims;     // record-slot mask of the perturbed primitives
     unsigned mats;      // mask of the bound materials
     int n_var;          // perturbed primitives
+    int areas;          // 1: the row holds the emitter areas
 };
 
 // Record of primitive slot `slot`: the lane's own for a perturbed primitive, else the
@@ -590,18 +592,20 @@ __device__ __forceinline__ const float4* prim_rec(const InstScene& S, int slot, 
     return S.prim[slot];
 }
 
+// Albedo row (albedo, type) of material m: the lane's own for a bound material.
 template <bool kGroup>
-__device__ __forceinline__ const float4* mat_rec(const InstScene& S, int m, const GroupLane* g) {
+__device__ __forceinline__ float4 mat_albedo(const InstScene& S, int m, const GroupLane* g) {
     if constexpr (kGroup) {
-        if ((g->mats >> m) & 1u) return g->rec + 4 * g->n_var + 2 * __popc(g->mats & ((1u << m) - 1u));
+        if ((g->mats >> m) & 1u) return g->rec[4 * g->n_var + __popc(g->mats & ((1u << m) - 1u))];
     }
-    return S.mat[m];
+    return S.mat[m][0];
 }
 
 template <bool kGroup>
 __device__ __forceinline__ float light_area(const InstScene& S, int li, const GroupLane* g) {
-    if constexpr (kGroup)
-        return reinterpret_cast<const float*>(g->rec + 4 * g->n_var + 2 * __popc(g->mats))[li];
+    if constexpr (kGroup) {
+        if (g->areas) return reinterpret_cast<const float*>(g->rec + 4 * g->n_var + __popc(g->mats))[li];
+    }
     return S.light_area[li];
 }
 
@@ -941,8 +945,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
         p.seg = (p.seg == 0u ? open_group<false>(*V, p) : p.seg) | kSegAll;
         return kAffected;
     }
-    const float4* M = mat_rec<kGroup>(S, mat, gl);
-    const float4 m0 = M[0], m1 = M[1];
+    const float4 m0 = mat_albedo<kGroup>(S, mat, gl), m1 = S.mat[mat][1];
     const int mtype = as_int(m0.w);
     const float3 emission = xyz(m1);
     float3 albedo = xyz(m0);
@@ -999,7 +1002,7 @@ __device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_sta
                     }
                     const float g = cx * cl * (inv_dist * inv_dist) * light_area<kGroup>(S, li, gl) *
                                     float(S.n_lights) * 0.3183098861837907f;
-                    const float3 Le = xyz(mat_rec<kGroup>(S, lt.w, gl)[1]);
+                    const float3 Le = xyz(S.mat[lt.w][1]);
                     if (kND > 0) tan_nee(*tn, *Jd, S, p.beta, albedo, mat, Le, lt.w, g);
                     p.L = p.L + p.beta * albedo * Le * g;
                 }
@@ -1600,11 +1603,10 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
                 if (q < 4 * n) {  // record of the (q / 4)-th perturbed primitive
                     const int slot = nth_set_bit(J.var_prims, q >> 2);
                     v = __ldg(&R.prim[slot][q & 3]);
-                } else if (q < 4 * n + 2 * nm) {  // record of a bound material
-                    const int m = nth_set_bit(J.var_mats, (q - 4 * n) >> 1);
-                    v = __ldg(&R.mat[m][(q - 4 * n) & 1]);
+                } else if (q < 4 * n + nm) {  // albedo row of a bound material
+                    v = __ldg(&R.mat[nth_set_bit(J.var_mats, q - 4 * n)][0]);
                 } else {  // emitter areas
-                    v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n - 2 * nm));
+                    v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n - nm));
                 }
                 W.tab[i] = v;
             }
@@ -1612,7 +1614,8 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
             cur_item_g = g;
         }
         const int gi = lane % G, ks = lane / G, nsg = 32 / G;  // render in group, sample group, groups
-        const GroupLane gl{W.tab + gi * stride, J.var_prims, J.var_mats, J.n_var};
+        const GroupLane gl{W.tab + gi * stride, J.var_prims, J.var_mats, J.n_var,
+                           stride > 4 * J.n_var + __popc(J.var_mats) ? 1 : 0};
         const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
         const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
         const int npx = vw * vh;

@@ -244,11 +244,24 @@ def test_path_sharing_is_bit_identical(ctx, make):
     assert 0 < paths < wl.renders * wl.width * wl.height * wl.spp
 
 
+def _small_radius_bound():
+    """The small scene with the sphere's radius bound beside its position (an emitter-free
+    radius binding: per-render areas rows in render-group mode)."""
+    wl = workloads.scaled(workloads.config_small(), width=40, height=36, spp=4, pairs=4)
+    wl.bindings = np.concatenate([wl.bindings, np.array([[workloads.BIND_SPHERE_RADIUS, 1, 0]], np.int32)])
+    wl.theta0 = np.concatenate([wl.theta0, [0.5]]).astype(np.float32)
+    wl.theta_ref = np.concatenate([wl.theta_ref, [0.45]]).astype(np.float32)
+    wl.sigma = np.concatenate([wl.sigma, [0.05]]).astype(np.float32)
+    return wl
+
+
 @pytest.mark.parametrize("make,groups", [
     # the caustic task: 64 renders, the light moves (a perturbed emitter in every lane's records)
     (lambda: workloads.scaled(workloads.config_caustic(), width=72, height=52, spp=4, pairs=32), (0, 32, 8, 2)),
     # the GI box: the light moves and two walls' albedos are bound (per-render materials)
-    (lambda: workloads.scaled(workloads.config_gi_box(), width=48, height=40, spp=4, pairs=16), (0, 16, 4)),
+    (lambda: workloads.scaled(workloads.config_gi_box(), width=48, height=40, spp=4, pairs=16), (0, 32, 16, 4)),
+    # a bound radius (emitter areas per render) on the small scene's sphere
+    (_small_radius_bound, (0, 8)),
     # ragged blocks, renders not a multiple of 4
     (lambda: workloads.scaled(workloads.config_caustic(), width=37, height=29, spp=3, pairs=3), (0, 2)),
     # a moving box with path sharing off, and Russian roulette
