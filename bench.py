@@ -366,8 +366,14 @@ def main():
     job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"],
                   render_groups=shape["render_groups"], use_tuned=False)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    # warm-up: at least W steps and at least one second of device work (clocks ramp up
+    # under sustained load; a few short steps after start-up run slow)
+    t_warm, n_warm = time.perf_counter(), 0
+    while n_warm < args.warmup or time.perf_counter() - t_warm < 1.0:
         job.step(stream)
+        n_warm += 1
+        if n_warm % 4 == 0:
+            torch.cuda.synchronize()
     torch.cuda.synchronize()
 
     # algorithmic work of one step (counting kernel variant, untimed)
@@ -400,8 +406,8 @@ def main():
     clocks = sampler.stop()
     trace_ms, launches = ctx.kernel_timing_read()
     ctx.kernel_timing(False)
-    step_ms = pdist.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, world,
-                                   device=f"cuda:{local}")
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = pdist.max_over_ranks(sum(per_step) / args.steps, world, device=f"cuda:{local}")
     state = job.read()
 
     # with path sharing: the per-render kernel on the same workload (sharing off), its own
@@ -488,6 +494,8 @@ def main():
             # ray segments (closest-hit rays + shadow rays) traced per second
             "msegments_per_s": world * (counts[5] + counts[6]) / (step_ms * 1e-3) / 1e6,
             "wall_s": wall,
+            "step_ms_min_median_max": [float(np.min(per_step)), float(np.median(per_step)), float(np.max(per_step))],
+            "warmup_steps_run": n_warm,
             "render_kernel_ms": trace_avg_ms,
             "work_per_step": {"sphere_tests": counts[0], "quad_tests": counts[1], "box_tests": counts[2],
                               "paths": counts[3], "vertices": counts[4], "shadow_rays": counts[5],
