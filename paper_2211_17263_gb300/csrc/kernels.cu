@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
     if (r == 0 && tid == 0 && J.share_reset)
         for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
     if (tid == 0 && J.aff_cursor) J.aff_cursor[r] = 0u;
+    if (J.aff_flags)  // this render's corrected-block bits, read by the last step's epilogue
+        for (int i = tid; i < J.flag_words; i += kInstBlock) J.aff_flags[size_t(r) * J.flag_words + i] = 0u;
     const unsigned step = J.step + (J.step_dev ? (unsigned)*J.step_dev : 0u);
     const float theta_d = (tid < D && J.theta) ? J.theta[(J.render_mode ? r * D : 0) + tid] : 0.0f;
     __syncthreads();
@@ -1800,6 +1802,13 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
                 if (dx) atomicAdd(a + 0, dx);
                 if (dy) atomicAdd(a + 1, dy);
                 if (dz) atomicAdd(a + 2, dz);
+                if (dx | dy | dz) {  // mark the pixel's block as corrected in render r
+                    const int y = div_magic(int(p.pixel), J.W, magic_W), x = int(p.pixel) - y * J.W;
+                    const int t = (y / J.bh) * J.tiles_x + x / J.bw;
+                    unsigned* fw = J.aff_flags + size_t(r) * J.flag_words + (t >> 5);
+                    const unsigned bit = 1u << (t & 31);
+                    if (!(__ldcg(fw) & bit)) atomicOr(fw, bit);
+                }
                 alive = false;
             }
         }
@@ -1858,12 +1867,15 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
         const float4 T = pix_ok ? __ldg(J.target + size_t(py) * J.W + px) : make_float4(0.f, 0.f, 0.f, 0.f);
         const size_t plane = size_t(J.W) * J.H * 3, pix3 = (size_t(py) * J.W + px) * 3;
         constexpr int kBatch = 4;  // rounds whose loads are issued before any store
+        const unsigned tbit = 1u << (t & 31);
         for (int rb = 0; rb < J.R; rb += kBatch * G) {
             unsigned long long a[kBatch][3];
+            bool corr[kBatch];  // render r corrected this block: read (and clear) its buffer
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) {
                 const int r = rb + q * G + sub;
-                const bool ok = pix_ok && r < J.R;
+                corr[q] = r < J.R && (__ldcg(J.aff_flags + size_t(r) * J.flag_words + (t >> 5)) & tbit) != 0u;
+                const bool ok = pix_ok && corr[q];
                 const unsigned long long* af = J.acc_aff + size_t(ok ? r : 0) * plane + (ok ? pix3 : 0);
                 a[q][0] = ok ? __ldcg(af + 0) : 0ull;
                 a[q][1] = ok ? __ldcg(af + 1) : 0ull;
@@ -1874,10 +1886,12 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
                 const int r = rb + q * G + sub;
                 double e = 0.0;
                 if (pix_ok && r < J.R) {
-                    unsigned long long* af = J.acc_aff + size_t(r) * plane + pix3;
-                    af[0] = 0ull;
-                    af[1] = 0ull;
-                    af[2] = 0ull;
+                    if (corr[q]) {
+                        unsigned long long* af = J.acc_aff + size_t(r) * plane + pix3;
+                        af[0] = 0ull;
+                        af[1] = 0ull;
+                        af[2] = 0ull;
+                    }
                     e = pixel_sq_error(s0 + a[q][0], s1 + a[q][1], s2 + a[q][2], T, unsigned(J.spp), inv);
                 }
                 for (int o = pw / 2; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
