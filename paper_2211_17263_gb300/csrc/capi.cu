@@ -65,7 +65,7 @@ struct Job {
     float4* varbox = nullptr;
     unsigned* cursor = nullptr;
     int* aff = nullptr;
-    unsigned* flags = nullptr;     // path sharing: [R][(blocks + 31) / 32] corrected-block bits
+    unsigned* flags = nullptr;     // path sharing: [R][(pixels + 31) / 32] corrected-pixel bits
     double *partials = nullptr, *losses_d = nullptr;
     unsigned* rdone = nullptr;
     int* step = nullptr;
@@ -117,7 +117,7 @@ struct prdpt_ctx {
     size_t s_varbox_n = 0;
     unsigned* s_cursor = nullptr; // path sharing: [R] per-render cursors
     size_t s_cursor_n = 0;
-    unsigned* s_flags = nullptr;  // path sharing: [R][(blocks + 31) / 32] corrected-block bits
+    unsigned* s_flags = nullptr;  // path sharing: [R][(pixels + 31) / 32] corrected-pixel bits
     size_t s_flags_n = 0;
     float* s_tex = nullptr;       // texture scenes: [R][D] per-render textures
     size_t s_tex_n = 0;
@@ -925,7 +925,7 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         if (prdpt_status st = grow(c, &c->s_afflist, &c->s_afflist_n, afflist_bytes(pix * o->spp))) return st;
         if (prdpt_status st = grow(c, &c->s_varbox, &c->s_varbox_n, (size_t)R * kMaxVariant * 2)) return st;
         if (prdpt_status st = grow(c, &c->s_cursor, &c->s_cursor_n, (size_t)R)) return st;
-        if (prdpt_status st = grow(c, &c->s_flags, &c->s_flags_n, (size_t)R * ((tiles + 31) / 32))) return st;
+        if (prdpt_status st = grow(c, &c->s_flags, &c->s_flags_n, (size_t)R * ((pix + 31) / 32))) return st;
     }
     if (prdpt_status st = grow(c, &c->s_scenes, &c->s_scenes_n, (size_t)R)) return st;
     if (prdpt_status st = grow(c, &c->s_w, &c->s_w_n, (size_t)R * D > (size_t)kMaxD ? (size_t)R * D : (size_t)kMaxD))
@@ -960,7 +960,7 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         IL.job0.var_box = c->s_varbox;
         IL.job0.aff_cursor = c->s_cursor;
         IL.job0.aff_flags = c->s_flags;
-        IL.job0.flag_words = (tiles + 31) / 32;
+        IL.job0.flag_words = int(((size_t)o->width * o->height + 31) / 32);
     }
     PRDPT_CUDA(launch_instantiate(IL, st_));
     TraceLaunch TL{};
@@ -996,7 +996,7 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
         J.var_box = c->s_varbox;
         J.aff_cursor = c->s_cursor;
         J.aff_flags = c->s_flags;
-        J.flag_words = (tiles + 31) / 32;
+        J.flag_words = int(((size_t)o->width * o->height + 31) / 32);
         J.aff_tiles = c->s_aff;
         J.share_ctl = c->s_ctl + 4;
     }
@@ -1220,7 +1220,7 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
                           ~size_t(255);
     const size_t off_af = (off_cu + (probe.share ? sizeof(unsigned) * (size_t)R : 0) + 255) & ~size_t(255);
     const size_t off_fl = (off_af + (probe.share ? sizeof(int) * (size_t)tiles : 0) + 255) & ~size_t(255);
-    const int flag_words = (tiles + 31) / 32;
+    const int flag_words = int(((size_t)W * H + 31) / 32);
     const size_t off_gp =
         (off_fl + (probe.share ? sizeof(unsigned) * (size_t)R * flag_words : 0) + 255) & ~size_t(255);
     const size_t off_rg = (off_gp + (probe.diff ? sizeof(double) * (size_t)R * tiles * D : 0) + 255) & ~size_t(255);

@@ -108,7 +108,7 @@ struct InstJob {
     // (min, max corner, inflated), written by the render's CTA; null when not sharing
     float4* var_box;
     unsigned* aff_cursor;     // [R] per-render cursors of the per-render pass, zeroed by the render's CTA
-    unsigned* aff_flags;      // [R][flag_words] blocks with corrections per render, zeroed by the render's CTA
+    unsigned* aff_flags;      // [R][flag_words] pixels with corrections per render, zeroed by the render's CTA
     int flag_words;
     int n_var;
     int var_prim[kMaxVariant];  // the perturbed primitives (natural order indices)
@@ -151,8 +151,8 @@ struct TraceJob {
     unsigned seg_cap;
     const float4* var_box;    // [R][kMaxVariant][2] per-render bounds of the perturbed primitives
     unsigned* aff_cursor;     // [R] next list entry of each render in the per-render pass
-    // [R][flag_words] bit t of render r: the per-render pass added a correction to block t of
-    // render r (the epilogue reads and clears only those blocks' correction buffers)
+    // [R][flag_words] bit p of render r: the per-render pass added a correction to pixel p of
+    // render r (the epilogue reads and clears only those pixels' corrections)
     unsigned* aff_flags;
     int flag_words;
     int* aff_tiles;           // [tiles] blocks with affected paths (appended by the shared pass)

@@ -1802,11 +1802,9 @@ __global__ void __launch_bounds__(kBlock, kTraceMinBlocks) k_trace_affected(cons
                 if (dx) atomicAdd(a + 0, dx);
                 if (dy) atomicAdd(a + 1, dy);
                 if (dz) atomicAdd(a + 2, dz);
-                if (dx | dy | dz) {  // mark the pixel's block as corrected in render r
-                    const int y = div_magic(int(p.pixel), J.W, magic_W), x = int(p.pixel) - y * J.W;
-                    const int t = (y / J.bh) * J.tiles_x + x / J.bw;
-                    unsigned* fw = J.aff_flags + size_t(r) * J.flag_words + (t >> 5);
-                    const unsigned bit = 1u << (t & 31);
+                if (dx | dy | dz) {  // mark the pixel as corrected in render r
+                    unsigned* fw = J.aff_flags + size_t(r) * J.flag_words + (p.pixel >> 5);
+                    const unsigned bit = 1u << (p.pixel & 31u);
                     if (!(__ldcg(fw) & bit)) atomicOr(fw, bit);
                 }
                 alive = false;
@@ -1866,16 +1864,17 @@ __global__ void __launch_bounds__(kBlock) k_shared_epilogue(const __grid_constan
                                  s2 = pix_ok ? __ldcg(sh + 64 + pl) : 0ull;
         const float4 T = pix_ok ? __ldg(J.target + size_t(py) * J.W + px) : make_float4(0.f, 0.f, 0.f, 0.f);
         const size_t plane = size_t(J.W) * J.H * 3, pix3 = (size_t(py) * J.W + px) * 3;
+        const unsigned pixel = pix_ok ? unsigned(py * J.W + px) : 0u, pbit = 1u << (pixel & 31u);
         constexpr int kBatch = 4;  // rounds whose loads are issued before any store
-        const unsigned tbit = 1u << (t & 31);
         for (int rb = 0; rb < J.R; rb += kBatch * G) {
             unsigned long long a[kBatch][3];
-            bool corr[kBatch];  // render r corrected this block: read (and clear) its buffer
+            bool corr[kBatch];  // render r corrected this pixel: read (and clear) its correction
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) {
                 const int r = rb + q * G + sub;
-                corr[q] = r < J.R && (__ldcg(J.aff_flags + size_t(r) * J.flag_words + (t >> 5)) & tbit) != 0u;
-                const bool ok = pix_ok && corr[q];
+                corr[q] = pix_ok && r < J.R &&
+                          (__ldcg(J.aff_flags + size_t(r) * J.flag_words + (pixel >> 5)) & pbit) != 0u;
+                const bool ok = corr[q];
                 const unsigned long long* af = J.acc_aff + size_t(ok ? r : 0) * plane + (ok ? pix3 : 0);
                 a[q][0] = ok ? __ldcg(af + 0) : 0ull;
                 a[q][1] = ok ? __ldcg(af + 1) : 0ull;
