@@ -5,7 +5,9 @@
   32 spp, depth 8 with Russian roulette): the whole gradient and every render's loss
   against the FP64 oracle on the same random streams;
 * caustic (512x512, 64 spp, depth 12): 512 sampled pixels of two full renders against
-  the oracle's per-pixel paths (the whole 64-render step is too long for the oracle);
+  the oracle's per-pixel paths (the whole 64-render step is too long for the oracle), and
+  the gradient of the full image traced in render groups with 8 renders at 64 spp or 64
+  renders at 8 spp;
 * bandwidth annealing (Sec. 3.3, warm start at half the run): a resident job's
   trajectory against the oracle's schedule.
 """
@@ -41,6 +43,27 @@ def test_full_size_gradient(ctx, make):
     g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
     torch.cuda.synchronize()
     ref = oracle.smoothed_grad(wl, target=target, step=3)
+    L = L.cpu().numpy()
+    assert np.allclose(L, ref["losses"], rtol=1e-4, atol=1e-9), np.max(np.abs(L / ref["losses"] - 1))
+    err = grad_rel_error(g.cpu().numpy(), ref["grad"], ref["weights"], ref["losses"])
+    assert err <= GRAD_REL, err
+
+
+@pytest.mark.parametrize("pairs,spp", [(4, 64), (32, 8)])
+def test_full_size_caustic_gradient_in_render_groups(ctx, pairs, spp):
+    """The caustic image at full size (512x512, depth 12, Russian roulette from vertex 3)
+    traced in render groups (8 renders at 64 spp; 64 renders at 8 spp, groups of 32): the
+    gradient and every loss against the FP64 oracle."""
+    wl = workloads.scaled(workloads.config_caustic(), spp=spp, pairs=pairs)
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = oracle.render_target(wl)
+    opts = scene.grad_opts(wl, step=2)
+    ctx.counters_enable(True)
+    g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
+    torch.cuda.synchronize()
+    assert ctx.counters_read()[3] == wl.renders * wl.width * wl.height * wl.spp
+    ctx.counters_enable(False)
+    ref = oracle.smoothed_grad(wl, target=target, step=2)
     L = L.cpu().numpy()
     assert np.allclose(L, ref["losses"], rtol=1e-4, atol=1e-9), np.max(np.abs(L / ref["losses"] - 1))
     err = grad_rel_error(g.cpu().numpy(), ref["grad"], ref["weights"], ref["losses"])
