@@ -660,7 +660,7 @@ static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
     J.gsize = 0;
     J.gstride = 0;
     if (J.share || o->render_groups < 0 || !o->crn || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT ||
-        B.tex_mat >= 0)
+        B.tex_mat >= 0 || B.n_prims > kGroupPrims || B.n_mats > kGroupMats)
         return;
     unsigned prims = 0u, mats = 0u;
     bool radius = false;

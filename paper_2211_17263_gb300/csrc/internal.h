@@ -263,6 +263,8 @@ cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, uns
 int trace_blocks_per_sm(bool render_mode);
 int trace_group_blocks_per_sm();
 constexpr int kGroupBlock = 128;    // render-group CTAs: 4 warps (their per-warp tables fit 48 KB)
+constexpr int kGroupPrims = 16;     // render-group mode: at most 16 primitives ...
+constexpr int kGroupMats = 16;      // ... and 16 materials (the staged copy is smaller)
 constexpr int kGroupTabRows = 192;  // float4 of a warp's per-render record table (render-group mode)
 constexpr int kDiffBlock = 128;
 int trace_diff_blocks_per_sm();

@@ -506,8 +506,8 @@ struct Hit {
 
 // Closest hit over all primitives, grouped by type. With kSkip, primitives whose
 // record slot is set in `skip` are left out (the perturbed ones, in shared mode).
-template <bool kCount, bool kSkip>
-__device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 d, Counters& cnt, unsigned skip) {
+template <bool kCount, bool kSkip, class Scn>
+__device__ __forceinline__ Hit closest_hit(const Scn& S, float3 o, float3 d, Counters& cnt, unsigned skip) {
     Hit h{INFINITY, -1, 0};
     const int ns = S.n_sph, nq = S.n_quad, nb = S.n_box;
     if (kCount) {
@@ -540,8 +540,8 @@ __device__ __forceinline__ Hit closest_hit(const InstScene& S, float3 o, float3 
 
 // Is anything but primitive slot `light` (and, with kSkip, the slots in `skip`) hit
 // closer than dist?
-template <bool kCount, bool kSkip>
-__device__ __forceinline__ bool occluded(const InstScene& S, float3 o, float3 d, float dist, int light,
+template <bool kCount, bool kSkip, class Scn>
+__device__ __forceinline__ bool occluded(const Scn& S, float3 o, float3 d, float dist, int light,
                                          Counters& cnt, unsigned skip) {
     const int ns = S.n_sph, nq = S.n_quad, nb = S.n_box;
     if (kCount) ++cnt.shadow;
@@ -586,8 +586,8 @@ struct GroupLane {
 
 // Record of primitive slot `slot`: the lane's own for a perturbed primitive, else the
 // staged scene's.
-template <bool kGroup>
-__device__ __forceinline__ const float4* prim_rec(const InstScene& S, int slot, const GroupLane* g) {
+template <bool kGroup, class Scn>
+__device__ __forceinline__ const float4* prim_rec(const Scn& S, int slot, const GroupLane* g) {
     if constexpr (kGroup) {
         if ((g->prims >> slot) & 1u) return g->rec + 4 * __popc(g->prims & ((1u << slot) - 1u));
     }
@@ -595,16 +595,16 @@ __device__ __forceinline__ const float4* prim_rec(const InstScene& S, int slot, 
 }
 
 // Albedo row (albedo, type) of material m: the lane's own for a bound material.
-template <bool kGroup>
-__device__ __forceinline__ float4 mat_albedo(const InstScene& S, int m, const GroupLane* g) {
+template <bool kGroup, class Scn>
+__device__ __forceinline__ float4 mat_albedo(const Scn& S, int m, const GroupLane* g) {
     if constexpr (kGroup) {
         if ((g->mats >> m) & 1u) return g->rec[4 * g->n_var + __popc(g->mats & ((1u << m) - 1u))];
     }
     return S.mat[m][0];
 }
 
-template <bool kGroup>
-__device__ __forceinline__ float light_area(const InstScene& S, int li, const GroupLane* g) {
+template <bool kGroup, class Scn>
+__device__ __forceinline__ float light_area(const Scn& S, int li, const GroupLane* g) {
     if constexpr (kGroup) {
         if (g->areas) return reinterpret_cast<const float*>(g->rec + 4 * g->n_var + __popc(g->mats))[li];
     }
@@ -613,8 +613,8 @@ __device__ __forceinline__ float light_area(const InstScene& S, int li, const Gr
 
 // The lane's perturbed primitives against a ray: closer hits replace h (the staged scene's
 // closest hit over the other primitives).
-template <bool kCount>
-__device__ __forceinline__ void group_hit(const InstScene& S, const GroupLane& g, float3 o, float3 d, Hit& h,
+template <bool kCount, class Scn>
+__device__ __forceinline__ void group_hit(const Scn& S, const GroupLane& g, float3 o, float3 d, Hit& h,
                                           Counters& cnt) {
     unsigned m = g.prims;
     for (int k = 0; m; ++k) {
@@ -641,8 +641,8 @@ __device__ __forceinline__ void group_hit(const InstScene& S, const GroupLane& g
 }
 
 // Is one of the lane's perturbed primitives other than slot `light` hit closer than dist?
-template <bool kCount>
-__device__ __forceinline__ bool group_occluded(const InstScene& S, const GroupLane& g, float3 o, float3 d, float dist,
+template <bool kCount, class Scn>
+__device__ __forceinline__ bool group_occluded(const Scn& S, const GroupLane& g, float3 o, float3 d, float dist,
                                                int light, Counters& cnt) {
     unsigned m = g.prims;
     for (int k = 0; m; ++k) {
@@ -770,7 +770,8 @@ __device__ __forceinline__ void note_touch(const VarBoxes& V, float3 o, float3 d
     p.seg = seg + 1u;
 }
 
-__device__ __forceinline__ uint4 path_words(const InstScene& S, unsigned pixel, int s, int b, int slot) {
+template <class Scn>
+__device__ __forceinline__ uint4 path_words(const Scn& S, unsigned pixel, int s, int b, int slot) {
     const unsigned c1 = unsigned(s) | (unsigned(b) << 16) | (unsigned(slot) << 24);
     return philox(make_uint4(pixel, c1, S.step, S.c3), S.seed_lo, S.seed_hi);
 }
@@ -787,7 +788,8 @@ __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
 // Albedo of a textured quad at hit point pt: texel (floor(s T), floor(t T)) with
 // s = (pt - c).u / |u|^2 + 1/2, t = (pt - c).v / |v|^2 + 1/2 (each clamped to [0, T-1]) of
 // the render's texture [T][T][3]; channels clamped to [0, 1].
-__device__ __forceinline__ float3 tex_albedo(const InstScene& S, const float4* P, float3 pt) {
+template <class Scn>
+__device__ __forceinline__ float3 tex_albedo(const Scn& S, const float4* P, float3 pt) {
     const float4 c = P[0], u = P[2], v = P[3];
     const float3 l = pt - xyz(c);
     const float s = fmaf(dot3(l, xyz(u)), u.w, 0.5f), t = fmaf(dot3(l, xyz(v)), v.w, 0.5f);
@@ -800,7 +802,8 @@ __device__ __forceinline__ float3 tex_albedo(const InstScene& S, const float4* P
 }
 
 // Camera ray of sample s through pixel (x, y): pinhole, box-filtered jitter (slot 2).
-__device__ __forceinline__ void start_path(const InstScene& S, int W, int H, int x, int y, int s, int slot,
+template <class Scn>
+__device__ __forceinline__ void start_path(const Scn& S, int W, int H, int x, int y, int s, int slot,
                                            Path& p) {
     p.pixel = unsigned(y * W + x);
     const uint4 jw = path_words(S, p.pixel, s, 0, 2);
@@ -849,8 +852,8 @@ __device__ __forceinline__ void tan_reset(Tangents<kND>& t) {
 }
 
 // L += beta * E (background or emitter seen on a camera or specular ray); E may be bound.
-template <int kND>
-__device__ __forceinline__ void tan_emit(Tangents<kND>& t, const TraceJob& J, const InstScene& S, float3 beta,
+template <int kND, class Scn>
+__device__ __forceinline__ void tan_emit(Tangents<kND>& t, const TraceJob& J, const Scn& S, float3 beta,
                                          float3 E, int mat) {
 #pragma unroll
     for (int k = 0; k < kND; ++k) {
@@ -863,8 +866,8 @@ __device__ __forceinline__ void tan_emit(Tangents<kND>& t, const TraceJob& J, co
 }
 
 // L += beta * albedo * Le * g (next-event estimation at a vertex of material mat).
-template <int kND>
-__device__ __forceinline__ void tan_nee(Tangents<kND>& t, const TraceJob& J, const InstScene& S, float3 beta,
+template <int kND, class Scn>
+__device__ __forceinline__ void tan_nee(Tangents<kND>& t, const TraceJob& J, const Scn& S, float3 beta,
                                         float3 albedo, int mat, float3 Le, int lmat, float g) {
 #pragma unroll
     for (int k = 0; k < kND; ++k) {
@@ -879,8 +882,8 @@ __device__ __forceinline__ void tan_nee(Tangents<kND>& t, const TraceJob& J, con
 }
 
 // beta <- beta * albedo (scattering at a vertex of material mat); beta is the old value.
-template <int kND>
-__device__ __forceinline__ void tan_scatter(Tangents<kND>& t, const TraceJob& J, const InstScene& S, float3 beta,
+template <int kND, class Scn>
+__device__ __forceinline__ void tan_scatter(Tangents<kND>& t, const TraceJob& J, const Scn& S, float3 beta,
                                             float3 albedo, int mat) {
 #pragma unroll
     for (int k = 0; k < kND; ++k) {
@@ -898,8 +901,8 @@ __device__ __forceinline__ void tan_rr(Tangents<kND>& t, float inv_q) {
     for (int k = 0; k < kND; ++k) t.dB[k] *= inv_q;
 }
 
-template <bool kCount, bool kShared, int kND = 0, bool kGroup = false>
-__device__ __forceinline__ int advance(const InstScene& S, int depth, int rr_start, Path& p, Counters& cnt,
+template <bool kCount, bool kShared, int kND = 0, bool kGroup = false, class Scn>
+__device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Path& p, Counters& cnt,
                                        const VarBoxes* V = nullptr, Tangents<kND>* tn = nullptr,
                                        const TraceJob* Jd = nullptr, const GroupLane* gl = nullptr) {
     if (kShared && p.seg == 0u) {
@@ -1250,8 +1253,8 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, int k) {
 // Ended paths add their radiance to acc[.][slot]. In shared mode a path that touched a
 // perturbed primitive's union box is also recorded -- its code, segment word and
 // shared-pass radiance -- in the job's list, and *recorded is set.
-template <bool kCount, bool kShared, class Decode, int kND = 0>
-__device__ __forceinline__ void run_pool(const InstScene& S, const TraceJob& J, int ntasks, int x0, int y0, int vw,
+template <bool kCount, bool kShared, class Decode, int kND = 0, class Scn>
+__device__ __forceinline__ void run_pool(const Scn& S, const TraceJob& J, int ntasks, int x0, int y0, int vw,
                                          unsigned magic_w, Decode decode, unsigned long long (&acc)[3][32],
                                          unsigned* recorded, const VarBoxes* V, Counters& cnt, int lane,
                                          unsigned long long (*dacc)[32] = nullptr) {
@@ -1525,15 +1528,56 @@ __global__ void __launch_bounds__(kND > 0 ? kDiffBlock : kBlock, kND > 0 ? kDiff
 constexpr int kGroupTab = kGroupTabRows;  // float4 per warp for the group's per-render records
 static_assert(offsetof(InstScene, light_area) % 16 == 0, "emitter areas are copied as two float4");
 
+// The render-group kernel's staged scene: the fields of InstScene with arrays for at most
+// kGroupPrims primitives and kGroupMats materials (the per-warp copy is then 1.9 KB instead
+// of 3.4 KB, so more warps fit an SM). Its header is laid out as InstScene's.
+struct __align__(16) GroupScene {
+    int n_sph, n_quad, n_box, n_lights;
+    unsigned seed_lo, seed_hi, step, c3;
+    float4 eye, fwd, right, up, bg;
+    int4 light[kMaxLights];
+    float light_area[kMaxLights];
+    float dclamp[kMaxDiff];
+    const float* tex;
+    int tex_mat, tex_res;
+    float4 mat[kGroupMats][2];
+    float4 prim[kGroupPrims][4];
+};
+static_assert(offsetof(GroupScene, light) == offsetof(InstScene, light) &&
+                  offsetof(GroupScene, light_area) == offsetof(InstScene, light_area) &&
+                  offsetof(GroupScene, tex) == offsetof(InstScene, tex) &&
+                  offsetof(GroupScene, mat) == offsetof(InstScene, mat),
+              "GroupScene's header must be laid out as InstScene's");
+
+// Copy render r's scene (header, used materials, used primitives) into a warp's GroupScene
+// (the job has at most kGroupPrims primitives and kGroupMats materials).
+__device__ __forceinline__ void stage_group_scene(GroupScene& S, const TraceJob& J, int r, int lane) {
+    const float4* src = reinterpret_cast<const float4*>(J.scenes + r);
+    float4* dst = reinterpret_cast<float4*>(&S);
+    constexpr int kHead = int(offsetof(InstScene, mat) / 16);
+    constexpr int kPrimSrc = int(offsetof(InstScene, prim) / 16);
+    constexpr int kPrimDst = int(offsetof(GroupScene, prim) / 16);
+    const int nm = 2 * J.n_mats, np = 4 * J.n_prims;
+    for (int i = lane; i < kHead + nm + np; i += 32) {
+        const bool is_prim = i >= kHead + nm;
+        const int o = is_prim ? i - kHead - nm : i;
+        dst[is_prim ? kPrimDst + o : o] = __ldg(src + (is_prim ? kPrimSrc + o : o));
+    }
+    __syncwarp();
+}
+
 struct GroupSmem {
-    InstScene scene;  // the invariant part (render g G's records of the other primitives)
+    GroupScene scene;  // the invariant part (render g G's records of the other primitives)
     TraceJob job;
     float4 tab[kGroupTab];
     double pair[5][32];  // each lane's pairwise-sum stack (touched once per pixel)
     unsigned long long acc[3][32];  // each lane's radiance sums of the current pixel, 2^-32 fixed point
 };
 
-constexpr int kGroupMinBlocks = 6;  // 128-thread CTAs, <= 85 registers: 24 resident warps per SM
+#ifndef PRDPT_GROUP_MIN_BLOCKS
+#define PRDPT_GROUP_MIN_BLOCKS 6  // 128-thread CTAs, <= 85 registers: 24 resident warps per SM
+#endif
+constexpr int kGroupMinBlocks = PRDPT_GROUP_MIN_BLOCKS;
 
 __device__ __forceinline__ int brev5(int q) { return int(__brev(unsigned(q)) >> 27); }
 
@@ -1591,12 +1635,13 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
         const int G = J.gsize, ngr = J.R / G, stride = J.gstride;
         const int li = int(item) - J.item_begin;
         const int g = li % ngr, t = li / ngr;  // group-interleaved: neighbouring items share pixels
-        if (G < 1 || G > 32 || (32 % G) != 0 || t >= J.tiles || G * stride > kGroupTab) {
+        if (G < 1 || G > 32 || (32 % G) != 0 || t >= J.tiles || G * stride > kGroupTab || J.n_prims > kGroupPrims ||
+            J.n_mats > kGroupMats) {
             if (lane == 0) atomicOr(L.status, kStatusBadItem);
             break;
         }
         if (g != cur_item_g) {  // stage render g G's scene and the group's per-render records
-            stage_scene(W.scene, J, g * G, lane);
+            stage_group_scene(W.scene, J, g * G, lane);
             const int n = J.n_var, nm = __popc(J.var_mats);
             for (int i = lane; i < G * stride; i += 32) {
                 const int gi = i / stride, q = i - gi * stride;
