@@ -659,7 +659,6 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
 static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o) {
     J.gsize = 0;
     J.gstride = 0;
-    J.grows_sphere = 1;
     if (J.share || o->render_groups < 0 || !o->crn || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT ||
         B.tex_mat >= 0 || B.n_prims > kGroupPrims || B.n_mats > kGroupMats)
         return;
@@ -674,16 +673,9 @@ static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
     }
     const int n = __builtin_popcount(prims), nm = __builtin_popcount(mats);
     if (n > kMaxVariant) return;
-    // per render: the leading rows of each perturbed primitive's record that its bindings
-    // change (a sphere's or quad's centre row, plus a sphere's r^2 / 1/r row when a radius
-    // is bound; a box's two corner rows), the bound materials' albedo rows, and the 8
-    // emitter areas when a radius binding can change one
-    int rows = 0;
-    for (unsigned m = prims; m; m &= m - 1u) {
-        const int slot = __builtin_ctz(m);
-        rows += slot < B.n_sph ? (radius ? 2 : 1) : (slot < B.n_sph + B.n_quad ? 1 : 2);
-    }
-    const int stride = rows + nm + (radius ? 2 : 0);
+    // per render: the perturbed primitives' records (4 float4 each), the bound materials'
+    // albedo rows, and the 8 emitter areas when a radius binding can change one
+    const int stride = 4 * n + nm + (radius ? 2 : 0);
     if (stride == 0) return;
     const int R = J.R;
     int G = 0;
@@ -700,7 +692,6 @@ static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
     if (!G) return;
     J.gsize = G;
     J.gstride = stride;
-    J.grows_sphere = radius ? 2 : 1;
     J.n_var = n;
     J.var_prims = prims;
     J.var_mats = mats;

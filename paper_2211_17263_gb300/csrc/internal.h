@@ -172,11 +172,10 @@ struct TraceJob {
     unsigned var_prims;       // record-slot bitmask of perturbed primitives
     unsigned var_mats;        // bitmask of materials whose parameters are bound
     // Render-group mode (k_trace_group): gsize renders per work item (0: per-render items);
-    // each render's row of the per-warp table holds gstride float4 (the leading rows of the
-    // n_var perturbed primitives' records that their bindings change, the albedo rows of the
-    // bound materials, and its emitter areas when a radius binding can change them)
+    // each render's row of the per-warp table holds gstride float4 (its records of the
+    // n_var perturbed primitives, the albedo rows of the bound materials, and its emitter
+    // areas when a radius binding can change them)
     int gsize, gstride;
-    int grows_sphere;         // rows of a moved sphere's record in a row: 1 (centre), 2 (radius bound)
 };
 struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)

@@ -433,8 +433,7 @@ struct Counters {
     unsigned sph, quad, box, paths, vertices, shadow, rays, pad;
 };
 
-template <class Rec>
-__device__ __forceinline__ float sphere_t(const Rec& P, float3 o, float3 d) {
+__device__ __forceinline__ float sphere_t(const float4* P, float3 o, float3 d) {
     const float4 a = P[0];
     const float r2 = P[1].x;
     const float3 oc = o - xyz(a);
@@ -448,8 +447,7 @@ __device__ __forceinline__ float sphere_t(const Rec& P, float3 o, float3 d) {
     return (t > kEps) ? t : INFINITY;
 }
 
-template <class Rec>
-__device__ __forceinline__ float quad_t(const Rec& P, float3 o, float3 d) {
+__device__ __forceinline__ float quad_t(const float4* P, float3 o, float3 d) {
     const float4 a = P[0], nb = P[1], uu = P[2], vv = P[3];
     const float3 n = xyz(nb);
     const float den = dot3(n, d);
@@ -463,8 +461,7 @@ __device__ __forceinline__ float quad_t(const Rec& P, float3 o, float3 d) {
 }
 
 // Slab test; returns the nearest t > eps (entering, or leaving from inside).
-template <class Rec>
-__device__ __forceinline__ float box_t(const Rec& P, float3 o, float3 inv) {
+__device__ __forceinline__ float box_t(const float4* P, float3 o, float3 inv) {
     const float3 lo = xyz(P[0]), hi = xyz(P[1]);
     const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
     const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
@@ -477,8 +474,7 @@ __device__ __forceinline__ float box_t(const Rec& P, float3 o, float3 inv) {
 }
 
 // Outward normal of box record P at the hit found by box_t.
-template <class Rec>
-__device__ __forceinline__ float3 box_normal(const Rec& P, float3 o, float3 d, float3 inv) {
+__device__ __forceinline__ float3 box_normal(const float4* P, float3 o, float3 d, float3 inv) {
     const float3 lo = xyz(P[0]), hi = xyz(P[1]);
     float tn[3], tf[3];
     const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z}, ii[3] = {inv.x, inv.y, inv.z};
@@ -573,66 +569,36 @@ __device__ __forceinline__ bool occluded(const Scn& S, float3 o, float3 d, float
 // Render-group mode: the lanes of a warp trace the same path samples for up to 32
 // renders of a job at once (with common random numbers the renders' paths agree until a
 // perturbed primitive intervenes, so the lanes stay coherent). The invariant part of the
-// scene is the warp's staged scene; each lane reads what differs between renders from its
-// row of a per-warp table. A binding changes only the leading rows of a primitive's record
-// (a sphere's or quad's centre row; a sphere's r^2 / 1/r row too when a radius is bound; a
-// box's two corner rows), so a row holds just those, then the albedo rows of the bound
-// materials, then the render's emitter areas when a radius binding can change them.
-struct GroupLayout {              // uniform over the warp (shared memory)
-    unsigned prims, mats;         // record-slot mask of the perturbed primitives; bound materials
-    int off[kMaxVariant];         // the k-th perturbed primitive's rows start at row off[k]
-    int rows[kMaxVariant];        // ... and number rows[k]
-    int mat_off, area_off;        // albedo rows; emitter areas (-1: the staged scene's)
-};
-
+// scene is the warp's staged InstScene; each lane reads what differs between renders from
+// its row of a per-warp table:
+//   [4 k .. 4 k + 3]   record of the k-th perturbed primitive (in record-slot order)
+//   [4 n + j]          albedo row (albedo, type) of the j-th bound material (only albedos
+//                      are bound in this mode; the emission row is the staged scene's)
+//   [4 n + m .. + 1]   the render's emitter areas (8 floats), only when a radius binding
+//                      can change an emitter's area (m = bound materials)
 struct GroupLane {
-    const float4* rec;            // this lane's row
-    const GroupLayout* lay;
+    const float4* rec;  // this lane's row
+    unsigned prims;     // record-slot mask of the perturbed primitives
+    unsigned mats;      // mask of the bound materials
+    int n_var;          // perturbed primitives
+    int areas;          // 1: the row holds the emitter areas
 };
 
-// A primitive record of which the first n rows are the lane's own and the rest the staged
-// scene's.
-struct RecView {
-    const float4* own;
-    const float4* base;
-    int n;
-    __device__ __forceinline__ float4 operator[](int q) const { return q < n ? own[q] : base[q]; }
-};
-
-// Record of primitive slot `slot`: partly the lane's own for a perturbed primitive.
+// Record of primitive slot `slot`: the lane's own for a perturbed primitive, else the
+// staged scene's.
 template <bool kGroup, class Scn>
-__device__ __forceinline__ auto prim_rec(const Scn& S, int slot, const GroupLane* g) {
+__device__ __forceinline__ const float4* prim_rec(const Scn& S, int slot, const GroupLane* g) {
     if constexpr (kGroup) {
-        const GroupLayout& L = *g->lay;
-        if ((L.prims >> slot) & 1u) {
-            const int k = __popc(L.prims & ((1u << slot) - 1u));
-            return RecView{g->rec + L.off[k], S.prim[slot], L.rows[k]};
-        }
-        return RecView{g->rec, S.prim[slot], 0};
-    } else {
-        return S.prim[slot];
+        if ((g->prims >> slot) & 1u) return g->rec + 4 * __popc(g->prims & ((1u << slot) - 1u));
     }
-}
-
-// Row q of primitive slot `slot`'s record: the lane's own where it differs between renders.
-template <bool kGroup, class Scn>
-__device__ __forceinline__ float4 prim_row(const Scn& S, int slot, int q, const GroupLane* g) {
-    if constexpr (kGroup) {
-        const GroupLayout& L = *g->lay;
-        if ((L.prims >> slot) & 1u) {
-            const int k = __popc(L.prims & ((1u << slot) - 1u));
-            if (q < L.rows[k]) return g->rec[L.off[k] + q];
-        }
-    }
-    return S.prim[slot][q];
+    return S.prim[slot];
 }
 
 // Albedo row (albedo, type) of material m: the lane's own for a bound material.
 template <bool kGroup, class Scn>
 __device__ __forceinline__ float4 mat_albedo(const Scn& S, int m, const GroupLane* g) {
     if constexpr (kGroup) {
-        const GroupLayout& L = *g->lay;
-        if ((L.mats >> m) & 1u) return g->rec[L.mat_off + __popc(L.mats & ((1u << m) - 1u))];
+        if ((g->mats >> m) & 1u) return g->rec[4 * g->n_var + __popc(g->mats & ((1u << m) - 1u))];
     }
     return S.mat[m][0];
 }
@@ -640,8 +606,7 @@ __device__ __forceinline__ float4 mat_albedo(const Scn& S, int m, const GroupLan
 template <bool kGroup, class Scn>
 __device__ __forceinline__ float light_area(const Scn& S, int li, const GroupLane* g) {
     if constexpr (kGroup) {
-        const int a = g->lay->area_off;
-        if (a >= 0) return reinterpret_cast<const float*>(g->rec + a)[li];
+        if (g->areas) return reinterpret_cast<const float*>(g->rec + 4 * g->n_var + __popc(g->mats))[li];
     }
     return S.light_area[li];
 }
@@ -651,12 +616,11 @@ __device__ __forceinline__ float light_area(const Scn& S, int li, const GroupLan
 template <bool kCount, class Scn>
 __device__ __forceinline__ void group_hit(const Scn& S, const GroupLane& g, float3 o, float3 d, Hit& h,
                                           Counters& cnt) {
-    const GroupLayout& L = *g.lay;
-    unsigned m = L.prims;
+    unsigned m = g.prims;
     for (int k = 0; m; ++k) {
         const int slot = __ffs(m) - 1;
         m &= m - 1u;
-        const RecView P{g.rec + L.off[k], S.prim[slot], L.rows[k]};
+        const float4* P = g.rec + 4 * k;
         float t;
         int type;
         if (slot < S.n_sph) {
@@ -680,13 +644,12 @@ __device__ __forceinline__ void group_hit(const Scn& S, const GroupLane& g, floa
 template <bool kCount, class Scn>
 __device__ __forceinline__ bool group_occluded(const Scn& S, const GroupLane& g, float3 o, float3 d, float dist,
                                                int light, Counters& cnt) {
-    const GroupLayout& L = *g.lay;
-    unsigned m = L.prims;
+    unsigned m = g.prims;
     for (int k = 0; m; ++k) {
         const int slot = __ffs(m) - 1;
         m &= m - 1u;
         if (slot == light) continue;
-        const RecView P{g.rec + L.off[k], S.prim[slot], L.rows[k]};
+        const float4* P = g.rec + 4 * k;
         float t;
         if (slot < S.n_sph) {
             t = sphere_t(P, o, d);
@@ -825,8 +788,8 @@ __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
 // Albedo of a textured quad at hit point pt: texel (floor(s T), floor(t T)) with
 // s = (pt - c).u / |u|^2 + 1/2, t = (pt - c).v / |v|^2 + 1/2 (each clamped to [0, T-1]) of
 // the render's texture [T][T][3]; channels clamped to [0, 1].
-template <class Scn, class Rec>
-__device__ __forceinline__ float3 tex_albedo(const Scn& S, const Rec& P, float3 pt) {
+template <class Scn>
+__device__ __forceinline__ float3 tex_albedo(const Scn& S, const float4* P, float3 pt) {
     const float4 c = P[0], u = P[2], v = P[3];
     const float3 l = pt - xyz(c);
     const float s = fmaf(dot3(l, xyz(u)), u.w, 0.5f), t = fmaf(dot3(l, xyz(v)), v.w, 0.5f);
@@ -953,7 +916,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
     }
     Hit h;
     if constexpr (kGroup) {  // the staged scene without the perturbed primitives, then the lane's own
-        h = closest_hit<kCount, true>(S, p.o, p.d, cnt, gl->lay->prims);
+        h = closest_hit<kCount, true>(S, p.o, p.d, cnt, gl->prims);
         group_hit<kCount>(S, *gl, p.o, p.d, h, cnt);
     } else {
         h = closest_hit<kCount, kShared>(S, p.o, p.d, cnt, kShared ? V->skip : 0u);
@@ -969,34 +932,19 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
     }
     if (kCount) ++cnt.vertices;
     const float3 pt = p.o + p.d * h.t;
+    const float4* P = prim_rec<kGroup>(S, h.slot, gl);
     float3 ng;
     int mat;
-    if constexpr (kGroup) {  // rows 0 and 1 of the hit record, the lane's own where they differ
-        const float4 P0 = prim_row<true>(S, h.slot, 0, gl), P1 = prim_row<true>(S, h.slot, 1, gl);
-        const float4 PP[2] = {P0, P1};
-        if (h.type == kSphere) {
-            ng = (pt - xyz(P0)) * P1.y;
-            mat = as_int(P1.z);
-        } else if (h.type == kQuad) {
-            ng = xyz(P1);
-            mat = as_int(P0.w);
-        } else {
-            ng = box_normal(PP, p.o, p.d, rcp3(p.d));
-            mat = as_int(P0.w);
-        }
+    if (h.type == kSphere) {
+        const float4 a = P[0];
+        ng = (pt - xyz(a)) * P[1].y;
+        mat = as_int(P[1].z);
+    } else if (h.type == kQuad) {
+        ng = xyz(P[1]);
+        mat = as_int(P[0].w);
     } else {
-        const float4* P = S.prim[h.slot];
-        if (h.type == kSphere) {
-            const float4 a = P[0];
-            ng = (pt - xyz(a)) * P[1].y;
-            mat = as_int(P[1].z);
-        } else if (h.type == kQuad) {
-            ng = xyz(P[1]);
-            mat = as_int(P[0].w);
-        } else {
-            ng = box_normal(P, p.o, p.d, rcp3(p.d));
-            mat = as_int(P[0].w);
-        }
+        ng = box_normal(P, p.o, p.d, rcp3(p.d));
+        mat = as_int(P[0].w);
     }
     if (kShared && ((V->mats >> mat) & 1u)) {  // every render from here (state: this vertex)
         p.seg = (p.seg == 0u ? open_group<false>(*V, p) : p.seg) | kSegAll;
@@ -1006,7 +954,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
     const int mtype = as_int(m0.w);
     const float3 emission = xyz(m1);
     float3 albedo = xyz(m0);
-    if (mat == S.tex_mat && h.type == kQuad) albedo = tex_albedo(S, prim_rec<kGroup>(S, h.slot, gl), pt);
+    if (mat == S.tex_mat && h.type == kQuad) albedo = tex_albedo(S, P, pt);
     if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f) {
         if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, emission, mat);
         p.L = p.L + p.beta * emission;
@@ -1023,12 +971,13 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
             int li = int((((w1.x >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
             li = min(li, S.n_lights - 1);
             const int4 lt = S.light[li];
+            const float4* LP = prim_rec<kGroup>(S, lt.y, gl);
             const float lu = u01(w0.x), lv = u01(w0.y);
             float3 yl, ny;
             if (lt.x == kQuad) {
-                const float3 uu = xyz(prim_row<kGroup>(S, lt.y, 2, gl)), vv = xyz(prim_row<kGroup>(S, lt.y, 3, gl));
-                yl = xyz(prim_row<kGroup>(S, lt.y, 0, gl)) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
-                ny = xyz(prim_row<kGroup>(S, lt.y, 1, gl));
+                const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
+                yl = xyz(LP[0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
+                ny = xyz(LP[1]);
             } else {
                 const float z = 1.0f - 2.0f * lu;
                 const float rr2 = fmaxf(0.0f, 1.0f - z * z);
@@ -1036,8 +985,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
                 float sp, cp;
                 sincospif(2.0f * lv, &sp, &cp);
                 ny = f3(rr_ * cp, rr_ * sp, z);
-                const float4 c = prim_row<kGroup>(S, lt.y, 0, gl);
-                yl = xyz(c) + ny * c.w;
+                yl = xyz(LP[0]) + ny * LP[0].w;
             }
             const float3 dv = yl - po;
             const float dist2 = dot3(dv, dv);
@@ -1048,7 +996,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
                 const float dist = dist2 * inv_dist;
                 bool blocked;
                 if constexpr (kGroup)
-                    blocked = occluded<kCount, true>(S, po, wi, dist, lt.y, cnt, gl->lay->prims) ||
+                    blocked = occluded<kCount, true>(S, po, wi, dist, lt.y, cnt, gl->prims) ||
                               group_occluded<kCount>(S, *gl, po, wi, dist, lt.y, cnt);
                 else
                     blocked = occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u);
@@ -1621,7 +1569,6 @@ __device__ __forceinline__ void stage_group_scene(GroupScene& S, const TraceJob&
 struct GroupSmem {
     GroupScene scene;  // the invariant part (render g G's records of the other primitives)
     TraceJob job;
-    GroupLayout lay;   // the rows of the table
     float4 tab[kGroupTab];
     double pair[5][32];  // each lane's pairwise-sum stack (touched once per pixel)
     unsigned long long acc[3][32];  // each lane's radiance sums of the current pixel, 2^-32 fixed point
@@ -1693,38 +1640,20 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
             if (lane == 0) atomicOr(L.status, kStatusBadItem);
             break;
         }
-        if (g != cur_item_g) {  // stage render g G's scene and the group's per-render rows
+        if (g != cur_item_g) {  // stage render g G's scene and the group's per-render records
             stage_group_scene(W.scene, J, g * G, lane);
-            if (lane == 0) {  // the row layout (see GroupLayout)
-                GroupLayout& L = W.lay;
-                L.prims = J.var_prims;
-                L.mats = J.var_mats;
-                int off = 0, k = 0;
-                for (unsigned m = J.var_prims; m; m &= m - 1u, ++k) {
-                    const int slot = __ffs(m) - 1;
-                    const int rows = slot < W.scene.n_sph ? J.grows_sphere : (slot < W.scene.n_sph + W.scene.n_quad ? 1 : 2);
-                    L.off[k] = off;
-                    L.rows[k] = rows;
-                    off += rows;
-                }
-                L.mat_off = off;
-                off += __popc(J.var_mats);
-                L.area_off = off < stride ? off : -1;
-            }
-            __syncwarp();
+            const int n = J.n_var, nm = __popc(J.var_mats);
             for (int i = lane; i < G * stride; i += 32) {
                 const int gi = i / stride, q = i - gi * stride;
                 const InstScene& R = J.scenes[g * G + gi];
-                const GroupLayout& L = W.lay;
                 float4 v;
-                if (q < L.mat_off) {  // a row of a perturbed primitive's record
-                    int k = 0;
-                    while (q >= L.off[k] + L.rows[k]) ++k;
-                    v = __ldg(&R.prim[nth_set_bit(L.prims, k)][q - L.off[k]]);
-                } else if (q < L.mat_off + __popc(L.mats)) {  // albedo row of a bound material
-                    v = __ldg(&R.mat[nth_set_bit(L.mats, q - L.mat_off)][0]);
+                if (q < 4 * n) {  // record of the (q / 4)-th perturbed primitive
+                    const int slot = nth_set_bit(J.var_prims, q >> 2);
+                    v = __ldg(&R.prim[slot][q & 3]);
+                } else if (q < 4 * n + nm) {  // albedo row of a bound material
+                    v = __ldg(&R.mat[nth_set_bit(J.var_mats, q - 4 * n)][0]);
                 } else {  // emitter areas
-                    v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - L.area_off));
+                    v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n - nm));
                 }
                 W.tab[i] = v;
             }
@@ -1732,7 +1661,8 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
             cur_item_g = g;
         }
         const int gi = lane % G, ks = lane / G, nsg = 32 / G;  // render in group, sample group, groups
-        const GroupLane gl{W.tab + gi * stride, &W.lay};
+        const GroupLane gl{W.tab + gi * stride, J.var_prims, J.var_mats, J.n_var,
+                           stride > 4 * J.n_var + __popc(J.var_mats) ? 1 : 0};
         const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
         const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
         const int npx = vw * vh;
