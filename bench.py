@@ -357,14 +357,14 @@ def main():
     tuned = None
     if args.block_pixels:
         shape = {"block_pixels": args.block_pixels, "ctas_per_sm": 0, "render_groups": args.render_groups,
-                 "source": "--block-pixels"}
+                 "no_path_sharing": 0, "source": "--block-pixels"}
     else:
         tuned = autotune.autotune(scene, wl, target_host)
         shape = {"block_pixels": tuned["block_pixels"], "ctas_per_sm": tuned["ctas_per_sm"],
-                 "render_groups": tuned.get("render_groups", 0),
+                 "render_groups": tuned.get("render_groups", 0), "no_path_sharing": tuned.get("no_path_sharing", 0),
                  "source": "autotuner (cached)" if tuned["cached"] else "autotuner"}
     job = api.Job(scene, wl, target_host, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"],
-                  render_groups=shape["render_groups"], use_tuned=False)
+                  render_groups=shape["render_groups"], no_path_sharing=shape["no_path_sharing"], use_tuned=False)
     stream = torch.cuda.current_stream()
     # warm-up: at least W steps and at least one second of device work (clocks ramp up
     # under sustained load; a few short steps after start-up run slow)
@@ -451,7 +451,7 @@ def main():
     h2d = 4 * (npx4 + 4 * D + 1)  # target; sigma, Adam's step, theta, m, v in one staged copy
     d2h = 4 * (4 * D + R)  # theta, m, v, gradient, losses in one copy
     opts = scene.grad_opts(wl, step=0, block_pixels=shape["block_pixels"], ctas_per_sm=shape["ctas_per_sm"],
-                           render_groups=shape["render_groups"])
+                           render_groups=shape["render_groups"], no_path_sharing=shape["no_path_sharing"])
 
     def e2e_step(k):
         opts.step = k
@@ -480,7 +480,8 @@ def main():
         value = world * 1000.0 / step_ms
         traffic = _profiled(wl.name, "dram_bytes_per_step")
         kernels = ("render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue, k_finalize)"
-                   if sharing else ("render-group kernel k_trace_group + k_finalize" if shape["render_groups"] >= 0
+                   if sharing else ("render-group kernel k_trace_group + k_finalize"
+                                    if shape["render_groups"] >= 0 and wl.crn and wl.D <= 64
                                     else "render kernel k_trace + k_finalize"))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -537,7 +538,8 @@ def main():
             issue["source"] = "warp instructions per step from the committed ncu summary; times from this run"
         line["issue_rate"] = issue
         if tuned is not None:
-            line["autotune"] = {"choice": {"block_pixels": tuned["block_pixels"], "ctas_per_sm": tuned["ctas_per_sm"]},
+            line["autotune"] = {"choice": {k: tuned.get(k) for k in ("block_pixels", "ctas_per_sm", "render_groups",
+                                                                     "no_path_sharing")},
                                 "cached": tuned["cached"], "ms": tuned.get("ms"),
                                 "tried": tuned.get("tried")}
         if world == 1 and args.serving_jobs > 0:

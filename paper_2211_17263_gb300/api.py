@@ -201,15 +201,17 @@ class Job:
             if self._target.shape != (wl.height, wl.width, 4):
                 raise ValueError("target must be [H, W, 4] float32")
         self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm,
-                             "render_groups": render_groups, "source": "given"}
-        if use_tuned and block_pixels == 0 and ctas_per_sm == 0 and render_groups == 0:
+                             "render_groups": render_groups, "no_path_sharing": no_path_sharing, "source": "given"}
+        if use_tuned and block_pixels == 0 and ctas_per_sm == 0 and render_groups == 0 and no_path_sharing == 0:
             from . import autotune
             hit = autotune.cached_shape(wl)
             if hit is not None:
                 block_pixels, ctas_per_sm = hit["block_pixels"], hit["ctas_per_sm"]
                 render_groups = hit.get("render_groups", 0)
+                no_path_sharing = hit.get("no_path_sharing", 0)
                 self.launch_shape = {"block_pixels": block_pixels, "ctas_per_sm": ctas_per_sm,
-                                     "render_groups": render_groups, "source": "autotuner cache"}
+                                     "render_groups": render_groups, "no_path_sharing": no_path_sharing,
+                                     "source": "autotuner cache"}
             else:
                 self.launch_shape["source"] = "library default"
         desc = capi.prdpt_job_desc(

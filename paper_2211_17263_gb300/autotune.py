@@ -1,14 +1,16 @@
 """Autotuner for the render kernel's launch shape.
 
-Candidates are (pixels per warp work item, resident CTAs per SM, render groups): the
-block of pixels a warp traces as one work item, how many 256-thread CTAs the persistent
-grid keeps per SM (the number of live warps), and whether renders are traced side by side
-in one warp (render_groups = 0: automatic group size; -1: one render per work item). Each
+Candidates are (pixels per warp work item, resident CTAs per SM, render groups, path
+sharing): the block of pixels a warp traces as one work item, how many 256-thread CTAs the
+persistent grid keeps per SM (the number of live warps), whether renders are traced side
+by side in one warp (render_groups = 0: automatic group size; -1: one render per work
+item), and whether paths that no perturbation can reach are traced once for all renders
+(no_path_sharing = 0, where the job allows it) or every render traces its own. Each
 candidate is timed with CUDA events on the render launches of a throwaway resident job of
 the same shape; the fastest is cached in a JSON file keyed by the shape, so later jobs of
 that shape start from the tuned launch (api.Job looks it up when given no shape). The CTA
-count and the render grouping never change results; the block shape regroups the FP64
-sums of per-block partials (results agree to rounding).
+count, the render grouping and path sharing never change results; the block shape
+regroups the FP64 sums of per-block partials (results agree to rounding).
 """
 from __future__ import annotations
 
@@ -26,7 +28,9 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "prdpt_gb300", "
 def default_cache() -> str:
     """The cache file: $PRDPT_AUTOTUNE_CACHE if set, else DEFAULT_CACHE."""
     return os.environ.get("PRDPT_AUTOTUNE_CACHE") or DEFAULT_CACHE
-CANDIDATES = [(px, cps, rg) for px in (32, 16, 8) for cps in (3, 2) for rg in (0, -1)]
+# (block pixels, CTAs per SM, render groups, no path sharing); with sharing allowed, render
+# groups apply only to jobs that cannot share paths
+CANDIDATES = [(px, cps, rg, nps) for px in (32, 16, 8) for cps in (3, 2) for rg, nps in ((0, 0), (-1, 0), (0, 1))]
 _lock = threading.Lock()
 
 
@@ -67,11 +71,11 @@ def cached_shape(wl, cache_path: str | None = ""):
 
 
 def time_candidate(scene: api.Scene, wl, target_host: np.ndarray, block_pixels: int, ctas_per_sm: int,
-                   steps: int = 3, render_groups: int = 0) -> float:
+                   steps: int = 3, render_groups: int = 0, no_path_sharing: int = 0) -> float:
     """Mean render-kernel time (ms) of `steps` resident steps with this launch shape."""
     ctx = scene.ctx
     job = api.Job(scene, wl, target_host, block_pixels=block_pixels, ctas_per_sm=ctas_per_sm,
-                  render_groups=render_groups, use_tuned=False)
+                  render_groups=render_groups, no_path_sharing=no_path_sharing, use_tuned=False)
     try:
         job.step()  # warm-up
         ctx.sync()
@@ -98,12 +102,14 @@ def autotune(scene: api.Scene, wl, target_host: np.ndarray, cache_path: str | No
         if hit:
             return dict(hit, cached=True)
     results = []
-    for px, cps, rg in (candidates or CANDIDATES):
-        ms = time_candidate(scene, wl, target_host, px, cps, steps, rg)
-        results.append({"block_pixels": px, "ctas_per_sm": cps, "render_groups": rg, "ms": ms})
+    for px, cps, rg, nps in (candidates or CANDIDATES):
+        ms = time_candidate(scene, wl, target_host, px, cps, steps, rg, nps)
+        results.append({"block_pixels": px, "ctas_per_sm": cps, "render_groups": rg, "no_path_sharing": nps,
+                        "ms": ms})
     best = min(results, key=lambda r: r["ms"])
     entry = {"block_pixels": best["block_pixels"], "ctas_per_sm": best["ctas_per_sm"],
-             "render_groups": best["render_groups"], "ms": best["ms"], "tried": results}
+             "render_groups": best["render_groups"], "no_path_sharing": best["no_path_sharing"], "ms": best["ms"],
+             "tried": results}
     if cache_path:
         with _lock:
             table = _load(cache_path)

@@ -172,7 +172,7 @@ def test_autotune_picks_and_caches(gpu_lib, tmp_path, monkeypatch):
         default = api.Job(scene, wl, target)  # empty cache: the library's default shape
         assert default.launch_shape["source"] == "library default"
         best = autotune(scene, wl, target, steps=2)
-        assert (best["block_pixels"], best["ctas_per_sm"], best["render_groups"]) in CANDIDATES
+        assert (best["block_pixels"], best["ctas_per_sm"], best["render_groups"], best["no_path_sharing"]) in CANDIDATES
         assert not best["cached"]
         again = autotune(scene, wl, target)
         assert again["cached"] and again["block_pixels"] == best["block_pixels"]
@@ -182,7 +182,8 @@ def test_autotune_picks_and_caches(gpu_lib, tmp_path, monkeypatch):
         assert tuned.launch_shape["source"] == "autotuner cache"
         assert tuned.launch_shape["block_pixels"] == best["block_pixels"]
         explicit = api.Job(scene, wl, target, block_pixels=best["block_pixels"], ctas_per_sm=best["ctas_per_sm"],
-                           render_groups=best["render_groups"], use_tuned=False)
+                           render_groups=best["render_groups"], no_path_sharing=best["no_path_sharing"],
+                           use_tuned=False)
         for j in (tuned, explicit, default):
             for _ in range(2):
                 j.step()
