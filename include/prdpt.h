@@ -240,10 +240,11 @@ prdpt_status prdpt_adam_step(prdpt_ctx* ctx, int32_t D, float* theta_dev, float*
 
 /* Create a resident job on a scene: copies theta0, sigma0, the target (target_host may be
  * NULL: then the target starts at zero and is rendered on the device by
- * prdpt_job_render_target) and the scene into library-owned device memory, charged to the
- * HBM budget. The block may be one a released job or scene left behind (see
- * prdpt_job_release). Synchronous, but the uploads run on a stream of the context's own
- * that waits for no other work on the device. */
+ * prdpt_job_render_target) and the scene into a block of the context's arena (see
+ * prdpt_job_release): chunks of 256 MB are reserved from the device while the HBM budget
+ * leaves room for four, else exactly what a block needs, and charged to the budget whole.
+ * Synchronous, but the uploads run on a stream of the context's own that waits for no
+ * other work on the device. */
 prdpt_status prdpt_job_create(prdpt_ctx* ctx, int32_t scene_id, const prdpt_job_desc* desc, int32_t* job_out);
 
 /* One optimisation step of a resident job, all on the device: draw perturbations,
@@ -264,12 +265,12 @@ prdpt_status prdpt_step_batch(prdpt_ctx* ctx, const int32_t* job_ids, int32_t n,
 prdpt_status prdpt_job_read(prdpt_ctx* ctx, int32_t job_id, float* theta_host, float* grad_host,
                             float* losses_host, int32_t* steps_host);
 
-/* Release a job. Does not wait for the device: the job's block is kept by the context
- * and reused (by a later prdpt_job_create or prdpt_scene_upload of a fitting size) only
- * once the job's last enqueued work has completed; blocks are returned to the device
- * when an allocation would otherwise exceed the budget or the device. A job stepped
- * inside a CUDA-graph capture waits for the device here (replays are not tracked); such a
- * graph must not be replayed after the release. */
+/* Release a job. Does not wait for the device: the job's block returns to the context's
+ * arena (device memory the context reserves in chunks and carves into job and scene
+ * blocks) once the job's last enqueued work has completed, and is carved again by later
+ * prdpt_job_create and prdpt_scene_upload calls. The arena's chunks are returned to the
+ * device by prdpt_destroy. A job stepped inside a CUDA-graph capture waits for the device
+ * here (replays are not tracked); such a graph must not be replayed after the release. */
 prdpt_status prdpt_job_release(prdpt_ctx* ctx, int32_t job_id);
 
 /* Render the target image of a job (Sec. 4.1: the target is a render at the reference
@@ -301,8 +302,8 @@ prdpt_status prdpt_counters_read(prdpt_ctx* ctx, uint64_t* counts_host);
 prdpt_status prdpt_kernel_timing_enable(prdpt_ctx* ctx, int32_t enable);
 prdpt_status prdpt_kernel_timing_read(prdpt_ctx* ctx, double* total_ms, int64_t* launches);
 
-/* Device memory the context currently holds (scenes, jobs, scratch, and released job and
- * scene blocks kept for reuse), in bytes. */
+/* Device memory the context currently holds (its arena's chunks, free space included,
+ * and the scratch of the stateless calls), in bytes. */
 prdpt_status prdpt_memory_used(prdpt_ctx* ctx, uint64_t* bytes_out);
 
 /* FP32 issue-rate probe (a measurement utility; the paper has no counterpart): one

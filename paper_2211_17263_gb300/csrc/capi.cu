@@ -145,16 +145,28 @@ struct prdpt_ctx {
     size_t h_desc_n = 0;
     cudaEvent_t h_desc_ev[2] = {nullptr, nullptr};
     int desc_slot = 0;
-    // released job and scene blocks kept for reuse (cudaFree would synchronise the device):
-    // a block is reused once the event recorded after its last use has completed
-    struct Cached {
-        void* p;
+    // Device memory of jobs and scenes: chunks reserved from the device (within the budget)
+    // and carved into blocks first-fit. A released block returns to its chunk's free ranges
+    // once the event recorded after its last use has completed. Reserving and returning
+    // device memory can wait for the device, so after warm-up, admitting and releasing jobs
+    // calls neither cudaMalloc nor cudaFree.
+    struct Chunk {
+        char* base;
         size_t bytes;
+        std::map<size_t, size_t> free;  // offset -> length, coalesced
+    };
+    struct Block {
+        int chunk;
+        size_t off, len;
+    };
+    struct Pending {
+        void* p;
         cudaEvent_t ready;  // null: idle already
     };
-    std::vector<Cached> cache;
-    size_t cached_bytes = 0;
-    std::vector<cudaEvent_t> ev_pool;  // unrecorded events for jobs and scenes
+    std::vector<Chunk> chunks;
+    std::map<void*, Block> blocks;       // blocks in use or pending
+    std::vector<Pending> pending;        // released, last use possibly still in flight
+    std::vector<cudaEvent_t> ev_pool;    // unrecorded events for jobs and scenes
     cudaStream_t io = nullptr;  // non-blocking stream of the synchronous uploads and reads
     std::mutex mu;
 };
@@ -239,57 +251,96 @@ bool event_done(cudaEvent_t e) {
     return true;
 }
 
-// Free every cached block whose last use has completed (cudaFree synchronises the device;
-// this runs only when an allocation would not fit otherwise).
-void trim_cache(prdpt_ctx* c) {
-    std::vector<prdpt_ctx::Cached> keep;
-    for (auto& b : c->cache) {
-        if (event_done(b.ready)) {
-            if (b.ready) c->ev_pool.push_back(b.ready);
-            c->cached_bytes -= b.bytes;
-            dev_free(c, b.p);
-        } else {
-            keep.push_back(b);
+constexpr size_t kChunkBytes = size_t(256) << 20;
+
+// Return a block's range to its chunk, merging it with free neighbours.
+void arena_free(prdpt_ctx* c, void* p) {
+    auto it = c->blocks.find(p);
+    if (it == c->blocks.end()) return;
+    const prdpt_ctx::Block b = it->second;
+    c->blocks.erase(it);
+    auto& fr = c->chunks[b.chunk].free;
+    size_t off = b.off, len = b.len;
+    auto nx = fr.lower_bound(off);
+    if (nx != fr.begin()) {
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == off) {
+            off = pv->first;
+            len += pv->second;
+            fr.erase(pv);
         }
     }
-    c->cache.swap(keep);
+    if (nx != fr.end() && off + len == nx->first) {
+        len += nx->second;
+        fr.erase(nx);
+    }
+    fr[off] = len;
 }
 
-// A job or scene block: a cached block of 1..2x the size whose last use has completed,
-// else a new allocation (after trimming the cache if the budget or the device is full).
+// Free the released blocks whose last use has completed (all of them with `wait`).
+void arena_collect(prdpt_ctx* c, bool wait) {
+    std::vector<prdpt_ctx::Pending> keep;
+    for (auto& q : c->pending) {
+        if (wait && q.ready) cudaEventSynchronize(q.ready);
+        if (event_done(q.ready)) {
+            if (q.ready) c->ev_pool.push_back(q.ready);
+            arena_free(c, q.p);
+        } else {
+            keep.push_back(q);
+        }
+    }
+    c->pending.swap(keep);
+}
+
+// First fit over the chunks' free ranges.
+void* arena_take(prdpt_ctx* c, size_t bytes) {
+    for (int k = 0; k < (int)c->chunks.size(); ++k) {
+        auto& fr = c->chunks[k].free;
+        for (auto it = fr.begin(); it != fr.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, rest = it->second - bytes;
+            fr.erase(it);
+            if (rest) fr[off + bytes] = rest;
+            void* p = c->chunks[k].base + off;
+            c->blocks[p] = {k, off, bytes};
+            return p;
+        }
+    }
+    return nullptr;
+}
+
+// A job or scene block from the arena. A new chunk is reserved when no free range fits: 256
+// MB while the budget leaves room for four, else exactly the request; if the budget or the
+// device refuses, the blocks still in flight are waited for and the search repeated.
 prdpt_status block_alloc(prdpt_ctx* c, void** p, size_t bytes) {
     bytes = (bytes + 255) & ~size_t(255);
-    int best = -1;
-    for (int i = 0; i < (int)c->cache.size(); ++i) {
-        const auto& b = c->cache[i];
-        if (b.bytes < bytes || b.bytes > 2 * bytes) continue;
-        if (best >= 0 && b.bytes >= c->cache[best].bytes) continue;
-        if (!event_done(b.ready)) continue;
-        best = i;
+    arena_collect(c, false);
+    if ((*p = arena_take(c, bytes))) return PRDPT_OK;
+    const bool roomy = !c->budget || (c->budget > c->used && c->budget - c->used >= 4 * kChunkBytes);
+    const size_t chunk = roomy ? std::max(bytes, kChunkBytes) : bytes;
+    void* base = nullptr;
+    prdpt_status st = dev_alloc(c, &base, chunk);
+    if (st != PRDPT_OK && !c->pending.empty()) {
+        arena_collect(c, true);
+        if ((*p = arena_take(c, bytes))) {
+            g_err = "no error";
+            return PRDPT_OK;
+        }
+        st = dev_alloc(c, &base, chunk);
     }
-    if (best >= 0) {
-        prdpt_ctx::Cached b = c->cache[best];
-        c->cache.erase(c->cache.begin() + best);
-        c->cached_bytes -= b.bytes;
-        if (b.ready) c->ev_pool.push_back(b.ready);
-        *p = b.p;
-        return PRDPT_OK;
-    }
-    prdpt_status st = dev_alloc(c, p, bytes);
-    if (st != PRDPT_OK && !c->cache.empty()) {
-        trim_cache(c);
-        st = dev_alloc(c, p, bytes);
-    }
-    return st;
+    if (st != PRDPT_OK) return st;
+    prdpt_ctx::Chunk ch{static_cast<char*>(base), chunk, {}};
+    ch.free[0] = chunk;
+    c->chunks.push_back(ch);
+    *p = arena_take(c, bytes);
+    return PRDPT_OK;
 }
 
-// Keep a released block for reuse; `ready` (owned by the cache from now on, may be null)
-// completes when the block's last use has.
+// Release a block; `ready` (owned by the arena from now on, may be null) completes when the
+// block's last use has.
 void block_release(prdpt_ctx* c, void* p, cudaEvent_t ready) {
-    auto it = c->allocs.find(p);
-    if (it == c->allocs.end()) return;
-    c->cache.push_back({p, it->second, ready});
-    c->cached_bytes += it->second;
+    if (!c->blocks.count(p)) return;
+    c->pending.push_back({p, ready});
 }
 
 bool is_emissive(const float* mp) { return mp[3] > 0.f || mp[4] > 0.f || mp[5] > 0.f; }
@@ -504,8 +555,8 @@ prdpt_status prdpt_destroy(prdpt_ctx* c) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
     }
-    for (auto& b : c->cache)
-        if (b.ready) cudaEventDestroy(b.ready);
+    for (auto& q : c->pending)
+        if (q.ready) cudaEventDestroy(q.ready);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (Scene* s : c->scenes)
         if (s) {

@@ -74,7 +74,9 @@ def test_budget_limits_admission(gpu_lib):
     from paper_2211_17263_gb300 import api, capi
     from paper_2211_17263_gb300.serve import Server, admit_job
     arrivals = [(0.0, a[1]) for a in _mix()]
-    probe = api.Context(0)  # measure what each job holds, then allow roughly two at a time
+    # measure what each job holds (a budget this small makes the context reserve exactly
+    # what each block needs), then allow roughly two at a time
+    probe = api.Context(0, hbm_budget_bytes=512 << 20)
     try:
         sizes = []
         side = torch.cuda.Stream()
@@ -125,8 +127,9 @@ def test_device_rendered_target_equals_host_target(gpu_lib):
 
 
 def test_released_blocks_are_reused(gpu_lib):
-    """A released job's block is kept and handed to the next job of a fitting size once its
-    work has completed (no new device memory); the new job's results are unaffected."""
+    """A released job's block returns to the context's arena once its work has completed and
+    is carved again for the next job (no new device memory); the new job's results are
+    unaffected."""
     from paper_2211_17263_gb300 import api
     wl = workloads.scaled(workloads.config_occlusion(seed=5), width=48, height=40, spp=2, pairs=2)
     ref = api.Context(0)
