@@ -179,7 +179,10 @@ prdpt_status dev_alloc(prdpt_ctx* c, void** p, size_t bytes) {
         return fail(PRDPT_E_OUT_OF_BUDGET, "allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget (" +
                                                std::to_string(c->used) + " of " + std::to_string(c->budget) + " used)");
     cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) return fail(PRDPT_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // an out-of-memory result is not sticky: keep it from later launch checks
+        return fail(PRDPT_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
     c->allocs[*p] = bytes;
     c->used += bytes;
     return PRDPT_OK;
@@ -309,15 +312,32 @@ void* arena_take(prdpt_ctx* c, size_t bytes) {
     return nullptr;
 }
 
+// Return the chunks that hold no block to the device (their slots stay, empty, so that the
+// blocks' chunk indices keep their meaning).
+bool arena_trim(prdpt_ctx* c) {
+    bool any = false;
+    for (auto& ch : c->chunks) {
+        if (!ch.base || ch.free.size() != 1 || ch.free.begin()->first != 0 || ch.free.begin()->second != ch.bytes)
+            continue;
+        dev_free(c, ch.base);
+        ch.base = nullptr;
+        ch.bytes = 0;
+        ch.free.clear();
+        any = true;
+    }
+    return any;
+}
+
 // A job or scene block from the arena. A new chunk is reserved when no free range fits: 256
-// MB while the budget leaves room for four, else exactly the request; if the budget or the
-// device refuses, the blocks still in flight are waited for and the search repeated.
+// MB while the budget leaves room for four, else exactly the request. If the budget or the
+// device refuses, the blocks still in flight are waited for and the search repeated, and
+// then the empty chunks are returned and an exact chunk is tried once more.
 prdpt_status block_alloc(prdpt_ctx* c, void** p, size_t bytes) {
     bytes = (bytes + 255) & ~size_t(255);
     arena_collect(c, false);
     if ((*p = arena_take(c, bytes))) return PRDPT_OK;
     const bool roomy = !c->budget || (c->budget > c->used && c->budget - c->used >= 4 * kChunkBytes);
-    const size_t chunk = roomy ? std::max(bytes, kChunkBytes) : bytes;
+    size_t chunk = roomy ? std::max(bytes, kChunkBytes) : bytes;
     void* base = nullptr;
     prdpt_status st = dev_alloc(c, &base, chunk);
     if (st != PRDPT_OK && !c->pending.empty()) {
@@ -328,10 +348,17 @@ prdpt_status block_alloc(prdpt_ctx* c, void** p, size_t bytes) {
         }
         st = dev_alloc(c, &base, chunk);
     }
+    if (st != PRDPT_OK && (arena_trim(c) || chunk != bytes)) {
+        chunk = bytes;
+        st = dev_alloc(c, &base, chunk);
+    }
     if (st != PRDPT_OK) return st;
-    prdpt_ctx::Chunk ch{static_cast<char*>(base), chunk, {}};
-    ch.free[0] = chunk;
-    c->chunks.push_back(ch);
+    g_err = "no error";
+    int k = 0;
+    while (k < (int)c->chunks.size() && c->chunks[k].base) ++k;
+    if (k == (int)c->chunks.size()) c->chunks.push_back({});
+    c->chunks[k] = prdpt_ctx::Chunk{static_cast<char*>(base), chunk, {}};
+    c->chunks[k].free[0] = chunk;
     *p = arena_take(c, bytes);
     return PRDPT_OK;
 }

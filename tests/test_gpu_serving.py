@@ -99,6 +99,51 @@ def test_budget_limits_admission(gpu_lib):
         ctx.close()
 
 
+def test_empty_chunks_are_returned_for_a_larger_job(gpu_lib):
+    """Under a budget too small for the arena's 256 MB chunks each block is reserved exactly.
+    When a larger job fits neither a free range nor the budget beside the released jobs'
+    chunks, the empty chunks go back to the device and the job is admitted."""
+    from paper_2211_17263_gb300 import api
+    small = workloads.scaled(workloads.config_occlusion(seed=8), width=48, height=40, spp=2, pairs=2)
+    big = workloads.scaled(workloads.config_occlusion(seed=8), width=128, height=96, spp=2, pairs=2)
+
+    def held(ctx, wl):  # bytes of the scene's and the job's exact chunks
+        before = ctx.memory_used()
+        scene = ctx.upload_scene(wl.scene, wl.bindings)
+        mid = ctx.memory_used()
+        api.Job(scene, wl, None).release()
+        return mid - before, ctx.memory_used() - mid
+
+    probe = api.Context(0, hbm_budget_bytes=512 << 20)
+    try:
+        base = probe.memory_used()
+        s_scene, s_small = held(probe, small)
+        _, s_big = held(probe, big)  # the big scene is carved from the released small job's chunk
+    finally:
+        probe.close()
+    assert s_big > s_small > 64 * 1024
+    budget = base + s_scene + s_small + s_big + 64 * 1024  # slack: the context's descriptor arrays
+    ctx = api.Context(0, hbm_budget_bytes=budget)
+    try:
+        scene = ctx.upload_scene(small.scene, small.bindings)
+        th = torch.as_tensor(np.ascontiguousarray(small.theta_ref, np.float32), device="cuda")
+        a, b = api.Job(scene, small, None), api.Job(scene, small, None)
+        for j in (a, b):
+            j.render_target(th)
+            j.step()
+        a.release()
+        b.release()
+        torch.cuda.synchronize()
+        c = api.Job(scene, big, None)  # refused by the budget unless the two chunks are returned
+        c.render_target(th)
+        c.step()
+        assert c.read()["steps"] == 1
+        assert ctx.memory_used() <= budget
+        c.release()
+    finally:
+        ctx.close()
+
+
 def test_device_rendered_target_equals_host_target(gpu_lib):
     """prdpt_job_render_target renders the same target as prdpt_render_batch: the job's
     trajectory is bit-identical to a job given that image from the host."""
