@@ -163,6 +163,18 @@ def _profiled(workload_name, key):
         return None
 
 
+def _emitter_bound(wl):
+    """Does a position or radius binding move an emitter (the emitter-sharing mode's jobs;
+    geometry-only jobs share paths through the shared-pass pipeline)?"""
+    import workloads
+    sc = wl.scene
+    for kind, idx, _ in np.asarray(wl.bindings):
+        if kind in (workloads.BIND_PRIM_POS, workloads.BIND_SPHERE_RADIUS):
+            if np.any(sc.mat_param[sc.prim_mat[idx], 3:6] > 0):
+                return True
+    return False
+
+
 CPU_SAMPLE_MAX_PATHS = 40_000_000  # larger steps are sampled (one pair, 4 spp) and scaled
 
 
@@ -479,10 +491,14 @@ def main():
         achieved = flops_step / (trace_avg_ms * 1e-3) / 1e12
         value = world * 1000.0 / step_ms
         traffic = _profiled(wl.name, "dram_bytes_per_step")
-        kernels = ("render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue, k_finalize)"
-                   if sharing else ("render-group kernel k_trace_group + k_finalize"
-                                    if shape["render_groups"] >= 0 and wl.crn and wl.D <= 64
-                                    else "render kernel k_trace + k_finalize"))
+        if sharing and _emitter_bound(wl):
+            kernels = "emitter-sharing kernel k_trace_emit + k_finalize"
+        elif sharing:
+            kernels = "render pipeline (k_trace shared pass, k_trace_affected, k_shared_epilogue, k_finalize)"
+        elif shape["render_groups"] >= 0 and wl.crn and wl.D <= 64:
+            kernels = "render-group kernel k_trace_group + k_finalize"
+        else:
+            kernels = "render kernel k_trace + k_finalize"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

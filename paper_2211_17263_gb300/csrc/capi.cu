@@ -81,7 +81,7 @@ struct Job {
 struct prdpt_ctx {
     int device = 0;
     int sms = 0;
-    int occ_grad = 1, occ_render = 1, occ_diff = 1, occ_group = 1;
+    int occ_grad = 1, occ_render = 1, occ_diff = 1, occ_group = 1, occ_emit = 1;
     uint64_t budget = 0, used = 0;
     std::map<void*, size_t> allocs;
     std::vector<Scene*> scenes;
@@ -103,7 +103,7 @@ struct prdpt_ctx {
     size_t s_partials_n = 0;
     double* s_losses = nullptr;
     size_t s_losses_n = 0;
-    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2..3] batch queues, [4..7] sharing
+    unsigned* s_ctl = nullptr;    // [0] queue, [1] done counter, [2..3], [8], [9] batch queues, [4..7] sharing
                                   // counters, [8] third batch queue (16 words)
     unsigned long long* s_share = nullptr;  // path sharing: [tiles][96] shared radiance
     size_t s_share_n = 0;
@@ -135,7 +135,7 @@ struct prdpt_ctx {
     int batch_blocks = 0;
     // the packed arrays hold the path-sharing jobs, then the render-group jobs, then the
     // per-render ones: jobs and work items of each kind (one render launch per kind)
-    int batch_jobs[3] = {0, 0, 0}, batch_items[3] = {0, 0, 0};
+    int batch_jobs[4] = {0, 0, 0, 0}, batch_items[4] = {0, 0, 0, 0};
     // optional CUDA-event timing of the render kernel, recorded on its launch stream
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -454,10 +454,18 @@ int grid_for_group(prdpt_ctx* c, int items, int ctas_per_sm) {
     return need < cap ? need : cap;
 }
 
-// Work items of a gradient job's render launch: pixel blocks (path sharing), (block, group
-// of gsize renders) (render-group mode) or (render, block).
+// Persistent grid of the emitter-sharing kernel: one work item per CTA of kGroupBlock threads
+// (ctas_per_sm counts 256-thread CTAs, as above).
+int grid_for_emit(prdpt_ctx* c, int items, int ctas_per_sm) {
+    const int per_sm = (ctas_per_sm > 0 && 2 * ctas_per_sm < c->occ_emit) ? 2 * ctas_per_sm : c->occ_emit;
+    const int cap = c->sms * per_sm;
+    return items < cap ? items : cap;
+}
+
+// Work items of a gradient job's render launch: pixel blocks (path sharing, emitter sharing),
+// (block, group of gsize renders) (render-group mode) or (render, block).
 long long job_items(const TraceJob& J) {
-    if (J.share) return J.tiles;
+    if (J.share || J.emit) return J.tiles;
     if (J.gsize > 0) return (long long)J.tiles * (J.R / J.gsize);
     return (long long)J.R * J.tiles;
 }
@@ -485,6 +493,7 @@ cudaError_t timed_trace(prdpt_ctx* c, const TraceLaunch* Ls, int nL, const Trace
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < nL; ++i) {
         const int grid = Ls[i].diff_nd ? grid_for_diff(c, Ls[i].total_items, ctas_per_sm)
+                         : (Ls[i].group == 2 && !render) ? grid_for_emit(c, Ls[i].total_items, ctas_per_sm)
                          : (Ls[i].group && !render) ? grid_for_group(c, Ls[i].total_items, ctas_per_sm)
                                                     : grid_for(c, Ls[i].total_items, render, ctas_per_sm);
         e = launch_trace(Ls[i], render, grid, stream);
@@ -536,6 +545,7 @@ prdpt_status prdpt_create(prdpt_ctx** out, int32_t device, uint64_t hbm_budget_b
     c->occ_render = trace_blocks_per_sm(true);
     c->occ_diff = trace_diff_blocks_per_sm();
     c->occ_group = trace_group_blocks_per_sm();
+    c->occ_emit = trace_emit_blocks_per_sm();
     e = cudaStreamCreateWithFlags(&c->io, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
@@ -737,6 +747,7 @@ static void fill_share(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
 static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o) {
     J.gsize = 0;
     J.gstride = 0;
+    J.emit = 0;
     if (J.share || o->render_groups < 0 || !o->crn || o->estimator != PRDPT_ESTIMATOR_KERNEL_GRADIENT ||
         B.tex_mat >= 0 || B.n_prims > kGroupPrims || B.n_mats > kGroupMats)
         return;
@@ -756,6 +767,19 @@ static void fill_group(TraceJob& J, const BaseScene& B, const prdpt_grad_opts* o
     const int stride = 4 * n + nm + (radius ? 2 : 0);
     if (stride == 0) return;
     const int R = J.R;
+    // Emitter sharing (k_trace_emit): every emitter perturbed, no bound material, at most 64
+    // renders; paths are traced once for all renders (path sharing's switch turns it off)
+    bool emitters_perturbed = n > 0 && mats == 0u && R >= 1 && R <= 64 && R * stride <= kEmitTabRows;
+    for (int i = 0; i < B.n_prims && emitters_perturbed; ++i)
+        if (is_emissive(B.mat_param[B.prim_mat[i]]) && !((prims >> B.prim_slot[i]) & 1u)) emitters_perturbed = false;
+    if (emitters_perturbed && !o->no_path_sharing) {
+        J.emit = 1;
+        J.gstride = stride;
+        J.n_var = n;
+        J.var_prims = prims;
+        J.var_mats = 0u;
+        return;
+    }
     int G = 0;
     if (o->render_groups > 0) {
         const int g = o->render_groups;
@@ -990,11 +1014,14 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
     const int R = 2 * o->pairs, D = s->D;
     TraceJob probe{};
     if (prdpt_status st = fill_diff(probe, s->host, o)) return st;
-    fill_share(probe, s->host, o);  // path sharing: items are blocks, not (render, block)
-    const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, o->width, o->height, false);
+    probe.R = R;
+    fill_share(probe, s->host, o);  // path or emitter sharing: items are blocks, not (render, block)
+    fill_group(probe, s->host, o);
+    const bool per_block = probe.share || probe.emit;
+    const int px = choose_block(c, o->block_pixels, per_block ? 1 : R, o->width, o->height, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, o->width, o->height, &bw, &bh, &tiles_x, &tiles);
-    if (prdpt_status st = check_items(probe.share ? (long long)tiles : (long long)R * tiles)) return st;
+    if (prdpt_status st = check_items(per_block ? (long long)tiles : (long long)R * tiles)) return st;
     if (probe.share) {
         const size_t pix = (size_t)o->width * o->height;
         if (prdpt_status st = grow(c, &c->s_share, &c->s_share_n, (size_t)tiles * 96)) return st;
@@ -1097,7 +1124,7 @@ prdpt_status smoothed_grad_locked(prdpt_ctx* c, int32_t scene_id, const float* t
     TL.diff_nd = diff_slots(J);
     TL.total_items = int(job_items(J));
     TL.share = J.share;
-    TL.group = J.gsize > 0 ? 1 : 0;
+    TL.group = J.emit ? 2 : (J.gsize > 0 ? 1 : 0);
     TL.queue = c->s_ctl + 0;
     TL.counters = c->counting ? c->counters : nullptr;
     TL.status = c->status;
@@ -1265,16 +1292,19 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     PRDPT_CUDA(cudaSetDevice(c->device));
     TraceJob probe{};
     if (prdpt_status st = fill_diff(probe, s->host, o)) return st;
+    probe.R = 2 * o->pairs;
     fill_share(probe, s->host, o);
+    fill_group(probe, s->host, o);
     Job* j = new Job();
     j->scene = scene_id;
     j->D = s->D;
     j->R = 2 * o->pairs;
     const int D = j->D, R = j->R, W = o->width, H = o->height;
-    const int px = choose_block(c, o->block_pixels, probe.share ? 1 : R, W, H, false);
+    const bool per_block = probe.share || probe.emit;
+    const int px = choose_block(c, o->block_pixels, per_block ? 1 : R, W, H, false);
     int bw, bh, tiles_x, tiles;
     tiles_for(px, W, H, &bw, &bh, &tiles_x, &tiles);
-    if (prdpt_status st = check_items(probe.share ? (long long)tiles : (long long)R * tiles)) {
+    if (prdpt_status st = check_items(per_block ? (long long)tiles : (long long)R * tiles)) {
         delete j;
         return st;
     }
@@ -1524,7 +1554,7 @@ prdpt_status prdpt_step(prdpt_ctx* c, int32_t job_id, void* stream) {
     TL.job0 = j->trace;
     TL.total_items = int(job_items(j->trace));
     TL.share = j->trace.share;
-    TL.group = j->trace.gsize > 0 ? 1 : 0;
+    TL.group = j->trace.emit ? 2 : (j->trace.gsize > 0 ? 1 : 0);
     TL.diff_nd = diff_slots(j->trace);
     TL.queue = j->queue;
     TL.counters = c->counting ? c->counters : nullptr;
@@ -1555,15 +1585,17 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
             if (j->trace.diff) return fail(PRDPT_E_INVALID_ARG, "pathwise-estimator jobs step alone (prdpt_step)");
             if (j->tex) return fail(PRDPT_E_INVALID_ARG, "texture jobs step alone (prdpt_step)");
         }
-        auto kind = [](const Job* j) { return j->trace.share ? 0 : (j->trace.gsize > 0 ? 1 : 2); };
-        for (int pass = 0; pass < 3; ++pass)
+        auto kind = [](const Job* j) {
+            return j->trace.share ? 0 : (j->trace.gsize > 0 ? 1 : (j->trace.emit ? 3 : 2));
+        };
+        for (int pass = 0; pass < 4; ++pass)
             for (int i = 0; i < n; ++i) {
                 Job* j = get_job(c, ids[i]);
                 if (kind(j) == pass) order.push_back(j);
             }
         std::vector<InstJob> inst(n);
         std::vector<TraceJob> trace(n);
-        int blocks = 0, jobs_of[3] = {0, 0, 0}, items_of[3] = {0, 0, 0};
+        int blocks = 0, jobs_of[4] = {0, 0, 0, 0}, items_of[4] = {0, 0, 0, 0};
         for (int i = 0; i < n; ++i) {
             Job* j = order[i];
             const int kd = kind(j);
@@ -1624,7 +1656,7 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
         PRDPT_CUDA(cudaEventRecord(c->h_desc_ev[k], st_));
         c->batch_ids = ids;
         c->batch_blocks = blocks;
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < 4; ++q) {
             c->batch_jobs[q] = jobs_of[q];
             c->batch_items[q] = items_of[q];
         }
@@ -1636,18 +1668,19 @@ prdpt_status prdpt_step_batch(prdpt_ctx* c, const int32_t* job_ids, int32_t n, v
     IL.queue_reset = c->s_ctl + 2;
     IL.queue_reset2 = c->s_ctl + 3;
     IL.queue_reset3 = c->s_ctl + 8;
+    IL.queue_reset4 = c->s_ctl + 9;
     PRDPT_CUDA(launch_instantiate(IL, st_));
-    TraceLaunch TL[3] = {};
+    TraceLaunch TL[4] = {};
     int nL = 0, first = 0;
-    unsigned* queues[3] = {c->s_ctl + 2, c->s_ctl + 3, c->s_ctl + 8};
-    for (int kd = 0; kd < 3; ++kd) {  // path-sharing jobs, render-group jobs, per-render jobs
+    unsigned* queues[4] = {c->s_ctl + 2, c->s_ctl + 3, c->s_ctl + 8, c->s_ctl + 9};
+    for (int kd = 0; kd < 4; ++kd) {  // path-sharing, render-group, per-render, emitter-sharing jobs
         if (c->batch_jobs[kd] > 0) {
             TraceLaunch& T = TL[nL++];
             T.jobs = c->d_trace + first;
             T.njobs = c->batch_jobs[kd];
             T.total_items = c->batch_items[kd];
             T.share = kd == 0 ? 1 : 0;
-            T.group = kd == 1 ? 1 : 0;
+            T.group = kd == 1 ? 1 : (kd == 3 ? 2 : 0);
             T.queue = queues[kd];
         }
         first += c->batch_jobs[kd];

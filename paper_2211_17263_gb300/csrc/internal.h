@@ -176,6 +176,10 @@ struct TraceJob {
     // n_var perturbed primitives, the albedo rows of the bound materials, and its emitter
     // areas when a radius binding can change them)
     int gsize, gstride;
+    // Emitter-sharing mode (k_trace_emit): 1 when the job's paths are traced once for all its
+    // renders, each render adding its own next-event estimates (gstride as above; items are
+    // pixel blocks of all renders)
+    int emit;
 };
 struct TraceLaunch {
     TraceJob job0;            // used when jobs == null (single job, passed by value)
@@ -183,7 +187,8 @@ struct TraceLaunch {
     int njobs, total_items;
     int share;                // 1: every job of the launch shares paths (selects the kernel variant)
     int diff_nd;              // pathwise estimator: tangent slots of the kernel variant (0, 4 or 8)
-    int group;                // 1: every job of the launch runs in render-group mode (k_trace_group)
+    int group;                // 1: every job of the launch runs in render-group mode (k_trace_group),
+                              // 2: in emitter-sharing mode (k_trace_emit)
     int fin_total;            // packed launch: finalisation CTAs (sum of R over jobs)
     unsigned* queue;          // work-queue head, zeroed by the instantiation launch
     unsigned long long* counters;  // [8] or null (null: the uncounted kernel variant runs)
@@ -197,6 +202,7 @@ struct InstLaunch {
     unsigned* queue_reset;    // zeroed by CTA 0
     unsigned* queue_reset2;   // zeroed by CTA 0 (second queue of a packed launch), or null
     unsigned* queue_reset3;   // zeroed by CTA 0 (third queue of a packed launch), or null
+    unsigned* queue_reset4;   // zeroed by CTA 0 (fourth queue of a packed launch), or null
 };
 
 // High-dimensional parameter draws (texture scenes, D > kMaxD): norms per draw, then
@@ -262,10 +268,12 @@ cudaError_t launch_philox(unsigned long long seed, unsigned c0, unsigned c1, uns
 // kDiffBlock threads.
 int trace_blocks_per_sm(bool render_mode);
 int trace_group_blocks_per_sm();
+int trace_emit_blocks_per_sm();
 constexpr int kGroupBlock = 128;    // render-group CTAs: 4 warps (their per-warp tables fit 48 KB)
 constexpr int kGroupPrims = 16;     // render-group mode: at most 16 primitives ...
 constexpr int kGroupMats = 16;      // ... and 16 materials (the staged copy is smaller)
 constexpr int kGroupTabRows = 192;  // float4 of a warp's per-render record table (render-group mode)
+constexpr int kEmitTabRows = 256;   // float4 of a CTA's per-render record table (emitter-sharing mode)
 constexpr int kDiffBlock = 128;
 int trace_diff_blocks_per_sm();
 

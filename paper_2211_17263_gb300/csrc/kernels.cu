@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kInstBlock) k_instantiate(const InstLaunch L) 
         if (L.queue_reset) *L.queue_reset = 0u;
         if (L.queue_reset2) *L.queue_reset2 = 0u;
         if (L.queue_reset3) *L.queue_reset3 = 0u;
+        if (L.queue_reset4) *L.queue_reset4 = 0u;
     }
     if (r == 0 && tid == 0 && J.share_reset)
         for (int i = 0; i < 4; ++i) J.share_reset[i] = 0u;
@@ -582,6 +583,8 @@ struct GroupLane {
     unsigned mats;      // mask of the bound materials
     int n_var;          // perturbed primitives
     int areas;          // 1: the row holds the emitter areas
+    const uint4* rng;   // the sample group's Philox blocks: [0] jitter, [1 + 2 b + k] vertex b, slot k
+    int bpre;           // vertices b < bpre have their blocks in `rng`
 };
 
 // Record of primitive slot `slot`: the lane's own for a perturbed primitive, else the
@@ -776,6 +779,16 @@ __device__ __forceinline__ uint4 path_words(const Scn& S, unsigned pixel, int s,
     return philox(make_uint4(pixel, c1, S.step, S.c3), S.seed_lo, S.seed_hi);
 }
 
+// Block `slot` of the path's current vertex: from the render group's table while the
+// vertex is within it (the same words, drawn ahead by the group's lanes), else drawn here.
+template <bool kGroup, class Scn>
+__device__ __forceinline__ uint4 vertex_words(const Scn& S, const Path& p, int slot, const GroupLane* gl) {
+    if constexpr (kGroup) {
+        if (p.b < gl->bpre) return gl->rng[1 + 2 * p.b + slot];
+    }
+    return path_words(S, p.pixel, p.s, p.b, slot);
+}
+
 // Orthonormal basis around unit n (Duff et al. 2017).
 __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
     const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
@@ -801,12 +814,13 @@ __device__ __forceinline__ float3 tex_albedo(const Scn& S, const float4* P, floa
               fminf(fmaxf(__ldg(q + 2), 0.0f), 1.0f));
 }
 
-// Camera ray of sample s through pixel (x, y): pinhole, box-filtered jitter (slot 2).
+// Camera ray of sample s through pixel (x, y): pinhole, box-filtered jitter (slot 2). The
+// jitter block is drawn here unless the caller passes it (`pre`).
 template <class Scn>
 __device__ __forceinline__ void start_path(const Scn& S, int W, int H, int x, int y, int s, int slot,
-                                           Path& p) {
+                                           Path& p, const uint4* pre = nullptr) {
     p.pixel = unsigned(y * W + x);
-    const uint4 jw = path_words(S, p.pixel, s, 0, 2);
+    const uint4 jw = pre ? *pre : path_words(S, p.pixel, s, 0, 2);
     const float th = S.eye.w, aspect = S.fwd.w;
     const float sx = (float(2 * x - W) + 2.0f * u01(jw.x)) * __fdividef(aspect * th, float(W));
     const float sy = (float(H - 2 * y) - 2.0f * u01(jw.y)) * __fdividef(th, float(H));
@@ -901,10 +915,90 @@ __device__ __forceinline__ void tan_rr(Tangents<kND>& t, float inv_q) {
     for (int k = 0; k < kND; ++k) t.dB[k] *= inv_q;
 }
 
-template <bool kCount, bool kShared, int kND = 0, bool kGroup = false, class Scn>
+// Next-event estimation at a diffuse vertex po with shading normal ns: emitter li chosen by
+// slot 1's first word wl, a uniform point on it from slot 0's first two words (wx, wy).
+// True, with the geometry term g (cosines over squared distance, times the emitter's area
+// and count over pi) and the emitter's material, when the point is visible from po.
+template <bool kCount, bool kShared, bool kGroup, class Scn>
+__device__ __forceinline__ bool nee_visible(const Scn& S, float3 po, float3 ns, unsigned wx, unsigned wy, unsigned wl,
+                                            Counters& cnt, unsigned skip, const GroupLane* gl, float3& wi,
+                                            float& dist, float& g, int& lmat) {
+    int li = int((((wl >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
+    li = min(li, S.n_lights - 1);
+    const int4 lt = S.light[li];
+    const float4* LP = prim_rec<kGroup>(S, lt.y, gl);
+    const float lu = u01(wx), lv = u01(wy);
+    float3 yl, ny;
+    if (lt.x == kQuad) {
+        const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
+        yl = xyz(LP[0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
+        ny = xyz(LP[1]);
+    } else {
+        const float z = 1.0f - 2.0f * lu;
+        const float rr2 = fmaxf(0.0f, 1.0f - z * z);
+        const float rr_ = rr2 * rsqrtf(fmaxf(rr2, 1e-30f));
+        float sp, cp;
+        sincospif(2.0f * lv, &sp, &cp);
+        ny = f3(rr_ * cp, rr_ * sp, z);
+        yl = xyz(LP[0]) + ny * LP[0].w;
+    }
+    const float3 dv = yl - po;
+    const float dist2 = dot3(dv, dv);
+    const float inv_dist = rsqrtf(dist2);
+    wi = dv * inv_dist;
+    const float cx = dot3(ns, wi), cl = -dot3(ny, wi);
+    if (!(cx > 0.0f && cl > 0.0f)) return false;
+    dist = dist2 * inv_dist;
+    bool blocked;
+    if constexpr (kGroup)
+        blocked = occluded<kCount, true>(S, po, wi, dist, lt.y, cnt, gl->prims) ||
+                  group_occluded<kCount>(S, *gl, po, wi, dist, lt.y, cnt);
+    else
+        blocked = occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, skip);
+    if (blocked) return false;
+    g = cx * cl * (inv_dist * inv_dist) * light_area<kGroup>(S, li, gl) * float(S.n_lights) * 0.3183098861837907f;
+    lmat = lt.w;
+    return true;
+}
+
+// The radiance terms of a path: L + ba Le g (next-event estimation, ba = beta * albedo) and
+// L + beta bg (a ray that leaves the scene).
+__device__ __forceinline__ float3 nee_add(float3 L, float3 ba, float3 Le, float g) { return L + ba * Le * g; }
+__device__ __forceinline__ float3 bg_add(float3 L, float3 beta, float3 bg) { return L + beta * bg; }
+
+// Emitter-sharing mode (k_trace_emit): a path is traced once in the invariant scene for all
+// renders; its diffuse vertices are kept (up to kEmitCap) so that each render evaluates its
+// own next-event estimate there, and a path whose ray could meet a perturbed primitive (its
+// segment touches their union bounds) stops so that each render traces it on from there.
+constexpr int kEmitCap = 3;      // diffuse vertices kept per path
+constexpr int kEmitFields = 12;  // po, ns, beta * albedo, slot 0's words x, y, slot 1's word x
+struct EmitLane {
+    const float4* ulo;  // union over the renders of each perturbed primitive's bounds
+    const float4* uhi;
+    int n_var;
+    unsigned skip;      // record slots of the perturbed primitives
+    float* ent;         // the warp's kept vertices: ent[(k * kEmitFields + field) * 32 + lane]
+    int lane;
+    int n;              // vertices kept by this lane's path
+    bool miss;          // the path ended by leaving the scene
+};
+
+// Does the segment o + t d, 0 <= t <= tmax, touch a union box of the perturbed primitives?
+template <bool kCount>
+__device__ __forceinline__ bool emit_touch(const EmitLane& E, float3 o, float3 d, float tmax, Counters& cnt) {
+    const float3 inv = rcp3(d);
+    const float tm = tmax * 1.0001f + 1e-3f;
+    bool hit = false;
+    for (int k = 0; k < E.n_var; ++k) hit = hit || slab_touch(xyz(E.ulo[k]), xyz(E.uhi[k]), o, inv, tm);
+    if (kCount) cnt.box += E.n_var;
+    return hit;
+}
+
+template <bool kCount, bool kShared, int kND = 0, bool kGroup = false, bool kEmit = false, class Scn>
 __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Path& p, Counters& cnt,
                                        const VarBoxes* V = nullptr, Tangents<kND>* tn = nullptr,
-                                       const TraceJob* Jd = nullptr, const GroupLane* gl = nullptr) {
+                                       const TraceJob* Jd = nullptr, const GroupLane* gl = nullptr,
+                                       EmitLane* el = nullptr) {
     if (kShared && p.seg == 0u) {
         const int t = threadIdx.x;
         s_stash[0][t] = p.o.x;
@@ -915,7 +1009,10 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
         s_stash[5][t] = p.d.z;
     }
     Hit h;
-    if constexpr (kGroup) {  // the staged scene without the perturbed primitives, then the lane's own
+    if constexpr (kEmit) {  // the invariant scene; a ray that could meet a perturbed primitive stops here
+        h = closest_hit<kCount, true>(S, p.o, p.d, cnt, el->skip);
+        if (emit_touch<kCount>(*el, p.o, p.d, h.slot < 0 ? 3.0e38f : h.t, cnt)) return kAffected;
+    } else if constexpr (kGroup) {  // the staged scene without the perturbed primitives, then the lane's own
         h = closest_hit<kCount, true>(S, p.o, p.d, cnt, gl->prims);
         group_hit<kCount>(S, *gl, p.o, p.d, h, cnt);
     } else {
@@ -926,8 +1023,12 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
         if (p.seg & kSegAll) return kAffected;
     }
     if (h.slot < 0) {
+        if constexpr (kEmit) {
+            el->miss = true;  // the background term is added per render, after its vertex terms
+            return kEnded;
+        }
         if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, xyz(S.bg), -1);
-        p.L = p.L + p.beta * xyz(S.bg);
+        p.L = bg_add(p.L, p.beta, xyz(S.bg));
         return kEnded;
     }
     if (kCount) ++cnt.vertices;
@@ -956,6 +1057,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
     float3 albedo = xyz(m0);
     if (mat == S.tex_mat && h.type == kQuad) albedo = tex_albedo(S, P, pt);
     if (p.specular && (emission.x > 0.f || emission.y > 0.f || emission.z > 0.f) && dot3(p.d, ng) < 0.0f) {
+        if constexpr (kEmit) return kAffected;  // an invariant emitter: not in this mode's jobs
         if (kND > 0) tan_emit(*tn, *Jd, S, p.beta, emission, mat);
         p.L = p.L + p.beta * emission;
     }
@@ -965,51 +1067,31 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
     if (mtype == kDiffuse) {
         const float3 ns = dot3(ng, p.d) < 0.0f ? ng : ng * -1.0f;
         const float3 po = pt + ns * kEps;
-        const uint4 w0 = path_words(S, p.pixel, p.s, p.b, 0);
-        if (S.n_lights > 1 || rr) w1 = path_words(S, p.pixel, p.s, p.b, 1);
+        const uint4 w0 = vertex_words<kGroup>(S, p, 0, gl);
+        if (S.n_lights > 1 || rr) w1 = vertex_words<kGroup>(S, p, 1, gl);
         if (S.n_lights > 0) {  // next-event estimation: one emitter, uniform area sample
-            int li = int((((w1.x >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
-            li = min(li, S.n_lights - 1);
-            const int4 lt = S.light[li];
-            const float4* LP = prim_rec<kGroup>(S, lt.y, gl);
-            const float lu = u01(w0.x), lv = u01(w0.y);
-            float3 yl, ny;
-            if (lt.x == kQuad) {
-                const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
-                yl = xyz(LP[0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
-                ny = xyz(LP[1]);
+            if constexpr (kEmit) {  // kept for the renders' own estimates (the renders' emitters differ)
+                if (el->n == kEmitCap) return kAffected;
+                float* e = el->ent + el->n * kEmitFields * 32 + el->lane;
+                const float3 ba = p.beta * albedo;
+                e[0] = po.x; e[32] = po.y; e[64] = po.z;
+                e[96] = ns.x; e[128] = ns.y; e[160] = ns.z;
+                e[192] = ba.x; e[224] = ba.y; e[256] = ba.z;
+                e[288] = __uint_as_float(w0.x); e[320] = __uint_as_float(w0.y); e[352] = __uint_as_float(w1.x);
+                ++el->n;
             } else {
-                const float z = 1.0f - 2.0f * lu;
-                const float rr2 = fmaxf(0.0f, 1.0f - z * z);
-                const float rr_ = rr2 * rsqrtf(fmaxf(rr2, 1e-30f));
-                float sp, cp;
-                sincospif(2.0f * lv, &sp, &cp);
-                ny = f3(rr_ * cp, rr_ * sp, z);
-                yl = xyz(LP[0]) + ny * LP[0].w;
-            }
-            const float3 dv = yl - po;
-            const float dist2 = dot3(dv, dv);
-            const float inv_dist = rsqrtf(dist2);
-            const float3 wi = dv * inv_dist;
-            const float cx = dot3(ns, wi), cl = -dot3(ny, wi);
-            if (cx > 0.0f && cl > 0.0f) {
-                const float dist = dist2 * inv_dist;
-                bool blocked;
-                if constexpr (kGroup)
-                    blocked = occluded<kCount, true>(S, po, wi, dist, lt.y, cnt, gl->prims) ||
-                              group_occluded<kCount>(S, *gl, po, wi, dist, lt.y, cnt);
-                else
-                    blocked = occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, kShared ? V->skip : 0u);
-                if (!blocked) {
+                float3 wi;
+                float dist, g;
+                int lmat;
+                if (nee_visible<kCount, kShared, kGroup>(S, po, ns, w0.x, w0.y, w1.x, cnt, kShared ? V->skip : 0u, gl,
+                                                         wi, dist, g, lmat)) {
                     if (kShared) {
                         note_touch<kCount, true>(*V, po, wi, dist, p, cnt);
                         if (p.seg & kSegAll) return kAffected;
                     }
-                    const float g = cx * cl * (inv_dist * inv_dist) * light_area<kGroup>(S, li, gl) *
-                                    float(S.n_lights) * 0.3183098861837907f;
-                    const float3 Le = xyz(S.mat[lt.w][1]);
-                    if (kND > 0) tan_nee(*tn, *Jd, S, p.beta, albedo, mat, Le, lt.w, g);
-                    p.L = p.L + p.beta * albedo * Le * g;
+                    const float3 Le = xyz(S.mat[lmat][1]);
+                    if (kND > 0) tan_nee(*tn, *Jd, S, p.beta, albedo, mat, Le, lmat, g);
+                    p.L = nee_add(p.L, p.beta * albedo, Le, g);
                 }
             }
         }
@@ -1029,7 +1111,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
         p.specular = false;
     } else if (mtype == kMirror) {
         if (last) return kEnded;
-        if (rr) w1 = path_words(S, p.pixel, p.s, p.b, 1);
+        if (rr) w1 = vertex_words<kGroup>(S, p, 1, gl);
         const float3 ns = dot3(ng, p.d) < 0.0f ? ng : ng * -1.0f;
         p.d = normalized(p.d - ns * (2.0f * dot3(p.d, ns)));
         p.o = pt + ns * kEps;
@@ -1038,7 +1120,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
         p.specular = true;
     } else {  // smooth dielectric: exact unpolarised Fresnel, reflect or refract
         if (last) return kEnded;
-        w1 = path_words(S, p.pixel, p.s, p.b, 1);
+        w1 = vertex_words<kGroup>(S, p, 1, gl);
         float ci = -dot3(p.d, ng);
         float eta;
         float3 n;
@@ -1572,6 +1654,7 @@ struct GroupSmem {
     float4 tab[kGroupTab];
     double pair[5][32];  // each lane's pairwise-sum stack (touched once per pixel)
     unsigned long long acc[3][32];  // each lane's radiance sums of the current pixel, 2^-32 fixed point
+    uint4 rng[32];  // each sample group's Philox blocks of its current path (G per group)
 };
 
 #ifndef PRDPT_GROUP_MIN_BLOCKS
@@ -1661,8 +1744,13 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
             cur_item_g = g;
         }
         const int gi = lane % G, ks = lane / G, nsg = 32 / G;  // render in group, sample group, groups
+        // Under common random numbers the G renders of a path sample draw the same Philox
+        // blocks, so the group's lanes draw them ahead, one block each: the jitter and
+        // slots 0 and 1 of vertices b < bpre.
+        const int bpre = (G - 1) >> 1;
         const GroupLane gl{W.tab + gi * stride, J.var_prims, J.var_mats, J.n_var,
-                           stride > 4 * J.n_var + __popc(J.var_mats) ? 1 : 0};
+                           stride > 4 * J.n_var + __popc(J.var_mats) ? 1 : 0, W.rng + ks * G, bpre};
+        const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (ks * G);
         const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
         const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
         const int npx = vw * vh;
@@ -1679,8 +1767,13 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
                 W.acc[1][lane] = 0ull;
                 W.acc[2][lane] = 0ull;
                 for (int smp = ks; smp < J.spp; smp += nsg) {
+                    __syncwarp(gmask);  // the group's lanes are done with the previous path's blocks
+                    if (gi == 0 || gi <= 2 * bpre)
+                        W.rng[lane] = path_words(W.scene, unsigned(py * J.W + px), smp, gi == 0 ? 0 : (gi - 1) >> 1,
+                                                 gi == 0 ? 2 : (gi - 1) & 1);
+                    __syncwarp(gmask);
                     Path p;
-                    start_path(W.scene, J.W, J.H, px, py, smp, slot, p);
+                    start_path(W.scene, J.W, J.H, px, py, smp, slot, p, gl.rng);
                     if (kCount) ++cnt.paths;
                     while (advance<kCount, false, 0, true>(W.scene, J.depth, J.rr_start, p, cnt, nullptr, nullptr,
                                                           nullptr, &gl) == kLive) {
@@ -1701,6 +1794,264 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
         }
         if (ks == 0) J.partials[size_t(g * G + gi) * J.tiles + t] = part;  // a5: one partial per block
         __syncwarp();
+    }
+    if (kCount) {
+        const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
+                                          warp_sum_u(cnt.paths), warp_sum_u(cnt.vertices), warp_sum_u(cnt.shadow),
+                                          warp_sum_u(cnt.rays), 0u};
+        if (lane == 0)
+            for (int i = 0; i < kNumCounters; ++i) atomicAdd(L.counters + i, (unsigned long long)v[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_trace_emit: emitter-sharing variant of the per-render kernel (a3-a5)
+// ---------------------------------------------------------------------------
+// For a job whose perturbed primitives include every emitter and whose materials are not
+// bound (e.g. a moving light): under common random numbers the renders' paths agree until
+// one of their rays could meet a perturbed primitive, and differ before that only in the
+// next-event estimates. A work item is one pixel block of all R <= 64 renders, taken by a
+// CTA of kEmitWarps warps; warp w takes the pixel slots of positions q = 8w .. 8w + 7 of
+// the bit-reversed order. For each pixel, 32 samples at a time:
+//   phase A  lane = sample: the path is traced once in the invariant scene, keeping its
+//            diffuse vertices (EmitLane) and its end: left the scene (the background term),
+//            ended, or stopped where a ray could meet a perturbed primitive;
+//   phase B  lane = render (lane and lane + 32): for each sample of the warp, in order, the
+//            render's own next-event estimates at the kept vertices, then the background
+//            term or, for a stopped path, the rest of the path traced in the render's scene
+//            (as in k_trace_group).
+// Each render's radiance is the same sum, term by term and in the same order, as tracing
+// the path in that render alone, so with the same block shape every partial is
+// bit-identical to the per-render kernel's; the warps' subtrees of the pairwise pixel sum
+// are combined as that sum's top two levels.
+constexpr int kEmitWarps = kGroupBlock / 32;
+constexpr int kEmitTab = kEmitTabRows;
+static_assert(32 % kEmitWarps == 0, "each warp takes 32 / kEmitWarps pixel slots");
+constexpr int kEmitSlots = 32 / kEmitWarps;
+static_assert(kEmitSlots == 8, "the warps' subtrees are the pairwise sum's levels 0-2");
+
+struct EmitWarp {
+    float ent[kEmitCap * kEmitFields * 32];  // kept vertices of the warp's 32 paths
+    float st[10][32];                        // end state: o, d, beta, vertex b (bits)
+    int n[32];                               // vertices kept
+    int kind[32];                            // 0 ended, 1 left the scene, 2 stopped (specular flag: 4)
+    double pair[2][3][32];                   // pairwise-sum stacks of the lane's two renders
+};
+struct EmitSmem {
+    GroupScene scene;  // the invariant part (render 0's records of the other primitives)
+    TraceJob job;
+    float4 tab[kEmitTab];  // per-render rows (as k_trace_group's), R x gstride
+    float4 ulo[kMaxVariant], uhi[kMaxVariant];
+    double sub[kEmitWarps][64];
+    EmitWarp w[kEmitWarps];
+    unsigned item;
+    int job_index;
+};
+
+#ifndef PRDPT_EMIT_MIN_BLOCKS
+#define PRDPT_EMIT_MIN_BLOCKS 4
+#endif
+constexpr int kEmitMinBlocks = PRDPT_EMIT_MIN_BLOCKS;
+
+template <bool kCount>
+__global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(const __grid_constant__ TraceLaunch L) {
+    __shared__ EmitSmem E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    EmitWarp& Wp = E.w[warp];
+    const TraceJob& J = E.job;
+    int cur_job = -1;
+    Counters cnt{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (!L.jobs) {  // a single job's descriptor is host data: copied before the wait
+        const unsigned* src = reinterpret_cast<const unsigned*>(&L.job0);
+        unsigned* dst = reinterpret_cast<unsigned*>(&E.job);
+        for (int i = threadIdx.x; i < int(sizeof(TraceJob) / 4); i += kGroupBlock) dst[i] = src[i];
+    }
+    __syncthreads();
+    pdl_enter();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned item = atomicAdd(L.queue, 1u);
+            int j = 0;
+            if (item < unsigned(L.total_items) && L.jobs) {
+                int lo = 0, hi = L.njobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) / 2;
+                    if (L.jobs[mid].item_begin <= int(item)) lo = mid; else hi = mid - 1;
+                }
+                j = lo;
+            }
+            E.item = item;
+            E.job_index = j;
+        }
+        __syncthreads();
+        const unsigned item = E.item;
+        const int j = E.job_index;
+        if (item >= unsigned(L.total_items)) break;
+        if (j != cur_job) {  // stage the job, its invariant scene, per-render rows and union bounds
+            if (L.jobs) {
+                const unsigned* src = reinterpret_cast<const unsigned*>(L.jobs + j);
+                unsigned* dst = reinterpret_cast<unsigned*>(&E.job);
+                for (int i = threadIdx.x; i < int(sizeof(TraceJob) / 4); i += kGroupBlock) dst[i] = src[i];
+                __syncthreads();
+            }
+            if (J.R < 1 || J.R > 64 || J.R * J.gstride > kEmitTab || J.gstride < 4 * J.n_var || J.n_var < 1 ||
+                J.n_var > kMaxVariant || J.n_prims > kGroupPrims || J.n_mats > kGroupMats) {
+                if (threadIdx.x == 0) atomicOr(L.status, kStatusBadItem);
+                break;
+            }
+            if (warp == 0) stage_group_scene(E.scene, J, 0, lane);
+            const int stride = J.gstride, n = J.n_var;
+            for (int i = threadIdx.x; i < J.R * stride; i += kGroupBlock) {
+                const int r = i / stride, q = i - r * stride;
+                const InstScene& R = J.scenes[r];
+                float4 v;
+                if (q < 4 * n) v = __ldg(&R.prim[nth_set_bit(J.var_prims, q >> 2)][q & 3]);
+                else v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n));  // emitter areas
+                E.tab[i] = v;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                for (int k = 0; k < n; ++k) {
+                    const int slot = nth_set_bit(J.var_prims, k);
+                    const int type = slot < E.scene.n_sph ? kSphere : (slot < E.scene.n_sph + E.scene.n_quad ? kQuad : kBox);
+                    float3 lo = f3(INFINITY, INFINITY, INFINITY), hi = f3(-INFINITY, -INFINITY, -INFINITY);
+                    for (int r = lane; r < J.R; r += 32) {
+                        float3 a, c;
+                        prim_bounds(E.tab + r * stride + 4 * k, type, a, c);
+                        lo = f3(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z));
+                        hi = f3(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+                        lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+                        lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+                        hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+                        hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+                        hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+                    }
+                    if (lane == 0) {
+                        E.ulo[k] = make_float4(lo.x, lo.y, lo.z, 0.f);
+                        E.uhi[k] = make_float4(hi.x, hi.y, hi.z, 0.f);
+                    }
+                }
+            }
+            __syncthreads();
+            cur_job = j;
+        }
+        const int t = int(item) - J.item_begin;
+        if (t < 0 || t >= J.tiles) {
+            if (threadIdx.x == 0) atomicOr(L.status, kStatusBadItem);
+            break;
+        }
+        const int R = J.R, nh = R > 32 ? 2 : 1, stride = J.gstride;
+        const int areas = stride > 4 * J.n_var ? 1 : 0;
+        const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
+        const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
+        const int npx = vw * vh;
+        const unsigned magic_w = 0xffffffffu / unsigned(vw) + 1u;
+        const float inv = mean_scale(J.spp);
+        EmitLane el{E.ulo, E.uhi, J.n_var, J.var_prims, Wp.ent, lane, 0, false};
+        double sub[2] = {0.0, 0.0};
+        for (int qq = 0; qq < kEmitSlots; ++qq) {
+            const int slot = brev5(warp * kEmitSlots + qq);  // pixels in bit-reversed slot order
+            double e[2] = {0.0, 0.0};
+            if (slot < npx) {
+                const int row = div_magic(slot, vw, magic_w);
+                const int px = x0 + slot - row * vw, py = y0 + row;
+                unsigned long long acc[2][3] = {{0ull, 0ull, 0ull}, {0ull, 0ull, 0ull}};
+                for (int s0 = 0; s0 < J.spp; s0 += 32) {
+                    // ---- phase A: one path per lane, traced once for all renders ----------
+                    __syncwarp();  // phase B of the previous samples is done with the table
+                    if (s0 + lane < J.spp) {
+                        Path p;
+                        start_path(E.scene, J.W, J.H, px, py, s0 + lane, slot, p);
+                        if (kCount) ++cnt.paths;
+                        el.n = 0;
+                        el.miss = false;
+                        int res;
+                        while ((res = advance<kCount, false, 0, false, true>(E.scene, J.depth, J.rr_start, p, cnt,
+                                                                             nullptr, nullptr, nullptr, nullptr,
+                                                                             &el)) == kLive) {
+                        }
+                        Wp.n[lane] = el.n;
+                        Wp.kind[lane] = (res == kAffected ? 2 : (el.miss ? 1 : 0)) | (p.specular ? 4 : 0);
+                        Wp.st[0][lane] = p.o.x;
+                        Wp.st[1][lane] = p.o.y;
+                        Wp.st[2][lane] = p.o.z;
+                        Wp.st[3][lane] = p.d.x;
+                        Wp.st[4][lane] = p.d.y;
+                        Wp.st[5][lane] = p.d.z;
+                        Wp.st[6][lane] = p.beta.x;
+                        Wp.st[7][lane] = p.beta.y;
+                        Wp.st[8][lane] = p.beta.z;
+                        Wp.st[9][lane] = __int_as_float(p.b);
+                    }
+                    __syncwarp();
+                    // ---- phase B: each render's terms of each sample, in sample order -----
+                    const int nsmp = min(32, J.spp - s0);
+                    for (int jj = 0; jj < nsmp; ++jj) {
+                        const int nk = Wp.n[jj], kind = Wp.kind[jj];
+                        for (int h = 0; h < nh; ++h) {
+                            const int r = lane + 32 * h;
+                            if (r >= R) continue;
+                            const GroupLane gl{E.tab + r * stride, J.var_prims, 0u, J.n_var, areas, nullptr, 0};
+                            float3 Lr = f3(0.f, 0.f, 0.f);
+                            for (int k = 0; k < nk; ++k) {
+                                const float* en = Wp.ent + k * kEmitFields * 32 + jj;
+                                const float3 po = f3(en[0], en[32], en[64]), nsv = f3(en[96], en[128], en[160]);
+                                float3 wi;
+                                float dist, g;
+                                int lmat;
+                                if (nee_visible<kCount, false, true>(E.scene, po, nsv, __float_as_uint(en[288]),
+                                                                     __float_as_uint(en[320]), __float_as_uint(en[352]),
+                                                                     cnt, 0u, &gl, wi, dist, g, lmat))
+                                    Lr = nee_add(Lr, f3(en[192], en[224], en[256]), xyz(E.scene.mat[lmat][1]), g);
+                            }
+                            const float3 beta = f3(Wp.st[6][jj], Wp.st[7][jj], Wp.st[8][jj]);
+                            if ((kind & 3) == 1) {
+                                Lr = bg_add(Lr, beta, xyz(E.scene.bg));
+                            } else if ((kind & 3) == 2) {  // the rest of the path in render r's scene
+                                Path p;
+                                p.o = f3(Wp.st[0][jj], Wp.st[1][jj], Wp.st[2][jj]);
+                                p.d = f3(Wp.st[3][jj], Wp.st[4][jj], Wp.st[5][jj]);
+                                p.beta = beta;
+                                p.L = Lr;
+                                p.pixel = unsigned(py * J.W + px);
+                                p.s = s0 + jj;
+                                p.b = __float_as_int(Wp.st[9][jj]);
+                                p.slot = slot;
+                                p.specular = (kind & 4) != 0;
+                                p.seg = 0u;
+                                while (advance<kCount, false, 0, true>(E.scene, J.depth, J.rr_start, p, cnt, nullptr,
+                                                                       nullptr, nullptr, &gl) == kLive) {
+                                }
+                                Lr = p.L;
+                            }
+                            acc[h][0] += to_fixed(Lr.x);
+                            acc[h][1] += to_fixed(Lr.y);
+                            acc[h][2] += to_fixed(Lr.z);
+                        }
+                    }
+                }
+                const float4 T = __ldg(J.target + size_t(py) * J.W + px);
+                for (int h = 0; h < nh; ++h)
+                    e[h] = pixel_sq_error(acc[h][0], acc[h][1], acc[h][2], T, unsigned(J.spp), inv);
+            }
+            for (int h = 0; h < 2; ++h) {  // levels 0-2 of the pairwise sum over this warp's slots
+                double v = e[h];
+                int l = 0;
+                for (; (qq >> l) & 1; ++l) v = Wp.pair[h][l][lane] + v;
+                if (l < 3) Wp.pair[h][l][lane] = v;
+                else sub[h] = v;
+            }
+        }
+        for (int h = 0; h < nh; ++h)
+            if (lane + 32 * h < R) E.sub[warp][lane + 32 * h] = sub[h];
+        __syncthreads();
+        for (int r = threadIdx.x; r < R; r += kGroupBlock)  // a5: levels 3 and 4
+            J.partials[size_t(r) * J.tiles + t] = (E.sub[0][r] + E.sub[1][r]) + (E.sub[2][r] + E.sub[3][r]);
+        __syncthreads();
     }
     if (kCount) {
         const unsigned v[kNumCounters] = {warp_sum_u(cnt.sph), warp_sum_u(cnt.quad), warp_sum_u(cnt.box),
@@ -2125,9 +2476,17 @@ int trace_group_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
+int trace_emit_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace_emit<false>, kGroupBlock, 0);
+    return n > 0 ? n : 1;
+}
+
 cudaError_t launch_trace(const TraceLaunch& L, bool render_mode, int grid, cudaStream_t stream) {
     if (L.total_items <= 0) return cudaSuccess;
     const bool count = L.counters != nullptr;
+    if (L.group == 2 && !render_mode)
+        return launch_pdl(count ? k_trace_emit<true> : k_trace_emit<false>, grid, kGroupBlock, stream, L);
     if (L.group && !render_mode)
         return launch_pdl(count ? k_trace_group<true> : k_trace_group<false>, grid, kGroupBlock, stream, L);
     const bool share = !render_mode && L.share;

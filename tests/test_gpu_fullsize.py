@@ -50,24 +50,31 @@ def test_full_size_gradient(ctx, make):
 
 
 @pytest.mark.parametrize("pairs,spp", [(4, 64), (32, 8)])
-def test_full_size_caustic_gradient_in_render_groups(ctx, pairs, spp):
-    """The caustic image at full size (512x512, depth 12, Russian roulette from vertex 3)
-    traced in render groups (8 renders at 64 spp; 64 renders at 8 spp, groups of 32): the
-    gradient and every loss against the FP64 oracle."""
+def test_full_size_caustic_gradient_shared_and_in_render_groups(ctx, pairs, spp):
+    """The caustic image at full size (512x512, depth 12, Russian roulette from vertex 3),
+    8 renders at 64 spp and 64 renders at 8 spp: with emitter sharing (each path traced
+    once for all renders) and in render groups (every render's paths traced): the gradient
+    and every loss against the FP64 oracle, and the two modes bit-identical."""
     wl = workloads.scaled(workloads.config_caustic(), spp=spp, pairs=pairs)
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     target = oracle.render_target(wl)
-    opts = scene.grad_opts(wl, step=2)
-    ctx.counters_enable(True)
-    g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
-    torch.cuda.synchronize()
-    assert ctx.counters_read()[3] == wl.renders * wl.width * wl.height * wl.spp
-    ctx.counters_enable(False)
     ref = oracle.smoothed_grad(wl, target=target, step=2)
-    L = L.cpu().numpy()
-    assert np.allclose(L, ref["losses"], rtol=1e-4, atol=1e-9), np.max(np.abs(L / ref["losses"] - 1))
-    err = grad_rel_error(g.cpu().numpy(), ref["grad"], ref["weights"], ref["losses"])
-    assert err <= GRAD_REL, err
+    res = {}
+    for mode, no_share, paths in (("emit", 0, wl.width * wl.height * wl.spp),
+                                  ("groups", 1, wl.renders * wl.width * wl.height * wl.spp)):
+        opts = scene.grad_opts(wl, step=2, no_path_sharing=no_share)
+        ctx.counters_enable(True)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
+        torch.cuda.synchronize()
+        assert ctx.counters_read()[3] == paths, mode
+        ctx.counters_enable(False)
+        L = L.cpu().numpy()
+        g = g.cpu().numpy()
+        assert np.allclose(L, ref["losses"], rtol=1e-4, atol=1e-9), (mode, np.max(np.abs(L / ref["losses"] - 1)))
+        err = grad_rel_error(g, ref["grad"], ref["weights"], ref["losses"])
+        assert err <= GRAD_REL, (mode, err)
+        res[mode] = (g, L)
+    assert np.array_equal(res["emit"][0], res["groups"][0]) and np.array_equal(res["emit"][1], res["groups"][1])
 
 
 def test_full_size_caustic_sampled_pixels(ctx):

@@ -109,21 +109,25 @@ def test_packed_mixed_sharing_equal_alone(ctx):
             jobs[i].release()
 
 
-def test_packed_three_kinds_equal_alone(ctx):
-    """A batch with path-sharing jobs, render-group jobs and one-render-per-item jobs: the
-    packed step runs one render launch per kind; every job matches its single-job step."""
+def test_packed_four_kinds_equal_alone(ctx):
+    """A batch with emitter-sharing jobs, path-sharing jobs, render-group jobs and
+    one-render-per-item jobs: the packed step runs one render launch per kind; every job
+    matches its single-job step."""
     from paper_2211_17263_gb300 import api
-    cfgs = [(workloads.config_caustic(seed=51), 40, 32, 2, 8, 0),     # render groups of 16
-            (workloads.config_occlusion(seed=52), 48, 40, 4, 3, 0),   # path sharing
-            (workloads.config_gi_box(seed=53), 40, 32, 2, 4, -1),     # one render per item
-            (workloads.config_gi_box(seed=54), 32, 24, 2, 2, 0)]      # render groups of 4
-    wls = [workloads.scaled(wl, width=w, height=h, spp=spp, pairs=p) for wl, w, h, spp, p, _ in cfgs]
+    cfgs = [(workloads.config_caustic(seed=51), 40, 32, 2, 8, 0, 1),   # render groups of 16
+            (workloads.config_occlusion(seed=52), 48, 40, 4, 3, 0, 0),  # path sharing
+            (workloads.config_gi_box(seed=53), 40, 32, 2, 4, -1, 0),    # one render per item
+            (workloads.config_gi_box(seed=54), 32, 24, 2, 2, 0, 0),     # render groups of 4
+            (workloads.config_caustic(seed=55), 36, 28, 3, 6, 0, 0)]    # emitter sharing
+    wls = [workloads.scaled(wl, width=w, height=h, spp=spp, pairs=p) for wl, w, h, spp, p, _, _ in cfgs]
     groups = [c[5] for c in cfgs]
+    no_share = [c[6] for c in cfgs]
     targets = [oracle.render_target(w) for w in wls]
 
     def make(i):
         scene = ctx.upload_scene(wls[i].scene, wls[i].bindings)
-        return api.Job(scene, wls[i], targets[i], render_groups=groups[i], use_tuned=False)
+        return api.Job(scene, wls[i], targets[i], render_groups=groups[i], no_path_sharing=no_share[i],
+                       use_tuned=False)
 
     alone = []
     for i in range(len(wls)):
@@ -132,7 +136,7 @@ def test_packed_three_kinds_equal_alone(ctx):
             j.step()
         alone.append(j.read())
         j.release()
-    order = [3, 0, 2, 1]
+    order = [3, 0, 4, 2, 1]
     jobs = {i: make(i) for i in order}
     for _ in range(2):
         api.step_batch(ctx, [jobs[i] for i in order])

@@ -298,9 +298,100 @@ def test_render_groups_match_oracle(ctx):
                workloads.scaled(workloads.config_gi_box(), width=48, height=40, spp=4, pairs=8)):
         scene = ctx.upload_scene(wl.scene, wl.bindings)
         target = oracle.render_target(wl)
-        opts = scene.grad_opts(wl, step=1, render_groups=16)
+        opts = scene.grad_opts(wl, step=1, render_groups=16, no_path_sharing=1)
         g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
         torch.cuda.synchronize()
+        ref = oracle.smoothed_grad(wl, target=target, step=1)
+        err = grad_rel_error(g.cpu().numpy(), ref["grad"], ref["weights"], ref["losses"])
+        assert err <= GRAD_REL, (wl.name, err)
+
+
+def _gi_box_moving_light():
+    """The GI box with only its light moving: long diffuse paths (more kept vertices than
+    the emitter-sharing mode keeps), mirror bounces and Russian roulette."""
+    wl = workloads.scaled(workloads.config_gi_box(), width=40, height=32, spp=5, pairs=3)
+    return _moving_primitive(wl, 8, (0.05, -0.03, -0.02))
+
+
+def _caustic_two_lights():
+    """The caustic scene with a second emitter, a small sphere whose radius is bound beside
+    the quad light's position: the next-event estimate first chooses an emitter, and the
+    sphere's area differs between renders."""
+    wl = workloads.scaled(workloads.config_caustic(), width=40, height=36, spp=4, pairs=4)
+    b = workloads.SceneBuilder()
+    m_floor = b.material(workloads.MAT_DIFFUSE, (0.8, 0.8, 0.8))
+    m_glass = b.material(workloads.MAT_DIELECTRIC, (1.0, 1.0, 1.0), ior=1.5)
+    m_light = b.material(workloads.MAT_DIFFUSE, (0.0, 0.0, 0.0), emission=(200.0, 200.0, 200.0))
+    m_bulb = b.material(workloads.MAT_DIFFUSE, (0.0, 0.0, 0.0), emission=(30.0, 20.0, 10.0))
+    b.quad((0, 0, 0), (10, 0, 0), (0, 10, 0), m_floor)
+    b.sphere((0.0, 0.0, 1.0), 0.5, m_glass)
+    bulb = b.sphere((-0.8, 0.6, 2.0), 0.15, m_bulb)
+    light = b.quad((0.6, 0.4, 2.6), (0.2, 0, 0), (0, -0.2, 0), m_light)
+    b.look_at((0, -4.0, 1.2), (0, 0, 0.6), (0, 0, 1), 40.0)
+    wl.scene = b.build()
+    wl.bindings = np.array([[workloads.BIND_PRIM_POS, light, c] for c in range(3)]
+                           + [[workloads.BIND_SPHERE_RADIUS, bulb, 0]], np.int32)
+    wl.theta_ref = np.array([0.6, 0.4, 2.6, 0.15], np.float32)
+    wl.theta0 = np.array([0.5, 0.3, 2.5, 0.2], np.float32)
+    wl.sigma = np.array([0.125, 0.125, 0.125, 0.03], np.float32)
+    return wl
+
+
+@pytest.mark.parametrize("make,block_pixels", [
+    # the caustic task's 64 renders
+    (lambda: workloads.scaled(workloads.config_caustic(), width=72, height=52, spp=4, pairs=32), 8),
+    (lambda: workloads.scaled(workloads.config_caustic(), width=72, height=52, spp=4, pairs=32), 32),
+    # ragged blocks, 6 renders
+    (lambda: workloads.scaled(workloads.config_caustic(), width=37, height=29, spp=3, pairs=3), 8),
+    # 40 samples (a second, partial round of 32) and 48 renders (a lane's second render
+    # only for lanes 0-15)
+    (lambda: workloads.scaled(workloads.config_caustic(), width=24, height=20, spp=40, pairs=24), 16),
+    # no Russian roulette, depth 3: the last vertex's estimate and the depth limit
+    (lambda: workloads.scaled(workloads.config_caustic(), width=40, height=32, spp=4, pairs=4, depth=3,
+                              rr_start=-1), 8),
+    (_gi_box_moving_light, 8),
+    (_gi_box_moving_light, 32),
+    (_caustic_two_lights, 16),
+])
+def test_emitter_sharing_is_bit_identical(ctx, make, block_pixels):
+    """Emitter sharing traces each path once in the invariant scene, keeps its diffuse
+    vertices, and lets every render add its own next-event estimates there (and trace on
+    where a ray could meet its perturbed primitives): every loss and the gradient equal
+    tracing one render per work item, and render groups, bit for bit."""
+    wl = make()
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = _t(oracle.render_target(wl))
+    res, paths = {}, {}
+    for key, kw in (("emit", {}), ("per-render", dict(no_path_sharing=1, render_groups=-1)),
+                    ("groups", dict(no_path_sharing=1))):
+        opts = scene.grad_opts(wl, step=4, block_pixels=block_pixels, **kw)
+        ctx.counters_enable(True)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
+        torch.cuda.synchronize()
+        paths[key] = ctx.counters_read()[3]
+        ctx.counters_enable(False)
+        res[key] = (g.cpu().numpy(), L.cpu().numpy())
+    for key in ("per-render", "groups"):
+        assert np.array_equal(res["emit"][1], res[key][1]), (key, res["emit"][1], res[key][1])
+        assert np.array_equal(res["emit"][0], res[key][0]), (key, res["emit"][0], res[key][0])
+    # each path sample was traced once for all renders
+    assert paths["emit"] == wl.width * wl.height * wl.spp < paths["per-render"]
+
+
+def test_emitter_sharing_matches_oracle(ctx):
+    """The caustic and moving-light GI-box gradients in emitter-sharing mode against the
+    FP64 oracle."""
+    for wl in (workloads.scaled(workloads.config_caustic(), width=64, height=48, spp=4, pairs=8),
+               _gi_box_moving_light(), _caustic_two_lights()):
+        scene = ctx.upload_scene(wl.scene, wl.bindings)
+        target = oracle.render_target(wl)
+        opts = scene.grad_opts(wl, step=1)
+        ctx.counters_enable(True)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
+        torch.cuda.synchronize()
+        paths = ctx.counters_read()[3]
+        ctx.counters_enable(False)
+        assert paths == wl.width * wl.height * wl.spp  # the mode was in use
         ref = oracle.smoothed_grad(wl, target=target, step=1)
         err = grad_rel_error(g.cpu().numpy(), ref["grad"], ref["weights"], ref["losses"])
         assert err <= GRAD_REL, (wl.name, err)
