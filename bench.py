@@ -310,6 +310,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--reduce", default="",
+                    help="W,H,SPP,PAIRS: run a reduced case of the workload (profiling only; the line says so)")
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -353,6 +355,9 @@ def main():
         pdist.barrier(world)
 
     wl = getattr(workloads, WORKLOADS[args.workload])(seed=rank)  # one independent replica per rank
+    if args.reduce:  # a reduced case of the workload, for profiling (not a bench line)
+        w, h, spp, pairs = (int(x) for x in args.reduce.split(","))
+        wl = workloads.scaled(wl, width=w, height=h, spp=spp, pairs=pairs)
     if args.estimator == "kernel":
         wl.estimator, wl.sampler = 0, workloads.SAMPLER_RADIAL
     elif args.estimator == "pathwise":
@@ -379,9 +384,12 @@ def main():
                   render_groups=shape["render_groups"], no_path_sharing=shape["no_path_sharing"], use_tuned=False)
     stream = torch.cuda.current_stream()
     # warm-up: at least W steps and at least one second of device work (clocks ramp up
-    # under sustained load; a few short steps after start-up run slow)
+    # under sustained load; a few short steps after start-up run slow), each after an L2
+    # flush as the timed steps are (so a profiler sees warm-up steps as timed ones)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > L2
     t_warm, n_warm = time.perf_counter(), 0
     while n_warm < args.warmup or time.perf_counter() - t_warm < 1.0:
+        flush.zero_()
         job.step(stream)
         n_warm += 1
         if n_warm % 4 == 0:
@@ -397,7 +405,6 @@ def main():
                   + counts[3] * FLOPS["path"] + counts[4] * FLOPS["vertex"])
     sharing = counts[3] < wl.paths_per_step  # path sharing traces fewer paths than R x H x W x S
 
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > L2
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -407,6 +414,7 @@ def main():
     # steps do not run at a lowered clock
     t_rw = time.perf_counter()
     while time.perf_counter() - t_rw < 0.2:
+        flush.zero_()
         job.step(stream)
         torch.cuda.synchronize()
     barrier()
@@ -507,6 +515,7 @@ def main():
                        "height": wl.height, "spp": wl.spp, "depth": wl.depth, "rr_start": wl.rr_start, "D": wl.D,
                        "estimator": "Eq. 9 (pathwise)" if getattr(wl, "estimator", 0) == 1 else "Eq. 10",
                        "launch_shape": shape, "path_sharing": bool(sharing),
+                       "reduced": bool(args.reduce),
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             # paths of the method per second: R x H x W x S per step; with path sharing
             # ("effective") fewer are traced -- mpaths_traced_per_s counts those

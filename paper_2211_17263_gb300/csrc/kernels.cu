@@ -919,15 +919,46 @@ __device__ __forceinline__ void tan_rr(Tangents<kND>& t, float inv_q) {
 // slot 1's first word wl, a uniform point on it from slot 0's first two words (wx, wy).
 // True, with the geometry term g (cosines over squared distance, times the emitter's area
 // and count over pi) and the emitter's material, when the point is visible from po.
+// Emitter of a next-event estimate: floor(u n) of slot 1's first word, exactly.
+template <class Scn>
+__device__ __forceinline__ int nee_light(const Scn& S, unsigned wl) {
+    const int li = int((((wl >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);
+    return min(li, S.n_lights - 1);
+}
+
+// Is one of the primitives whose record slots are set in `cand` hit closer than dist?
+template <bool kCount, class Scn>
+__device__ __forceinline__ bool occluded_set(const Scn& S, float3 o, float3 d, float dist, unsigned cand,
+                                             Counters& cnt) {
+    if (kCount) ++cnt.shadow;
+    const int ns = S.n_sph, nsq = S.n_sph + S.n_quad;
+    while (cand) {
+        const int i = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        float t;
+        if (i < ns) {
+            if (kCount) ++cnt.sph;
+            t = sphere_t(S.prim[i], o, d);
+        } else if (i < nsq) {
+            if (kCount) ++cnt.quad;
+            t = quad_t(S.prim[i], o, d);
+        } else {
+            if (kCount) ++cnt.box;
+            t = box_t(S.prim[i], o, rcp3(d));
+        }
+        if (t < dist) return true;
+    }
+    return false;
+}
+
+// The estimate toward emitter li at the point (lu, lv) of its parameterisation (see
+// nee_visible).
 template <bool kCount, bool kShared, bool kGroup, class Scn>
-__device__ __forceinline__ bool nee_visible(const Scn& S, float3 po, float3 ns, unsigned wx, unsigned wy, unsigned wl,
-                                            Counters& cnt, unsigned skip, const GroupLane* gl, float3& wi,
-                                            float& dist, float& g, int& lmat) {
-    int li = int((((wl >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);  // floor(u * n) exactly
-    li = min(li, S.n_lights - 1);
+__device__ __forceinline__ bool nee_to(const Scn& S, float3 po, float3 ns, float lu, float lv, int li, Counters& cnt,
+                                       unsigned skip, const GroupLane* gl, float3& wi, float& dist, float& g,
+                                       int& lmat) {
     const int4 lt = S.light[li];
     const float4* LP = prim_rec<kGroup>(S, lt.y, gl);
-    const float lu = u01(wx), lv = u01(wy);
     float3 yl, ny;
     if (lt.x == kQuad) {
         const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
@@ -950,15 +981,26 @@ __device__ __forceinline__ bool nee_visible(const Scn& S, float3 po, float3 ns, 
     if (!(cx > 0.0f && cl > 0.0f)) return false;
     dist = dist2 * inv_dist;
     bool blocked;
-    if constexpr (kGroup)  // skip: invariant primitives known not to meet the shadow ray
-        blocked = occluded<kCount, true>(S, po, wi, dist, lt.y, cnt, gl->prims | skip) ||
+    if constexpr (kGroup) {  // skip: invariant primitives known not to meet the shadow ray
+        const int np = S.n_sph + S.n_quad + S.n_box;
+        const unsigned all = np >= 32 ? 0xffffffffu : (1u << np) - 1u;
+        blocked = occluded_set<kCount>(S, po, wi, dist, all & ~(gl->prims | skip | (1u << lt.y)), cnt) ||
                   group_occluded<kCount>(S, *gl, po, wi, dist, lt.y, cnt);
-    else
+    } else {
         blocked = occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, skip);
+    }
     if (blocked) return false;
     g = cx * cl * (inv_dist * inv_dist) * light_area<kGroup>(S, li, gl) * float(S.n_lights) * 0.3183098861837907f;
     lmat = lt.w;
     return true;
+}
+
+template <bool kCount, bool kShared, bool kGroup, class Scn>
+__device__ __forceinline__ bool nee_visible(const Scn& S, float3 po, float3 ns, unsigned wx, unsigned wy, unsigned wl,
+                                            Counters& cnt, unsigned skip, const GroupLane* gl, float3& wi,
+                                            float& dist, float& g, int& lmat) {
+    return nee_to<kCount, kShared, kGroup>(S, po, ns, u01(wx), u01(wy), nee_light(S, wl), cnt, skip, gl, wi, dist, g,
+                                          lmat);
 }
 
 // The radiance terms of a path: L + ba Le g (next-event estimation, ba = beta * albedo) and
@@ -971,7 +1013,7 @@ __device__ __forceinline__ float3 bg_add(float3 L, float3 beta, float3 bg) { ret
 // own next-event estimate there, and a path whose ray could meet a perturbed primitive (its
 // segment touches their union bounds) stops so that each render traces it on from there.
 constexpr int kEmitCap = 3;      // diffuse vertices kept per path
-constexpr int kEmitFields = 13;  // po, ns, beta * albedo, slot 0's words x, y, slot 1's word x, cull mask
+constexpr int kEmitFields = 13;  // po, ns, beta * albedo, the emitter point (lu, lv), emitter li, cull mask
 struct EmitLane {
     const float4* ulo;  // union over the renders of each perturbed primitive's bounds
     const float4* uhi;
@@ -983,8 +1025,8 @@ struct EmitLane {
     bool miss;          // the path ended by leaving the scene
 };
 
-// Invariant primitives that no render's shadow ray from po to its emitter li (chosen by slot
-// 1's first word wl, as in nee_visible) can meet, as a record-slot mask: every such ray lies
+// Invariant primitives that no render's shadow ray from po to its emitter li can meet, as a
+// record-slot mask: every such ray lies
 // in the cone from po over the emitter's union bounds (centre b, half-diagonal rb: the ray
 // to a point y deviates from the axis po -> b by at most t rb at parameter t). A primitive
 // is left out when its bounding sphere (a sphere itself; a quad's or box's enclosing one)
@@ -992,9 +1034,7 @@ struct EmitLane {
 // on one side. The margins exceed the FP32 rounding of the intersection tests, so leaving
 // these primitives out never changes a shadow ray's outcome.
 template <class Scn>
-__device__ __forceinline__ unsigned shadow_cull(const Scn& S, const EmitLane& E, float3 po, unsigned wl) {
-    int li = int((((wl >> 9) * 2u + 1u) * unsigned(S.n_lights)) >> 24);
-    li = min(li, S.n_lights - 1);
+__device__ __forceinline__ unsigned shadow_cull(const Scn& S, const EmitLane& E, float3 po, int li) {
     const int slot = S.light[li].y;
     if (!((E.skip >> slot) & 1u)) return 0u;
     const int k = __popc(E.skip & ((1u << slot) - 1u));
@@ -1137,8 +1177,9 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
                 e[0] = po.x; e[32] = po.y; e[64] = po.z;
                 e[96] = ns.x; e[128] = ns.y; e[160] = ns.z;
                 e[192] = ba.x; e[224] = ba.y; e[256] = ba.z;
-                e[288] = __uint_as_float(w0.x); e[320] = __uint_as_float(w0.y); e[352] = __uint_as_float(w1.x);
-                e[384] = __uint_as_float(shadow_cull(S, *el, po, w1.x));
+                const int li = nee_light(S, w1.x);
+                e[288] = u01(w0.x); e[320] = u01(w0.y); e[352] = __int_as_float(li);
+                e[384] = __uint_as_float(shadow_cull(S, *el, po, li));
                 ++el->n;
             } else {
                 float3 wi;
@@ -2086,10 +2127,9 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
                                 float3 wi;
                                 float dist, g;
                                 int lmat;
-                                if (nee_visible<kCount, false, true>(E.scene, po, nsv, __float_as_uint(en[288]),
-                                                                     __float_as_uint(en[320]), __float_as_uint(en[352]),
-                                                                     cnt, __float_as_uint(en[384]), &gl, wi, dist, g,
-                                                                     lmat))
+                                if (nee_to<kCount, false, true>(E.scene, po, nsv, en[288], en[320],
+                                                                __float_as_int(en[352]), cnt, __float_as_uint(en[384]),
+                                                                &gl, wi, dist, g, lmat))
                                     Lr = nee_add(Lr, f3(en[192], en[224], en[256]), xyz(E.scene.mat[lmat][1]), g);
                             }
                             const float3 beta = f3(Wp.st[6][jj], Wp.st[7][jj], Wp.st[8][jj]);
