@@ -557,6 +557,14 @@ def main():
                 "bound": "alu", "achieved": p_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": p_achieved / fp32_peak, "kernel": "k_trace (path sharing off) + k_finalize",
                 "ms_per_step": per_render["ms"], "paths_per_step": per_render["counts"][3]}
+            # the method's work (every render's paths traced, counted by the per-render kernel)
+            # over this step's kernel time: what sharing buys, not a hardware efficiency
+            e_achieved = per_render["flops"] / (trace_avg_ms * 1e-3) / 1e12
+            line["roofline_effective"] = {
+                "bound": "alu", "achieved": e_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": e_achieved / fp32_peak,
+                "basis": "model FP32 flop of tracing every render's paths (the per-render kernel's work counters) "
+                         "/ mean CUDA-event time of this step's kernels"}
         issue = _issue_rate(wl.name, props.multi_processor_count, sm_max, trace_avg_ms,
                             per_render["ms"] if per_render else None)
         if issue is not None:

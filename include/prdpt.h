@@ -134,7 +134,11 @@ typedef struct {
     int32_t block_pixels;      /* pixels per warp work item (8, 16 or 32); 0 = automatic */
     int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
     int32_t no_path_sharing;   /* 0: with crn = 1, trace paths that no perturbation can touch once for
-                                  all renders (same result, bit for bit); 1: trace every render */
+                                  all renders (geometry-only perturbations), or, when every emitter is
+                                  perturbed and only positions and radii are bound (at most 64
+                                  renders, Eq. 10, no texture), trace each path once with each
+                                  render's own next-event estimates (emitter sharing); same result,
+                                  bit for bit; 1: trace every render */
     int32_t estimator;         /* PRDPT_ESTIMATOR_*: 0 = Eq. 10 (kernel-gradient weights times render
                                   losses); 1 = Eq. 9 (mean over the renders of each render's pathwise
                                   loss gradient: requires sampler = GAUSS, every binding an albedo or
