@@ -496,7 +496,12 @@ def main():
         sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
         fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
         trace_avg_ms = trace_ms / max(launches, 1)
-        achieved = flops_step / (trace_avg_ms * 1e-3) / 1e12
+        model_achieved = flops_step / (trace_avg_ms * 1e-3) / 1e12
+        # FP32 flop per step counted by ncu (2 x FFMA + FADD + FMUL thread instructions of the
+        # step's render kernel) when the committed summary was taken on these kernel sources;
+        # else the work-counter model
+        fp32_counted = _profiled(wl.name, "fp32_flop_per_step")
+        achieved = fp32_counted / (trace_avg_ms * 1e-3) / 1e12 if fp32_counted else model_achieved
         value = world * 1000.0 / step_ms
         traffic = _profiled(wl.name, "dram_bytes_per_step")
         if sharing and _emitter_bound(wl):
@@ -537,8 +542,12 @@ def main():
                          "traffic_source": (f"ncu, profiles/{os.path.basename(_profile_path(wl.name))} (kernel "
                                             "source hash matches)") if traffic is not None else None,
                          "kernel": kernels,
-                         "achieved_basis": "model FP32 flop per step from the kernels' work counters / mean "
-                                           "CUDA-event time of the step's kernels",
+                         "achieved_basis": ("ncu-counted FP32 flop per step (2 FFMA + FADD + FMUL, profiles/, "
+                                            "kernel source hash matches) / mean CUDA-event time of the step's "
+                                            "kernels") if fp32_counted else
+                                           ("model FP32 flop per step from the kernels' work counters / mean "
+                                            "CUDA-event time of the step's kernels"),
+                         "model_achieved": model_achieved,
                          "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes"
                                        f" x 2 flop x {sm_max:.0f} MHz"},
             "fp32_probe": {"achieved_tflops": probe_tflops, "ms": probe_ms,
