@@ -1058,7 +1058,10 @@ __device__ __forceinline__ float3 bg_add(float3 L, float3 beta, float3 bg) { ret
 // renders; its diffuse vertices are kept (up to kEmitCap) so that each render evaluates its
 // own next-event estimate there, and a path whose ray could meet a perturbed primitive (its
 // segment touches their union bounds) stops so that each render traces it on from there.
-constexpr int kEmitCap = 3;      // diffuse vertices kept per path
+#ifndef PRDPT_EMIT_CAP
+#define PRDPT_EMIT_CAP 2
+#endif
+constexpr int kEmitCap = PRDPT_EMIT_CAP;  // diffuse vertices kept per path
 constexpr int kEmitFields = 13;  // po, ns, beta * albedo, the emitter point (lu, lv), emitter li, cull mask
 struct EmitLane {
     const float4* ulo;  // union over the renders of each perturbed primitive's bounds
@@ -2102,6 +2105,10 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
             break;
         }
         const int R = J.R, nh = R > 32 ? 2 : 1, stride = J.gstride;
+        // phase B lanes: render gi = lane mod G of sample group ks = lane / G (G the power of
+        // two >= R, at most 32): with few renders a warp takes 32 / G samples at a time
+        const int G = R >= 32 ? 32 : (R <= 1 ? 1 : 1 << (32 - __clz(R - 1)));
+        const int nsg = 32 / G, gi = lane % G, ks = lane / G;
         const int areas = stride > 4 * J.n_var ? 1 : 0;
         const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
         const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
@@ -2157,12 +2164,16 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
                     unsigned todo = __ballot_sync(kFull, work);
 #pragma unroll 1
                     while (todo) {
-                        const int jj = __ffs(todo) - 1;
-                        todo &= todo - 1u;
+                        int jj = -1;  // sample group ks takes the ks-th of the next nsg samples
+                        for (int i = 0; i < nsg && todo; ++i) {
+                            if (i == ks) jj = __ffs(todo) - 1;
+                            todo &= todo - 1u;
+                        }
+                        if (jj < 0) continue;
                         const int nk = Wp.n[jj], kind = Wp.kind[jj];
 #pragma unroll 1
                         for (int h = 0; h < nh; ++h) {
-                            const int r = lane + 32 * h;
+                            const int r = gi + 32 * h;
                             if (r >= R) continue;
                             const GroupLane gl{E.tab + r * stride, J.var_prims, 0u, J.n_var, areas, nullptr, 0};
                             float3 Lr = f3(0.f, 0.f, 0.f);
@@ -2203,6 +2214,11 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
                         }
                     }
                 }
+                for (int o = G; o < 32; o <<= 1) {  // the render's other sample groups
+                    acc[0][0] += __shfl_xor_sync(kFull, acc[0][0], o);
+                    acc[0][1] += __shfl_xor_sync(kFull, acc[0][1], o);
+                    acc[0][2] += __shfl_xor_sync(kFull, acc[0][2], o);
+                }
                 const float4 T = __ldg(J.target + size_t(py) * J.W + px);
                 for (int h = 0; h < nh; ++h)
                     e[h] = pixel_sq_error(acc[h][0], acc[h][1], acc[h][2], T, unsigned(J.spp), inv);
@@ -2216,7 +2232,7 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
             }
         }
         for (int h = 0; h < nh; ++h)
-            if (lane + 32 * h < R) E.sub[warp][lane + 32 * h] = sub[h];
+            if (ks == 0 && gi + 32 * h < R) E.sub[warp][gi + 32 * h] = sub[h];
         __syncthreads();
         for (int r = threadIdx.x; r < R; r += kGroupBlock)  // a5: levels 3 and 4
             J.partials[size_t(r) * J.tiles + t] = (E.sub[0][r] + E.sub[1][r]) + (E.sub[2][r] + E.sub[3][r]);
