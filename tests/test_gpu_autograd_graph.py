@@ -100,9 +100,13 @@ def test_torch_adam_on_autograd_matches_resident_job(ctx):
     assert np.allclose(theta.detach().cpu().numpy(), st["theta"], rtol=0, atol=1e-5)
 
 
-def test_cuda_graph_of_300_steps_is_bit_identical(ctx):
+@pytest.mark.parametrize("make", [
+    lambda: workloads.scaled(workloads.config_gi_box(), width=32, height=24, spp=2, pairs=2),  # render groups
+    lambda: workloads.scaled(workloads.config_caustic(), width=32, height=24, spp=4, pairs=4),  # emitter sharing
+])
+def test_cuda_graph_of_300_steps_is_bit_identical(ctx, make):
     from paper_2211_17263_gb300 import api
-    wl = workloads.scaled(workloads.config_gi_box(), width=32, height=24, spp=2, pairs=2)
+    wl = make()
     target = oracle.render_target(wl)
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     eager = api.Job(scene, wl, target)

@@ -378,6 +378,25 @@ def test_emitter_sharing_is_bit_identical(ctx, make, block_pixels):
     assert paths["emit"] == wl.width * wl.height * wl.spp < paths["per-render"]
 
 
+def test_emitter_sharing_falls_back_beyond_64_renders(ctx):
+    """A moving-light job with more renders than emitter sharing serves (80) runs in render
+    groups: every path of every render is traced, with the same results as path sharing off."""
+    wl = workloads.scaled(workloads.config_caustic(), width=24, height=20, spp=2, pairs=40)
+    scene = ctx.upload_scene(wl.scene, wl.bindings)
+    target = _t(oracle.render_target(wl))
+    res = []
+    for no_share in (0, 1):
+        opts = scene.grad_opts(wl, step=2, block_pixels=8, no_path_sharing=no_share)
+        ctx.counters_enable(True)
+        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
+        torch.cuda.synchronize()
+        paths = ctx.counters_read()[3]
+        ctx.counters_enable(False)
+        assert paths == wl.renders * wl.width * wl.height * wl.spp
+        res.append((g.cpu().numpy(), L.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
 def test_emitter_sharing_matches_oracle(ctx):
     """The caustic and moving-light GI-box gradients in emitter-sharing mode against the
     FP64 oracle."""
