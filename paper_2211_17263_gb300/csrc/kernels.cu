@@ -1967,10 +1967,12 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
 //   phase A  lane = sample: the path is traced once in the invariant scene, keeping its
 //            diffuse vertices (EmitLane) and its end: left the scene (the background term),
 //            ended, or stopped where a ray could meet a perturbed primitive;
-//   phase B  lane = render (lane and lane + 32): for each sample of the warp, in order, the
-//            render's own next-event estimates at the kept vertices, then the background
-//            term or, for a stopped path, the rest of the path traced in the render's scene
-//            (as in k_trace_group).
+//   phase B  lane = render (lane and lane + 32; with R <= 16, render lane mod G of sample
+//            group lane / G, G the power of two >= R): for each sample that adds anything,
+//            the render's own next-event estimates at the kept vertices (occlusion tested
+//            against the primitives the vertex's cull mask leaves), then the background term
+//            or, for a stopped path, the rest of the path traced in the render's scene (as in
+//            k_trace_group).
 // Each render's radiance is the same sum, term by term and in the same order, as tracing
 // the path in that render alone, so with the same block shape every partial is
 // bit-identical to the per-render kernel's; the warps' subtrees of the pairwise pixel sum
