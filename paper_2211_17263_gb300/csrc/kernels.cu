@@ -434,7 +434,10 @@ struct Counters {
     unsigned sph, quad, box, paths, vertices, shadow, rays, pad;
 };
 
-__device__ __forceinline__ float sphere_t(const float4* P, float3 o, float3 d) {
+// The intersection tests read a primitive record through P[j]: a pointer to its four float4,
+// or a strided view of a per-render table (SRec).
+template <class Rec>
+__device__ __forceinline__ float sphere_t(const Rec& P, float3 o, float3 d) {
     const float4 a = P[0];
     const float r2 = P[1].x;
     const float3 oc = o - xyz(a);
@@ -448,7 +451,8 @@ __device__ __forceinline__ float sphere_t(const float4* P, float3 o, float3 d) {
     return (t > kEps) ? t : INFINITY;
 }
 
-__device__ __forceinline__ float quad_t(const float4* P, float3 o, float3 d) {
+template <class Rec>
+__device__ __forceinline__ float quad_t(const Rec& P, float3 o, float3 d) {
     const float4 a = P[0], nb = P[1], uu = P[2], vv = P[3];
     const float3 n = xyz(nb);
     const float den = dot3(n, d);
@@ -462,7 +466,8 @@ __device__ __forceinline__ float quad_t(const float4* P, float3 o, float3 d) {
 }
 
 // Slab test; returns the nearest t > eps (entering, or leaving from inside).
-__device__ __forceinline__ float box_t(const float4* P, float3 o, float3 inv) {
+template <class Rec>
+__device__ __forceinline__ float box_t(const Rec& P, float3 o, float3 inv) {
     const float3 lo = xyz(P[0]), hi = xyz(P[1]);
     const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
     const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
@@ -475,7 +480,8 @@ __device__ __forceinline__ float box_t(const float4* P, float3 o, float3 inv) {
 }
 
 // Outward normal of box record P at the hit found by box_t.
-__device__ __forceinline__ float3 box_normal(const float4* P, float3 o, float3 d, float3 inv) {
+template <class Rec>
+__device__ __forceinline__ float3 box_normal(const Rec& P, float3 o, float3 d, float3 inv) {
     const float3 lo = xyz(P[0]), hi = xyz(P[1]);
     float tn[3], tf[3];
     const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z}, ii[3] = {inv.x, inv.y, inv.z};
@@ -577,31 +583,43 @@ __device__ __forceinline__ bool occluded(const Scn& S, float3 o, float3 d, float
 //                      are bound in this mode; the emission row is the staged scene's)
 //   [4 n + m .. + 1]   the render's emitter areas (8 floats), only when a radius binding
 //                      can change an emitter's area (m = bound materials)
+// A record in a per-render table kept field-major (field j of every render contiguous), so
+// that lanes reading their own renders' fields load consecutive float4 without bank
+// conflicts: field j at p[j * s].
+struct SRec {
+    const float4* p;
+    int s;
+    __device__ __forceinline__ float4 operator[](int j) const { return p[j * s]; }
+};
+
 struct GroupLane {
-    const float4* rec;  // this lane's row
+    const float4* rec;  // this lane's row: field q at rec[q * rs]
     unsigned prims;     // record-slot mask of the perturbed primitives
     unsigned mats;      // mask of the bound materials
     int n_var;          // perturbed primitives
     int areas;          // 1: the row holds the emitter areas
     const uint4* rng;   // the sample group's Philox blocks: [0] jitter, [1 + 2 b + k] vertex b, slot k
     int bpre;           // vertices b < bpre have their blocks in `rng`
+    int rs;             // float4 between consecutive fields of a row (the table's render count)
 };
 
 // Record of primitive slot `slot`: the lane's own for a perturbed primitive, else the
 // staged scene's.
 template <bool kGroup, class Scn>
-__device__ __forceinline__ const float4* prim_rec(const Scn& S, int slot, const GroupLane* g) {
+__device__ __forceinline__ auto prim_rec(const Scn& S, int slot, const GroupLane* g) {
     if constexpr (kGroup) {
-        if ((g->prims >> slot) & 1u) return g->rec + 4 * __popc(g->prims & ((1u << slot) - 1u));
+        if ((g->prims >> slot) & 1u) return SRec{g->rec + 4 * __popc(g->prims & ((1u << slot) - 1u)) * g->rs, g->rs};
+        return SRec{S.prim[slot], 1};
+    } else {
+        return static_cast<const float4*>(S.prim[slot]);
     }
-    return S.prim[slot];
 }
 
 // Albedo row (albedo, type) of material m: the lane's own for a bound material.
 template <bool kGroup, class Scn>
 __device__ __forceinline__ float4 mat_albedo(const Scn& S, int m, const GroupLane* g) {
     if constexpr (kGroup) {
-        if ((g->mats >> m) & 1u) return g->rec[4 * g->n_var + __popc(g->mats & ((1u << m) - 1u))];
+        if ((g->mats >> m) & 1u) return g->rec[(4 * g->n_var + __popc(g->mats & ((1u << m) - 1u))) * g->rs];
     }
     return S.mat[m][0];
 }
@@ -609,7 +627,8 @@ __device__ __forceinline__ float4 mat_albedo(const Scn& S, int m, const GroupLan
 template <bool kGroup, class Scn>
 __device__ __forceinline__ float light_area(const Scn& S, int li, const GroupLane* g) {
     if constexpr (kGroup) {
-        if (g->areas) return reinterpret_cast<const float*>(g->rec + 4 * g->n_var + __popc(g->mats))[li];
+        if (g->areas)
+            return reinterpret_cast<const float*>(g->rec + (4 * g->n_var + __popc(g->mats) + (li >> 2)) * g->rs)[li & 3];
     }
     return S.light_area[li];
 }
@@ -623,7 +642,7 @@ __device__ __forceinline__ void group_hit(const Scn& S, const GroupLane& g, floa
     for (int k = 0; m; ++k) {
         const int slot = __ffs(m) - 1;
         m &= m - 1u;
-        const float4* P = g.rec + 4 * k;
+        const SRec P{g.rec + 4 * k * g.rs, g.rs};
         float t;
         int type;
         if (slot < S.n_sph) {
@@ -652,7 +671,7 @@ __device__ __forceinline__ bool group_occluded(const Scn& S, const GroupLane& g,
         const int slot = __ffs(m) - 1;
         m &= m - 1u;
         if (slot == light) continue;
-        const float4* P = g.rec + 4 * k;
+        const SRec P{g.rec + 4 * k * g.rs, g.rs};
         float t;
         if (slot < S.n_sph) {
             t = sphere_t(P, o, d);
@@ -801,8 +820,8 @@ __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
 // Albedo of a textured quad at hit point pt: texel (floor(s T), floor(t T)) with
 // s = (pt - c).u / |u|^2 + 1/2, t = (pt - c).v / |v|^2 + 1/2 (each clamped to [0, T-1]) of
 // the render's texture [T][T][3]; channels clamped to [0, 1].
-template <class Scn>
-__device__ __forceinline__ float3 tex_albedo(const Scn& S, const float4* P, float3 pt) {
+template <class Scn, class Rec>
+__device__ __forceinline__ float3 tex_albedo(const Scn& S, const Rec& P, float3 pt) {
     const float4 c = P[0], u = P[2], v = P[3];
     const float3 l = pt - xyz(c);
     const float s = fmaf(dot3(l, xyz(u)), u.w, 0.5f), t = fmaf(dot3(l, xyz(v)), v.w, 0.5f);
@@ -993,6 +1012,15 @@ __device__ __forceinline__ NeePrep nee_prep(const Scn& S, float lu, float lv, in
     return q;
 }
 
+// The emitter's record for one render: the lane's own when it is perturbed.
+template <bool kGroup, class Scn>
+__device__ __forceinline__ auto nee_rec(const Scn& S, const NeePrep& q, const GroupLane* gl) {
+    if constexpr (kGroup)
+        return q.k >= 0 ? SRec{gl->rec + 4 * q.k * gl->rs, gl->rs} : SRec{S.prim[q.lt.y], 1};
+    else
+        return static_cast<const float4*>(S.prim[q.lt.y]);
+}
+
 // One render's estimate from po (shading normal ns) toward the point prepared in q: true,
 // with the geometry term g (cosines over squared distance, times the emitter's area and
 // count over pi), when the point is visible. skip: primitives left out of the occlusion test
@@ -1000,10 +1028,7 @@ __device__ __forceinline__ NeePrep nee_prep(const Scn& S, float lu, float lv, in
 template <bool kCount, bool kShared, bool kGroup, class Scn>
 __device__ __forceinline__ bool nee_eval(const Scn& S, const NeePrep& q, float3 po, float3 ns, int li, Counters& cnt,
                                          unsigned skip, const GroupLane* gl, float3& wi, float& dist, float& g) {
-    const float4* LP = S.prim[q.lt.y];
-    if constexpr (kGroup) {
-        if (q.k >= 0) LP = gl->rec + 4 * q.k;
-    }
+    const auto LP = nee_rec<kGroup>(S, q, gl);
     float3 yl, ny;
     if (q.lt.x == kQuad) {
         const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
@@ -1182,7 +1207,7 @@ __device__ __forceinline__ int advance(const Scn& S, int depth, int rr_start, Pa
     }
     if (kCount) ++cnt.vertices;
     const float3 pt = p.o + p.d * h.t;
-    const float4* P = prim_rec<kGroup>(S, h.slot, gl);
+    const auto P = prim_rec<kGroup>(S, h.slot, gl);
     float3 ng;
     int mat;
     if (h.type == kSphere) {
@@ -1889,7 +1914,7 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
                 } else {  // emitter areas
                     v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n - nm));
                 }
-                W.tab[i] = v;
+                W.tab[q * G + gi] = v;  // field-major: the lanes' loads of one field are contiguous
             }
             __syncwarp();
             cur_item_g = g;
@@ -1899,8 +1924,8 @@ __global__ void __launch_bounds__(kGroupBlock, kGroupMinBlocks) k_trace_group(co
         // blocks, so the group's lanes draw them ahead, one block each: the jitter and
         // slots 0 and 1 of vertices b < bpre.
         const int bpre = (G - 1) >> 1;
-        const GroupLane gl{W.tab + gi * stride, J.var_prims, J.var_mats, J.n_var,
-                           stride > 4 * J.n_var + __popc(J.var_mats) ? 1 : 0, W.rng + ks * G, bpre};
+        const GroupLane gl{W.tab + gi, J.var_prims, J.var_mats, J.n_var,
+                           stride > 4 * J.n_var + __popc(J.var_mats) ? 1 : 0, W.rng + ks * G, bpre, G};
         const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (ks * G);
         const int x0 = (t % J.tiles_x) * J.bw, y0 = (t / J.tiles_x) * J.bh;
         const int vw = min(J.bw, J.W - x0), vh = min(J.bh, J.H - y0);
@@ -2069,7 +2094,7 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
                 float4 v;
                 if (q < 4 * n) v = __ldg(&R.prim[nth_set_bit(J.var_prims, q >> 2)][q & 3]);
                 else v = __ldg(reinterpret_cast<const float4*>(R.light_area) + (q - 4 * n));  // emitter areas
-                E.tab[i] = v;
+                E.tab[q * J.R + r] = v;  // field-major, as k_trace_group's table
             }
             __syncthreads();
             if (warp == 0) {
@@ -2079,7 +2104,9 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
                     float3 lo = f3(INFINITY, INFINITY, INFINITY), hi = f3(-INFINITY, -INFINITY, -INFINITY);
                     for (int r = lane; r < J.R; r += 32) {
                         float3 a, c;
-                        prim_bounds(E.tab + r * stride + 4 * k, type, a, c);
+                        const float4 rec[4] = {E.tab[(4 * k) * J.R + r], E.tab[(4 * k + 1) * J.R + r],
+                                               E.tab[(4 * k + 2) * J.R + r], E.tab[(4 * k + 3) * J.R + r]};
+                        prim_bounds(rec, type, a, c);
                         lo = f3(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z));
                         hi = f3(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
                     }
@@ -2177,7 +2204,7 @@ __global__ void __launch_bounds__(kGroupBlock, kEmitMinBlocks) k_trace_emit(cons
                         for (int h = 0; h < nh; ++h) {
                             const int r = gi + 32 * h;
                             if (r >= R) continue;
-                            const GroupLane gl{E.tab + r * stride, J.var_prims, 0u, J.n_var, areas, nullptr, 0};
+                            const GroupLane gl{E.tab + r, J.var_prims, 0u, J.n_var, areas, nullptr, 0, R};
                             float3 Lr = f3(0.f, 0.f, 0.f);
 #pragma unroll 1
                             for (int k = 0; k < nk; ++k) {
