@@ -970,72 +970,26 @@ __device__ __forceinline__ bool occluded_set(const Scn& S, float3 o, float3 d, f
     return false;
 }
 
-// What a next-event estimate toward emitter li at the point (lu, lv) of its
-// parameterisation shares between the renders of a render group: the emitter, its row in a
-// lane's records (-1: invariant), the quad offsets or the sphere direction of the point, and
-// the candidate occluders (see nee_eval).
-struct NeePrep {
-    int4 lt;         // emitter: type, record slot, material
-    int k;           // the emitter's record among a lane's perturbed primitives, or -1
-    float a, b;      // quad: lu - 1/2, lv - 1/2
-    float3 ny;       // sphere: unit direction of the point from the centre
-    unsigned cand;   // render-group mode: invariant primitives to test (not culled, not the emitter)
-    bool pert;       // render-group mode: a lane's perturbed primitives other than the emitter exist
-};
-
-template <bool kGroup, class Scn>
-__device__ __forceinline__ NeePrep nee_prep(const Scn& S, float lu, float lv, int li, unsigned skip,
-                                            const GroupLane* gl) {
-    NeePrep q;
-    q.lt = S.light[li];
-    q.k = -1;
-    q.cand = 0u;
-    q.pert = false;
-    if constexpr (kGroup) {
-        if ((gl->prims >> q.lt.y) & 1u) q.k = __popc(gl->prims & ((1u << q.lt.y) - 1u));
-        const int np = S.n_sph + S.n_quad + S.n_box;
-        const unsigned all = np >= 32 ? 0xffffffffu : (1u << np) - 1u;
-        q.cand = all & ~(gl->prims | skip | (1u << q.lt.y));
-        q.pert = (gl->prims & ~(1u << q.lt.y)) != 0u;
-    }
-    if (q.lt.x == kQuad) {
-        q.a = lu - 0.5f;
-        q.b = lv - 0.5f;
+// The estimate toward emitter li at the point (lu, lv) of its parameterisation (see
+// nee_visible).
+template <bool kCount, bool kShared, bool kGroup, class Scn>
+__device__ __forceinline__ bool nee_to(const Scn& S, float3 po, float3 ns, float lu, float lv, int li, Counters& cnt,
+                                       unsigned skip, const GroupLane* gl, float3& wi, float& dist, float& g,
+                                       int& lmat) {
+    const int4 lt = S.light[li];
+    const auto LP = prim_rec<kGroup>(S, lt.y, gl);
+    float3 yl, ny;
+    if (lt.x == kQuad) {
+        const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
+        yl = xyz(LP[0]) + uu * (lu - 0.5f) + vv * (lv - 0.5f);
+        ny = xyz(LP[1]);
     } else {
         const float z = 1.0f - 2.0f * lu;
         const float rr2 = fmaxf(0.0f, 1.0f - z * z);
         const float rr_ = rr2 * rsqrtf(fmaxf(rr2, 1e-30f));
         float sp, cp;
         sincospif(2.0f * lv, &sp, &cp);
-        q.ny = f3(rr_ * cp, rr_ * sp, z);
-    }
-    return q;
-}
-
-// The emitter's record for one render: the lane's own when it is perturbed.
-template <bool kGroup, class Scn>
-__device__ __forceinline__ auto nee_rec(const Scn& S, const NeePrep& q, const GroupLane* gl) {
-    if constexpr (kGroup)
-        return q.k >= 0 ? SRec{gl->rec + 4 * q.k * gl->rs, gl->rs} : SRec{S.prim[q.lt.y], 1};
-    else
-        return static_cast<const float4*>(S.prim[q.lt.y]);
-}
-
-// One render's estimate from po (shading normal ns) toward the point prepared in q: true,
-// with the geometry term g (cosines over squared distance, times the emitter's area and
-// count over pi), when the point is visible. skip: primitives left out of the occlusion test
-// besides the emitter (shared mode: the perturbed ones; render-group mode: q.cand instead).
-template <bool kCount, bool kShared, bool kGroup, class Scn>
-__device__ __forceinline__ bool nee_eval(const Scn& S, const NeePrep& q, float3 po, float3 ns, int li, Counters& cnt,
-                                         unsigned skip, const GroupLane* gl, float3& wi, float& dist, float& g) {
-    const auto LP = nee_rec<kGroup>(S, q, gl);
-    float3 yl, ny;
-    if (q.lt.x == kQuad) {
-        const float3 uu = xyz(LP[2]), vv = xyz(LP[3]);
-        yl = xyz(LP[0]) + uu * q.a + vv * q.b;
-        ny = xyz(LP[1]);
-    } else {
-        ny = q.ny;
+        ny = f3(rr_ * cp, rr_ * sp, z);
         yl = xyz(LP[0]) + ny * LP[0].w;
     }
     const float3 dv = yl - po;
@@ -1046,24 +1000,18 @@ __device__ __forceinline__ bool nee_eval(const Scn& S, const NeePrep& q, float3 
     if (!(cx > 0.0f && cl > 0.0f)) return false;
     dist = dist2 * inv_dist;
     bool blocked;
-    if constexpr (kGroup)
-        blocked = occluded_set<kCount>(S, po, wi, dist, q.cand, cnt) ||
-                  (q.pert && group_occluded<kCount>(S, *gl, po, wi, dist, q.lt.y, cnt));
-    else
-        blocked = occluded<kCount, kShared>(S, po, wi, dist, q.lt.y, cnt, skip);
+    if constexpr (kGroup) {  // skip: invariant primitives known not to meet the shadow ray
+        const int np = S.n_sph + S.n_quad + S.n_box;
+        const unsigned all = np >= 32 ? 0xffffffffu : (1u << np) - 1u;
+        blocked = occluded_set<kCount>(S, po, wi, dist, all & ~(gl->prims | skip | (1u << lt.y)), cnt) ||
+                  group_occluded<kCount>(S, *gl, po, wi, dist, lt.y, cnt);
+    } else {
+        blocked = occluded<kCount, kShared>(S, po, wi, dist, lt.y, cnt, skip);
+    }
     if (blocked) return false;
     g = cx * cl * (inv_dist * inv_dist) * light_area<kGroup>(S, li, gl) * float(S.n_lights) * 0.3183098861837907f;
+    lmat = lt.w;
     return true;
-}
-
-// The estimate toward emitter li at the point (lu, lv) for one render (see nee_visible).
-template <bool kCount, bool kShared, bool kGroup, class Scn>
-__device__ __forceinline__ bool nee_to(const Scn& S, float3 po, float3 ns, float lu, float lv, int li, Counters& cnt,
-                                       unsigned skip, const GroupLane* gl, float3& wi, float& dist, float& g,
-                                       int& lmat) {
-    const NeePrep q = nee_prep<kGroup>(S, lu, lv, li, skip, gl);
-    lmat = q.lt.w;
-    return nee_eval<kCount, kShared, kGroup>(S, q, po, ns, li, cnt, skip, gl, wi, dist, g);
 }
 
 template <bool kCount, bool kShared, bool kGroup, class Scn>
