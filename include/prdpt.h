@@ -152,7 +152,8 @@ typedef struct {
                                   bit): 0 = automatic (the largest of 32, 16, 8, 4, 2 that divides 2P
                                   and whose per-render records fit), -1 = off (one render per work
                                   item), or 2, 4, 8, 16, 32. Used with crn = 1, the Eq. 10 estimator
-                                  and no texture or emission bindings; ignored otherwise */
+                                  and no texture or emission bindings; ignored otherwise, and when
+                                  emitter sharing applies (see no_path_sharing) */
 } prdpt_grad_opts;
 #define PRDPT_ESTIMATOR_KERNEL_GRADIENT 0 /* Eq. 10: sum_r w_r L_r */
 #define PRDPT_ESTIMATOR_PATHWISE 1        /* Eq. 9: mean_r dL/dtheta (theta + tau_r) */

@@ -4,8 +4,10 @@ Candidates are (pixels per warp work item, resident CTAs per SM, render groups, 
 sharing): the block of pixels a warp traces as one work item, how many 256-thread CTAs the
 persistent grid keeps per SM (the number of live warps), whether renders are traced side
 by side in one warp (render_groups = 0: automatic group size; -1: one render per work
-item), and whether paths that no perturbation can reach are traced once for all renders
-(no_path_sharing = 0, where the job allows it) or every render traces its own. Each
+item), and whether paths are shared across renders where the job allows it
+(no_path_sharing = 0: paths no perturbation can reach traced once for geometry-only
+perturbations; each path traced once with each render's own next-event estimates when only
+emitters move) or every render traces its own. Each
 candidate is timed with CUDA events on the render launches of a throwaway resident job of
 the same shape; the fastest is cached in a JSON file keyed by the shape, so later jobs of
 that shape start from the tuned launch (api.Job looks it up when given no shape). The CTA
@@ -29,7 +31,8 @@ def default_cache() -> str:
     """The cache file: $PRDPT_AUTOTUNE_CACHE if set, else DEFAULT_CACHE."""
     return os.environ.get("PRDPT_AUTOTUNE_CACHE") or DEFAULT_CACHE
 # (block pixels, CTAs per SM, render groups, no path sharing); with sharing allowed, render
-# groups apply only to jobs that cannot share paths
+# groups apply only to jobs that cannot share paths (for the others the two sharing
+# candidates of a block shape run the same launch)
 CANDIDATES = [(px, cps, rg, nps) for px in (32, 16, 8) for cps in (3, 2) for rg, nps in ((0, 0), (-1, 0), (0, 1))]
 _lock = threading.Lock()
 
