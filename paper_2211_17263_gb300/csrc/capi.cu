@@ -168,6 +168,10 @@ struct prdpt_ctx {
     std::vector<Pending> pending;        // released, last use possibly still in flight
     std::vector<cudaEvent_t> ev_pool;    // unrecorded events for jobs and scenes
     cudaStream_t io = nullptr;  // non-blocking stream of the synchronous uploads and reads
+    // Page-locked zeros: device memory that must start at zero is cleared by copies from
+    // here (copy engines), not by memset kernels, which would queue behind the persistent
+    // render kernels that fill every SM, so that creating a job never waits for a step.
+    unsigned char* h_zero = nullptr;
     std::mutex mu;
 };
 
@@ -196,6 +200,26 @@ void dev_free(prdpt_ctx* c, void* p) {
     c->used -= it->second;
     c->allocs.erase(it);
     cudaFree(p);
+}
+
+constexpr size_t kZeroBytes = size_t(4) << 20;
+
+// Clear `bytes` at dst on `st` with copies from the context's page-locked zeros.
+cudaError_t zero_async(prdpt_ctx* c, void* dst, size_t bytes, cudaStream_t st) {
+    if (!c->h_zero) {
+        void* h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, kZeroBytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) return e;
+        std::memset(h, 0, kZeroBytes);
+        c->h_zero = static_cast<unsigned char*>(h);
+    }
+    char* d = static_cast<char*>(dst);
+    for (size_t off = 0; off < bytes; off += kZeroBytes) {
+        const cudaError_t e = cudaMemcpyAsync(d + off, c->h_zero, std::min(kZeroBytes, bytes - off),
+                                              cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -580,6 +604,7 @@ prdpt_status prdpt_destroy(prdpt_ctx* c) {
     cudaDeviceSynchronize();
     for (auto& kv : c->allocs) cudaFree(kv.first);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_zero) cudaFreeHost(c->h_zero);
     for (int k = 0; k < 2; ++k) {
         if (c->h_desc[k]) cudaFreeHost(c->h_desc[k]);
         if (c->h_desc_ev[k]) cudaEventDestroy(c->h_desc_ev[k]);
@@ -1383,7 +1408,7 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
     // uploads on the context's own stream (they wait for no other work on the device); the
     // block may be a reused one, so everything that must start at zero is cleared here
     cudaStream_t io = c->io;
-    cudaError_t e = cudaMemsetAsync(base, 0, off_w, io);
+    cudaError_t e = zero_async(c, base, off_w, io);
     if (tex) {
         j->theta = reinterpret_cast<float*>(b + off_hs);
         j->m = j->theta + D;
@@ -1392,8 +1417,8 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         j->grad = j->sigma0 + D;
         j->tex_all = reinterpret_cast<float*>(b + off_tx);
         j->norms = reinterpret_cast<HdNorm*>(b + off_nr);
-        if (e == cudaSuccess) e = cudaMemsetAsync(j->theta, 0, sizeof(float) * 5 * (size_t)D, io);
-        if (e == cudaSuccess) e = cudaMemsetAsync(j->norms, 0, sizeof(HdNorm) * (size_t)R, io);  // part counters
+        if (e == cudaSuccess) e = zero_async(c, j->theta, sizeof(float) * 5 * (size_t)D, io);
+        if (e == cudaSuccess) e = zero_async(c, j->norms, sizeof(HdNorm) * (size_t)R, io);  // part counters
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(j->scene_copy, &s->host, sizeof(BaseScene), cudaMemcpyHostToDevice, io);
@@ -1405,10 +1430,10 @@ prdpt_status prdpt_job_create(prdpt_ctx* c, int32_t scene_id, const prdpt_job_de
         if (d->target_host)
             e = cudaMemcpyAsync(j->target, d->target_host, sizeof(float4) * (size_t)W * H, cudaMemcpyHostToDevice, io);
         else  // rendered later on the device (prdpt_job_render_target)
-            e = cudaMemsetAsync(j->target, 0, sizeof(float4) * (size_t)W * H, io);
+            e = zero_async(c, j->target, sizeof(float4) * (size_t)W * H, io);
     }
     if (e == cudaSuccess && probe.share)
-        e = cudaMemsetAsync(j->accaff, 0, sizeof(unsigned long long) * 3 * (size_t)R * pix, io);
+        e = zero_async(c, j->accaff, sizeof(unsigned long long) * 3 * (size_t)R * pix, io);
     if (e == cudaSuccess) e = cudaStreamSynchronize(io);
     if (e != cudaSuccess) {
         c->ev_pool.push_back(j->last);
