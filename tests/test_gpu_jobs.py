@@ -147,6 +147,37 @@ def test_packed_four_kinds_equal_alone(ctx):
         jobs[i].release()
 
 
+def test_packed_emitter_sharing_jobs_of_different_shapes_equal_alone(ctx):
+    """Emitter-sharing jobs of different render counts, images and scenes packed into one
+    launch: the kernel's CTAs restage the job, scene, per-render records and union bounds
+    whenever their next block belongs to another job; every job matches its single-job step."""
+    from paper_2211_17263_gb300 import api
+    wls = [workloads.scaled(workloads.config_caustic(seed=61), width=40, height=32, spp=3, pairs=3),
+           workloads.scaled(workloads.config_caustic(seed=62), width=24, height=24, spp=2, pairs=32),
+           workloads.scaled(workloads.config_caustic(seed=63), width=32, height=20, spp=5, pairs=12)]
+    targets = [oracle.render_target(w) for w in wls]
+
+    def make(i):
+        scene = ctx.upload_scene(wls[i].scene, wls[i].bindings)
+        return api.Job(scene, wls[i], targets[i], block_pixels=8, use_tuned=False)
+
+    alone = []
+    for i in range(len(wls)):
+        j = make(i)
+        for _ in range(2):
+            j.step()
+        alone.append(j.read())
+        j.release()
+    jobs = [make(i) for i in (2, 0, 1)]
+    for _ in range(2):
+        api.step_batch(ctx, jobs)
+    for i, j in zip((2, 0, 1), jobs):
+        b = j.read()
+        for key in ("theta", "grad", "losses"):
+            assert np.array_equal(alone[i][key], b[key]), (i, key)
+        j.release()
+
+
 def test_job_release_and_reuse_of_batch(ctx):
     from paper_2211_17263_gb300 import api
     wl = workloads.scaled(workloads.config_small(), width=16, height=16, spp=1, pairs=1)
