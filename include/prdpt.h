@@ -119,7 +119,9 @@ typedef struct {
     uint32_t step, tag;        /* Philox counter word 2 and stream tag (2 = path, 3 = target) */
     int32_t crn;               /* 1: every render uses path field 0; 0: render i uses field i */
     int32_t block_pixels;      /* pixels per warp work item (8, 16 or 32); 0 = automatic */
-    int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
+    int32_t ctas_per_sm;       /* resident render CTAs per SM, counted as 256-thread CTAs (kernels with
+                                  smaller CTAs keep proportionally more; capped at the occupancy
+                                  limit); 0 = occupancy limit */
 } prdpt_render_opts;
 
 /* Gradient-estimator options (Eq. 10 / Eq. 9, Algorithm 1). R = 2 * pairs renders. */
@@ -132,7 +134,9 @@ typedef struct {
     uint64_t seed;
     uint32_t step;             /* optimiser step: Philox counter word 2 of every draw */
     int32_t block_pixels;      /* pixels per warp work item (8, 16 or 32); 0 = automatic */
-    int32_t ctas_per_sm;       /* resident render CTAs per SM (1..occupancy limit); 0 = occupancy limit */
+    int32_t ctas_per_sm;       /* resident render CTAs per SM, counted as 256-thread CTAs (kernels with
+                                  smaller CTAs keep proportionally more; capped at the occupancy
+                                  limit); 0 = occupancy limit */
     int32_t no_path_sharing;   /* 0: with crn = 1, trace paths that no perturbation can touch once for
                                   all renders (geometry-only perturbations), or, when every emitter is
                                   perturbed and only positions and radii are bound (at most 64

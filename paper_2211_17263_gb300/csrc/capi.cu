@@ -463,7 +463,9 @@ int grid_for(prdpt_ctx* c, int items, bool render, int ctas_per_sm) {
 
 // Persistent grid of the pathwise-estimator render kernel (CTAs of kDiffBlock threads).
 int grid_for_diff(prdpt_ctx* c, int items, int ctas_per_sm) {
-    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < c->occ_diff) ? ctas_per_sm : c->occ_diff;
+    // ctas_per_sm counts 256-thread CTAs, as for the other render kernels
+    const int want = ctas_per_sm * (kBlock / kDiffBlock);
+    const int per_sm = (want > 0 && want < c->occ_diff) ? want : c->occ_diff;
     const int cap = c->sms * per_sm;
     const int need = (items + kDiffBlock / 32 - 1) / (kDiffBlock / 32);
     return need < cap ? need : cap;
