@@ -63,8 +63,10 @@ def test_full_size_caustic_gradient_shared_and_in_render_groups(ctx, pairs, spp)
     for mode, no_share, paths in (("emit", 0, wl.width * wl.height * wl.spp),
                                   ("groups", 1, wl.renders * wl.width * wl.height * wl.spp)):
         opts = scene.grad_opts(wl, step=2, no_path_sharing=no_share)
-        ctx.counters_enable(True)
         g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
+        torch.cuda.synchronize()
+        ctx.counters_enable(True)  # the counting kernel variant, only for its path count
+        scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), _t(target), opts)
         torch.cuda.synchronize()
         assert ctx.counters_read()[3] == paths, mode
         ctx.counters_enable(False)

@@ -244,6 +244,20 @@ def test_path_sharing_is_bit_identical(ctx, make):
     assert 0 < paths < wl.renders * wl.width * wl.height * wl.spp
 
 
+def _grad_and_paths(ctx, scene, wl, target, opts, paths, key):
+    """The gradient and losses of the timed kernels, and (in a second, counted call) the
+    paths they trace. The counting variants are separate code and are compared with the
+    timed kernels only through their counts."""
+    g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
+    torch.cuda.synchronize()
+    ctx.counters_enable(True)
+    scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
+    torch.cuda.synchronize()
+    paths[key] = ctx.counters_read()[3]
+    ctx.counters_enable(False)
+    return g.cpu().numpy(), L.cpu().numpy()
+
+
 def _small_radius_bound():
     """The small scene with the sphere's radius bound beside its position (an emitter-free
     radius binding: per-render areas rows in render-group mode)."""
@@ -280,12 +294,7 @@ def test_render_groups_are_bit_identical(ctx, make, groups, block_pixels):
     res, paths = {}, {}
     for rg in (-1,) + tuple(groups):
         opts = scene.grad_opts(wl, step=3, block_pixels=block_pixels, no_path_sharing=1, render_groups=rg)
-        ctx.counters_enable(True)
-        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
-        torch.cuda.synchronize()
-        paths[rg] = ctx.counters_read()[3]
-        ctx.counters_enable(False)
-        res[rg] = (g.cpu().numpy(), L.cpu().numpy())
+        res[rg] = _grad_and_paths(ctx, scene, wl, target, opts, paths, rg)
     for rg in groups:
         assert np.array_equal(res[rg][1], res[-1][1]), (rg, res[rg][1], res[-1][1])
         assert np.array_equal(res[rg][0], res[-1][0]), (rg, res[rg][0], res[-1][0])
@@ -365,12 +374,7 @@ def test_emitter_sharing_is_bit_identical(ctx, make, block_pixels):
     for key, kw in (("emit", {}), ("per-render", dict(no_path_sharing=1, render_groups=-1)),
                     ("groups", dict(no_path_sharing=1))):
         opts = scene.grad_opts(wl, step=4, block_pixels=block_pixels, **kw)
-        ctx.counters_enable(True)
-        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
-        torch.cuda.synchronize()
-        paths[key] = ctx.counters_read()[3]
-        ctx.counters_enable(False)
-        res[key] = (g.cpu().numpy(), L.cpu().numpy())
+        res[key] = _grad_and_paths(ctx, scene, wl, target, opts, paths, key)
     for key in ("per-render", "groups"):
         assert np.array_equal(res["emit"][1], res[key][1]), (key, res["emit"][1], res[key][1])
         assert np.array_equal(res["emit"][0], res[key][0]), (key, res["emit"][0], res[key][0])
@@ -384,16 +388,11 @@ def test_emitter_sharing_falls_back_beyond_64_renders(ctx):
     wl = workloads.scaled(workloads.config_caustic(), width=24, height=20, spp=2, pairs=40)
     scene = ctx.upload_scene(wl.scene, wl.bindings)
     target = _t(oracle.render_target(wl))
-    res = []
+    res, paths = [], {}
     for no_share in (0, 1):
         opts = scene.grad_opts(wl, step=2, block_pixels=8, no_path_sharing=no_share)
-        ctx.counters_enable(True)
-        g, L = scene.smoothed_grad(_t(wl.theta0), _t(wl.sigma), target, opts)
-        torch.cuda.synchronize()
-        paths = ctx.counters_read()[3]
-        ctx.counters_enable(False)
-        assert paths == wl.renders * wl.width * wl.height * wl.spp
-        res.append((g.cpu().numpy(), L.cpu().numpy()))
+        res.append(_grad_and_paths(ctx, scene, wl, target, opts, paths, no_share))
+        assert paths[no_share] == wl.renders * wl.width * wl.height * wl.spp
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
