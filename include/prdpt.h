@@ -348,10 +348,10 @@ prdpt_status prdpt_sync(prdpt_ctx* ctx, void* stream);
  * overlap on the GPU (different streams, no ordering) race and must not be issued.
  * Calls from several host threads enqueue one after another (a lock per device), so
  * calls on one stream are ordered. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and the device's SM count; make that first call
- * before any stream capture. Errors are written to err (err_len bytes, may be NULL);
- * there is no context to query, and the kernels' device status word is not reported
- * (the host checks above leave the kernels nothing to refuse). Only
+ * device address (cudaGetSymbolAddress) and the device's SM count. Errors are written
+ * to err (err_len bytes, may be NULL); there is no context to query, and the kernels'
+ * device status word is not reported (the host checks above leave the kernels nothing
+ * to refuse). Only
  * opts->estimator = PRDPT_ESTIMATOR_KERNEL_GRADIENT. The paper has no counterpart to
  * this entry point. */
 prdpt_status prdpt_smoothed_grad_static(const prdpt_scene_desc* scene, const prdpt_param_binding* binds, int32_t D,
