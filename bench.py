@@ -560,8 +560,9 @@ def main():
                            "frac_of_peak": probe_tflops / fp32_peak},
             "e2e": e2e,
             # sampler, render kernel(s), finalisation; path sharing adds the per-render and
-            # epilogue passes; texture scenes add the D-dimensional draws and gradient kernels
-            "gpu_launches": ((5 if sharing else 3)
+            # epilogue passes (emitter sharing runs one render kernel); texture scenes add the
+            # D-dimensional draws and gradient kernels
+            "gpu_launches": ((5 if sharing and not _emitter_bound(wl) else 3)
                              + ((3 if wl.sampler == workloads.SAMPLER_RADIAL else 2) if wl.D > 64 else 0)) * args.steps,
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
