@@ -175,6 +175,17 @@ def _emitter_bound(wl):
     return False
 
 
+def _launches_per_step(wl, sharing):
+    """The library's kernel launches in one resident step: sampler, render kernel,
+    finalisation; path sharing adds the per-render and epilogue passes (emitter sharing runs
+    one render kernel); texture scenes add the D-dimensional draws and gradient kernels."""
+    import workloads
+    n = 5 if sharing and not _emitter_bound(wl) else 3
+    if wl.D > 64:
+        n += 3 if wl.sampler == workloads.SAMPLER_RADIAL else 2
+    return n
+
+
 CPU_SAMPLE_MAX_PATHS = 40_000_000  # larger steps are sampled (one pair, 4 spp) and scaled
 
 
@@ -559,11 +570,7 @@ def main():
             "fp32_probe": {"achieved_tflops": probe_tflops, "ms": probe_ms,
                            "frac_of_peak": probe_tflops / fp32_peak},
             "e2e": e2e,
-            # sampler, render kernel(s), finalisation; path sharing adds the per-render and
-            # epilogue passes (emitter sharing runs one render kernel); texture scenes add the
-            # D-dimensional draws and gradient kernels
-            "gpu_launches": ((5 if sharing and not _emitter_bound(wl) else 3)
-                             + ((3 if wl.sampler == workloads.SAMPLER_RADIAL else 2) if wl.D > 64 else 0)) * args.steps,
+            "gpu_launches": _launches_per_step(wl, sharing) * args.steps,
             "clocks": clocks,
             "final_loss_mean": float(np.mean(state["losses"])),
         }

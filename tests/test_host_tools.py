@@ -76,3 +76,12 @@ def test_bench_profile_values_parse(tmp_path, monkeypatch):
     (prof / "render_pipeline_w_ncu.md").write_text(body.format("other"))
     assert bench._profiled("w", "dram_bytes_per_step") is None
     assert bench._profiled("missing", "dram_bytes_per_step") is None
+
+
+def test_bench_launch_count_per_step():
+    """Launches per resident step by job kind (the launch lists in profiles/ show the same)."""
+    import bench
+    assert bench._launches_per_step(workloads.config_caustic(), sharing=True) == 3  # emitter sharing
+    assert bench._launches_per_step(workloads.config_occlusion(), sharing=True) == 5  # path sharing
+    assert bench._launches_per_step(workloads.config_gi_box(), sharing=False) == 3  # render groups
+    assert bench._launches_per_step(workloads.config_texture(), sharing=False) == 6  # + draws, norms, gradient
